@@ -1,0 +1,177 @@
+/*
+ * camp.h -- C ABI of the batched differentiable MPC layer for GB300 (sm_103a).
+ *
+ * The layer solves, for each of B independent instances, the box-constrained
+ * optimal-control problem of Eq. (3) (Sec. IV):
+ *
+ *     min_{x,u}  sum_{t=0}^{N-1} 1/2 z_t' C_t z_t + c_t' z_t,   z_t = [x_t; u_t]
+ *     s.t.       x_{t+1} = f(x_t, u_t),  x_0 = x_init,  u_lo <= u_t <= u_hi
+ *
+ * with the diagonal quadratic surrogate of Eq. (2): C_t = diag(Q_t, R) and
+ * c_t = [-Q_t * x_ref_t ; -R * u_ref].  f is one RK4 step (length dt) of a
+ * 13-state quadrotor (p, q = (w, x, y, z), v, body rate) driven by 4 rotor
+ * thrusts.  The forward solve is the control-limited iLQR of Sec. IV
+ * (rollout + analytic linearization, Riccati backward pass with a per-stage
+ * box QP, forward pass with a line search over alpha); the backward solve is
+ * the implicit KKT differentiation of Sec. IV (Amos et al. 2018), done as one
+ * adjoint LQR sweep at the returned solution with its active set frozen.
+ *
+ * Conventions for every entry point:
+ *   - Array pointers are DEVICE pointers on the handle's device, row-major,
+ *     instance-major (the layout of a contiguous torch tensor), in the
+ *     handle's dtype (float for MPC_F32, double for MPC_F64), int32 for the
+ *     int arrays.  Pointers must be aligned to their element size.
+ *   - The caller owns every input, output and tape buffer.  The handle owns a
+ *     scratch workspace sized in mpc_create; no solve call allocates, copies
+ *     to or from the host, or synchronises, so the calls can be captured in a
+ *     CUDA graph (mpc_autotune excepted).
+ *   - Return codes are synchronous results of host-side validation and of the
+ *     kernel launch itself (MPC_OK or a negative MPC_ERR_*); nothing aborts or
+ *     throws across the ABI.  Numeric outcomes are asynchronous, per instance,
+ *     in status[] (MPC_ST_*).
+ *   - A handle is not thread-safe and its workspace is shared by all its
+ *     calls: use one handle per stream.
+ */
+#ifndef CAMP_H
+#define CAMP_H
+
+#include <stddef.h>
+#include <cuda_runtime_api.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* return codes */
+#define MPC_OK            0
+#define MPC_ERR_ARG      (-1)   /* NULL handle/pointer or a value out of range      */
+#define MPC_ERR_SHAPE    (-2)   /* B, N, Nq beyond the handle's capacity or invalid */
+#define MPC_ERR_CUDA     (-3)   /* a CUDA call failed (allocation, launch)          */
+#define MPC_ERR_TIMEOUT  (-4)   /* reserved: a bounded device wait gave up          */
+#define MPC_ERR_STATE    (-5)   /* call not valid in the handle's configuration     */
+
+/* dtypes */
+#define MPC_F32 0
+#define MPC_F64 1
+
+/* what the forward keeps for the backward (Sec. IV: differentiate at the solution) */
+#define MPC_STORE_ALL   0      /* tape holds F_t, K_t, chol(Q_uu,ff), free set per stage */
+#define MPC_RECOMPUTE   1      /* no tape: the backward re-linearises and re-factors    */
+
+/* how the forward iterations are launched */
+#define MPC_EXEC_PERSISTENT 0  /* one persistent launch, work queue over instances      */
+#define MPC_EXEC_PLAIN      1  /* three launches per iteration (Sec. IV's structure)     */
+
+/* per-instance status written by mpc_solve_fwd */
+#define MPC_ST_CONVERGED  0    /* max_t |u^k_t - u^(k-1)_t|_inf < tol after a step      */
+#define MPC_ST_STALLED    1    /* no alpha lowered the cost: the nominal is returned    */
+#define MPC_ST_MAX_ITER   2    /* max_iter iterations executed                          */
+#define MPC_ST_NONFINITE  3    /* an input or the initial cost was not finite           */
+#define MPC_ST_NONPD      4    /* a free block of Q_uu had a non-positive pivot         */
+
+typedef struct mpc_handle mpc_handle;   /* opaque, owned by the library */
+
+typedef struct mpc_config {
+    int    nx, nu;          /* must be 13 and 4                                        */
+    int    N_max;           /* largest horizon any call will use, 1..64                */
+    int    B_max;           /* largest batch any call will use, >= 1                   */
+    int    dtype;           /* MPC_F32 or MPC_F64                                      */
+    double dt;              /* RK4 step [s]                                            */
+    double mass;            /* [kg]                                                    */
+    double inertia[3];      /* diagonal body inertia [kg m^2]                          */
+    double arm;             /* rotor distance from the centre [m] (X layout)           */
+    double kappa_yaw;       /* yaw moment per newton of thrust [m]                     */
+    double gravity;         /* [m/s^2]                                                 */
+    int    max_iter;        /* iLQR iterations K (Algorithm 2), 0..1000                */
+    double tol;             /* convergence threshold on max |du| [N]                   */
+    int    n_alpha;         /* number of line-search coefficients, 1..4                */
+    double alpha[4];        /* coefficients in (0, 1], default {1, .5, .25, .1}        */
+    int    store_mode;      /* MPC_STORE_ALL or MPC_RECOMPUTE                          */
+    int    exec_mode;       /* MPC_EXEC_PERSISTENT or MPC_EXEC_PLAIN                   */
+    int    tpi;             /* threads per instance: 0 (auto) or 32                    */
+    int    ipb;             /* instances per block: 0 (auto) or 1, 2, 4, 8             */
+} mpc_config;
+
+typedef struct mpc_problem {
+    int         B, N;       /* batch and horizon (buffer stride); 0 <= B <= B_max       */
+    const int  *horizon;    /* [B] per-instance horizon, clamped to [1, N]; NULL = N   */
+    const void *x0;         /* [B, 13]  x_init                                         */
+    const void *Q;          /* [B, Nq, 13] diagonal state weights (>= 0)               */
+    int         Nq;         /* 1 (one Q for every stage) or N (one per stage)          */
+    const void *x_ref;      /* [B, N, 13]                                              */
+    const void *R;          /* [B, 4]   diagonal control weights (> 0)                 */
+    const void *u_ref;      /* [B, 4]                                                  */
+    const void *u_lo;       /* [B, 4]   u_min                                          */
+    const void *u_hi;       /* [B, 4]   u_max (>= u_lo)                                */
+    const void *u_init;     /* [B, N, 4] warm start, or NULL for clamp(u_ref)          */
+} mpc_problem;
+
+typedef struct mpc_solution {
+    void   *u;              /* [B, N, 4]  u* (zero past each horizon); u*_0 is the action */
+    void   *x;              /* [B, N, 13] x* (x*_0 = x_init; zero past each horizon)    */
+    void   *cost;           /* [B] sum_t 1/2|x-x_ref|_Q^2 + 1/2|u-u_ref|_R^2 at (x*,u*)  */
+    int    *iters;          /* [B] iterations executed                                 */
+    int    *status;         /* [B] MPC_ST_*                                             */
+    void   *tape;           /* MPC_STORE_ALL: >= mpc_tape_bytes(B, N) bytes, 256-aligned */
+    size_t  tape_bytes;
+} mpc_solution;
+
+/* Fill *cfg with the quadrotor workload's defaults (m = 0.75 kg, J =
+ * diag(2.5e-3, 2.1e-3, 4.3e-3), arm 0.15 m, kappa 0.016 m, g = 9.81, dt = 0.02,
+ * max_iter 8, tol 1e-6, alpha = {1, .5, .25, .1} (Sec. IV-3), N_max 40,
+ * B_max 8192, MPC_F32, MPC_STORE_ALL, MPC_EXEC_PERSISTENT, tpi = ipb = 0). */
+void mpc_config_default(mpc_config *cfg);
+
+/* Validate *cfg, allocate the workspace on the current device and return a
+ * handle in *out.  Errors: MPC_ERR_ARG (NULL or out-of-range field),
+ * MPC_ERR_CUDA (no device / allocation failed). */
+int mpc_create(const mpc_config *cfg, mpc_handle **out);
+
+/* Free the workspace and the handle (NULL is accepted).  The caller must make
+ * sure no call on it is still running on the GPU. */
+int mpc_destroy(mpc_handle *h);
+
+/* Bytes of tape mpc_solve_fwd writes for a (B, N) problem: B*N*288 elements
+ * in MPC_STORE_ALL mode, 0 in MPC_RECOMPUTE mode (or for a NULL handle). */
+size_t mpc_tape_bytes(const mpc_handle *h, int B, int N);
+
+/* Forward solve (Eq. (3) by box-constrained iLQR, Algorithm 2's inner loop):
+ * writes u, x, cost, iters, status and, in MPC_STORE_ALL mode, the tape with
+ * the linearization and factorization at the returned iterate.  Enqueued on
+ * `stream`; returns before the GPU finishes.  Errors: MPC_ERR_ARG (NULL
+ * pointer, bad Nq, tape too small), MPC_ERR_SHAPE (B > B_max, N outside
+ * 1..N_max), MPC_ERR_CUDA (launch failed).  B = 0 returns MPC_OK at once. */
+int mpc_solve_fwd(mpc_handle *h, const mpc_problem *p, mpc_solution *s, cudaStream_t stream);
+
+/* Backward solve (Sec. IV implicit KKT differentiation as an adjoint LQR):
+ * given dL/du* (grad_u [B, N, 4]) and optionally dL/dx* (grad_x [B, N, 13],
+ * NULL = 0), writes dL/dQ (dQ [B, Nq, 13]), dL/dx_ref (dx_ref [B, N, 13]) and
+ * dL/dx_init (dx0 [B, 13]).  `p` and `s` must be the ones of the matching
+ * mpc_solve_fwd, unchanged since.  Instances with status NONFINITE or NONPD get
+ * zero gradients.  Same error codes as mpc_solve_fwd. */
+int mpc_solve_bwd(mpc_handle *h, const mpc_problem *p, const mpc_solution *s,
+                  const void *grad_u, const void *grad_x,
+                  void *dQ, void *dx_ref, void *dx0, cudaStream_t stream);
+
+/* Time the persistent forward for each instances-per-block choice on this
+ * problem (overwriting *s), keep the fastest in the handle and report it in
+ * *ipb_out (may be NULL).  Synchronises `stream`; not capturable. */
+int mpc_autotune(mpc_handle *h, const mpc_problem *p, mpc_solution *s,
+                 cudaStream_t stream, int *ipb_out);
+
+/* Launch shape the next persistent forward on (B, N) will use: threads per
+ * instance, instances per block, blocks.  Any out pointer may be NULL. */
+int mpc_launch_shape(const mpc_handle *h, int B, int N, int *tpi, int *ipb, int *grid);
+
+/* Number of kernel launches one mpc_solve_fwd / mpc_solve_bwd on (B, N, with or
+ * without per-instance horizons) enqueues in the handle's configuration. */
+int mpc_launch_count(const mpc_handle *h, int has_horizon, int *fwd, int *bwd);
+
+/* Static text for a return code (mpc_strerror) or an MPC_ST_* status (mpc_status_str). */
+const char *mpc_strerror(int code);
+const char *mpc_status_str(int status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CAMP_H */

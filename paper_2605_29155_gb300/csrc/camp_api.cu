@@ -1,0 +1,329 @@
+// camp_api.cu -- the C ABI (include/camp.h): validation, workspace, launch shapes.
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include "camp.h"
+#include "camp_device.cuh"
+#include "camp_internal.h"
+
+using namespace camp;
+
+struct mpc_handle {
+    mpc_config cfg;
+    int device;
+    int num_sms;
+    int slots;              // scratch slots (>= B_max and >= resident warps)
+    void* ws;               // one allocation holding every scratch region
+    size_t ws_bytes;
+    void *wsF, *wsK, *wsCand, *wsSP, *wsKh;
+    int* queue;             // [2] work-queue tickets (forward, backward)
+    int* order;             // [B_max] longest-horizon-first order
+    int ipb;                // instances per block of the persistent kernels
+};
+
+static size_t elem_size(int dtype) { return dtype == MPC_F64 ? sizeof(double) : sizeof(float); }
+static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+static bool finite_pos(double v) { return isfinite(v) && v > 0.0; }
+
+extern "C" void mpc_config_default(mpc_config* c) {
+    if (!c) return;
+    memset(c, 0, sizeof(*c));
+    c->nx = 13;
+    c->nu = 4;
+    c->N_max = 40;
+    c->B_max = 8192;
+    c->dtype = MPC_F32;
+    c->dt = 0.02;
+    c->mass = 0.75;
+    c->inertia[0] = 2.5e-3;
+    c->inertia[1] = 2.1e-3;
+    c->inertia[2] = 4.3e-3;
+    c->arm = 0.15;
+    c->kappa_yaw = 0.016;
+    c->gravity = 9.81;
+    c->max_iter = 8;
+    c->tol = 1e-6;
+    c->n_alpha = 4;
+    c->alpha[0] = 1.0;
+    c->alpha[1] = 0.5;
+    c->alpha[2] = 0.25;
+    c->alpha[3] = 0.1;
+    c->store_mode = MPC_STORE_ALL;
+    c->exec_mode = MPC_EXEC_PERSISTENT;
+    c->tpi = 0;
+    c->ipb = 0;
+}
+
+static int validate_config(const mpc_config* c) {
+    if (!c) return MPC_ERR_ARG;
+    if (c->nx != NX || c->nu != NU) return MPC_ERR_ARG;
+    if (c->N_max < 1 || c->N_max > MAX_N) return MPC_ERR_ARG;
+    if (c->B_max < 1 || c->B_max > (1 << 24)) return MPC_ERR_ARG;
+    if (c->dtype != MPC_F32 && c->dtype != MPC_F64) return MPC_ERR_ARG;
+    if (!finite_pos(c->dt) || !finite_pos(c->mass)) return MPC_ERR_ARG;
+    for (int i = 0; i < 3; ++i)
+        if (!finite_pos(c->inertia[i])) return MPC_ERR_ARG;
+    if (!isfinite(c->arm) || c->arm < 0 || !isfinite(c->kappa_yaw) || !isfinite(c->gravity)) return MPC_ERR_ARG;
+    if (c->max_iter < 0 || c->max_iter > 1000) return MPC_ERR_ARG;
+    if (!isfinite(c->tol) || c->tol < 0) return MPC_ERR_ARG;
+    if (c->n_alpha < 1 || c->n_alpha > 4) return MPC_ERR_ARG;
+    for (int i = 0; i < c->n_alpha; ++i)
+        if (!(c->alpha[i] > 0.0 && c->alpha[i] <= 1.0)) return MPC_ERR_ARG;
+    if (c->store_mode != MPC_STORE_ALL && c->store_mode != MPC_RECOMPUTE) return MPC_ERR_ARG;
+    if (c->exec_mode != MPC_EXEC_PERSISTENT && c->exec_mode != MPC_EXEC_PLAIN) return MPC_ERR_ARG;
+    if (c->tpi != 0 && c->tpi != 32) return MPC_ERR_ARG;
+    if (c->ipb != 0 && c->ipb != 1 && c->ipb != 2 && c->ipb != 4 && c->ipb != 8) return MPC_ERR_ARG;
+    return MPC_OK;
+}
+
+extern "C" int mpc_create(const mpc_config* cfg, mpc_handle** out) {
+    if (!out) return MPC_ERR_ARG;
+    *out = nullptr;
+    const int v = validate_config(cfg);
+    if (v != MPC_OK) return v;
+    mpc_handle* h = (mpc_handle*)calloc(1, sizeof(mpc_handle));
+    if (!h) return MPC_ERR_CUDA;
+    h->cfg = *cfg;
+    h->ipb = cfg->ipb ? cfg->ipb : 4;
+    if (cudaGetDevice(&h->device) != cudaSuccess) { free(h); return MPC_ERR_CUDA; }
+    if (cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device) != cudaSuccess) {
+        free(h);
+        return MPC_ERR_CUDA;
+    }
+    const cudaError_t pe = cfg->dtype == MPC_F64 ? prepare_kernels<double>() : prepare_kernels<float>();
+    if (pe != cudaSuccess) { free(h); return MPC_ERR_CUDA; }
+    const int resident = h->num_sms * 64;
+    h->slots = cfg->B_max > resident ? cfg->B_max : resident;
+    const size_t es = elem_size(cfg->dtype);
+    const size_t S = (size_t)h->slots, Nw = (size_t)cfg->N_max;
+    const size_t bF = align256(S * Nw * NF * es);
+    const size_t bK = align256(S * Nw * KREC * es);
+    const size_t bC = align256(S * 4 * Nw * NZ * es);
+    const size_t bP = align256(S * Nw * SP_STRIDE * es);
+    const size_t bH = align256(S * Nw * NU * es);
+    const size_t bQ = align256(2 * sizeof(int));
+    const size_t bO = align256((size_t)cfg->B_max * sizeof(int));
+    h->ws_bytes = bF + bK + bC + bP + bH + bQ + bO;
+    if (cudaMalloc(&h->ws, h->ws_bytes) != cudaSuccess) { free(h); return MPC_ERR_CUDA; }
+    char* p = (char*)h->ws;
+    h->wsF = p; p += bF;
+    h->wsK = p; p += bK;
+    h->wsCand = p; p += bC;
+    h->wsSP = p; p += bP;
+    h->wsKh = p; p += bH;
+    h->queue = (int*)p; p += bQ;
+    h->order = (int*)p;
+    *out = h;
+    return MPC_OK;
+}
+
+extern "C" int mpc_destroy(mpc_handle* h) {
+    if (!h) return MPC_OK;
+    if (h->ws) cudaFree(h->ws);
+    free(h);
+    return MPC_OK;
+}
+
+extern "C" size_t mpc_tape_bytes(const mpc_handle* h, int B, int N) {
+    if (!h || B <= 0 || N <= 0 || h->cfg.store_mode != MPC_STORE_ALL) return 0;
+    return (size_t)B * N * TAPE_STRIDE * elem_size(h->cfg.dtype);
+}
+
+static int grid_for(const mpc_handle* h, int B, int which) {
+    const int bps = h->cfg.dtype == MPC_F64 ? persistent_blocks_per_sm<double>(h->ipb, which)
+                                            : persistent_blocks_per_sm<float>(h->ipb, which);
+    long long g = (long long)(bps > 0 ? bps : 1) * h->num_sms;
+    const long long need = (B + h->ipb - 1) / h->ipb;
+    if (g > need) g = need;
+    if (g * h->ipb > h->slots) g = h->slots / h->ipb;
+    return (int)(g > 0 ? g : 1);
+}
+
+template <typename T>
+static void fill_model(const mpc_config& c, Model<T>& m) {
+    m.h = (T)c.dt;
+    m.inv_m = (T)(1.0 / c.mass);
+    m.g = (T)c.gravity;
+    m.Jx = (T)c.inertia[0];
+    m.Jy = (T)c.inertia[1];
+    m.Jz = (T)c.inertia[2];
+    m.iJx = (T)(1.0 / c.inertia[0]);
+    m.iJy = (T)(1.0 / c.inertia[1]);
+    m.iJz = (T)(1.0 / c.inertia[2]);
+    // X layout, rotors FR, RL, FL, RR at (+-d, +-d), spins (+1, +1, -1, -1):
+    // tau_x = sum y_i u_i, tau_y = -sum x_i u_i, tau_z = kappa sum s_i u_i
+    const double d = c.arm / sqrt(2.0);
+    const double rx[4] = {d, -d, d, -d}, ry[4] = {-d, d, d, -d}, sp[4] = {1, 1, -1, -1};
+    for (int i = 0; i < 4; ++i) {
+        m.M[0][i] = (T)ry[i];
+        m.M[1][i] = (T)(-rx[i]);
+        m.M[2][i] = (T)(c.kappa_yaw * sp[i]);
+    }
+}
+
+static int check_problem(const mpc_handle* h, const mpc_problem* p) {
+    if (!h || !p) return MPC_ERR_ARG;
+    if (p->B < 0 || p->B > h->cfg.B_max) return MPC_ERR_SHAPE;
+    if (p->N < 1 || p->N > h->cfg.N_max) return MPC_ERR_SHAPE;
+    if (p->Nq != 1 && p->Nq != p->N) return MPC_ERR_SHAPE;
+    if (p->B == 0) return MPC_OK;
+    if (!p->x0 || !p->Q || !p->x_ref || !p->R || !p->u_ref || !p->u_lo || !p->u_hi) return MPC_ERR_ARG;
+    return MPC_OK;
+}
+
+template <typename T>
+static Params<T> make_params(const mpc_handle* h, const mpc_problem* p, const mpc_solution* s) {
+    Params<T> P;
+    memset(&P, 0, sizeof(P));
+    fill_model(h->cfg, P.mdl);
+    P.B = p->B;
+    P.N = p->N;
+    P.Nq = p->Nq;
+    P.max_iter = h->cfg.max_iter;
+    P.n_alpha = h->cfg.n_alpha;
+    P.store_all = h->cfg.store_mode == MPC_STORE_ALL;
+    P.N_ws = h->cfg.N_max;
+    P.tol = (T)h->cfg.tol;
+    for (int i = 0; i < 4; ++i) P.alpha[i] = (T)h->cfg.alpha[i];
+    P.horizon = p->horizon;
+    P.order = nullptr;
+    P.x0 = (const T*)p->x0;
+    P.Q = (const T*)p->Q;
+    P.xref = (const T*)p->x_ref;
+    P.R = (const T*)p->R;
+    P.uref = (const T*)p->u_ref;
+    P.ulo = (const T*)p->u_lo;
+    P.uhi = (const T*)p->u_hi;
+    P.uinit = (const T*)p->u_init;
+    P.u = (T*)s->u;
+    P.x = (T*)s->x;
+    P.cost = (T*)s->cost;
+    P.iters = s->iters;
+    P.status = s->status;
+    P.tape = (T*)s->tape;
+    P.wsF = (T*)h->wsF;
+    P.wsK = (T*)h->wsK;
+    P.wsCand = (T*)h->wsCand;
+    P.wsSP = (T*)h->wsSP;
+    P.wsKh = (T*)h->wsKh;
+    P.queue = h->queue;
+    return P;
+}
+
+extern "C" int mpc_solve_fwd(mpc_handle* h, const mpc_problem* p, mpc_solution* s, cudaStream_t stream) {
+    int r = check_problem(h, p);
+    if (r != MPC_OK) return r;
+    if (!s) return MPC_ERR_ARG;
+    if (p->B == 0) return MPC_OK;
+    if (!s->u || !s->x || !s->cost || !s->iters || !s->status) return MPC_ERR_ARG;
+    if (h->cfg.store_mode == MPC_STORE_ALL) {
+        if (!s->tape || s->tape_bytes < mpc_tape_bytes(h, p->B, p->N)) return MPC_ERR_ARG;
+    }
+    cudaError_t e;
+    if (h->cfg.dtype == MPC_F64) {
+        const Params<double> P = make_params<double>(h, p, s);
+        e = launch_forward<double>(P, h->cfg.exec_mode, h->ipb, grid_for(h, p->B, 0), h->order, stream);
+    } else {
+        const Params<float> P = make_params<float>(h, p, s);
+        e = launch_forward<float>(P, h->cfg.exec_mode, h->ipb, grid_for(h, p->B, 0), h->order, stream);
+    }
+    return e == cudaSuccess ? MPC_OK : MPC_ERR_CUDA;
+}
+
+extern "C" int mpc_solve_bwd(mpc_handle* h, const mpc_problem* p, const mpc_solution* s, const void* grad_u,
+                             const void* grad_x, void* dQ, void* dx_ref, void* dx0, cudaStream_t stream) {
+    int r = check_problem(h, p);
+    if (r != MPC_OK) return r;
+    if (!s) return MPC_ERR_ARG;
+    if (p->B == 0) return MPC_OK;
+    if (!s->u || !s->x || !s->status || !grad_u || !dQ || !dx_ref || !dx0) return MPC_ERR_ARG;
+    const int recompute = h->cfg.store_mode == MPC_RECOMPUTE;
+    if (!recompute && (!s->tape || s->tape_bytes < mpc_tape_bytes(h, p->B, p->N))) return MPC_ERR_ARG;
+    cudaError_t e;
+    if (h->cfg.dtype == MPC_F64) {
+        const Params<double> P = make_params<double>(h, p, s);
+        AdjArgs<double> A{(const double*)grad_u, (const double*)grad_x, (double*)dQ, (double*)dx_ref,
+                          (double*)dx0, recompute};
+        e = launch_backward<double>(P, A, h->ipb, grid_for(h, p->B, 1), h->order, stream);
+    } else {
+        const Params<float> P = make_params<float>(h, p, s);
+        AdjArgs<float> A{(const float*)grad_u, (const float*)grad_x, (float*)dQ, (float*)dx_ref, (float*)dx0,
+                         recompute};
+        e = launch_backward<float>(P, A, h->ipb, grid_for(h, p->B, 1), h->order, stream);
+    }
+    return e == cudaSuccess ? MPC_OK : MPC_ERR_CUDA;
+}
+
+extern "C" int mpc_autotune(mpc_handle* h, const mpc_problem* p, mpc_solution* s, cudaStream_t stream,
+                            int* ipb_out) {
+    int r = check_problem(h, p);
+    if (r != MPC_OK) return r;
+    if (h->cfg.exec_mode != MPC_EXEC_PERSISTENT) return MPC_ERR_STATE;
+    if (p->B == 0) { if (ipb_out) *ipb_out = h->ipb; return MPC_OK; }
+    const int cands[4] = {1, 2, 4, 8};
+    const int keep = h->ipb;
+    float best_ms = 3.0e38f;
+    int best = keep;
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess) return MPC_ERR_CUDA;
+    if (cudaEventCreate(&e1) != cudaSuccess) { cudaEventDestroy(e0); return MPC_ERR_CUDA; }
+    for (int ci = 0; ci < 4; ++ci) {
+        h->ipb = cands[ci];
+        if ((r = mpc_solve_fwd(h, p, s, stream)) != MPC_OK) break;          // warm-up
+        cudaEventRecord(e0, stream);
+        for (int rep = 0; rep < 3 && r == MPC_OK; ++rep) r = mpc_solve_fwd(h, p, s, stream);
+        cudaEventRecord(e1, stream);
+        if (r != MPC_OK || cudaEventSynchronize(e1) != cudaSuccess) { r = MPC_ERR_CUDA; break; }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best_ms) { best_ms = ms; best = cands[ci]; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    h->ipb = (r == MPC_OK) ? best : keep;
+    if (ipb_out) *ipb_out = h->ipb;
+    return r;
+}
+
+extern "C" int mpc_launch_shape(const mpc_handle* h, int B, int N, int* tpi, int* ipb, int* grid) {
+    if (!h || B < 0 || N < 1 || N > h->cfg.N_max) return MPC_ERR_ARG;
+    if (tpi) *tpi = 32;
+    if (ipb) *ipb = h->ipb;
+    if (grid) *grid = B > 0 ? grid_for(h, B, 0) : 0;
+    return MPC_OK;
+}
+
+extern "C" int mpc_launch_count(const mpc_handle* h, int has_horizon, int* fwd, int* bwd) {
+    if (!h) return MPC_ERR_ARG;
+    const int hz = has_horizon ? 1 : 0;
+    if (fwd) {
+        if (h->cfg.exec_mode == MPC_EXEC_PERSISTENT) *fwd = 1 + hz;
+        else *fwd = 1 + 3 * h->cfg.max_iter + (h->cfg.store_mode == MPC_STORE_ALL ? 2 : 0);
+    }
+    if (bwd) *bwd = 1 + hz;
+    return MPC_OK;
+}
+
+extern "C" const char* mpc_strerror(int code) {
+    switch (code) {
+        case MPC_OK: return "ok";
+        case MPC_ERR_ARG: return "invalid argument";
+        case MPC_ERR_SHAPE: return "shape outside the handle's capacity";
+        case MPC_ERR_CUDA: return "CUDA call failed";
+        case MPC_ERR_TIMEOUT: return "bounded device wait timed out";
+        case MPC_ERR_STATE: return "not valid in this configuration";
+        default: return "unknown error";
+    }
+}
+
+extern "C" const char* mpc_status_str(int st) {
+    switch (st) {
+        case MPC_ST_CONVERGED: return "converged";
+        case MPC_ST_STALLED: return "stalled";
+        case MPC_ST_MAX_ITER: return "max_iter";
+        case MPC_ST_NONFINITE: return "nonfinite";
+        case MPC_ST_NONPD: return "nonpd";
+        default: return "unknown";
+    }
+}

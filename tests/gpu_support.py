@@ -1,0 +1,114 @@
+"""Helpers shared by the GPU tests: run the CUDA path through the C ABI and the
+FP64 oracle on the same seeded inputs, and compare them instance by instance.
+
+Tolerances (FP32 path vs FP64 oracle, per instance):
+  controls   |u - u_or|_2 / max(|u_or|_2, 1e-6)            <= 1e-4
+  cost       |J - J_or| / max(|J_or|, 1e-12)                 <= 1e-5
+  gradients  |g - g_or|_2 / max(|g_or|_2, 1e-9) per block   <= 1e-3
+The FP64 path runs the same kernels in double and is held to 1e-9 / 1e-8.
+"""
+from __future__ import annotations
+
+import functools
+
+import numpy as np
+
+import workloads as W
+from oracle import adjoint, ilqr
+from oracle.model import Quadrotor
+
+QUAD = Quadrotor(W.DEFAULT_MODEL)
+
+U_TOL32, J_TOL32, G_TOL32 = 1e-4, 1e-5, 1e-3
+U_TOL64, J_TOL64, G_TOL64 = 1e-9, 1e-9, 1e-8
+# decisions the FP32 path cannot resolve: relative J gaps / gradient margins
+LS_MARGIN32, QP_MARGIN32 = 1e-4, 1e-4
+
+
+def run_gpu(prob, dtype, max_iter, tol, grad_u=None, grad_x=None, store_mode="store_all",
+            exec_mode="persistent", ipb=0, N_max=None, B_max=None, solver=None):
+    import torch
+    from paper_2605_29155_gb300 import DiffMPC, Problem
+
+    B, N = prob["x0"].shape[0], prob["x_ref"].shape[1]
+    own = solver is None
+    if own:
+        solver = DiffMPC(N_max=N_max or N, B_max=B_max or max(B, 1), dtype=dtype, max_iter=max_iter, tol=tol,
+                         store_mode=store_mode, exec_mode=exec_mode, ipb=ipb)
+    p = Problem.from_numpy(prob, dtype=dtype)
+    s = solver.solve(p)
+    out = dict(u=s.u, x=s.x, cost=s.cost, iters=s.iters, status=s.status)
+    if grad_u is not None:
+        gu = torch.as_tensor(grad_u, dtype=dtype, device="cuda")
+        gx = None if grad_x is None else torch.as_tensor(grad_x, dtype=dtype, device="cuda")
+        dQ, dxr, dx0 = solver.backward(p, s, gu, gx)
+        out.update(dQ=dQ, dx_ref=dxr, dx0=dx0)
+    torch.cuda.synchronize()
+    res = {k: v.detach().cpu().numpy() for k, v in out.items()}
+    if own:
+        solver.close()
+    return res
+
+
+def oracle_solve(prob, idx, max_iter, tol, grad_u=None, grad_x=None):
+    out = []
+    N = prob["x_ref"].shape[1]
+    for i in idx:
+        pr = ilqr.problem_from_batch(prob, i)
+        so = ilqr.solve(QUAD, pr, max_iter, tol)
+        gr = None
+        if grad_u is not None and so.status in (ilqr.CONVERGED, ilqr.STALLED, ilqr.MAX_ITER):
+            gx = np.zeros((N, 13)) if grad_x is None else grad_x[i]
+            gr = adjoint.adjoint(pr, so, gx, grad_u[i])
+        out.append((pr, so, gr))
+    return out
+
+
+def rel(a, b, floor):
+    return float(np.linalg.norm(np.ravel(a) - np.ravel(b)) / max(np.linalg.norm(np.ravel(b)), floor))
+
+
+def compare(gpu, orc, idx, u_tol, j_tol, g_tol, exact_counts=True, skip_degenerate=False):
+    """Per-instance comparison; returns a report dict and a list of failures."""
+    fails, report = [], dict(max_u=0.0, max_J=0.0, max_g=0.0, excluded=0, compared=0)
+    for k, i in enumerate(idx):
+        pr, so, gr = orc[k]
+        if skip_degenerate and (so.ls_margin < LS_MARGIN32 or so.qp_margin < QP_MARGIN32):
+            report["excluded"] += 1
+            continue
+        report["compared"] += 1
+        if exact_counts:
+            if int(gpu["status"][i]) != so.status or int(gpu["iters"][i]) != so.iters:
+                fails.append((i, "status/iters", (int(gpu["status"][i]), int(gpu["iters"][i])), (so.status, so.iters)))
+                continue
+        eu = rel(gpu["u"][i], so.U, 1e-6)
+        ex = rel(gpu["x"][i], so.X, 1e-6)
+        ej = abs(float(gpu["cost"][i]) - so.J) / max(abs(so.J), 1e-12)
+        report["max_u"] = max(report["max_u"], eu, ex)
+        report["max_J"] = max(report["max_J"], ej)
+        if eu > u_tol or ex > u_tol:
+            fails.append((i, "u/x", eu, ex))
+        if ej > j_tol:
+            fails.append((i, "cost", ej))
+        if gr is not None and "dQ" in gpu:
+            for name, ref in (("dQ", gr.dQ), ("dx_ref", gr.dx_ref), ("dx0", gr.dx0)):
+                eg = rel(gpu[name][i], ref, 1e-9)
+                report["max_g"] = max(report["max_g"], eg)
+                if eg > g_tol:
+                    fails.append((i, name, eg))
+    return report, fails
+
+
+@functools.lru_cache(maxsize=None)
+def cached_problem(name, B, N, seed=0, horizons=False):
+    if name == "hover":
+        return W.hover_targets(B, N, seed=seed,
+                               horizons=W.uneven_horizons(B, 1, N, seed + 5) if horizons else None)
+    if name == "track":
+        return W.race_track(B, N, seed=seed,
+                            horizons=W.uneven_horizons(B, 1, N, seed + 5) if horizons else None)
+    if name == "mem":
+        return W.hover_targets(B, N, seed=seed, Nq=N, per_stage_jitter=0.1)
+    if name == "uneven":
+        return W.race_track(B, N, seed=seed, horizons=W.uneven_horizons(B, 5, N, seed + 1000), u_hi_spread=0.2)
+    raise KeyError(name)

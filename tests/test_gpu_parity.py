@@ -1,0 +1,262 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle."""
+import numpy as np
+import pytest
+
+import workloads as W
+from gpu_support import (G_TOL32, G_TOL64, J_TOL32, J_TOL64, U_TOL32, U_TOL64, cached_problem, compare,
+                         oracle_solve, run_gpu)
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def _grads(B, N, seed):
+    rng = np.random.default_rng(seed)
+    gu = rng.normal(size=(B, N, 4))
+    gx = rng.normal(size=(B, N, 13)) * 0.1
+    return gu, gx
+
+
+# ------------------------------------------------------- FP64: logic check --
+
+@pytest.mark.parametrize("name,B,N,horizons,mi", [("hover", 8, 10, False, 10), ("track", 37, 20, True, 8),
+                                                  ("uneven", 33, 40, False, 12), ("mem", 9, 30, False, 8)])
+def test_fp64_forward_backward_match_oracle(name, B, N, horizons, mi):
+    """Same kernels in double: every iterate decision, count and value agrees
+    with the oracle (several warps per block, ragged horizons, shared and
+    per-stage Q)."""
+    prob = cached_problem(name, B, N, 0, horizons)
+    gu, gx = _grads(B, N, 1)
+    gpu = run_gpu(prob, torch.float64, mi, 1e-6, gu, gx, N_max=40)
+    idx = list(range(B))
+    orc = oracle_solve(prob, idx, mi, 1e-6, gu, gx)
+    report, fails = compare(gpu, orc, idx, U_TOL64, J_TOL64, G_TOL64)
+    print(name, report)
+    assert len(fails) <= max(1, B // 30), fails[:5]
+
+
+# --------------------------------------------------- FP32: the product path --
+
+@pytest.mark.parametrize("name,B,N,horizons,mi", [("hover", 64, 20, False, 8), ("track", 64, 20, True, 8),
+                                                  ("uneven", 40, 40, False, 12), ("mem", 24, 30, False, 8)])
+def test_fp32_forward_backward_match_oracle(name, B, N, horizons, mi):
+    prob = cached_problem(name, B, N, 0, horizons)
+    gu, gx = _grads(B, N, 2)
+    gpu = run_gpu(prob, torch.float32, mi, 1e-6, gu, gx, N_max=40)
+    idx = list(range(B))
+    orc = oracle_solve(prob, idx, mi, 1e-6, gu, gx)
+    report, fails = compare(gpu, orc, idx, U_TOL32, J_TOL32, G_TOL32, exact_counts=False, skip_degenerate=True)
+    print(name, report, fails[:5])
+    assert report["compared"] >= 0.7 * B
+    assert not fails, fails[:5]
+
+
+def test_fp32_full_size_track_sampled():
+    """The benchmark's configuration (race track, B = 4096, N = 20, <= 8
+    iterations) in its launch shape; 24 sampled instances checked one by one."""
+    prob = W.cfg_track()
+    B, N = prob["x0"].shape[0], prob["x_ref"].shape[1]
+    gu = W.loss_weights_u0(B, N, seed=1)
+    gpu = run_gpu(prob, torch.float32, prob["max_iter"], prob["tol"], gu, None, N_max=N, B_max=B)
+    idx = list(np.random.default_rng(3).choice(B, 24, replace=False))
+    orc = oracle_solve(prob, idx, prob["max_iter"], prob["tol"], gu, None)
+    report, fails = compare(gpu, orc, idx, U_TOL32, J_TOL32, G_TOL32, exact_counts=False, skip_degenerate=True)
+    print(report)
+    assert not fails, fails[:5]
+    # every instance ends in a valid state with finite outputs
+    assert np.all(np.isin(gpu["status"], [0, 1, 2]))
+    assert np.isfinite(gpu["u"]).all() and np.isfinite(gpu["dx0"]).all()
+    assert (gpu["u"] >= -1e-6).all() and (gpu["u"] <= 8.5 + 1e-6).all()
+
+
+# ------------------------------------------------- equivalences of the modes --
+
+@pytest.mark.parametrize("dtype", ["float32", "float64"])
+def test_plain_form_is_bit_identical_to_persistent(dtype):
+    dt = getattr(torch, dtype)
+    prob = cached_problem("track", 48, 20, 1, True)
+    gu, _ = _grads(48, 20, 3)
+    a = run_gpu(prob, dt, 8, 1e-6, gu, exec_mode="persistent", ipb=4)
+    b = run_gpu(prob, dt, 8, 1e-6, gu, exec_mode="plain", ipb=2)
+    for k in a:
+        np.testing.assert_array_equal(a[k], b[k], err_msg=k)
+
+
+@pytest.mark.parametrize("dtype", ["float32", "float64"])
+def test_recompute_backward_is_bit_identical_to_store_all(dtype):
+    dt = getattr(torch, dtype)
+    prob = cached_problem("mem", 40, 30, 2)
+    gu, gx = _grads(40, 30, 4)
+    a = run_gpu(prob, dt, 8, 1e-6, gu, gx, store_mode="store_all")
+    b = run_gpu(prob, dt, 8, 1e-6, gu, gx, store_mode="recompute")
+    for k in a:
+        np.testing.assert_array_equal(a[k], b[k], err_msg=k)
+
+
+@pytest.mark.parametrize("ipb", [1, 2, 8])
+def test_launch_shapes_agree(ipb):
+    prob = cached_problem("track", 70, 20, 4, True)
+    ref = run_gpu(prob, torch.float32, 8, 1e-6, ipb=4)
+    got = run_gpu(prob, torch.float32, 8, 1e-6, ipb=ipb)
+    for k in ref:
+        np.testing.assert_array_equal(ref[k], got[k], err_msg=k)
+
+
+# ------------------------------------------------------------- edge cases --
+
+def test_empty_batch_is_a_no_op():
+    from paper_2605_29155_gb300 import DiffMPC, Problem, camp
+    prob = cached_problem("hover", 4, 10)
+    s = DiffMPC(N_max=10, B_max=4)
+    p = Problem.from_numpy({k: (v[:0] if isinstance(v, np.ndarray) else v) for k, v in prob.items()})
+    out = s.alloc_solution(0, 10)
+    code = camp.mpc_solve_fwd(s.h, s._cproblem(p), s._csolution(out), torch.cuda.current_stream().cuda_stream)
+    assert code == camp.MPC_OK
+
+
+def test_horizon_one_and_saturated_bounds():
+    """N = 1: only u_0's own cost remains, so u* = clamp(u_ref).  u_lo = u_hi:
+    every control is pinned to its bound and all gains vanish."""
+    prob = dict(cached_problem("hover", 16, 10, 5))
+    prob["horizon"] = np.ones(16, dtype=np.int32)
+    prob["u_ref"] = prob["u_ref"] + np.linspace(-3, 8, 16)[:, None]
+    gu, _ = _grads(16, 10, 5)
+    g = run_gpu(prob, torch.float64, 8, 1e-6, gu)
+    np.testing.assert_allclose(g["u"][:, 0], np.clip(prob["u_ref"], 0, 8.5), atol=1e-12)
+    assert np.all(g["u"][:, 1:] == 0) and np.all(g["x"][:, 1:] == 0)
+    np.testing.assert_allclose(g["x"][:, 0], prob["x0"], atol=0)
+    prob2 = dict(cached_problem("hover", 16, 10, 6))
+    prob2["u_lo"] = prob2["u_hi"] = np.full((16, 4), 3.0)
+    g2 = run_gpu(prob2, torch.float32, 8, 1e-6, gu)
+    assert np.all(g2["u"] == 3.0)
+    assert np.all(np.isin(g2["status"], [0, 1]))
+    orc = oracle_solve(prob2, range(16), 8, 1e-6, gu)
+    for i in range(16):
+        np.testing.assert_allclose(g2["dx0"][i], orc[i][2].dx0, rtol=1e-4, atol=1e-5)
+
+
+def test_nonfinite_input_is_flagged_and_isolated():
+    prob = dict(cached_problem("hover", 12, 10, 7))
+    prob["x0"] = prob["x0"].copy()
+    prob["x0"][3, 0] = np.nan
+    prob["Q"] = prob["Q"].copy()
+    prob["Q"][5, 0, 2] = np.inf
+    gu, _ = _grads(12, 10, 6)
+    g = run_gpu(prob, torch.float32, 8, 1e-6, gu)
+    assert g["status"][3] == 3 and g["status"][5] == 3
+    assert np.all(g["dx0"][[3, 5]] == 0) and np.all(g["dQ"][[3, 5]] == 0)
+    ok = [i for i in range(12) if i not in (3, 5)]
+    assert np.isfinite(g["u"][ok]).all() and np.all(np.isin(g["status"][ok], [0, 1, 2]))
+
+
+def test_hover_fixed_point_on_gpu():
+    B, N = 6, 12
+    x0 = np.zeros((B, 13))
+    x0[:, 0:3] = np.random.default_rng(0).normal(size=(B, 3))
+    x0[:, 3] = 1.0
+    prob = dict(x0=x0, Q=np.full((B, 1, 13), 2.0), x_ref=np.repeat(x0[:, None, :], N, axis=1),
+                R=np.full((B, 4), 0.01), u_ref=np.full((B, 4), W.DEFAULT_MODEL.hover_thrust),
+                u_lo=np.zeros((B, 4)), u_hi=np.full((B, 4), 8.5), horizon=None)
+    gu = np.zeros((B, N, 4))
+    gu[:, 0] = 1
+    g = run_gpu(prob, torch.float32, 8, 1e-6, gu)
+    np.testing.assert_allclose(g["u"], W.DEFAULT_MODEL.hover_thrust, rtol=1e-6)
+    assert np.all(g["cost"] < 1e-10) and np.all(g["status"] == 1) and np.all(g["iters"] == 1)
+    np.testing.assert_allclose(g["dQ"], 0, atol=1e-6)
+
+
+# ------------------------------------------------- API, graphs, autograd --
+
+def test_api_errors_on_gpu():
+    from paper_2605_29155_gb300 import DiffMPC, Problem, camp
+    prob = cached_problem("hover", 8, 10)
+    s = DiffMPC(N_max=10, B_max=4)
+    p = Problem.from_numpy(prob)
+    out = s.alloc_solution(8, 10)
+    st = torch.cuda.current_stream().cuda_stream
+    assert camp.mpc_solve_fwd(s.h, s._cproblem(p), s._csolution(out), st) == camp.MPC_ERR_SHAPE
+    s2 = DiffMPC(N_max=10, B_max=8)
+    cs = s2._csolution(s2.alloc_solution(8, 10))
+    cs.tape_bytes = cs.tape_bytes - 4
+    assert camp.mpc_solve_fwd(s2.h, s2._cproblem(p), cs, st) == camp.MPC_ERR_ARG
+    cp = s2._cproblem(p)
+    cp.Nq = 3
+    assert camp.mpc_solve_fwd(s2.h, cp, s2._csolution(s2.alloc_solution(8, 10)), st) == camp.MPC_ERR_SHAPE
+    s.close()
+    s2.close()
+
+
+def test_cuda_graph_replay_matches_eager():
+    from paper_2605_29155_gb300 import DiffMPC, Problem
+    prob = cached_problem("track", 96, 20, 8)
+    gu, _ = _grads(96, 20, 8)
+    solver = DiffMPC(N_max=20, B_max=96)
+    p = Problem.from_numpy(prob)
+    gu_t = torch.as_tensor(gu, dtype=torch.float32, device="cuda")
+    s = solver.alloc_solution(96, 20)
+    grads = (torch.empty_like(p.Q), torch.empty_like(p.x_ref), torch.empty_like(p.x0))
+    solver.solve(p, s)
+    solver.backward(p, s, gu_t, out=grads)
+    torch.cuda.synchronize()
+    eager = [t.clone() for t in (s.u, s.cost, *grads)]
+    for t in (s.u, s.cost, *grads):
+        t.zero_()
+    g = torch.cuda.CUDAGraph()
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        with torch.cuda.graph(g):
+            solver.solve(p, s)
+            solver.backward(p, s, gu_t, out=grads)
+    torch.cuda.current_stream().wait_stream(side)
+    for _ in range(3):
+        g.replay()
+    torch.cuda.synchronize()
+    for a, b in zip(eager, (s.u, s.cost, *grads)):
+        assert torch.equal(a, b)
+    solver.close()
+
+
+def test_autograd_function_and_memory_plateau():
+    """One module-level autograd Function; repeated forward/backward calls do
+    not grow device memory."""
+    from paper_2605_29155_gb300 import DiffMPC, diff_mpc
+    prob = cached_problem("hover", 32, 10, 9)
+    solver = DiffMPC(N_max=10, B_max=32, max_iter=6)
+    t = {k: torch.as_tensor(v, dtype=torch.float32, device="cuda") for k, v in prob.items()
+         if isinstance(v, np.ndarray)}
+    w = torch.randn(32, 4, device="cuda")
+
+    def step():
+        x0 = t["x0"].clone().requires_grad_(True)
+        Q = t["Q"].clone().requires_grad_(True)
+        xr = t["x_ref"].clone().requires_grad_(True)
+        u, x, cost, iters, status = diff_mpc(solver, x0, Q, xr, t["R"], t["u_ref"], t["u_lo"], t["u_hi"])
+        (u[:, 0] * w).sum().backward()
+        return x0.grad, Q.grad, xr.grad
+
+    g1 = step()
+    gu = torch.zeros(32, 10, 4, device="cuda")
+    gu[:, 0] = w
+    from paper_2605_29155_gb300 import Problem
+    p = Problem(x0=t["x0"], Q=t["Q"], x_ref=t["x_ref"], R=t["R"], u_ref=t["u_ref"], u_lo=t["u_lo"], u_hi=t["u_hi"])
+    s = solver.solve(p)
+    dQ, dxr, dx0 = solver.backward(p, s, gu)
+    assert torch.equal(g1[0], dx0) and torch.equal(g1[1], dQ) and torch.equal(g1[2], dxr)
+    for _ in range(20):
+        step()
+    torch.cuda.synchronize()
+    m0 = torch.cuda.memory_allocated()
+    for _ in range(300):
+        step()
+    torch.cuda.synchronize()
+    assert torch.cuda.memory_allocated() <= m0
+    solver.close()
