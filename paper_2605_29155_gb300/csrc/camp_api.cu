@@ -16,7 +16,7 @@ struct mpc_handle {
     int slots;              // scratch slots (>= B_max and >= resident warps)
     void* ws;               // one allocation holding every scratch region
     size_t ws_bytes;
-    void *wsF, *wsK, *wsCand, *wsSP, *wsKh;
+    void *wsF, *wsK, *wsCand, *wsSP, *wsKh, *wsXlo;
     int* queue;             // [2] work-queue tickets (forward, backward)
     int* order;             // [B_max] longest-horizon-first order
     int ipb;                // instances per block of the persistent kernels
@@ -99,12 +99,13 @@ extern "C" int mpc_create(const mpc_config* cfg, mpc_handle** out) {
     const size_t S = (size_t)h->slots, Nw = (size_t)cfg->N_max;
     const size_t bF = align256(S * Nw * NF * es);
     const size_t bK = align256(S * Nw * KREC * es);
-    const size_t bC = align256(S * 4 * Nw * NZ * es);
+    const size_t bC = align256(S * 4 * Nw * CREC * es);
+    const size_t bX = align256(S * Nw * NX * es);
     const size_t bP = align256(S * Nw * SP_STRIDE * es);
     const size_t bH = align256(S * Nw * NU * es);
     const size_t bQ = align256(2 * sizeof(int));
     const size_t bO = align256((size_t)cfg->B_max * sizeof(int));
-    h->ws_bytes = bF + bK + bC + bP + bH + bQ + bO;
+    h->ws_bytes = bF + bK + bC + bP + bH + bX + bQ + bO;
     if (cudaMalloc(&h->ws, h->ws_bytes) != cudaSuccess) { free(h); return MPC_ERR_CUDA; }
     char* p = (char*)h->ws;
     h->wsF = p; p += bF;
@@ -112,6 +113,7 @@ extern "C" int mpc_create(const mpc_config* cfg, mpc_handle** out) {
     h->wsCand = p; p += bC;
     h->wsSP = p; p += bP;
     h->wsKh = p; p += bH;
+    h->wsXlo = p; p += bX;
     h->queue = (int*)p; p += bQ;
     h->order = (int*)p;
     *out = h;
@@ -207,6 +209,7 @@ static Params<T> make_params(const mpc_handle* h, const mpc_problem* p, const mp
     P.wsCand = (T*)h->wsCand;
     P.wsSP = (T*)h->wsSP;
     P.wsKh = (T*)h->wsKh;
+    P.wsXlo = (T*)h->wsXlo;
     P.queue = h->queue;
     return P;
 }

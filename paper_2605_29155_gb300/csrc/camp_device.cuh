@@ -20,6 +20,7 @@ constexpr int TAPE_STRIDE = 288;       // tape record per stage (elements)
 constexpr int TAPE_F = 0, TAPE_K = 221, TAPE_L = 273, TAPE_MASK = 283;
 constexpr int KREC = 56;               // K_t (52, row-major) + k_t (4)
 constexpr int SP_STRIDE = 32;          // RK4 stage points per stage: 4 x (q, w, pad)
+constexpr int CREC = 30;               // line-search candidate per stage: x hi (13), x lo (13), u (4)
 constexpr int NTRI_Q = NZ * (NZ + 1) / 2;   // 153 upper-triangle entries of Q_t
 constexpr int NTRI_V = NX * (NX + 1) / 2;   // 91 upper-triangle entries of V_t
 constexpr int QP_MAX_IT = 20, QP_MAX_LS = 30;
@@ -45,7 +46,7 @@ template <typename T> struct Params {
     T *u, *x, *cost;
     int *iters, *status;
     T* tape;
-    T *wsF, *wsK, *wsCand, *wsSP, *wsKh;
+    T *wsF, *wsK, *wsCand, *wsSP, *wsKh, *wsXlo;
     int* queue;
 };
 
@@ -131,6 +132,41 @@ __device__ __forceinline__ void rk4_step(const Model<T>& m, T* x, const T* u) {
     const T h6 = m.h / T(6);
 #pragma unroll
     for (int i = 0; i < NX; ++i) x[i] = x[i] + h6 * (acc[i] + k[i]);
+}
+
+// (hi, lo) += d: the rounding error of hi + d is carried in lo (2Sum, then a
+// fast renormalisation), so a trajectory accumulated over many steps keeps the
+// increments' precision instead of the state's.
+template <typename T>
+__device__ __forceinline__ void acc2(T& hi, T& lo, T d) {
+    const T s = hi + d;
+    const T bb = s - hi;
+    const T err = (hi - (s - bb)) + (d - bb);
+    const T l = lo + err;
+    hi = s + l;
+    lo = l - (hi - s);
+}
+
+// RK4 step whose state is the unevaluated sum hi + lo: the four stages are
+// evaluated at hi in working precision, the increment h/6 (k1+2k2+2k3+k4) is
+// added with acc2.
+template <typename T>
+__device__ __forceinline__ void rk4_step2(const Model<T>& m, T* xh, T* xl, const T* u) {
+    T k[NX], acc[NX], xs[NX];
+    const T hh = T(0.5) * m.h;
+    f_cont(m, xh, u, k);
+#pragma unroll
+    for (int i = 0; i < NX; ++i) { acc[i] = k[i]; xs[i] = xh[i] + hh * k[i]; }
+    f_cont(m, xs, u, k);
+#pragma unroll
+    for (int i = 0; i < NX; ++i) { acc[i] = acc[i] + T(2) * k[i]; xs[i] = xh[i] + hh * k[i]; }
+    f_cont(m, xs, u, k);
+#pragma unroll
+    for (int i = 0; i < NX; ++i) { acc[i] = acc[i] + T(2) * k[i]; xs[i] = xh[i] + m.h * k[i]; }
+    f_cont(m, xs, u, k);
+    const T h6 = m.h / T(6);
+#pragma unroll
+    for (int i = 0; i < NX; ++i) acc2(xh[i], xl[i], h6 * (acc[i] + k[i]));
 }
 
 // RK4 stage points of one step: for s = 1..4 the (q, w) of xi_s (xi_1 = x,
@@ -386,6 +422,7 @@ template <typename T> struct Inst {
     T* cand;          // slot scratch: candidates [4][N_ws][17]
     T* sp;            // slot scratch: stage points [N_ws][32]
     T* kh;            // slot scratch: adjoint k-hat [N_ws][4]
+    T* xlo;           // slot scratch: low part of the nominal state [N_ws][13]
 };
 
 template <typename T>
@@ -403,9 +440,10 @@ __device__ __forceinline__ Inst<T> make_inst(const Params<T>& P, int b, int slot
     const size_t s = (size_t)slot;
     I.F = P.wsF + s * P.N_ws * NF;
     I.Kr = P.wsK + s * P.N_ws * KREC;
-    I.cand = P.wsCand + s * 4 * P.N_ws * NZ;
+    I.cand = P.wsCand + s * 4 * P.N_ws * CREC;
     I.sp = P.wsSP + s * P.N_ws * SP_STRIDE;
     I.kh = P.wsKh + s * P.N_ws * NU;
+    I.xlo = P.wsXlo + s * P.N_ws * NX;
     return I;
 }
 
@@ -426,19 +464,9 @@ __device__ __forceinline__ void load_instance(const Params<T>& P, const Inst<T>&
     __syncwarp();
 }
 
-// Centred stage cost 1/2 (x-x_ref)'Q(x-x_ref) + 1/2 (u-u_ref)'R(u-u_ref).
-template <typename T>
-__device__ __forceinline__ T stage_cost(const T* x, const T* u, const T* Qt, const T* xr, const WarpSmem<T>& S) {
-    T sx = T(0), su = T(0);
-#pragma unroll
-    for (int i = 0; i < NX; ++i) { const T e = x[i] - xr[i]; sx += e * (Qt[i] * e); }
-#pragma unroll
-    for (int a = 0; a < NU; ++a) { const T e = u[a] - S.uref[a]; su += e * (S.R[a] * e); }
-    return T(0.5) * sx + T(0.5) * su;
-}
-
 // --------------------------------------------------------- A1 rollout -------
-// U^0 = clamp(u_init or u_ref), X^0 by RK4 from x_init (lane 0), J^0.
+// U^0 = clamp(u_init or u_ref), X^0 by RK4 from x_init (lane 0), J^0.  States
+// are carried as hi + lo (rk4_step2); hi is the output x, lo stays in the slot.
 // Stages past the horizon are zero-filled.  Returns J^0 on every lane.
 template <typename T>
 __device__ T initial_rollout(const Params<T>& P, const Inst<T>& I, const WarpSmem<T>& S, int lane) {
@@ -447,9 +475,9 @@ __device__ T initial_rollout(const Params<T>& P, const Inst<T>& I, const WarpSme
     for (int e = n * NX + lane; e < P.N * NX; e += 32) I.xb[e] = T(0);
     T J = T(0);
     if (lane == 0) {
-        T xs[NX], us[NU];
+        T xh[NX], xl[NX], us[NU];
 #pragma unroll
-        for (int i = 0; i < NX; ++i) xs[i] = S.x0[i];
+        for (int i = 0; i < NX; ++i) { xh[i] = S.x0[i]; xl[i] = T(0); }
         for (int t = 0; t < n; ++t) {
 #pragma unroll
             for (int a = 0; a < NU; ++a) {
@@ -457,10 +485,20 @@ __device__ T initial_rollout(const Params<T>& P, const Inst<T>& I, const WarpSme
                 us[a] = clampT(u0, S.ulo[a], S.uhi[a]);
                 I.ub[t * NU + a] = us[a];
             }
+            const T* Qt = Qrow(P, I, t);
+            const T* xr = I.xrefb + t * NX;
+            T sx = T(0), su = T(0);
 #pragma unroll
-            for (int i = 0; i < NX; ++i) I.xb[t * NX + i] = xs[i];
-            J += stage_cost(xs, us, Qrow(P, I, t), I.xrefb + t * NX, S);
-            if (t < n - 1) rk4_step(P.mdl, xs, us);
+            for (int i = 0; i < NX; ++i) {
+                I.xb[t * NX + i] = xh[i];
+                I.xlo[t * NX + i] = xl[i];
+                const T e = (xh[i] - xr[i]) + xl[i];
+                sx += e * (Qt[i] * e);
+            }
+#pragma unroll
+            for (int a = 0; a < NU; ++a) { const T e = us[a] - S.uref[a]; su += e * (S.R[a] * e); }
+            J += T(0.5) * sx + T(0.5) * su;
+            if (t < n - 1) rk4_step2(P.mdl, xh, xl, us);
         }
     }
     __syncwarp();
@@ -666,57 +704,74 @@ __device__ bool riccati(const Params<T>& P, const Inst<T>& I, WarpSmem<T>& S, in
 
 // ------------------------------------------------- A4 line search ----------
 // Sec. IV-3: every alpha rolled out on its own lane,
-//   u_hat_t = clamp(u_t + alpha k_t + K_t (x_hat_t - x_t)),  x_hat_{t+1} = RK4,
-// J(alpha) accumulated stage by stage; alpha* = first argmin; the step is
-// taken only if J(alpha*) < J.  Returns: 0 step taken (du, J updated),
-// 1 no decrease (stalled).
+//   u_hat_t = clamp(u_t + alpha k_t + K_t (x_hat_t - x_t)),  x_hat_{t+1} = RK4.
+// The candidates are compared through their cost change with respect to the
+// nominal, accumulated stage by stage from the differences themselves,
+//   dJ_t = (x_hat - x)' Q (x - x_ref + (x_hat - x)/2) + (u_hat - u)' R (u - u_ref + (u_hat - u)/2),
+// which equals J(alpha) - J exactly for the quadratic cost but does not cancel
+// against J's magnitude; with the hi + lo states it resolves decrements far
+// below the working precision of J.  alpha* = first argmin; the step is taken
+// only if dJ(alpha*) < 0.  Returns 0 (step taken: du, J updated) or 1 (stalled).
 template <typename T>
 __device__ int line_search(const Params<T>& P, const Inst<T>& I, WarpSmem<T>& S, int lane, T& Jnom, T& du_out) {
     const int n = I.n;
     if (lane < P.n_alpha) {
         const T alpha = P.alpha[lane];
-        T xh[NX], uh[NU];
+        T xh[NX], xl[NX], uh[NU];
 #pragma unroll
-        for (int i = 0; i < NX; ++i) xh[i] = S.x0[i];
-        T J = T(0);
-        T* cd = I.cand + (size_t)lane * P.N_ws * NZ;
+        for (int i = 0; i < NX; ++i) { xh[i] = S.x0[i]; xl[i] = T(0); }
+        T dJ = T(0);
+        T* cd = I.cand + (size_t)lane * P.N_ws * CREC;
         for (int t = 0; t < n; ++t) {
             const T* kr = I.Kr + (size_t)t * KREC;
+            const T* Qt = Qrow(P, I, t);
+            const T* xr = I.xrefb + t * NX;
             T dxv[NX];
 #pragma unroll
-            for (int i = 0; i < NX; ++i) dxv[i] = xh[i] - I.xb[t * NX + i];
+            for (int i = 0; i < NX; ++i) dxv[i] = (xh[i] - I.xb[t * NX + i]) + (xl[i] - I.xlo[t * NX + i]);
+            T sx = T(0), su = T(0);
 #pragma unroll
             for (int a = 0; a < NU; ++a) {
                 T s = T(0);
 #pragma unroll
                 for (int i = 0; i < NX; ++i) s += kr[a * NX + i] * dxv[i];
-                const T un = I.ub[t * NU + a] + alpha * kr[NU * NX + a] + s;
+                const T ub = I.ub[t * NU + a];
+                const T un = ub + alpha * kr[NU * NX + a] + s;
                 uh[a] = clampT(un, S.ulo[a], S.uhi[a]);
+                const T d = uh[a] - ub;
+                su += d * (S.R[a] * ((ub - S.uref[a]) + T(0.5) * d));
             }
-            J += stage_cost(xh, uh, Qrow(P, I, t), I.xrefb + t * NX, S);
 #pragma unroll
-            for (int i = 0; i < NX; ++i) cd[t * NZ + i] = xh[i];
+            for (int i = 0; i < NX; ++i) {
+                const T eb = (I.xb[t * NX + i] - xr[i]) + I.xlo[t * NX + i];
+                sx += dxv[i] * (Qt[i] * (eb + T(0.5) * dxv[i]));
+            }
+            dJ += sx + su;
 #pragma unroll
-            for (int a = 0; a < NU; ++a) cd[t * NZ + NX + a] = uh[a];
-            if (t < n - 1) rk4_step(P.mdl, xh, uh);
+            for (int i = 0; i < NX; ++i) { cd[t * CREC + i] = xh[i]; cd[t * CREC + NX + i] = xl[i]; }
+#pragma unroll
+            for (int a = 0; a < NU; ++a) cd[t * CREC + 2 * NX + a] = uh[a];
+            if (t < n - 1) rk4_step2(P.mdl, xh, xl, uh);
         }
-        S.Jc[lane] = finiteT(J) ? J : T(INFINITY);
+        S.Jc[lane] = finiteT(dJ) ? dJ : T(INFINITY);
     }
     __syncwarp();
     int best = 0;
     T Jb = S.Jc[0];
     for (int c = 1; c < P.n_alpha; ++c)
         if (S.Jc[c] < Jb) { Jb = S.Jc[c]; best = c; }
-    if (!(Jb < Jnom)) return 1;
-    const T* cd = I.cand + (size_t)best * P.N_ws * NZ;
+    if (!(Jb < T(0))) return 1;
+    const T* cd = I.cand + (size_t)best * P.N_ws * CREC;
     T dmax = T(0);
-    for (int e = lane; e < n * NZ; e += 32) {
-        const int t = e / NZ, j = e - t * NZ;
+    for (int e = lane; e < n * CREC; e += 32) {
+        const int t = e / CREC, j = e - t * CREC;
         const T val = cd[e];
         if (j < NX) {
             I.xb[t * NX + j] = val;
+        } else if (j < 2 * NX) {
+            I.xlo[t * NX + j - NX] = val;
         } else {
-            T* up = I.ub + t * NU + (j - NX);
+            T* up = I.ub + t * NU + (j - 2 * NX);
             const T d = fabs(val - *up);
             dmax = d > dmax ? d : dmax;
             *up = val;
@@ -728,7 +783,7 @@ __device__ int line_search(const Params<T>& P, const Inst<T>& I, WarpSmem<T>& S,
         dmax = other > dmax ? other : dmax;
     }
     __syncwarp();
-    Jnom = Jb;
+    Jnom = Jnom + Jb;
     du_out = dmax;
     return 0;
 }
