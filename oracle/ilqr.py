@@ -18,7 +18,10 @@ Readings where the paper is silent (each listed in the design notes):
             1/2 (x_ref'Q x_ref + u_ref'R u_ref) per stage.
   R4 line search  every alpha is rolled out; alpha* = argmin J(alpha), ties to
             the earlier (larger) alpha; accepted only if J(alpha*) < J_nominal,
-            otherwise the solve stops with status STALLED.
+            otherwise the solve stops with status STALLED.  J(alpha) - J is
+            evaluated as the sum of the stage-wise cost changes (cost_change),
+            an exact identity for the quadratic cost that does not lose the
+            decrement to the rounding of J's total.
   R5 converged    max_t |u^k_t - u^{k-1}_t|_inf < tol after an accepted step;
             at most max_iter iterations; every executed iteration is counted.
   R6 start  U^0 = clamp(u_ref) (or clamp(u_init) when given).
@@ -77,6 +80,19 @@ def total_cost(prob: Problem, X, U):
         du = U[t] - prob.u_ref
         J += 0.5 * (dx @ (prob.Qt(t) * dx)) + 0.5 * (du @ (prob.R * du))
     return J
+
+
+def cost_change(prob: Problem, X, U, Xa, Ua):
+    """J(Xa, Ua) - J(X, U) summed stage by stage from the differences,
+    d' C (z - z_ref + d/2) with d = z_a - z: the exact change of the quadratic
+    cost, evaluated without cancelling against the size of J (reading R4)."""
+    dJ = 0.0
+    for t in range(prob.n):
+        dx = Xa[t] - X[t]
+        du = Ua[t] - U[t]
+        dJ += dx @ (prob.Qt(t) * ((X[t] - prob.x_ref[t]) + 0.5 * dx))
+        dJ += du @ (prob.R * ((U[t] - prob.u_ref) + 0.5 * du))
+    return dJ
 
 
 @dataclasses.dataclass
@@ -198,9 +214,9 @@ def solve(model, prob: Problem, max_iter=10, tol=1e-6, alphas=ALPHAS) -> Solutio
         cands = []
         for a in alphas:
             Xa, Ua = forward_pass(model, prob, X, U, bp, a)
-            Ja = total_cost(prob, Xa, Ua)
-            cands.append((Ja if np.isfinite(Ja) else np.inf, Xa, Ua))
-        Js = np.array([c[0] for c in cands])
+            dJa = cost_change(prob, X, U, Xa, Ua)
+            cands.append((dJa if np.isfinite(dJa) else np.inf, Xa, Ua))
+        Js = np.array([c[0] for c in cands])      # J(alpha) - J for every alpha
         best = int(np.argmin(Js))          # first minimum: the larger alpha on ties
         # Degeneracy bookkeeping (reading R11): the relative J gap behind each
         # decision whose alternatives differ materially in the controls.
@@ -211,19 +227,20 @@ def solve(model, prob: Problem, max_iter=10, tol=1e-6, alphas=ALPHAS) -> Solutio
                 ls_margin = min(ls_margin, abs(c[0] - Js[best]) / scale)
         du = float(np.max(np.abs(Ub[:n] - U[:n])))
         if np.isfinite(Js[best]) and du > MATERIAL_DU:
-            ls_margin = min(ls_margin, abs(J - Js[best]) / scale)
-        if not (Js[best] < J):
+            ls_margin = min(ls_margin, abs(Js[best]) / scale)
+        if not (Js[best] < 0.0):
             status = STALLED
             hist.append(None)
             break
         hist.append(alphas[best])
-        J, X, U = cands[best]
+        J = J + Js[best]
+        X, U = cands[best][1], cands[best][2]
         if du < tol:
             status = CONVERGED
             break
     F = linearize(model, prob, X, U)
     bp = backward_pass(prob, X, U, F)
-    return Solution(X, U, J, iters, status, F, bp, ls_margin, qp_margin, hist)
+    return Solution(X, U, total_cost(prob, X, U), iters, status, F, bp, ls_margin, qp_margin, hist)
 
 
 def solve_batch(model, batch: dict, idx=None, max_iter=None, tol=None):

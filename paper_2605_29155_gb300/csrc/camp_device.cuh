@@ -550,17 +550,28 @@ __device__ bool riccati(const Params<T>& P, const Inst<T>& I, WarpSmem<T>& S, in
                         const int* triQ, const int* triV, const T* Fsrc, T* tape,
                         const AdjArgs<T>* adj) {
     const int n = I.n;
+    // Iterations take the cost gradient at the full hi + lo nominal; the final
+    // factorization (tape or recompute backward) takes x* as returned, so both
+    // backward modes see identical inputs.
+    const bool use_lo = (tape == nullptr && adj == nullptr);
     for (int e = lane; e < NX * NX; e += 32) S.V[e] = T(0);
     if (lane < NX) { S.v[lane] = T(0); S.vh[lane] = T(0); }
     __syncwarp();
     for (int t = n - 1; t >= 0; --t) {
         const T* Qt = Qrow(P, I, t);
         if (lane < NZ) {
-            T cd, z, zr;
-            if (lane < NX) { cd = Qt[lane]; z = I.xb[t * NX + lane]; zr = I.xrefb[t * NX + lane]; }
-            else { const int a = lane - NX; cd = S.R[a]; z = I.ub[t * NU + a]; zr = S.uref[a]; }
+            T cd, e;
+            if (lane < NX) {
+                cd = Qt[lane];
+                e = I.xb[t * NX + lane] - I.xrefb[t * NX + lane];
+                if (use_lo) e += I.xlo[t * NX + lane];
+            } else {
+                const int a = lane - NX;
+                cd = S.R[a];
+                e = I.ub[t * NU + a] - S.uref[a];
+            }
             S.Cd[lane] = cd;
-            S.c[lane] = cd * (z - zr);
+            S.c[lane] = cd * e;
         }
         const bool dyn = (t < n - 1);
         if (dyn) {
@@ -720,7 +731,7 @@ __device__ int line_search(const Params<T>& P, const Inst<T>& I, WarpSmem<T>& S,
         T xh[NX], xl[NX], uh[NU];
 #pragma unroll
         for (int i = 0; i < NX; ++i) { xh[i] = S.x0[i]; xl[i] = T(0); }
-        T dJ = T(0);
+        T dJ = T(0), dJl = T(0);
         T* cd = I.cand + (size_t)lane * P.N_ws * CREC;
         for (int t = 0; t < n; ++t) {
             const T* kr = I.Kr + (size_t)t * KREC;
@@ -746,13 +757,14 @@ __device__ int line_search(const Params<T>& P, const Inst<T>& I, WarpSmem<T>& S,
                 const T eb = (I.xb[t * NX + i] - xr[i]) + I.xlo[t * NX + i];
                 sx += dxv[i] * (Qt[i] * (eb + T(0.5) * dxv[i]));
             }
-            dJ += sx + su;
+            acc2(dJ, dJl, sx + su);
 #pragma unroll
             for (int i = 0; i < NX; ++i) { cd[t * CREC + i] = xh[i]; cd[t * CREC + NX + i] = xl[i]; }
 #pragma unroll
             for (int a = 0; a < NU; ++a) cd[t * CREC + 2 * NX + a] = uh[a];
             if (t < n - 1) rk4_step2(P.mdl, xh, xl, uh);
         }
+        dJ = dJ + dJl;
         S.Jc[lane] = finiteT(dJ) ? dJ : T(INFINITY);
     }
     __syncwarp();
