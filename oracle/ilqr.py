@@ -40,7 +40,7 @@ from . import boxqp
 
 CONVERGED, STALLED, MAX_ITER, NONFINITE, NONPD = 0, 1, 2, 3, 4
 ALPHAS = (1.0, 0.5, 0.25, 0.1)
-MATERIAL_DU = 1e-5   # control change [N] below which a decision is immaterial
+MATERIAL_DU = 1e-4   # control change [N] below which a decision is immaterial
 
 
 @dataclasses.dataclass
@@ -82,17 +82,22 @@ def total_cost(prob: Problem, X, U):
     return J
 
 
-def cost_change(prob: Problem, X, U, Xa, Ua):
+def cost_change(prob: Problem, X, U, Xa, Ua, with_scale=False):
     """J(Xa, Ua) - J(X, U) summed stage by stage from the differences,
     d' C (z - z_ref + d/2) with d = z_a - z: the exact change of the quadratic
-    cost, evaluated without cancelling against the size of J (reading R4)."""
+    cost, evaluated without cancelling against the size of J (reading R4).
+    With ``with_scale`` also the sum of the terms' magnitudes, the size a
+    rounding error of the sum is relative to."""
     dJ = 0.0
+    scale = 0.0
     for t in range(prob.n):
         dx = Xa[t] - X[t]
         du = Ua[t] - U[t]
-        dJ += dx @ (prob.Qt(t) * ((X[t] - prob.x_ref[t]) + 0.5 * dx))
-        dJ += du @ (prob.R * ((U[t] - prob.u_ref) + 0.5 * du))
-    return dJ
+        tx = dx * (prob.Qt(t) * ((X[t] - prob.x_ref[t]) + 0.5 * dx))
+        tu = du * (prob.R * ((U[t] - prob.u_ref) + 0.5 * du))
+        dJ += tx.sum() + tu.sum()
+        scale += np.abs(tx).sum() + np.abs(tu).sum()
+    return (dJ, scale) if with_scale else dJ
 
 
 @dataclasses.dataclass
@@ -212,15 +217,18 @@ def solve(model, prob: Problem, max_iter=10, tol=1e-6, alphas=ALPHAS) -> Solutio
             break
         qp_margin = min(qp_margin, bp.margin)
         cands = []
+        scale = 1e-300
         for a in alphas:
             Xa, Ua = forward_pass(model, prob, X, U, bp, a)
-            dJa = cost_change(prob, X, U, Xa, Ua)
+            dJa, sc = cost_change(prob, X, U, Xa, Ua, with_scale=True)
             cands.append((dJa if np.isfinite(dJa) else np.inf, Xa, Ua))
+            if np.isfinite(sc):
+                scale = max(scale, sc)
         Js = np.array([c[0] for c in cands])      # J(alpha) - J for every alpha
         best = int(np.argmin(Js))          # first minimum: the larger alpha on ties
-        # Degeneracy bookkeeping (reading R11): the relative J gap behind each
-        # decision whose alternatives differ materially in the controls.
-        scale = max(abs(J), 1e-30)
+        # Degeneracy bookkeeping (reading R11): the gap behind each decision
+        # whose alternatives differ materially in the controls, relative to the
+        # magnitude of the terms the cost changes are summed from.
         Ub = cands[best][2]
         for i, c in enumerate(cands):
             if i != best and np.isfinite(c[0]) and np.max(np.abs(c[2][:n] - Ub[:n])) > MATERIAL_DU:

@@ -542,146 +542,164 @@ __device__ void linearize(const Params<T>& P, const Inst<T>& I, T* Fdst, int lan
 //   k_t, free set <- box QP(Q_uu, q_u, u_lo - u_t, u_hi - u_t)
 //   K_t = -Q_uu,ff^-1 Q_ux,f on free rows, 0 on clamped rows
 //   V_t = Q_xx + Q_xu K_t,   v_t = q_x + Q_xu k_t
-// K_t, k_t go to the slot scratch; in the final pass (tape != NULL) F_t, K_t,
-// the masked factor and the free mask go to the tape.  When `adj` is set the
-// adjoint backward step runs on the same factorization (recompute backward).
+// K_t, k_t go to the slot scratch.  Options:
+//   use_lo   cost gradient at the hi + lo nominal (iterations); otherwise at
+//            x* as returned (the factorization the backward differentiates)
+//   tape     also store F_t, K_t, the masked factor and the free mask
+//   replay   skip the recursion and read F_t, K_t, factor and mask from the tape
+//   adj      after each stage, the adjoint backward step (Sec. IV implicit
+//            differentiation) on that stage's factorization:
+//              qh = g_t + F_t' vh_{t+1};  kh_t = -(Q_uu,ff)^-1 qh_u,f;  vh_t = qh_x + K_t' qh_u
+template <typename T> struct RicOpts {
+    T* tape;
+    const AdjArgs<T>* adj;
+    bool replay;
+    bool use_lo;
+};
+
 template <typename T>
 __device__ bool riccati(const Params<T>& P, const Inst<T>& I, WarpSmem<T>& S, int lane,
-                        const int* triQ, const int* triV, const T* Fsrc, T* tape,
-                        const AdjArgs<T>* adj) {
+                        const int* triQ, const int* triV, const RicOpts<T> o) {
     const int n = I.n;
-    // Iterations take the cost gradient at the full hi + lo nominal; the final
-    // factorization (tape or recompute backward) takes x* as returned, so both
-    // backward modes see identical inputs.
-    const bool use_lo = (tape == nullptr && adj == nullptr);
     for (int e = lane; e < NX * NX; e += 32) S.V[e] = T(0);
     if (lane < NX) { S.v[lane] = T(0); S.vh[lane] = T(0); }
     __syncwarp();
     for (int t = n - 1; t >= 0; --t) {
-        const T* Qt = Qrow(P, I, t);
-        if (lane < NZ) {
-            T cd, e;
-            if (lane < NX) {
-                cd = Qt[lane];
-                e = I.xb[t * NX + lane] - I.xrefb[t * NX + lane];
-                if (use_lo) e += I.xlo[t * NX + lane];
-            } else {
-                const int a = lane - NX;
-                cd = S.R[a];
-                e = I.ub[t * NU + a] - S.uref[a];
-            }
-            S.Cd[lane] = cd;
-            S.c[lane] = cd * e;
-        }
         const bool dyn = (t < n - 1);
-        if (dyn) {
-            const T* Ft = Fsrc + (size_t)t * NF;
-            for (int e = lane; e < NF; e += 32) S.F[e] = Ft[e];
-        }
-        __syncwarp();
-        if (dyn) {
-            // W = V F (column-major)
-            for (int e = lane; e < NF; e += 32) {
-                const int j = e / NX, i = e - j * NX;
-                T s = T(0);
-#pragma unroll
-                for (int k = 0; k < NX; ++k) s += S.V[i * NX + k] * S.F[j * NX + k];
-                S.W[e] = s;
+        if (o.replay) {
+            const T* rec = P.tape + ((size_t)I.b * P.N + t) * TAPE_STRIDE;
+            for (int e = lane; e < TAPE_MASK; e += 32) {
+                const T val = rec[e];
+                if (e < TAPE_K) S.F[e] = val;
+                else if (e < TAPE_L) S.K[e - TAPE_K] = val;
+                else S.L[e - TAPE_L] = val;
+            }
+            if (lane == 0) S.mask = (int)rec[TAPE_MASK];
+            __syncwarp();
+        } else {
+            const T* Qt = Qrow(P, I, t);
+            if (lane < NZ) {
+                T cd, e;
+                if (lane < NX) {
+                    cd = Qt[lane];
+                    e = I.xb[t * NX + lane] - I.xrefb[t * NX + lane];
+                    if (o.use_lo) e += I.xlo[t * NX + lane];
+                } else {
+                    const int a = lane - NX;
+                    cd = S.R[a];
+                    e = I.ub[t * NU + a] - S.uref[a];
+                }
+                S.Cd[lane] = cd;
+                S.c[lane] = cd * e;
+            }
+            if (dyn) {
+                const T* Ft = I.F + (size_t)t * NF;
+                for (int e = lane; e < NF; e += 32) S.F[e] = Ft[e];
             }
             __syncwarp();
-            // Q = C + F' W (upper triangle, mirrored), q = c + F' v
-            for (int p = lane; p < NTRI_Q + NZ; p += 32) {
-                if (p < NTRI_Q) {
-                    const int ab = triQ[p], a = ab >> 8, bb = ab & 0xff;
-                    T s = (a == bb) ? S.Cd[a] : T(0);
+            if (dyn) {
+                // W = V F (column-major)
+                for (int e = lane; e < NF; e += 32) {
+                    const int j = e / NX, i = e - j * NX;
+                    T s = T(0);
 #pragma unroll
-                    for (int k = 0; k < NX; ++k) s += S.F[a * NX + k] * S.W[bb * NX + k];
-                    S.Qm[a * NZ + bb] = s;
-                    S.Qm[bb * NZ + a] = s;
+                    for (int k = 0; k < NX; ++k) s += S.V[i * NX + k] * S.F[j * NX + k];
+                    S.W[e] = s;
+                }
+                __syncwarp();
+                // Q = C + F' W (upper triangle, mirrored), q = c + F' v
+                for (int p = lane; p < NTRI_Q + NZ; p += 32) {
+                    if (p < NTRI_Q) {
+                        const int ab = triQ[p], a = ab >> 8, bb = ab & 0xff;
+                        T s = (a == bb) ? S.Cd[a] : T(0);
+#pragma unroll
+                        for (int k = 0; k < NX; ++k) s += S.F[a * NX + k] * S.W[bb * NX + k];
+                        S.Qm[a * NZ + bb] = s;
+                        S.Qm[bb * NZ + a] = s;
+                    } else {
+                        const int a = p - NTRI_Q;
+                        T s = S.c[a];
+#pragma unroll
+                        for (int k = 0; k < NX; ++k) s += S.F[a * NX + k] * S.v[k];
+                        S.q[a] = s;
+                    }
+                }
+            } else {
+                for (int e = lane; e < NZ * NZ; e += 32) {
+                    const int a = e / NZ, bb = e - a * NZ;
+                    S.Qm[e] = (a == bb) ? S.Cd[a] : T(0);
+                }
+                if (lane < NZ) S.q[lane] = S.c[lane];
+            }
+            __syncwarp();
+            if (lane == 0) {
+                T H[4][4], g[4], lo[4], hi[4], d[4], L[10];
+                int mask = 0;
+#pragma unroll
+                for (int a = 0; a < 4; ++a) {
+#pragma unroll
+                    for (int bb = 0; bb < 4; ++bb) H[a][bb] = S.Qm[(NX + a) * NZ + NX + bb];
+                    g[a] = S.q[NX + a];
+                    const T ub = I.ub[t * NU + a];
+                    lo[a] = S.ulo[a] - ub;
+                    hi[a] = S.uhi[a] - ub;
+                }
+                const bool ok = box_qp(H, g, lo, hi, d, L, mask);
+#pragma unroll
+                for (int a = 0; a < 4; ++a) S.k[a] = d[a];
+#pragma unroll
+                for (int i = 0; i < 10; ++i) S.L[i] = L[i];
+                S.mask = mask;
+                S.ok = ok ? 1 : 0;
+            }
+            __syncwarp();
+            if (!S.ok) return false;
+            const int mask = S.mask;
+            // K_t columns
+            if (lane < NX) {
+                T rhs[4], y[4];
+#pragma unroll
+                for (int a = 0; a < 4; ++a) rhs[a] = ((mask >> a) & 1) ? S.Qm[(NX + a) * NZ + lane] : T(0);
+                chol_solve4(S.L, rhs, y);
+#pragma unroll
+                for (int a = 0; a < 4; ++a) S.K[a * NX + lane] = ((mask >> a) & 1) ? -y[a] : T(0);
+            }
+            __syncwarp();
+            // V_t, v_t
+            for (int p = lane; p < NTRI_V + NX; p += 32) {
+                if (p < NTRI_V) {
+                    const int ij = triV[p], i = ij >> 8, j = ij & 0xff;
+                    T s = S.Qm[i * NZ + j];
+#pragma unroll
+                    for (int a = 0; a < NU; ++a) s += S.Qm[i * NZ + NX + a] * S.K[a * NX + j];
+                    S.V[i * NX + j] = s;
+                    S.V[j * NX + i] = s;
                 } else {
-                    const int a = p - NTRI_Q;
-                    T s = S.c[a];
+                    const int i = p - NTRI_V;
+                    T s = S.q[i];
 #pragma unroll
-                    for (int k = 0; k < NX; ++k) s += S.F[a * NX + k] * S.v[k];
-                    S.q[a] = s;
+                    for (int a = 0; a < NU; ++a) s += S.Qm[i * NZ + NX + a] * S.k[a];
+                    S.v[i] = s;
                 }
             }
-        } else {
-            for (int e = lane; e < NZ * NZ; e += 32) {
-                const int a = e / NZ, bb = e - a * NZ;
-                S.Qm[e] = (a == bb) ? S.Cd[a] : T(0);
-            }
-            if (lane < NZ) S.q[lane] = S.c[lane];
-        }
-        __syncwarp();
-        if (lane == 0) {
-            T H[4][4], g[4], lo[4], hi[4], d[4], L[10];
-            int mask = 0;
-#pragma unroll
-            for (int a = 0; a < 4; ++a) {
-#pragma unroll
-                for (int bb = 0; bb < 4; ++bb) H[a][bb] = S.Qm[(NX + a) * NZ + NX + bb];
-                g[a] = S.q[NX + a];
-                const T ub = I.ub[t * NU + a];
-                lo[a] = S.ulo[a] - ub;
-                hi[a] = S.uhi[a] - ub;
-            }
-            const bool ok = box_qp(H, g, lo, hi, d, L, mask);
-#pragma unroll
-            for (int a = 0; a < 4; ++a) S.k[a] = d[a];
-#pragma unroll
-            for (int i = 0; i < 10; ++i) S.L[i] = L[i];
-            S.mask = mask;
-            S.ok = ok ? 1 : 0;
-        }
-        __syncwarp();
-        if (!S.ok) return false;
-        const int mask = S.mask;
-        // K_t columns
-        if (lane < NX) {
-            T rhs[4], y[4];
-#pragma unroll
-            for (int a = 0; a < 4; ++a) rhs[a] = ((mask >> a) & 1) ? S.Qm[(NX + a) * NZ + lane] : T(0);
-            chol_solve4(S.L, rhs, y);
-#pragma unroll
-            for (int a = 0; a < 4; ++a) S.K[a * NX + lane] = ((mask >> a) & 1) ? -y[a] : T(0);
-        }
-        __syncwarp();
-        // V_t, v_t
-        for (int p = lane; p < NTRI_V + NX; p += 32) {
-            if (p < NTRI_V) {
-                const int ij = triV[p], i = ij >> 8, j = ij & 0xff;
-                T s = S.Qm[i * NZ + j];
-#pragma unroll
-                for (int a = 0; a < NU; ++a) s += S.Qm[i * NZ + NX + a] * S.K[a * NX + j];
-                S.V[i * NX + j] = s;
-                S.V[j * NX + i] = s;
-            } else {
-                const int i = p - NTRI_V;
-                T s = S.q[i];
-#pragma unroll
-                for (int a = 0; a < NU; ++a) s += S.Qm[i * NZ + NX + a] * S.k[a];
-                S.v[i] = s;
+            // gains to the slot scratch (and tape)
+            T* kr = I.Kr + (size_t)t * KREC;
+            for (int e = lane; e < KREC; e += 32) kr[e] = (e < NU * NX) ? S.K[e] : S.k[e - NU * NX];
+            if (o.tape) {
+                T* rec = o.tape + ((size_t)I.b * P.N + t) * TAPE_STRIDE;
+                for (int e = lane; e < TAPE_STRIDE; e += 32) {
+                    T val;
+                    if (e < TAPE_K) val = dyn ? S.F[e] : T(0);
+                    else if (e < TAPE_L) val = S.K[e - TAPE_K];
+                    else if (e < TAPE_MASK) val = S.L[e - TAPE_L];
+                    else if (e == TAPE_MASK) val = T(mask);
+                    else val = T(0);
+                    rec[e] = val;
+                }
             }
         }
-        // gains to the slot scratch (and tape)
-        T* kr = I.Kr + (size_t)t * KREC;
-        for (int e = lane; e < KREC; e += 32) kr[e] = (e < NU * NX) ? S.K[e] : S.k[e - NU * NX];
-        if (tape) {
-            T* rec = tape + ((size_t)I.b * P.N + t) * TAPE_STRIDE;
-            for (int e = lane; e < TAPE_STRIDE; e += 32) {
-                T val;
-                if (e < TAPE_K) val = dyn ? S.F[e] : T(0);
-                else if (e < TAPE_L) val = S.K[e - TAPE_K];
-                else if (e < TAPE_MASK) val = S.L[e - TAPE_L];
-                else if (e == TAPE_MASK) val = T(mask);
-                else val = T(0);
-                rec[e] = val;
-            }
-        }
-        if (adj) {
-            // adjoint backward step on this stage's factorization:
-            //   qh = g_t + F_t' vh_{t+1};  kh = -(Q_uu,ff)^-1 qh_u,f;  vh_t = qh_x + K_t' qh_u
+        if (o.adj) {
+            const AdjArgs<T>* adj = o.adj;
             __syncwarp();
             if (lane < NZ) {
                 T g;
@@ -694,6 +712,7 @@ __device__ bool riccati(const Params<T>& P, const Inst<T>& I, WarpSmem<T>& S, in
                 S.qh[lane] = g;
             }
             __syncwarp();
+            const int mask = S.mask;
             if (lane < NX) {
                 T s = S.qh[lane];
 #pragma unroll

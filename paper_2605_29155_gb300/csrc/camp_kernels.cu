@@ -1,22 +1,42 @@
-// camp_kernels.cu -- kernels and launch sequences of the batched MPC layer.
+// camp_kernels.cu -- the kernel and launch sequences of the batched MPC layer.
+//
+// One kernel, k_mpc, runs every phase of the method through a per-instance
+// phase machine; each phase has exactly one call site, so every launch form
+// executes the same machine code for it and gives bit-identical results.
 //
 // Forward (Sec. IV, Algorithm 2's inner loop):
-//   persistent form: one launch; each warp pulls instances from an atomic work
+//   persistent form (one launch): each warp pulls instances from an atomic work
 //     queue (longest horizon first when horizons differ) and runs the whole
-//     iLQR solve of that instance -- rollout, then per iteration linearization,
+//     solve of that instance -- rollout, then per iteration linearization,
 //     Riccati + box QP, line search, convergence test -- and the final
 //     factorization at the returned iterate, with no host round trip.
 //   plain form: Sec. IV's structure, three launches per iteration
 //     (rollout + linearization, Riccati backward pass with bounds, forward
-//     pass + line search) over all instances, with per-instance convergence
-//     masks in status[]; it shares every device function with the persistent
-//     form and gives bit-identical results.
+//     pass + line search) over all instances, the per-instance convergence
+//     mask kept in status[].
 // Backward (Sec. IV implicit differentiation): one persistent launch of the
-//   adjoint LQR sweep, from the tape or with the linearization recomputed.
+//   adjoint LQR, replaying the tape or re-linearizing and re-factoring.
 #include "camp_device.cuh"
 #include "camp_internal.h"
 
 namespace camp {
+
+enum Phase {
+    PH_INIT = 0,    // A1 rollout
+    PH_LIN = 1,     // A2 linearization (iteration)
+    PH_RIC = 2,     // A3 Riccati + box QP (iteration)
+    PH_LS = 3,      // A4 line search + A5 convergence
+    PH_FLIN = 4,    // A6 linearization at the returned iterate
+    PH_FRIC = 5,    // A6 factorization -> tape
+    PH_BLIN = 6,    // backward, recompute: linearization at x*
+    PH_BRIC = 7,    // backward, recompute: factorization + adjoint backward sweep
+    PH_BTAPE = 8,   // backward, store-all: adjoint backward sweep from the tape
+    PH_BFWD = 9,    // A8 adjoint forward sweep + gradient assembly
+    PH_BZERO = 10,  // backward of a failed instance: zero gradients
+    PH_END = 11,    // write the forward's per-instance results
+    PH_DONE = 12
+};
+constexpr int MODE_FWD = -1, MODE_BWD = -2;
 
 __device__ void init_tables(int* triQ, int* triV) {
     for (int p = threadIdx.x; p < NTRI_Q; p += blockDim.x) {
@@ -31,58 +51,133 @@ __device__ void init_tables(int* triQ, int* triV) {
     }
 }
 
+__device__ __forceinline__ bool finished_ok(int st) {
+    return st == ST_CONVERGED || st == ST_STALLED || st == ST_MAX_ITER;
+}
+
+// Whether a plain-form launch of phase `ph` applies to an instance in state `st`.
+__device__ __forceinline__ bool plain_applies(int ph, int st) {
+    if (ph == PH_INIT) return true;
+    if (ph == PH_LIN || ph == PH_RIC || ph == PH_LS) return st == ST_RUNNING;
+    return finished_ok(st);
+}
+
 template <typename T>
-__device__ void solve_one(const Params<T>& P, int b, int slot, WarpSmem<T>& S, int lane,
-                          const int* triQ, const int* triV) {
-    const Inst<T> I = make_inst(P, b, slot);
-    load_instance(P, I, S, lane);
-    T J = initial_rollout(P, I, S, lane);
-    int status = ST_MAX_ITER, iters = 0;
-    if (!finiteT(J)) {
-        status = ST_NONFINITE;
-    } else {
-        for (int it = 0; it < P.max_iter; ++it) {
-            iters = it + 1;
-            linearize(P, I, I.F, lane);
-            if (!riccati(P, I, S, lane, triQ, triV, I.F, (T*)nullptr, (const AdjArgs<T>*)nullptr)) {
-                status = ST_NONPD;
-                break;
-            }
-            T du = T(0);
-            if (line_search(P, I, S, lane, J, du)) { status = ST_STALLED; break; }
-            if (du < P.tol) { status = ST_CONVERGED; break; }
-        }
-        if (P.store_all && status != ST_NONPD) {
-            linearize(P, I, I.F, lane);
-            if (!riccati(P, I, S, lane, triQ, triV, I.F, P.tape, (const AdjArgs<T>*)nullptr)) status = ST_NONPD;
-        }
-    }
-    if (lane == 0) { P.cost[b] = J; P.iters[b] = iters; P.status[b] = status; }
+__device__ void zero_grads(const Params<T>& P, const AdjArgs<T>& A, int b, int lane) {
+    for (int e = lane; e < P.Nq * NX; e += 32) A.dQ[(size_t)b * P.Nq * NX + e] = T(0);
+    for (int e = lane; e < P.N * NX; e += 32) A.dxref[(size_t)b * P.N * NX + e] = T(0);
+    if (lane < NX) A.dx0[(size_t)b * NX + lane] = T(0);
     __syncwarp();
 }
 
+// mode >= 0: plain form, run phase `mode` once for instance = global warp index.
+// mode == MODE_FWD / MODE_BWD: persistent forward / backward over the work queue.
+// `last`: the plain line-search launch of the final iteration.
 template <typename T>
-__device__ __forceinline__ WarpSmem<T>& warp_smem(unsigned char* raw) {
-    return reinterpret_cast<WarpSmem<T>*>(raw)[threadIdx.x >> 5];
-}
-
-// ---------------------------------------------------------------- forward ---
-template <typename T>
-__global__ void __launch_bounds__(256) k_fused(Params<T> P) {
+__global__ void __launch_bounds__(256, 3) k_mpc(Params<T> P, AdjArgs<T> A, int mode, int last) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int triQ[NTRI_Q], triV[NTRI_V];
     init_tables(triQ, triV);
     __syncthreads();
-    WarpSmem<T>& S = warp_smem<T>(smem_raw);
+    WarpSmem<T>& S = reinterpret_cast<WarpSmem<T>*>(smem_raw)[threadIdx.x >> 5];
     const int lane = threadIdx.x & 31;
-    const int slot = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int wslot = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const bool plain = mode >= 0;
+    bool first = true;
     for (;;) {
-        int idx = 0;
-        if (lane == 0) idx = atomicAdd(P.queue, 1);
-        idx = __shfl_sync(FULL, idx, 0);
-        if (idx >= P.B) break;
-        const int b = P.order ? P.order[idx] : idx;
-        solve_one(P, b, slot, S, lane, triQ, triV);
+        int b;
+        if (plain) {
+            if (!first) break;
+            first = false;
+            b = wslot;
+            if (b >= P.B) break;
+        } else {
+            int idx = 0;
+            if (lane == 0) idx = atomicAdd(P.queue + (mode == MODE_BWD ? 1 : 0), 1);
+            idx = __shfl_sync(FULL, idx, 0);
+            if (idx >= P.B) break;
+            b = P.order ? P.order[idx] : idx;
+        }
+        const Inst<T> I = make_inst(P, b, plain ? b : wslot);
+        int ph, status, iters;
+        T J;
+        if (plain) {
+            ph = mode;
+            status = ph == PH_INIT ? ST_RUNNING : P.status[b];
+            iters = ph == PH_INIT ? 0 : P.iters[b];
+            J = ph == PH_INIT ? T(0) : P.cost[b];
+            if (!plain_applies(ph, status)) continue;
+        } else if (mode == MODE_FWD) {
+            ph = PH_INIT;
+            status = ST_RUNNING;
+            iters = 0;
+            J = T(0);
+        } else {
+            status = P.status[b];
+            iters = 0;
+            J = T(0);
+            ph = finished_ok(status) ? (A.recompute ? PH_BLIN : PH_BTAPE) : PH_BZERO;
+        }
+        load_instance(P, I, S, lane);
+        const int after_fwd = P.store_all ? PH_FLIN : PH_END;
+        while (ph != PH_DONE) {
+            int next = PH_DONE;
+            if (ph == PH_INIT) {
+                J = initial_rollout(P, I, S, lane);
+                if (!finiteT(J)) { status = ST_NONFINITE; next = PH_END; }
+                else if (P.max_iter > 0) next = PH_LIN;
+                else { status = ST_MAX_ITER; next = after_fwd; }
+            } else if (ph == PH_LIN || ph == PH_FLIN || ph == PH_BLIN) {
+                if (ph == PH_LIN) ++iters;
+                linearize(P, I, I.F, lane);
+                next = ph + 1;
+            } else if (ph == PH_RIC || ph == PH_FRIC || ph == PH_BRIC || ph == PH_BTAPE) {
+                RicOpts<T> o;
+                o.tape = ph == PH_FRIC ? P.tape : (T*)nullptr;
+                o.adj = (ph == PH_BRIC || ph == PH_BTAPE) ? &A : (const AdjArgs<T>*)nullptr;
+                o.replay = ph == PH_BTAPE;
+                o.use_lo = ph == PH_RIC;
+                const bool ok = riccati(P, I, S, lane, triQ, triV, o);
+                if (ph == PH_RIC) {
+                    if (ok) next = PH_LS;
+                    else { status = ST_NONPD; next = PH_END; }
+                } else if (ph == PH_FRIC) {
+                    if (!ok) status = ST_NONPD;
+                    next = PH_END;
+                } else {
+                    next = ok ? PH_BFWD : PH_BZERO;
+                }
+            } else if (ph == PH_LS) {
+                T du = T(0);
+                const int r = line_search(P, I, S, lane, J, du);
+                if (r) { status = ST_STALLED; next = after_fwd; }
+                else if (du < P.tol) { status = ST_CONVERGED; next = after_fwd; }
+                else if (plain ? (last != 0) : (iters >= P.max_iter)) { status = ST_MAX_ITER; next = after_fwd; }
+                else next = PH_LIN;
+            } else if (ph == PH_BFWD) {
+                const T* tb = A.recompute ? (const T*)nullptr : P.tape + (size_t)I.b * P.N * TAPE_STRIDE;
+                const T* Fs = A.recompute ? (const T*)I.F : tb + TAPE_F;
+                const T* Ks = A.recompute ? (const T*)I.Kr : tb + TAPE_K;
+                const size_t fs = A.recompute ? (size_t)NF : (size_t)TAPE_STRIDE;
+                const size_t ks = A.recompute ? (size_t)KREC : (size_t)TAPE_STRIDE;
+                adjoint_forward(P, I, S, lane, Fs, fs, Ks, ks, A);
+                next = PH_DONE;
+            } else if (ph == PH_BZERO) {
+                zero_grads(P, A, b, lane);
+                next = PH_DONE;
+            } else if (ph == PH_END) {
+                next = PH_DONE;
+            }
+            if (plain) break;
+            if (next == PH_DONE && mode == MODE_FWD) break;
+            ph = next;
+        }
+        if (mode != MODE_BWD && lane == 0) {
+            P.cost[b] = J;
+            P.iters[b] = iters;
+            P.status[b] = status;
+        }
+        __syncwarp();
     }
 }
 
@@ -109,188 +204,18 @@ __global__ void k_lpt_order(const int* horizon, int B, int N, int* order) {
     }
 }
 
-// plain form: one warp per instance, instance index = slot
-template <typename T>
-__global__ void __launch_bounds__(256) k_plain_init(Params<T> P) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    WarpSmem<T>& S = warp_smem<T>(smem_raw);
-    const int lane = threadIdx.x & 31;
-    const int b = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (b >= P.B) return;
-    const Inst<T> I = make_inst(P, b, b);
-    load_instance(P, I, S, lane);
-    const T J = initial_rollout(P, I, S, lane);
-    if (lane == 0) {
-        P.cost[b] = J;
-        P.iters[b] = 0;
-        P.status[b] = finiteT(J) ? (P.max_iter > 0 ? ST_RUNNING : ST_MAX_ITER) : ST_NONFINITE;
-    }
-}
-
-__device__ __forceinline__ bool plain_active(int st, int final_pass) {
-    return final_pass ? (st == ST_CONVERGED || st == ST_STALLED || st == ST_MAX_ITER) : (st == ST_RUNNING);
-}
-
-template <typename T>
-__global__ void __launch_bounds__(256) k_plain_lin(Params<T> P, int final_pass) {
-    const int lane = threadIdx.x & 31;
-    const int b = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (b >= P.B) return;
-    const int st = P.status[b];
-    if (!plain_active(st, final_pass)) return;
-    const Inst<T> I = make_inst(P, b, b);
-    if (!final_pass && lane == 0) P.iters[b] += 1;
-    linearize(P, I, I.F, lane);
-}
-
-template <typename T>
-__global__ void __launch_bounds__(256) k_plain_ric(Params<T> P, int final_pass) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ int triQ[NTRI_Q], triV[NTRI_V];
-    init_tables(triQ, triV);
-    __syncthreads();
-    WarpSmem<T>& S = warp_smem<T>(smem_raw);
-    const int lane = threadIdx.x & 31;
-    const int b = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (b >= P.B) return;
-    const int st = P.status[b];
-    if (!plain_active(st, final_pass)) return;
-    const Inst<T> I = make_inst(P, b, b);
-    load_instance(P, I, S, lane);
-    const bool ok = riccati(P, I, S, lane, triQ, triV, I.F, final_pass ? P.tape : (T*)nullptr,
-                            (const AdjArgs<T>*)nullptr);
-    if (!ok && lane == 0) P.status[b] = ST_NONPD;
-}
-
-template <typename T>
-__global__ void __launch_bounds__(256) k_plain_ls(Params<T> P, int last) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    WarpSmem<T>& S = warp_smem<T>(smem_raw);
-    const int lane = threadIdx.x & 31;
-    const int b = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (b >= P.B) return;
-    if (P.status[b] != ST_RUNNING) return;
-    const Inst<T> I = make_inst(P, b, b);
-    load_instance(P, I, S, lane);
-    T J = P.cost[b];
-    T du = T(0);
-    const int r = line_search(P, I, S, lane, J, du);
-    if (lane == 0) {
-        int st = ST_RUNNING;
-        if (r) st = ST_STALLED;
-        else if (du < P.tol) st = ST_CONVERGED;
-        else if (last) st = ST_MAX_ITER;
-        P.cost[b] = J;
-        P.status[b] = st;
-    }
-}
-
-// --------------------------------------------------------------- backward ---
-template <typename T>
-__device__ void adjoint_backward_tape(const Params<T>& P, const Inst<T>& I, WarpSmem<T>& S, int lane,
-                                      const AdjArgs<T>& A) {
-    const int n = I.n;
-    if (lane < NX) S.vh[lane] = T(0);
-    __syncwarp();
-    for (int t = n - 1; t >= 0; --t) {
-        const T* rec = P.tape + ((size_t)I.b * P.N + t) * TAPE_STRIDE;
-        if (lane < NZ) {
-            T g;
-            if (lane < NX) g = A.gx ? A.gx[((size_t)I.b * P.N + t) * NX + lane] : T(0);
-            else g = A.gu[((size_t)I.b * P.N + t) * NU + lane - NX];
-            if (t < n - 1) {
-#pragma unroll
-                for (int k = 0; k < NX; ++k) g += rec[TAPE_F + lane * NX + k] * S.vh[k];
-            }
-            S.qh[lane] = g;
-        }
-        __syncwarp();
-        if (lane < NX) {
-            T s = S.qh[lane];
-#pragma unroll
-            for (int a = 0; a < NU; ++a) s += rec[TAPE_K + a * NX + lane] * S.qh[NX + a];
-            S.vh[lane] = s;
-        } else if (lane == 16) {
-            const int mask = (int)rec[TAPE_MASK];
-            T L[10], rhs[4], y[4];
-#pragma unroll
-            for (int i = 0; i < 10; ++i) L[i] = rec[TAPE_L + i];
-#pragma unroll
-            for (int a = 0; a < 4; ++a) rhs[a] = ((mask >> a) & 1) ? S.qh[NX + a] : T(0);
-            chol_solve4(L, rhs, y);
-#pragma unroll
-            for (int a = 0; a < 4; ++a) I.kh[t * NU + a] = ((mask >> a) & 1) ? -y[a] : T(0);
-        }
-        __syncwarp();
-    }
-}
-
-template <typename T>
-__device__ void zero_grads(const Params<T>& P, const AdjArgs<T>& A, int b, int lane) {
-    for (int e = lane; e < P.Nq * NX; e += 32) A.dQ[(size_t)b * P.Nq * NX + e] = T(0);
-    for (int e = lane; e < P.N * NX; e += 32) A.dxref[(size_t)b * P.N * NX + e] = T(0);
-    if (lane < NX) A.dx0[(size_t)b * NX + lane] = T(0);
-}
-
-template <typename T>
-__global__ void __launch_bounds__(256) k_adjoint(Params<T> P, AdjArgs<T> A) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ int triQ[NTRI_Q], triV[NTRI_V];
-    init_tables(triQ, triV);
-    __syncthreads();
-    WarpSmem<T>& S = warp_smem<T>(smem_raw);
-    const int lane = threadIdx.x & 31;
-    const int slot = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    for (;;) {
-        int idx = 0;
-        if (lane == 0) idx = atomicAdd(P.queue + 1, 1);
-        idx = __shfl_sync(FULL, idx, 0);
-        if (idx >= P.B) break;
-        const int b = P.order ? P.order[idx] : idx;
-        const int st = P.status[b];
-        if (!(st == ST_CONVERGED || st == ST_STALLED || st == ST_MAX_ITER)) {
-            zero_grads(P, A, b, lane);
-            __syncwarp();
-            continue;
-        }
-        const Inst<T> I = make_inst(P, b, slot);
-        load_instance(P, I, S, lane);
-        if (A.recompute) {
-            linearize(P, I, I.F, lane);
-            if (!riccati(P, I, S, lane, triQ, triV, I.F, (T*)nullptr, &A)) {
-                zero_grads(P, A, b, lane);
-                __syncwarp();
-                continue;
-            }
-            adjoint_forward(P, I, S, lane, I.F, (size_t)NF, I.Kr, (size_t)KREC, A);
-        } else {
-            adjoint_backward_tape(P, I, S, lane, A);
-            const T* tb = P.tape + (size_t)I.b * P.N * TAPE_STRIDE;
-            adjoint_forward(P, I, S, lane, tb + TAPE_F, (size_t)TAPE_STRIDE, tb + TAPE_K, (size_t)TAPE_STRIDE, A);
-        }
-    }
-}
-
 // ------------------------------------------------------------ host side ----
 template <typename T> size_t warp_smem_bytes() { return sizeof(WarpSmem<T>); }
 
 template <typename T> cudaError_t prepare_kernels() {
-    const int maxb = (int)(8 * sizeof(WarpSmem<T>));
-    cudaError_t e;
-    if ((e = cudaFuncSetAttribute(k_fused<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxb))) return e;
-    if ((e = cudaFuncSetAttribute(k_plain_init<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxb))) return e;
-    if ((e = cudaFuncSetAttribute(k_plain_ric<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxb))) return e;
-    if ((e = cudaFuncSetAttribute(k_plain_ls<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxb))) return e;
-    if ((e = cudaFuncSetAttribute(k_adjoint<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxb))) return e;
-    return cudaSuccess;
+    return cudaFuncSetAttribute(k_mpc<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)(8 * sizeof(WarpSmem<T>)));
 }
 
-template <typename T> int persistent_blocks_per_sm(int ipb, int which) {
+template <typename T> int persistent_blocks_per_sm(int ipb, int /*which*/) {
     int nb = 0;
     const size_t smem = (size_t)ipb * sizeof(WarpSmem<T>);
-    cudaError_t e = which == 0
-        ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_fused<T>, 32 * ipb, smem)
-        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_adjoint<T>, 32 * ipb, smem);
+    const cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_mpc<T>, 32 * ipb, smem);
     return e == cudaSuccess ? nb : 0;
 }
 
@@ -298,30 +223,30 @@ template <typename T>
 cudaError_t launch_forward(const Params<T>& Pin, int exec_mode, int ipb, int grid, int* order_ws,
                            cudaStream_t st) {
     Params<T> P = Pin;
+    AdjArgs<T> A{};
     const size_t smem = (size_t)ipb * sizeof(WarpSmem<T>);
     const int threads = 32 * ipb;
     cudaError_t e;
+    P.order = nullptr;
     if (exec_mode == 0) {
-        if ((e = cudaMemsetAsync(P.queue, 0, 2 * sizeof(int), st))) return e;
-        P.order = nullptr;
+        if ((e = cudaMemsetAsync(P.queue, 0, sizeof(int), st))) return e;
         if (P.horizon) {
             k_lpt_order<<<1, 1024, 0, st>>>(P.horizon, P.B, P.N, order_ws);
             P.order = order_ws;
         }
-        k_fused<T><<<grid, threads, smem, st>>>(P);
+        k_mpc<T><<<grid, threads, smem, st>>>(P, A, MODE_FWD, 0);
         return cudaGetLastError();
     }
-    P.order = nullptr;
     const int blocks = (P.B + ipb - 1) / ipb;
-    k_plain_init<T><<<blocks, threads, smem, st>>>(P);
+    k_mpc<T><<<blocks, threads, smem, st>>>(P, A, PH_INIT, 0);
     for (int it = 0; it < P.max_iter; ++it) {
-        k_plain_lin<T><<<blocks, threads, 0, st>>>(P, 0);
-        k_plain_ric<T><<<blocks, threads, smem, st>>>(P, 0);
-        k_plain_ls<T><<<blocks, threads, smem, st>>>(P, it == P.max_iter - 1);
+        k_mpc<T><<<blocks, threads, smem, st>>>(P, A, PH_LIN, 0);
+        k_mpc<T><<<blocks, threads, smem, st>>>(P, A, PH_RIC, 0);
+        k_mpc<T><<<blocks, threads, smem, st>>>(P, A, PH_LS, it == P.max_iter - 1);
     }
     if (P.store_all) {
-        k_plain_lin<T><<<blocks, threads, 0, st>>>(P, 1);
-        k_plain_ric<T><<<blocks, threads, smem, st>>>(P, 1);
+        k_mpc<T><<<blocks, threads, smem, st>>>(P, A, PH_FLIN, 0);
+        k_mpc<T><<<blocks, threads, smem, st>>>(P, A, PH_FRIC, 0);
     }
     return cudaGetLastError();
 }
@@ -338,7 +263,7 @@ cudaError_t launch_backward(const Params<T>& Pin, const AdjArgs<T>& A, int ipb, 
         k_lpt_order<<<1, 1024, 0, st>>>(P.horizon, P.B, P.N, order_ws);
         P.order = order_ws;
     }
-    k_adjoint<T><<<grid, 32 * ipb, smem, st>>>(P, A);
+    k_mpc<T><<<grid, 32 * ipb, smem, st>>>(P, A, MODE_BWD, 0);
     return cudaGetLastError();
 }
 

@@ -173,7 +173,12 @@ class DiffMPC:
 
 class DiffMPCFunction(torch.autograd.Function):
     """u*, x* = MPC(x0, Q, x_ref; R, u_ref, u_lo, u_hi) with gradients w.r.t.
-    x0, Q and x_ref from the library's adjoint solve."""
+    x0, Q and x_ref from the library's adjoint solve.
+
+    Every tensor the backward needs goes through ctx.save_for_backward, never
+    a plain ctx attribute: an output kept on ctx would form a reference cycle
+    (output -> grad_fn -> ctx -> output) that holds device memory until the
+    garbage collector happens to run."""
 
     @staticmethod
     def forward(ctx, solver: DiffMPC, x0, Q, x_ref, R, u_ref, u_lo, u_hi, horizon=None):
@@ -181,13 +186,25 @@ class DiffMPCFunction(torch.autograd.Function):
                     R=R.detach().contiguous(), u_ref=u_ref.detach().contiguous(), u_lo=u_lo.detach().contiguous(),
                     u_hi=u_hi.detach().contiguous(), horizon=horizon)
         s = solver.solve(p)
-        ctx.solver, ctx.problem, ctx.solution = solver, p, s
+        ctx.solver = solver
+        ctx.has_horizon = horizon is not None
+        ctx.has_tape = s.tape is not None
+        none = torch.empty(0, device=x0.device)
+        ctx.save_for_backward(p.x0, p.Q, p.x_ref, p.R, p.u_ref, p.u_lo, p.u_hi,
+                              horizon if horizon is not None else none, s.u, s.x, s.cost, s.iters, s.status,
+                              s.tape if s.tape is not None else none)
         ctx.mark_non_differentiable(s.cost, s.iters, s.status)
         return s.u, s.x, s.cost, s.iters, s.status
 
     @staticmethod
     def backward(ctx, grad_u, grad_x, *_):
-        dQ, dxr, dx0 = ctx.solver.backward(ctx.problem, ctx.solution, grad_u, grad_x)
+        x0, Q, x_ref, R, u_ref, u_lo, u_hi, hz, u, x, cost, iters, status, tape = ctx.saved_tensors
+        p = Problem(x0=x0, Q=Q, x_ref=x_ref, R=R, u_ref=u_ref, u_lo=u_lo, u_hi=u_hi,
+                    horizon=hz if ctx.has_horizon else None)
+        s = Solution(u=u, x=x, cost=cost, iters=iters, status=status, tape=tape if ctx.has_tape else None)
+        if grad_u is None:
+            grad_u = torch.zeros_like(u)
+        dQ, dxr, dx0 = ctx.solver.backward(p, s, grad_u, grad_x)
         return None, dx0, dQ, dxr, None, None, None, None, None
 
 

@@ -5,7 +5,10 @@ Tolerances (FP32 path vs FP64 oracle, per instance):
   controls   |u - u_or|_2 / max(|u_or|_2, 1e-6)            <= 1e-4
   cost       |J - J_or| / max(|J_or|, 1e-12)                 <= 1e-5
   gradients  |g - g_or|_2 / max(|g_or|_2, 1e-9) per block   <= 1e-3
-The FP64 path runs the same kernels in double and is held to 1e-9 / 1e-8.
+The FP64 path runs the same kernels in double: with every decision the same
+(early iterations, tol = 0) it agrees to 1e-10; run to convergence, the last
+accepted step (smaller than tol by definition) may go either way, so controls
+agree to about tol.
 """
 from __future__ import annotations
 
@@ -20,7 +23,8 @@ from oracle.model import Quadrotor
 QUAD = Quadrotor(W.DEFAULT_MODEL)
 
 U_TOL32, J_TOL32, G_TOL32 = 1e-4, 1e-5, 1e-3
-U_TOL64, J_TOL64, G_TOL64 = 1e-9, 1e-9, 1e-8
+U_TOL64, J_TOL64, G_TOL64 = 1e-10, 1e-10, 1e-9      # identical decisions (early iterations)
+U_TOL64C, J_TOL64C, G_TOL64C = 1e-6, 1e-9, 1e-5     # to convergence: last step < tol may differ
 # decisions the FP32 path cannot resolve: relative J gaps / gradient margins
 LS_MARGIN32, QP_MARGIN32 = 1e-4, 1e-4
 
@@ -68,8 +72,14 @@ def rel(a, b, floor):
     return float(np.linalg.norm(np.ravel(a) - np.ravel(b)) / max(np.linalg.norm(np.ravel(b)), floor))
 
 
-def compare(gpu, orc, idx, u_tol, j_tol, g_tol, exact_counts=True, skip_degenerate=False):
-    """Per-instance comparison; returns a report dict and a list of failures."""
+def compare(gpu, orc, idx, u_tol, j_tol, g_tol, counts="exact", skip_degenerate=False):
+    """Per-instance comparison; returns a report dict and a list of failures.
+
+    counts: "exact"  status and iteration count identical;
+            "final"  CONVERGED and STALLED (both normal ends) count as equal and
+                     the counts may differ by one: the last accepted step of a
+                     converging solve is below tol and can fall either way;
+            None     not compared."""
     fails, report = [], dict(max_u=0.0, max_J=0.0, max_g=0.0, excluded=0, compared=0)
     for k, i in enumerate(idx):
         pr, so, gr = orc[k]
@@ -77,9 +87,14 @@ def compare(gpu, orc, idx, u_tol, j_tol, g_tol, exact_counts=True, skip_degenera
             report["excluded"] += 1
             continue
         report["compared"] += 1
-        if exact_counts:
-            if int(gpu["status"][i]) != so.status or int(gpu["iters"][i]) != so.iters:
-                fails.append((i, "status/iters", (int(gpu["status"][i]), int(gpu["iters"][i])), (so.status, so.iters)))
+        gs, gi = int(gpu["status"][i]), int(gpu["iters"][i])
+        if counts == "exact" and (gs != so.status or gi != so.iters):
+            fails.append((i, "status/iters", (gs, gi), (so.status, so.iters)))
+            continue
+        if counts == "final":
+            cls = lambda st: 0 if st in (0, 1) else st
+            if cls(gs) != cls(so.status) or abs(gi - so.iters) > 1:
+                fails.append((i, "status/iters", (gs, gi), (so.status, so.iters)))
                 continue
         eu = rel(gpu["u"][i], so.U, 1e-6)
         ex = rel(gpu["x"][i], so.X, 1e-6)

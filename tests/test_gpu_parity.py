@@ -3,8 +3,8 @@ import numpy as np
 import pytest
 
 import workloads as W
-from gpu_support import (G_TOL32, G_TOL64, J_TOL32, J_TOL64, U_TOL32, U_TOL64, cached_problem, compare,
-                         oracle_solve, run_gpu)
+from gpu_support import (G_TOL32, G_TOL64, G_TOL64C, J_TOL32, J_TOL64, J_TOL64C, U_TOL32, U_TOL64, U_TOL64C,
+                         cached_problem, compare, oracle_solve, run_gpu)
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
@@ -27,20 +27,33 @@ def _grads(B, N, seed):
 
 # ------------------------------------------------------- FP64: logic check --
 
+@pytest.mark.parametrize("name,B,N,horizons", [("hover", 8, 10, False), ("track", 37, 20, True),
+                                               ("uneven", 33, 40, False), ("mem", 9, 30, False)])
+def test_fp64_early_iterations_identical_to_oracle(name, B, N, horizons):
+    """Same kernels in double, three iterations with tol = 0: every decision
+    (alpha, free sets, stall) is clear-cut, so values agree to rounding
+    (several warps per block, ragged horizons, shared and per-stage Q)."""
+    prob = cached_problem(name, B, N, 0, horizons)
+    gu, gx = _grads(B, N, 1)
+    gpu = run_gpu(prob, torch.float64, 3, 0.0, gu, gx, N_max=40)
+    idx = list(range(B))
+    orc = oracle_solve(prob, idx, 3, 0.0, gu, gx)
+    report, fails = compare(gpu, orc, idx, U_TOL64, J_TOL64, G_TOL64)
+    print(name, report)
+    assert not fails, fails[:5]
+
+
 @pytest.mark.parametrize("name,B,N,horizons,mi", [("hover", 8, 10, False, 10), ("track", 37, 20, True, 8),
                                                   ("uneven", 33, 40, False, 12), ("mem", 9, 30, False, 8)])
-def test_fp64_forward_backward_match_oracle(name, B, N, horizons, mi):
-    """Same kernels in double: every iterate decision, count and value agrees
-    with the oracle (several warps per block, ragged horizons, shared and
-    per-stage Q)."""
+def test_fp64_to_convergence_matches_oracle(name, B, N, horizons, mi):
     prob = cached_problem(name, B, N, 0, horizons)
     gu, gx = _grads(B, N, 1)
     gpu = run_gpu(prob, torch.float64, mi, 1e-6, gu, gx, N_max=40)
     idx = list(range(B))
     orc = oracle_solve(prob, idx, mi, 1e-6, gu, gx)
-    report, fails = compare(gpu, orc, idx, U_TOL64, J_TOL64, G_TOL64)
+    report, fails = compare(gpu, orc, idx, U_TOL64C, J_TOL64C, G_TOL64C, counts="final")
     print(name, report)
-    assert len(fails) <= max(1, B // 30), fails[:5]
+    assert not fails, fails[:5]
 
 
 # --------------------------------------------------- FP32: the product path --
@@ -53,7 +66,7 @@ def test_fp32_forward_backward_match_oracle(name, B, N, horizons, mi):
     gpu = run_gpu(prob, torch.float32, mi, 1e-6, gu, gx, N_max=40)
     idx = list(range(B))
     orc = oracle_solve(prob, idx, mi, 1e-6, gu, gx)
-    report, fails = compare(gpu, orc, idx, U_TOL32, J_TOL32, G_TOL32, exact_counts=False, skip_degenerate=True)
+    report, fails = compare(gpu, orc, idx, U_TOL32, J_TOL32, G_TOL32, counts=None, skip_degenerate=True)
     print(name, report, fails[:5])
     assert report["compared"] >= 0.7 * B
     assert not fails, fails[:5]
@@ -68,7 +81,7 @@ def test_fp32_full_size_track_sampled():
     gpu = run_gpu(prob, torch.float32, prob["max_iter"], prob["tol"], gu, None, N_max=N, B_max=B)
     idx = list(np.random.default_rng(3).choice(B, 24, replace=False))
     orc = oracle_solve(prob, idx, prob["max_iter"], prob["tol"], gu, None)
-    report, fails = compare(gpu, orc, idx, U_TOL32, J_TOL32, G_TOL32, exact_counts=False, skip_degenerate=True)
+    report, fails = compare(gpu, orc, idx, U_TOL32, J_TOL32, G_TOL32, counts=None, skip_degenerate=True)
     print(report)
     assert not fails, fails[:5]
     # every instance ends in a valid state with finite outputs
@@ -168,9 +181,14 @@ def test_hover_fixed_point_on_gpu():
     gu = np.zeros((B, N, 4))
     gu[:, 0] = 1
     g = run_gpu(prob, torch.float32, 8, 1e-6, gu)
+    # in FP32 m g / 4 is not an exact equilibrium: a sub-micro-newton correction
+    # may be found and taken before the solve stops
     np.testing.assert_allclose(g["u"], W.DEFAULT_MODEL.hover_thrust, rtol=1e-6)
-    assert np.all(g["cost"] < 1e-10) and np.all(g["status"] == 1) and np.all(g["iters"] == 1)
-    np.testing.assert_allclose(g["dQ"], 0, atol=1e-6)
+    assert np.all(g["cost"] < 1e-8) and np.all(np.isin(g["status"], [0, 1])) and np.all(g["iters"] <= 2)
+    np.testing.assert_allclose(g["dQ"], 0, atol=1e-5)
+    g64 = run_gpu(prob, torch.float64, 8, 1e-6, gu)
+    np.testing.assert_allclose(g64["u"], W.DEFAULT_MODEL.hover_thrust, rtol=1e-14)
+    assert np.all(g64["status"] == 1) and np.all(g64["iters"] == 1)
 
 
 # ------------------------------------------------- API, graphs, autograd --
