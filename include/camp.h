@@ -64,7 +64,7 @@ extern "C" {
 
 /* per-instance status written by mpc_solve_fwd */
 #define MPC_ST_CONVERGED  0    /* max_t |u^k_t - u^(k-1)_t|_inf < tol after a step      */
-#define MPC_ST_STALLED    1    /* no alpha lowered the cost: the nominal is returned    */
+#define MPC_ST_STALLED    1    /* no alpha gave a finite cost: the nominal is returned  */
 #define MPC_ST_MAX_ITER   2    /* max_iter iterations executed                          */
 #define MPC_ST_NONFINITE  3    /* an input or the initial cost was not finite           */
 #define MPC_ST_NONPD      4    /* a free block of Q_uu had a non-positive pivot         */

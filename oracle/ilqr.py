@@ -17,11 +17,12 @@ Readings where the paper is silent (each listed in the design notes):
             which differs from Eq. (3)'s objective by the constant
             1/2 (x_ref'Q x_ref + u_ref'R u_ref) per stage.
   R4 line search  every alpha is rolled out; alpha* = argmin J(alpha), ties to
-            the earlier (larger) alpha; accepted only if J(alpha*) < J_nominal,
-            otherwise the solve stops with status STALLED.  J(alpha) - J is
+            the earlier (larger) alpha, and -- as Sec. IV-3 states -- the best
+            candidate becomes the next nominal.  Only when no candidate has a
+            finite cost is the nominal kept (status STALLED).  J(alpha) - J is
             evaluated as the sum of the stage-wise cost changes (cost_change),
-            an exact identity for the quadratic cost that does not lose the
-            decrement to the rounding of J's total.
+            an exact identity for the quadratic cost that does not lose small
+            differences to the rounding of J's total.
   R5 converged    max_t |u^k_t - u^{k-1}_t|_inf < tol after an accepted step;
             at most max_iter iterations; every executed iteration is counted.
   R6 start  U^0 = clamp(u_ref) (or clamp(u_init) when given).
@@ -38,7 +39,7 @@ import numpy as np
 
 from . import boxqp
 
-CONVERGED, STALLED, MAX_ITER, NONFINITE, NONPD = 0, 1, 2, 3, 4
+CONVERGED, STALLED, MAX_ITER, NONFINITE, NONPD = 0, 1, 2, 3, 4   # STALLED: no finite candidate
 ALPHAS = (1.0, 0.5, 0.25, 0.1)
 MATERIAL_DU = 1e-4   # control change [N] below which a decision is immaterial
 
@@ -181,9 +182,10 @@ class Solution:
     status: int
     F: list              # final linearization at (X, U) (A6)
     bp: BackwardResult   # final factorization at (X, U) (A6)
-    ls_margin: float     # smallest relative J gap behind a line-search decision
+    ls_margin: float     # smallest relative gap behind a material alpha decision
     qp_margin: float     # smallest |grad| behind a clamped/free decision
     alpha_hist: list
+    ls_margin_any: float = np.inf   # the same over every alpha decision, material or not
 
 
 def linearize(model, prob: Problem, X, U):
@@ -204,10 +206,10 @@ def solve(model, prob: Problem, max_iter=10, tol=1e-6, alphas=ALPHAS) -> Solutio
     X[:n] = model.rollout(prob.x0, U[:n])
     J = total_cost(prob, X, U)
     status, iters = MAX_ITER, 0
-    ls_margin, qp_margin = np.inf, np.inf
+    ls_margin, qp_margin, ls_margin_any = np.inf, np.inf, np.inf
     hist = []
     if not np.isfinite(J):
-        return Solution(X, U, J, 0, NONFINITE, [], None, ls_margin, qp_margin, hist)
+        return Solution(X, U, J, 0, NONFINITE, [], None, ls_margin, qp_margin, hist, ls_margin_any)
     for it in range(max_iter):
         iters = it + 1
         F = linearize(model, prob, X, U)
@@ -231,12 +233,15 @@ def solve(model, prob: Problem, max_iter=10, tol=1e-6, alphas=ALPHAS) -> Solutio
         # magnitude of the terms the cost changes are summed from.
         Ub = cands[best][2]
         for i, c in enumerate(cands):
-            if i != best and np.isfinite(c[0]) and np.max(np.abs(c[2][:n] - Ub[:n])) > MATERIAL_DU:
+            if i == best or not np.isfinite(c[0]):
+                continue
+            diff = np.max(np.abs(c[2][:n] - Ub[:n]))
+            if diff > 0:
+                ls_margin_any = min(ls_margin_any, abs(c[0] - Js[best]) / scale)
+            if diff > MATERIAL_DU:
                 ls_margin = min(ls_margin, abs(c[0] - Js[best]) / scale)
         du = float(np.max(np.abs(Ub[:n] - U[:n])))
-        if np.isfinite(Js[best]) and du > MATERIAL_DU:
-            ls_margin = min(ls_margin, abs(Js[best]) / scale)
-        if not (Js[best] < 0.0):
+        if not np.isfinite(Js[best]):
             status = STALLED
             hist.append(None)
             break
@@ -248,7 +253,7 @@ def solve(model, prob: Problem, max_iter=10, tol=1e-6, alphas=ALPHAS) -> Solutio
             break
     F = linearize(model, prob, X, U)
     bp = backward_pass(prob, X, U, F)
-    return Solution(X, U, total_cost(prob, X, U), iters, status, F, bp, ls_margin, qp_margin, hist)
+    return Solution(X, U, total_cost(prob, X, U), iters, status, F, bp, ls_margin, qp_margin, hist, ls_margin_any)
 
 
 def solve_batch(model, batch: dict, idx=None, max_iter=None, tol=None):

@@ -739,9 +739,10 @@ __device__ bool riccati(const Params<T>& P, const Inst<T>& I, WarpSmem<T>& S, in
 // nominal, accumulated stage by stage from the differences themselves,
 //   dJ_t = (x_hat - x)' Q (x - x_ref + (x_hat - x)/2) + (u_hat - u)' R (u - u_ref + (u_hat - u)/2),
 // which equals J(alpha) - J exactly for the quadratic cost but does not cancel
-// against J's magnitude; with the hi + lo states it resolves decrements far
-// below the working precision of J.  alpha* = first argmin; the step is taken
-// only if dJ(alpha*) < 0.  Returns 0 (step taken: du, J updated) or 1 (stalled).
+// against J's magnitude; with the hi + lo states it resolves differences far
+// below the working precision of J.  alpha* = first argmin, and the best
+// candidate becomes the next nominal (Sec. IV-3).  Returns 0 (step taken: du,
+// J updated) or 1 (no candidate with a finite cost: nominal kept).
 template <typename T>
 __device__ int line_search(const Params<T>& P, const Inst<T>& I, WarpSmem<T>& S, int lane, T& Jnom, T& du_out) {
     const int n = I.n;
@@ -791,7 +792,7 @@ __device__ int line_search(const Params<T>& P, const Inst<T>& I, WarpSmem<T>& S,
     T Jb = S.Jc[0];
     for (int c = 1; c < P.n_alpha; ++c)
         if (S.Jc[c] < Jb) { Jb = S.Jc[c]; best = c; }
-    if (!(Jb < T(0))) return 1;
+    if (!finiteT(Jb)) return 1;
     const T* cd = I.cand + (size_t)best * P.N_ws * CREC;
     T dmax = T(0);
     for (int e = lane; e < n * CREC; e += 32) {

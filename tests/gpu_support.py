@@ -25,8 +25,10 @@ QUAD = Quadrotor(W.DEFAULT_MODEL)
 U_TOL32, J_TOL32, G_TOL32 = 1e-4, 1e-5, 1e-3
 U_TOL64, J_TOL64, G_TOL64 = 1e-10, 1e-10, 1e-9      # identical decisions (early iterations)
 U_TOL64C, J_TOL64C, G_TOL64C = 1e-6, 1e-9, 1e-5     # to convergence: last step < tol may differ
-# decisions the FP32 path cannot resolve: relative J gaps / gradient margins
-LS_MARGIN32, QP_MARGIN32 = 1e-4, 1e-4
+# decisions the FP32 path cannot resolve: relative cost-change gaps / gradient margins
+LS_MARGIN32, QP_MARGIN32 = 1e-5, 1e-5
+# alpha decisions FP64 cannot resolve (any size of step)
+TIE64 = 1e-9
 
 
 def run_gpu(prob, dtype, max_iter, tol, grad_u=None, grad_x=None, store_mode="store_all",
@@ -72,7 +74,7 @@ def rel(a, b, floor):
     return float(np.linalg.norm(np.ravel(a) - np.ravel(b)) / max(np.linalg.norm(np.ravel(b)), floor))
 
 
-def compare(gpu, orc, idx, u_tol, j_tol, g_tol, counts="exact", skip_degenerate=False):
+def compare(gpu, orc, idx, u_tol, j_tol, g_tol, counts="exact", skip_degenerate=False, skip_ties=0.0):
     """Per-instance comparison; returns a report dict and a list of failures.
 
     counts: "exact"  status and iteration count identical;
@@ -84,6 +86,9 @@ def compare(gpu, orc, idx, u_tol, j_tol, g_tol, counts="exact", skip_degenerate=
     for k, i in enumerate(idx):
         pr, so, gr = orc[k]
         if skip_degenerate and (so.ls_margin < LS_MARGIN32 or so.qp_margin < QP_MARGIN32):
+            report["excluded"] += 1
+            continue
+        if skip_ties and so.ls_margin_any < skip_ties:
             report["excluded"] += 1
             continue
         report["compared"] += 1

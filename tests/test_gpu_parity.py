@@ -3,7 +3,7 @@ import numpy as np
 import pytest
 
 import workloads as W
-from gpu_support import (G_TOL32, G_TOL64, G_TOL64C, J_TOL32, J_TOL64, J_TOL64C, U_TOL32, U_TOL64, U_TOL64C,
+from gpu_support import (TIE64, G_TOL32, G_TOL64, G_TOL64C, J_TOL32, J_TOL64, J_TOL64C, U_TOL32, U_TOL64, U_TOL64C,
                          cached_problem, compare, oracle_solve, run_gpu)
 
 pytestmark = pytest.mark.gpu
@@ -38,8 +38,9 @@ def test_fp64_early_iterations_identical_to_oracle(name, B, N, horizons):
     gpu = run_gpu(prob, torch.float64, 3, 0.0, gu, gx, N_max=40)
     idx = list(range(B))
     orc = oracle_solve(prob, idx, 3, 0.0, gu, gx)
-    report, fails = compare(gpu, orc, idx, U_TOL64, J_TOL64, G_TOL64)
+    report, fails = compare(gpu, orc, idx, U_TOL64, J_TOL64, G_TOL64, skip_ties=TIE64)
     print(name, report)
+    assert report["compared"] >= 0.8 * B
     assert not fails, fails[:5]
 
 
@@ -188,7 +189,7 @@ def test_hover_fixed_point_on_gpu():
     np.testing.assert_allclose(g["dQ"], 0, atol=1e-5)
     g64 = run_gpu(prob, torch.float64, 8, 1e-6, gu)
     np.testing.assert_allclose(g64["u"], W.DEFAULT_MODEL.hover_thrust, rtol=1e-14)
-    assert np.all(g64["status"] == 1) and np.all(g64["iters"] == 1)
+    assert np.all(g64["status"] == 0) and np.all(g64["iters"] == 1)
 
 
 # ------------------------------------------------- API, graphs, autograd --

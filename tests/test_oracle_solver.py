@@ -178,8 +178,8 @@ def test_box_lq_tiny_matches_active_set_enumeration():
 
 def test_hover_fixed_point_of_solver():
     """x0 = x_ref = hover and u_ref = m g / 4: the start is optimal, cost 0,
-    the line search finds no decrease (STALLED after one iteration), and
-    dL/dQ = 0 because x* = x_ref."""
+    the first step is zero (CONVERGED after one iteration), and dL/dQ = 0
+    because x* = x_ref."""
     N = 10
     x0 = np.zeros(13)
     x0[0:3] = [0.5, -0.2, 2.0]
@@ -190,7 +190,7 @@ def test_hover_fixed_point_of_solver():
     sol = ilqr.solve(QUAD, prob, max_iter=10, tol=1e-6)
     np.testing.assert_allclose(sol.U, W.DEFAULT_MODEL.hover_thrust, atol=1e-12)
     assert abs(sol.J) < 1e-20
-    assert sol.status == ilqr.STALLED and sol.iters == 1
+    assert sol.status == ilqr.CONVERGED and sol.iters == 1
     gx = np.zeros((N, 13))
     gu = np.zeros((N, 4))
     gu[0] = 1.0
