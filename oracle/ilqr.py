@@ -256,6 +256,20 @@ def solve(model, prob: Problem, max_iter=10, tol=1e-6, alphas=ALPHAS) -> Solutio
     return Solution(X, U, total_cost(prob, X, U), iters, status, F, bp, ls_margin, qp_margin, hist, ls_margin_any)
 
 
+def at_iterate(model, prob: Problem, U) -> Solution:
+    """The record of a given control sequence U (clamped to the bounds): its
+    rollout, its cost, and the linearization and factorization at it that the
+    backward pass differentiates (the final step of ``solve``)."""
+    n, N = prob.n, prob.x_ref.shape[0]
+    Uc = np.zeros((N, prob.u_ref.shape[0]))
+    Uc[:n] = np.clip(U[:n], prob.u_lo, prob.u_hi)
+    X = np.zeros((N, prob.x0.shape[0]))
+    X[:n] = model.rollout(prob.x0, Uc[:n])
+    F = linearize(model, prob, X, Uc)
+    bp = backward_pass(prob, X, Uc, F)
+    return Solution(X, Uc, total_cost(prob, X, Uc), 0, MAX_ITER, F, bp, np.inf, np.inf, [])
+
+
 def solve_batch(model, batch: dict, idx=None, max_iter=None, tol=None):
     """Solve instances ``idx`` of a workload dict one by one."""
     B = batch["x0"].shape[0]

@@ -4,7 +4,7 @@ import pytest
 
 import workloads as W
 from gpu_support import (TIE64, G_TOL32, G_TOL64, G_TOL64C, J_TOL32, J_TOL64, J_TOL64C, U_TOL32, U_TOL64, U_TOL64C,
-                         cached_problem, compare, oracle_solve, run_gpu)
+                         cached_problem, compare, compare32, oracle_solve, run_gpu)
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
@@ -59,36 +59,37 @@ def test_fp64_to_convergence_matches_oracle(name, B, N, horizons, mi):
 
 # --------------------------------------------------- FP32: the product path --
 
-@pytest.mark.parametrize("name,B,N,horizons,mi", [("hover", 64, 20, False, 8), ("track", 64, 20, True, 8),
-                                                  ("uneven", 40, 40, False, 12), ("mem", 24, 30, False, 8)])
+@pytest.mark.parametrize("name,B,N,horizons,mi", [("hover", 64, 20, False, 20), ("track", 64, 20, True, 20),
+                                                  ("uneven", 40, 40, False, 20), ("mem", 24, 30, False, 20)])
 def test_fp32_forward_backward_match_oracle(name, B, N, horizons, mi):
     prob = cached_problem(name, B, N, 0, horizons)
     gu, gx = _grads(B, N, 2)
     gpu = run_gpu(prob, torch.float32, mi, 1e-6, gu, gx, N_max=40)
     idx = list(range(B))
     orc = oracle_solve(prob, idx, mi, 1e-6, gu, gx)
-    report, fails = compare(gpu, orc, idx, U_TOL32, J_TOL32, G_TOL32, counts=None, skip_degenerate=True)
+    report, fails = compare32(gpu, prob, orc, idx, gu, gx)
     print(name, report, fails[:5])
-    assert report["compared"] >= 0.7 * B
+    assert report["converged"] >= 0.5 * B
+    assert report["grad_skipped"] <= 0.1 * B
     assert not fails, fails[:5]
 
 
 def test_fp32_full_size_track_sampled():
     """The benchmark's configuration (race track, B = 4096, N = 20, <= 8
-    iterations) in its launch shape; 24 sampled instances checked one by one."""
+    iterations) in its launch shape; 32 sampled instances checked one by one."""
     prob = W.cfg_track()
     B, N = prob["x0"].shape[0], prob["x_ref"].shape[1]
     gu = W.loss_weights_u0(B, N, seed=1)
     gpu = run_gpu(prob, torch.float32, prob["max_iter"], prob["tol"], gu, None, N_max=N, B_max=B)
-    idx = list(np.random.default_rng(3).choice(B, 24, replace=False))
+    idx = list(np.random.default_rng(3).choice(B, 32, replace=False))
     orc = oracle_solve(prob, idx, prob["max_iter"], prob["tol"], gu, None)
-    report, fails = compare(gpu, orc, idx, U_TOL32, J_TOL32, G_TOL32, counts=None, skip_degenerate=True)
+    report, fails = compare32(gpu, prob, orc, idx, gu, None)
     print(report)
     assert not fails, fails[:5]
-    # every instance ends in a valid state with finite outputs
+    # every instance ends in a valid state with finite outputs inside the bounds
     assert np.all(np.isin(gpu["status"], [0, 1, 2]))
     assert np.isfinite(gpu["u"]).all() and np.isfinite(gpu["dx0"]).all()
-    assert (gpu["u"] >= -1e-6).all() and (gpu["u"] <= 8.5 + 1e-6).all()
+    assert (gpu["u"] >= 0).all() and (gpu["u"] <= 8.5).all()
 
 
 # ------------------------------------------------- equivalences of the modes --
