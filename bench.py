@@ -1,0 +1,391 @@
+"""Benchmark of the batched differentiable MPC layer on GB300.
+
+One step = one forward (box-constrained iLQR, <= 8 iterations, tol 1e-6) plus
+one backward (adjoint LQR: dL/dQ, dL/dx_ref, dL/dx0) over B = 4096 race-track
+instances of horizon N = 20 in FP32, inputs resident in HBM, replayed from two
+CUDA graphs (forward, backward) with L2 flushed between steps.
+
+Besides the headline value the JSON line carries the forward latency
+distribution, the three-launches-per-iteration form on the same inputs, the
+end-to-end number through the public API with host buffers, the roofline of
+the dominant kernel, the FP64 CPU oracle on a bounded sample, and the SM clocks
+sampled during the timed region.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank solves its own B instances (a different seed
+per rank; instances are independent, so there is no collective on the data
+path) and the slowest rank's time is reported: weak scaling.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import multiprocessing as mp
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+B, N, MAX_ITER, TOL = 4096, 20, 8, 1e-6
+METRIC = "DiffMPC fwd+bwd solves/s at B=4096,N=20 FP32 vs plain; p50/p99 fwd latency"
+UNIT = "solves/s"
+WORKLOAD = "race-track MPC batch: B=4096 instances, N=20, <=8 iLQR iterations (tol 1e-6), forward + adjoint backward"
+# Algorithmic FP32 flops (FMA = 2), fixed from the method's steps:
+#   per stage and executed iteration: RK4 rollout 0.53k + RK4 Jacobian 10.5k
+#   + Riccati with box QP 11.9k + line search 4 x 0.72k  = 25.8k
+#   final linearization + factorization at x* (store-all): 10.5k + 11.9k = 22.4k per stage
+#   adjoint sweeps from the tape: 1.2k per stage
+FLOP_STAGE_ITER = 25.8e3
+FLOP_STAGE_FINAL = 22.4e3
+FLOP_STAGE_BWD = 1.2e3
+FP32_LANES_PER_SM = 128
+L2_FLUSH_BYTES = 256 << 20
+
+
+def _kernel_hash():
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_2605_29155_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        h.update(open(os.path.join(d, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def _traffic():
+    """DRAM bytes per forward launch from the committed ncu summary, if it was
+    taken on the current kernel source; else None."""
+    p = os.path.join(ROOT, "profiles", "k_mpc_forward_traffic.json")
+    try:
+        d = json.load(open(p))
+    except (OSError, ValueError):
+        return None
+    return d.get("bytes_per_launch") if d.get("kernel_hash") == _kernel_hash() else None
+
+
+# ------------------------------------------------------------------ oracle --
+
+def _oracle_chunk(args):
+    prob, idx, gu = args
+    from oracle import adjoint, ilqr
+    from oracle.model import Quadrotor
+    quad = Quadrotor(W.DEFAULT_MODEL)
+    for i in idx:
+        pr = ilqr.problem_from_batch(prob, i)
+        so = ilqr.solve(quad, pr, MAX_ITER, TOL)
+        if so.status in (ilqr.CONVERGED, ilqr.STALLED, ilqr.MAX_ITER):
+            adjoint.adjoint(pr, so, np.zeros((pr.x_ref.shape[0], 13)), gu[i])
+    return len(idx)
+
+
+def oracle_rate(n_inst, seed=0, pool=None, cores=1):
+    """Solves/s of the FP64 oracle (forward + backward) on n_inst track instances."""
+    prob = W.cfg_track(seed=seed, B=n_inst)
+    gu = W.loss_weights_u0(n_inst, N, seed=1)
+    chunks = [list(range(k, n_inst, cores)) for k in range(cores)]
+    t0 = time.perf_counter()
+    if pool is None:
+        _oracle_chunk((prob, list(range(n_inst)), gu))
+    else:
+        sum(pool.map(_oracle_chunk, [(prob, c, gu) for c in chunks if c]))
+    return n_inst / (time.perf_counter() - t0)
+
+
+def run_reference(args, rank, world):
+    """The reference arm: the FP64 oracle on the host cores, bounded sample per step."""
+    if rank != 0:
+        return
+    cores = os.cpu_count() or 1
+    per_step = max(cores, 32)
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(cores, initializer=_pin_threads) as pool:
+        for _ in range(args.warmup):
+            oracle_rate(cores, seed=99, pool=pool, cores=cores)
+        rates, t_all = [], time.perf_counter()
+        for k in range(args.steps):
+            rates.append(oracle_rate(per_step, seed=k, pool=pool, cores=cores))
+        wall = time.perf_counter() - t_all
+    value = per_step * args.steps / wall
+    line = dict(impl="reference", metric=METRIC, value=value, unit=UNIT, n_gpus=1, steps=args.steps,
+                warmup=args.warmup, ms_per_step=1e3 * wall / args.steps, higher_is_better=True, scaling="weak",
+                vs_baseline=None, dtype="f64", data="synthetic",
+                config=dict(workload=WORKLOAD + " (FP64 CPU oracle, one instance at a time per process)",
+                            B=B, N=N, sample=f"{per_step} instances per step"),
+                cpu_baseline=dict(value=value, unit=UNIT, cores=cores, kind="oracle",
+                                  sample=f"{per_step} race-track instances per step, fwd+bwd, {args.steps} steps"),
+                e2e=dict(value=value, unit=UNIT, h2d_bytes_per_step=0, d2h_bytes_per_step=0))
+    print(json.dumps(line), flush=True)
+
+
+def _pin_threads():
+    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[v] = "1"
+
+
+# ------------------------------------------------------------------ clocks --
+
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index, self.proc, self.out = index, None, None
+
+    def __enter__(self):
+        try:
+            self.out = open(os.path.join("/tmp", f"camp_clocks_{os.getpid()}.csv"), "w+")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.out, stderr=subprocess.DEVNULL)
+        except (OSError, ValueError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if self.proc is None or self.out is None:
+            return None
+        self.out.seek(0)
+        rows = [r.split(",") for r in self.out.read().strip().splitlines() if r.count(",") >= 7]
+        if not rows:
+            return None
+        sm = [float(r[0]) for r in rows]
+        mx = max(float(r[1]) for r in rows)
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[j] for r in rows for j in range(4) if r[4 + j].strip().lower() == "active"})
+        return dict(sm_mhz=statistics.median(sm), sm_max_mhz=mx, reasons=reasons, samples=len(rows),
+                    power_w_max=max(float(r[2]) for r in rows))
+
+
+# ------------------------------------------------------------- GPU arm -----
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2605_29155_gb300 import DiffMPC, Problem
+
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+
+    # CPU baseline first (spawned pool, before any further GPU work), rank 0 only
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cores = os.cpu_count() or 1
+        sample = max(4 * cores, 64)
+        with mp.get_context("spawn").Pool(cores, initializer=_pin_threads) as pool:
+            oracle_rate(cores, seed=99, pool=pool, cores=cores)
+            rate = oracle_rate(sample, seed=0, pool=pool, cores=cores)
+        cpu = dict(value=rate, unit=UNIT, cores=cores, kind="oracle",
+                   sample=f"first {sample} instances of the race-track workload, fwd+bwd, FP64, {cores} processes")
+
+    prob = W.cfg_track(seed=rank)
+    gu_np = W.loss_weights_u0(B, N, seed=1 + rank)
+    p = Problem.from_numpy(prob, device=dev)
+    gu = torch.as_tensor(gu_np, dtype=torch.float32, device=dev)
+
+    solver = DiffMPC(N_max=N, B_max=B, max_iter=MAX_ITER, tol=TOL, device=dev)
+    s = solver.alloc_solution(B, N)
+    grads = (torch.empty_like(p.Q), torch.empty_like(p.x_ref), torch.empty_like(p.x0))
+    ipb = solver.autotune(p, s)
+    tpi, ipb, grid = solver.launch_shape(B, N)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    # capture forward and backward graphs
+    for _ in range(3):
+        solver.solve(p, s)
+        solver.backward(p, s, gu, out=grads)
+    torch.cuda.synchronize()
+    g_fwd, g_bwd = torch.cuda.CUDAGraph(), torch.cuda.CUDAGraph()
+    side = torch.cuda.Stream(device=dev)
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        with torch.cuda.graph(g_fwd):
+            solver.solve(p, s)
+        with torch.cuda.graph(g_bwd):
+            solver.backward(p, s, gu, out=grads)
+    torch.cuda.current_stream().wait_stream(side)
+    stream = torch.cuda.current_stream()
+
+    def step(ev):
+        flush.fill_(1.0)
+        ev[0].record(stream)
+        g_fwd.replay()
+        ev[1].record(stream)
+        g_bwd.replay()
+        ev[2].record(stream)
+
+    for _ in range(args.warmup):
+        step([torch.cuda.Event(enable_timing=True) for _ in range(3)])
+    torch.cuda.synchronize()
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local_rank) as clk:
+        t0 = time.perf_counter()
+        for k in range(args.steps):
+            step(evs[k])
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+    if dist:
+        dist.barrier()
+    step_ms = [e[0].elapsed_time(e[2]) for e in evs]
+    fwd_ms = [e[0].elapsed_time(e[1]) for e in evs]
+    ms = statistics.fmean(step_ms)
+    ms_fwd = statistics.fmean(fwd_ms)
+    if dist:
+        t = torch.tensor([ms, ms_fwd], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms, ms_fwd = float(t[0]), float(t[1])
+    status = s.status.cpu().numpy()
+    iters = s.iters.cpu().numpy()
+
+    # forward latency distribution (graph replays, cold L2)
+    lat = []
+    for _ in range(args.latency_reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        flush.fill_(1.0)
+        e0.record(stream)
+        g_fwd.replay()
+        e1.record(stream)
+        e1.synchronize()
+        lat.append(e0.elapsed_time(e1))
+    lat.sort()
+    p50 = lat[len(lat) // 2]
+    p99 = lat[min(len(lat) - 1, int(0.99 * len(lat)))]
+
+    # plain form (three launches per iteration, eager, as Sec. IV structures it)
+    plain = DiffMPC(N_max=N, B_max=B, max_iter=MAX_ITER, tol=TOL, exec_mode="plain", ipb=ipb, device=dev)
+    sp = plain.alloc_solution(B, N)
+    gp = (torch.empty_like(p.Q), torch.empty_like(p.x_ref), torch.empty_like(p.x0))
+    for _ in range(2):
+        plain.solve(p, sp)
+        plain.backward(p, sp, gu, out=gp)
+    torch.cuda.synchronize()
+    pms = []
+    for _ in range(max(3, args.steps // 2)):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        flush.fill_(1.0)
+        e0.record(stream)
+        plain.solve(p, sp)
+        plain.backward(p, sp, gu, out=gp)
+        e1.record(stream)
+        e1.synchronize()
+        pms.append(e0.elapsed_time(e1))
+    plain_ms = statistics.fmean(pms)
+    same = bool(torch.equal(sp.u, s.u) and torch.equal(gp[0], grads[0]))
+    plain_launches = plain.launch_count(False)
+    plain.close()
+
+    # end to end through the public API with pinned host buffers
+    names = ("x0", "Q", "x_ref", "R", "u_ref", "u_lo", "u_hi")
+    host_in = {k: torch.as_tensor(prob[k], dtype=torch.float32).pin_memory() for k in names}
+    host_gu = torch.as_tensor(gu_np, dtype=torch.float32).pin_memory()
+    host_out = [torch.empty(t.shape, dtype=t.dtype).pin_memory() for t in (s.u, grads[0], grads[1], grads[2])]
+    dev_in = {k: getattr(p, k) for k in names}
+    h2d = sum(t.numel() * 4 for t in host_in.values()) + host_gu.numel() * 4
+    d2h = sum(t.numel() * t.element_size() for t in host_out)
+    e2e_ms = []
+    for k in range(args.warmup + args.steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        flush.fill_(1.0)
+        e0.record(stream)
+        for n_ in names:
+            dev_in[n_].copy_(host_in[n_], non_blocking=True)
+        gu.copy_(host_gu, non_blocking=True)
+        solver.solve(p, s)
+        solver.backward(p, s, gu, out=grads)
+        for h, d in zip(host_out, (s.u, grads[0], grads[1], grads[2])):
+            h.copy_(d, non_blocking=True)
+        e1.record(stream)
+        e1.synchronize()
+        if k >= args.warmup:
+            e2e_ms.append(e0.elapsed_time(e1))
+    e2e = statistics.fmean(e2e_ms)
+
+    # roofline of the dominant kernel (the persistent forward launch)
+    props = torch.cuda.get_device_properties(dev)
+    sms = props.multi_processor_count
+    clocks = clk.summary()
+    sm_max_mhz = (clocks or {}).get("sm_max_mhz") or 2070.0
+    peak_tflops = sms * FP32_LANES_PER_SM * 2 * sm_max_mhz * 1e6 / 1e12
+    hz = np.full(B, N)
+    fwd_flops = float(np.sum(iters * (hz - 1)) * FLOP_STAGE_ITER + np.sum(hz - 1) * FLOP_STAGE_FINAL)
+    achieved = fwd_flops / (ms_fwd * 1e-3) / 1e12
+    fwd_launches, bwd_launches = solver.launch_count(False)
+    solver.close()
+
+    if rank != 0:
+        return
+    value = B * world / (ms * 1e-3)
+    line = dict(
+        metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=args.steps, warmup=args.warmup,
+        ms_per_step=ms, higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f32", data="synthetic",
+        config=dict(workload=WORKLOAD, B_per_gpu=B, N=N, max_iter=MAX_ITER, tol=TOL,
+                    exec="persistent forward + adjoint backward, each one CUDA graph replay",
+                    launch=dict(threads_per_instance=tpi, instances_per_block=ipb, blocks=grid),
+                    l2="flushed between steps (256 MiB write, outside the timed events)",
+                    inputs="seeded synthetic race track (7 gates, 30 m loop, 0-20 m/s)"),
+        p50_fwd_ms=p50, p99_fwd_ms=p99, fwd_ms=ms_fwd, bwd_ms=ms - ms_fwd,
+        fwd_solves_per_s=B * world / (ms_fwd * 1e-3),
+        plain=dict(value=B * world / (plain_ms * 1e-3), unit=UNIT, ms_per_step=plain_ms,
+                   launches_per_step=plain_launches[0] + plain_launches[1], exec="eager, 3 launches per iteration",
+                   bit_identical_to_persistent=same),
+        speedup_vs_plain=plain_ms / ms,
+        iters_mean=float(iters.mean()), status_counts=np.bincount(status, minlength=5).tolist(),
+        e2e=dict(value=B * world / (e2e * 1e-3), unit=UNIT, ms_per_step=e2e, h2d_bytes_per_step=int(h2d),
+                 d2h_bytes_per_step=int(d2h), api="paper_2605_29155_gb300.DiffMPC.solve/backward (ctypes C ABI), eager"),
+        roofline=dict(kernel="k_mpc<float> persistent forward", bound="alu", achieved=achieved, peak=peak_tflops,
+                      unit="TFLOP/s", frac=achieved / peak_tflops, traffic=_traffic(),
+                      peak_note=f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 flop x {sm_max_mhz:.0f} MHz",
+                      flops_per_launch=fwd_flops),
+        cpu_baseline=cpu,
+        clocks=clocks,
+        gpu_launches=(fwd_launches + bwd_launches) * args.steps,
+        wall_s_timed=wall,
+    )
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--latency-reps", type=int, default=200)
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", args.gpus if args.gpus == 1 else 1))
+    local_rank = int(os.environ.get("LOCAL_RANK", 0))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    main()

@@ -113,11 +113,13 @@ class BackwardResult:
     margin: float  # smallest |grad_i| over bound-decided dimensions (degeneracy)
 
 
-def backward_pass(prob: Problem, X, U, F) -> BackwardResult:
+def backward_pass(prob: Problem, X, U, F, free_override=None) -> BackwardResult:
     """Sec. IV-2: Riccati recursion with the per-stage box QP, t = n-1 .. 0.
 
     Q_t = C_t + F_t' V_{t+1} F_t,  q_t = (C_t z_t + c_t) + F_t' v_{t+1}
-    (V_n = 0, v_n = 0; stage n-1 has no dynamics term)."""
+    (V_n = 0, v_n = 0; stage n-1 has no dynamics term).  ``free_override``
+    (a free mask per stage) replaces the box QP's free sets in K_t, the
+    factor and the value update: the LQR of a given active set."""
     n, nx, nu = prob.n, X.shape[1], U.shape[1]
     V = np.zeros((nx, nx))
     v = np.zeros(nx)
@@ -141,6 +143,10 @@ def backward_pass(prob: Problem, X, U, F) -> BackwardResult:
         k, free, L, ok = boxqp.solve(Quu, qu, lo, hi)
         if not ok:
             return BackwardResult(False, Ks, ks, frees, Ls, Quus, Quxs, margin)
+        if free_override is not None:
+            free = np.asarray(free_override[t], dtype=bool)
+            fi0 = np.flatnonzero(free)
+            L = boxqp.cholesky(Quu[np.ix_(fi0, fi0)]) if fi0.size else None
         grad = qu + Quu @ k
         atb = (k <= lo) | (k >= hi)
         if atb.any():
@@ -256,17 +262,18 @@ def solve(model, prob: Problem, max_iter=10, tol=1e-6, alphas=ALPHAS) -> Solutio
     return Solution(X, U, total_cost(prob, X, U), iters, status, F, bp, ls_margin, qp_margin, hist, ls_margin_any)
 
 
-def at_iterate(model, prob: Problem, U) -> Solution:
+def at_iterate(model, prob: Problem, U, free_override=None) -> Solution:
     """The record of a given control sequence U (clamped to the bounds): its
     rollout, its cost, and the linearization and factorization at it that the
-    backward pass differentiates (the final step of ``solve``)."""
+    backward pass differentiates (the final step of ``solve``), optionally
+    with given free sets."""
     n, N = prob.n, prob.x_ref.shape[0]
     Uc = np.zeros((N, prob.u_ref.shape[0]))
     Uc[:n] = np.clip(U[:n], prob.u_lo, prob.u_hi)
     X = np.zeros((N, prob.x0.shape[0]))
     X[:n] = model.rollout(prob.x0, Uc[:n])
     F = linearize(model, prob, X, Uc)
-    bp = backward_pass(prob, X, Uc, F)
+    bp = backward_pass(prob, X, Uc, F, free_override)
     return Solution(X, Uc, total_cost(prob, X, Uc), 0, MAX_ITER, F, bp, np.inf, np.inf, [])
 
 

@@ -107,6 +107,9 @@ extern "C" int mpc_create(const mpc_config* cfg, mpc_handle** out) {
     const size_t bO = align256((size_t)cfg->B_max * sizeof(int));
     h->ws_bytes = bF + bK + bC + bP + bH + bX + bQ + bO;
     if (cudaMalloc(&h->ws, h->ws_bytes) != cudaSuccess) { free(h); return MPC_ERR_CUDA; }
+    // All-ones bytes are NaN in float and double: a read of scratch that no
+    // phase wrote surfaces as a NaN result instead of stale data.
+    if (cudaMemset(h->ws, 0xff, h->ws_bytes) != cudaSuccess) { cudaFree(h->ws); free(h); return MPC_ERR_CUDA; }
     char* p = (char*)h->ws;
     h->wsF = p; p += bF;
     h->wsK = p; p += bK;

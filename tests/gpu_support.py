@@ -50,6 +50,8 @@ def run_gpu(prob, dtype, max_iter, tol, grad_u=None, grad_x=None, store_mode="st
     p = Problem.from_numpy(prob, dtype=dtype)
     s = solver.solve(p)
     out = dict(u=s.u, x=s.x, cost=s.cost, iters=s.iters, status=s.status)
+    if s.tape is not None:
+        out["masks"] = s.tape.view(B, N, 288)[:, :, 283].to(torch.int32)
     if grad_u is not None:
         gu = torch.as_tensor(grad_u, dtype=dtype, device="cuda")
         gx = None if grad_x is None else torch.as_tensor(grad_x, dtype=dtype, device="cuda")
@@ -140,14 +142,31 @@ def cached_problem(name, B, N, seed=0, horizons=False):
     raise KeyError(name)
 
 
+def _mask_bits(m):
+    return np.array([(int(m) >> a) & 1 for a in range(4)], dtype=bool)
+
+
+def _degenerate(prob_i, so_bp, U, t, a, du=1e-4, rel_grad=1e-4):
+    """A free/clamped decision FP32 cannot be expected to reproduce: the
+    control lies within du of a bound, or its gradient at the bound is tiny."""
+    lo, hi = prob_i.u_lo[a], prob_i.u_hi[a]
+    if min(abs(U[t][a] - lo), abs(hi - U[t][a])) < du:
+        return True
+    return so_bp.margin < rel_grad
+
+
 def compare32(gpu, prob, orc, idx, grad_u, grad_x=None):
     """FP32 gate: converged instances against the oracle's solution, the rest
-    at their own returned iterate.  Returns (report, failures)."""
+    at their own returned iterate.  Gradients are compared with the oracle's
+    adjoint on the GPU's own final free sets (tape masks); a free set that
+    differs from the oracle's must differ only at degenerate controls.
+    Returns (report, failures)."""
     N = prob["x_ref"].shape[1]
-    rep = dict(converged=0, at_iterate=0, grad_skipped=0, max_u=0.0, max_J=0.0, max_g=0.0, max_roll=0.0)
+    rep = dict(converged=0, at_iterate=0, mask_differs=0, max_u=0.0, max_J=0.0, max_g=0.0, max_roll=0.0)
     fails = []
     for k, i in enumerate(idx):
         pr, so, gr = orc[k]
+        gx = np.zeros((N, 13)) if grad_x is None else grad_x[i]
         if so.status == ilqr.CONVERGED:
             rep["converged"] += 1
             ref, ref_gr = so, gr
@@ -163,7 +182,6 @@ def compare32(gpu, prob, orc, idx, grad_u, grad_x=None):
             rep["max_roll"] = max(rep["max_roll"], er)
             if er > U_TOL32:
                 fails.append((i, "rollout", er))
-            gx = np.zeros((N, 13)) if grad_x is None else grad_x[i]
             ref_gr = adjoint.adjoint(pr, ref, gx, grad_u[i]) if grad_u is not None else None
         ej = abs(float(gpu["cost"][i]) - ref.J) / max(abs(ref.J), 1e-12)
         rep["max_J"] = max(rep["max_J"], ej)
@@ -171,9 +189,17 @@ def compare32(gpu, prob, orc, idx, grad_u, grad_x=None):
             fails.append((i, "cost", ej))
         if ref_gr is None or "dQ" not in gpu:
             continue
-        if ref.bp.margin < QP_MARGIN32:
-            rep["grad_skipped"] += 1
-            continue
+        if "masks" in gpu:
+            gm = [_mask_bits(gpu["masks"][i][t]) for t in range(pr.n)]
+            diff = [(t, a) for t in range(pr.n) for a in range(4) if gm[t][a] != ref.bp.free[t][a]]
+            if diff:
+                rep["mask_differs"] += 1
+                if not all(_degenerate(pr, ref.bp, ref.U, t, a) for t, a in diff):
+                    fails.append((i, "free set", diff[:4]))
+                    continue
+                ref2 = ilqr.at_iterate(QUAD, pr, ref.U, free_override=gm)
+                ref2.X = ref.X
+                ref_gr = adjoint.adjoint(pr, ref2, gx, grad_u[i])
         for name, r in (("dQ", ref_gr.dQ), ("dx_ref", ref_gr.dx_ref), ("dx0", ref_gr.dx0)):
             eg = rel(gpu[name][i], r, 1e-9)
             rep["max_g"] = max(rep["max_g"], eg)
