@@ -133,19 +133,33 @@ def _pin_threads():
 # ------------------------------------------------------------------ clocks --
 
 class ClockSampler:
+    """nvidia-smi sampled every 100 ms in the background; mark() brackets the
+    timed region, and the summary keeps the samples taken inside it (all
+    samples when the region is shorter than the sampling interval)."""
     FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
               "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
               "clocks_event_reasons.sw_power_cap")
 
     def __init__(self, index):
-        self.index, self.proc, self.out = index, None, None
+        self.index, self.proc, self.out, self.marks = index, None, None, []
+
+    def mark(self):
+        self.marks.append(self._lines())
+
+    def _lines(self):
+        if self.out is None:
+            return 0
+        self.out.flush()
+        self.out.seek(0)
+        return len(self.out.read().strip().splitlines())
 
     def __enter__(self):
         try:
             self.out = open(os.path.join("/tmp", f"camp_clocks_{os.getpid()}.csv"), "w+")
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
                                          stdout=self.out, stderr=subprocess.DEVNULL)
+            time.sleep(0.5)
         except (OSError, ValueError):
             self.proc = None
         return self
@@ -162,7 +176,10 @@ class ClockSampler:
         if self.proc is None or self.out is None:
             return None
         self.out.seek(0)
-        rows = [r.split(",") for r in self.out.read().strip().splitlines() if r.count(",") >= 7]
+        lines = self.out.read().strip().splitlines()
+        if len(self.marks) == 2 and self.marks[1] - self.marks[0] >= 3:
+            lines = lines[self.marks[0]:self.marks[1]]
+        rows = [r.split(",") for r in lines if r.count(",") >= 7]
         if not rows:
             return None
         sm = [float(r[0]) for r in rows]
@@ -236,19 +253,21 @@ def run_ours(args, rank, world, local_rank):
         g_bwd.replay()
         ev[2].record(stream)
 
-    for _ in range(args.warmup):
-        step([torch.cuda.Event(enable_timing=True) for _ in range(3)])
-    torch.cuda.synchronize()
     evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
     with ClockSampler(local_rank) as clk:
+        for _ in range(args.warmup):
+            step([torch.cuda.Event(enable_timing=True) for _ in range(3)])
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        clk.mark()
         t0 = time.perf_counter()
         for k in range(args.steps):
             step(evs[k])
         torch.cuda.synchronize()
         wall = time.perf_counter() - t0
+        clk.mark()
     if dist:
         dist.barrier()
     step_ms = [e[0].elapsed_time(e[2]) for e in evs]
@@ -372,8 +391,8 @@ def run_ours(args, rank, world, local_rank):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--latency-reps", type=int, default=200)
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")

@@ -101,6 +101,7 @@ def test_plain_form_is_bit_identical_to_persistent(dtype):
     gu, _ = _grads(48, 20, 3)
     a = run_gpu(prob, dt, 8, 1e-6, gu, exec_mode="persistent", ipb=4)
     b = run_gpu(prob, dt, 8, 1e-6, gu, exec_mode="plain", ipb=2)
+    assert set(a) == set(b)
     for k in a:
         np.testing.assert_array_equal(a[k], b[k], err_msg=k)
 
@@ -112,7 +113,8 @@ def test_recompute_backward_is_bit_identical_to_store_all(dtype):
     gu, gx = _grads(40, 30, 4)
     a = run_gpu(prob, dt, 8, 1e-6, gu, gx, store_mode="store_all")
     b = run_gpu(prob, dt, 8, 1e-6, gu, gx, store_mode="recompute")
-    for k in a:
+    assert "masks" in a and "masks" not in b          # only store-all writes a tape
+    for k in b:
         np.testing.assert_array_equal(a[k], b[k], err_msg=k)
 
 
@@ -121,6 +123,7 @@ def test_launch_shapes_agree(ipb):
     prob = cached_problem("track", 70, 20, 4, True)
     ref = run_gpu(prob, torch.float32, 8, 1e-6, ipb=4)
     got = run_gpu(prob, torch.float32, 8, 1e-6, ipb=ipb)
+    assert set(ref) == set(got)
     for k in ref:
         np.testing.assert_array_equal(ref[k], got[k], err_msg=k)
 
