@@ -167,6 +167,25 @@ int mpc_launch_shape(const mpc_handle *h, int B, int N, int *tpi, int *ipb, int 
  * without per-instance horizons) enqueues in the handle's configuration. */
 int mpc_launch_count(const mpc_handle *h, int has_horizon, int *fwd, int *bwd);
 
+/* Forward solve that allocates nothing.  The paper has no counterpart: this is
+ * for callers that cannot allocate device memory while they run (a real-time
+ * control loop that must not allocate after start-up, a plug-in whose host
+ * application owns every device allocation).  Same problem, outputs and
+ * per-instance statuses as mpc_solve_fwd in the persistent form, without a
+ * handle: the scratch is one statically allocated device array (18.6 MB,
+ * held on every device the library runs on until the process exits).
+ *   cfg    as for mpc_create, dtype must be MPC_F32 (exec_mode, tpi, ipb,
+ *          N_max and B_max are ignored); MPC_STORE_ALL writes the tape.
+ *   p, s   device pointers as for mpc_solve_fwd; B <= MPC_NOALLOC_B_MAX and
+ *          N <= MPC_NOALLOC_N_MAX, else MPC_ERR_SHAPE.
+ * The first call on a device looks the array up with that device current;
+ * make it before any stream capture.  All calls share the array: calls whose
+ * GPU work overlaps race on it and must not be issued.  Errors as for
+ * mpc_solve_fwd. */
+#define MPC_NOALLOC_B_MAX 256
+#define MPC_NOALLOC_N_MAX 40
+int mpc_solve_fwd_noalloc(const mpc_config *cfg, const mpc_problem *p, mpc_solution *s, cudaStream_t stream);
+
 /* Static text for a return code (mpc_strerror) or an MPC_ST_* status (mpc_status_str). */
 const char *mpc_strerror(int code);
 const char *mpc_status_str(int status);

@@ -21,7 +21,8 @@ TAPE_STRIDE = 288
 
 EXPORTED = ("mpc_config_default", "mpc_create", "mpc_destroy", "mpc_tape_bytes", "mpc_solve_fwd",
             "mpc_solve_bwd", "mpc_autotune", "mpc_launch_shape", "mpc_launch_count", "mpc_strerror",
-            "mpc_status_str")
+            "mpc_status_str", "mpc_solve_fwd_noalloc")
+MPC_NOALLOC_B_MAX, MPC_NOALLOC_N_MAX = 256, 40
 
 
 class mpc_config(ctypes.Structure):
@@ -71,6 +72,8 @@ def _load():
     lib.mpc_strerror.restype = ctypes.c_char_p
     lib.mpc_status_str.argtypes = [c_int]
     lib.mpc_status_str.restype = ctypes.c_char_p
+    lib.mpc_solve_fwd_noalloc.argtypes = [POINTER(mpc_config), POINTER(mpc_problem), POINTER(mpc_solution), c_void_p]
+    lib.mpc_solve_fwd_noalloc.restype = c_int
     return lib
 
 
@@ -139,6 +142,10 @@ def mpc_launch_count(h, has_horizon: bool):
     f, b = c_int(), c_int()
     code = _lib.mpc_launch_count(h, 1 if has_horizon else 0, byref(f), byref(b))
     return code, f.value, b.value
+
+
+def mpc_solve_fwd_noalloc(cfg: mpc_config, prob: mpc_problem, sol: mpc_solution, stream: int) -> int:
+    return _lib.mpc_solve_fwd_noalloc(byref(cfg), byref(prob), byref(sol), c_void_p(stream))
 
 
 def mpc_strerror(code: int) -> str:
