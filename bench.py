@@ -388,6 +388,36 @@ def run_ours(args, rank, world, local_rank):
     print(json.dumps(line), flush=True)
 
 
+def run_kernels_only(args):
+    """W + K eager forward+backward steps on the benchmark workload, nothing
+    else: the command the committed ncu summaries were taken with."""
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2605_29155_gb300 import DiffMPC, Problem
+
+    Bk = args.batch
+    prob = W.cfg_track(B=Bk)
+    p = Problem.from_numpy(prob)
+    gu = torch.as_tensor(W.loss_weights_u0(Bk, N, seed=1), dtype=torch.float32, device="cuda")
+    solver = DiffMPC(N_max=N, B_max=Bk, max_iter=MAX_ITER, tol=TOL)
+    s = solver.alloc_solution(Bk, N)
+    grads = (torch.empty_like(p.Q), torch.empty_like(p.x_ref), torch.empty_like(p.x0))
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for k in range(args.warmup + args.steps):
+        if k == args.warmup:
+            torch.cuda.synchronize()
+            e0.record()
+        solver.solve(p, s)
+        solver.backward(p, s, gu, out=grads)
+    e1.record()
+    torch.cuda.synchronize()
+    print(json.dumps(dict(mode="kernels", B=Bk, N=N, steps=args.steps, ms_per_step=e0.elapsed_time(e1) / args.steps,
+                          launch=solver.launch_shape(Bk, N), iters_mean=float(s.iters.float().mean()))))
+    solver.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -396,7 +426,13 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--latency-reps", type=int, default=200)
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--mode", default="full", choices=["full", "kernels"],
+                    help="kernels: only W + K eager forward+backward steps of the workload (for profilers)")
+    ap.add_argument("--batch", type=int, default=B, help="instances (kernels mode only)")
     args = ap.parse_args()
+    if args.mode == "kernels":
+        run_kernels_only(args)
+        return
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", args.gpus if args.gpus == 1 else 1))
     local_rank = int(os.environ.get("LOCAL_RANK", 0))
