@@ -17,7 +17,8 @@ namespace camp {
 constexpr int NX = 13, NU = 4, NZ = 17;
 constexpr int NF = NX * NZ;            // entries of F_t = [A_t B_t], stored column-major
 constexpr int TAPE_STRIDE = 288;       // tape record per stage (elements)
-constexpr int TAPE_F = 0, TAPE_K = 221, TAPE_L = 273, TAPE_MASK = 283;
+constexpr int TAPE_F = 0, TAPE_K = 221, TAPE_L = 273, TAPE_MASK = 287;
+constexpr int NL = 14;                 // factor: packed lower 4x4 (10) + reciprocal diagonal (4)
 constexpr int KREC = 56;               // K_t (52, row-major) + k_t (4)
 constexpr int SP_STRIDE = 32;          // RK4 stage points per stage: 4 x (q, w, pad)
 constexpr int CREC = 30;               // line-search candidate per stage: x hi (13), x lo (13), u (4)
@@ -68,10 +69,11 @@ template <typename T> struct WarpSmem {
     T Cd[NZ];          // diag C_t
     T K[NU * NX];      // K_t row-major
     T k[NU];           // k_t
-    T L[10];           // Cholesky of Q_uu on the free set (packed lower, masked)
+    T L[NL];           // Cholesky of Q_uu on the free set (packed lower, masked) + 1/diag
     T x0[NX];
     T R[NU], uref[NU], ulo[NU], uhi[NU];
     T Jc[4];
+    T stg[2][112];     // line search: next stage's K, k, x, x lo, u, Q, x_ref (double buffered)
     T vh[NX];          // adjoint value gradient
     T qh[NZ];          // adjoint q-hat
     T dx[NX];          // adjoint forward-sweep state
@@ -114,26 +116,6 @@ __device__ __forceinline__ void f_cont(const Model<T>& m, const T* x, const T* u
     d[12] = (tz - (wx * jwy - wy * jwx)) * m.iJz;
 }
 
-// One classic RK4 step of length h with u held constant (in place).
-template <typename T>
-__device__ __forceinline__ void rk4_step(const Model<T>& m, T* x, const T* u) {
-    T k[NX], acc[NX], xs[NX];
-    const T hh = T(0.5) * m.h;
-    f_cont(m, x, u, k);
-#pragma unroll
-    for (int i = 0; i < NX; ++i) { acc[i] = k[i]; xs[i] = x[i] + hh * k[i]; }
-    f_cont(m, xs, u, k);
-#pragma unroll
-    for (int i = 0; i < NX; ++i) { acc[i] = acc[i] + T(2) * k[i]; xs[i] = x[i] + hh * k[i]; }
-    f_cont(m, xs, u, k);
-#pragma unroll
-    for (int i = 0; i < NX; ++i) { acc[i] = acc[i] + T(2) * k[i]; xs[i] = x[i] + m.h * k[i]; }
-    f_cont(m, xs, u, k);
-    const T h6 = m.h / T(6);
-#pragma unroll
-    for (int i = 0; i < NX; ++i) x[i] = x[i] + h6 * (acc[i] + k[i]);
-}
-
 // (hi, lo) += d: the rounding error of hi + d is carried in lo (2Sum, then a
 // fast renormalisation), so a trajectory accumulated over many steps keeps the
 // increments' precision instead of the state's.
@@ -147,45 +129,48 @@ __device__ __forceinline__ void acc2(T& hi, T& lo, T d) {
     lo = l - (hi - s);
 }
 
-// RK4 step whose state is the unevaluated sum hi + lo: the four stages are
-// evaluated at hi in working precision, the increment h/6 (k1+2k2+2k3+k4) is
-// added with acc2.
+// One classic RK4 step of length h with u held constant, on a state carried
+// as the unevaluated sum hi + lo: the four stages are evaluated at hi in
+// working precision, the increment h/6 (k1 + 2k2 + 2k3 + k4) is added with acc2.
 template <typename T>
 __device__ __forceinline__ void rk4_step2(const Model<T>& m, T* xh, T* xl, const T* u) {
     T k[NX], acc[NX], xs[NX];
     const T hh = T(0.5) * m.h;
-    f_cont(m, xh, u, k);
 #pragma unroll
-    for (int i = 0; i < NX; ++i) { acc[i] = k[i]; xs[i] = xh[i] + hh * k[i]; }
-    f_cont(m, xs, u, k);
+    for (int i = 0; i < NX; ++i) xs[i] = xh[i];
 #pragma unroll
-    for (int i = 0; i < NX; ++i) { acc[i] = acc[i] + T(2) * k[i]; xs[i] = xh[i] + hh * k[i]; }
-    f_cont(m, xs, u, k);
+    for (int st = 0; st < 4; ++st) {
+        f_cont(m, xs, u, k);
+        const T w = (st == 0 || st == 3) ? T(1) : T(2);
+        const T c = (st < 2) ? hh : m.h;
 #pragma unroll
-    for (int i = 0; i < NX; ++i) { acc[i] = acc[i] + T(2) * k[i]; xs[i] = xh[i] + m.h * k[i]; }
-    f_cont(m, xs, u, k);
+        for (int i = 0; i < NX; ++i) {
+            acc[i] = (st == 0) ? k[i] : acc[i] + w * k[i];
+            xs[i] = xh[i] + c * k[i];
+        }
+    }
     const T h6 = m.h / T(6);
 #pragma unroll
-    for (int i = 0; i < NX; ++i) acc2(xh[i], xl[i], h6 * (acc[i] + k[i]));
+    for (int i = 0; i < NX; ++i) acc2(xh[i], xl[i], h6 * acc[i]);
 }
 
 // RK4 stage points of one step: for s = 1..4 the (q, w) of xi_s (xi_1 = x,
 // xi_2 = x + h/2 k1, xi_3 = x + h/2 k2, xi_4 = x + h k3) and the thrust.
 template <typename T>
-__device__ __forceinline__ void rk4_stage_points(const Model<T>& m, const T* x, const T* u, T* sp) {
+__device__ __forceinline__ void rk4_stage_points(const Model<T>& m, const T* x, const T* u, T* __restrict__ sp) {
     T k[NX], xs[NX];
     const T hh = T(0.5) * m.h;
 #pragma unroll
     for (int i = 0; i < NX; ++i) xs[i] = x[i];
 #pragma unroll
-    for (int s = 0; s < 4; ++s) {
+    for (int st = 0; st < 4; ++st) {
 #pragma unroll
-        for (int i = 0; i < 4; ++i) sp[s * 8 + i] = xs[3 + i];
+        for (int i = 0; i < 4; ++i) sp[st * 8 + i] = xs[3 + i];
 #pragma unroll
-        for (int i = 0; i < 3; ++i) sp[s * 8 + 4 + i] = xs[10 + i];
-        if (s < 3) {
+        for (int i = 0; i < 3; ++i) sp[st * 8 + 4 + i] = xs[10 + i];
+        if (st < 3) {
             f_cont(m, xs, u, k);
-            const T c = (s < 2) ? hh : m.h;
+            const T c = (st < 2) ? hh : m.h;
 #pragma unroll
             for (int i = 0; i < NX; ++i) xs[i] = x[i] + c * k[i];
         }
@@ -227,30 +212,40 @@ __device__ __forceinline__ void jvp_cont(const Model<T>& m, const T* sp8, T th, 
     out[12] = (tz - gz) * m.iJz;
 }
 
+// The 6 columns of F_t for p and v are constant: position enters nothing
+// (F[:, p_i] = e_{p_i}) and velocity only the position (F[:, v_i] = e_{v_i} +
+// h e_{p_i}, h written as (h/6) * 6 as the RK4 combination forms it).  The
+// other 11 columns (q, w, u) are computed; GCOL maps 0..10 to them.
+__device__ __forceinline__ int gcol(int jj) { return jj < 4 ? 3 + jj : 6 + jj; }
+__device__ __forceinline__ int tcol(int jj) { return jj < 3 ? jj : jj + 4; }
+constexpr int NGC = 11, NTC = 6;
+template <typename T> __device__ __forceinline__ T hv_coef(const Model<T>& m) { return (m.h / T(6)) * T(6); }
+
 // Column j of F_t = d RK4 / d(x, u): forward tangent through the four stages,
 // d_s = J_c(xi_s) [dx + c_s d_{s-1}; du],  col = dx + h/6 (d1 + 2 d2 + 2 d3 + d4).
 template <typename T>
-__device__ __forceinline__ void tangent_column(const Model<T>& m, const T* sp, int j, T* col) {
+__device__ __forceinline__ void tangent_column(const Model<T>& m, const T* __restrict__ sp, int j, T* col) {
     T dx[NX], du[NU], arg[NX], d[NX], acc[NX];
 #pragma unroll
-    for (int i = 0; i < NX; ++i) dx[i] = (i == j) ? T(1) : T(0);
+    for (int i = 0; i < NX; ++i) { dx[i] = (i == j) ? T(1) : T(0); arg[i] = dx[i]; }
 #pragma unroll
     for (int a = 0; a < NU; ++a) du[a] = (NX + a == j) ? T(1) : T(0);
     const T th = sp[7];
     const T hh = T(0.5) * m.h;
-    jvp_cont(m, sp + 0, th, dx, du, d);
 #pragma unroll
-    for (int i = 0; i < NX; ++i) { acc[i] = d[i]; arg[i] = dx[i] + hh * d[i]; }
-    jvp_cont(m, sp + 8, th, arg, du, d);
+    for (int st = 0; st < 4; ++st) {
+        jvp_cont(m, sp + 8 * st, th, arg, du, d);
+        const T w = (st == 0 || st == 3) ? T(1) : T(2);
+        const T c = (st < 2) ? hh : m.h;
 #pragma unroll
-    for (int i = 0; i < NX; ++i) { acc[i] = acc[i] + T(2) * d[i]; arg[i] = dx[i] + hh * d[i]; }
-    jvp_cont(m, sp + 16, th, arg, du, d);
-#pragma unroll
-    for (int i = 0; i < NX; ++i) { acc[i] = acc[i] + T(2) * d[i]; arg[i] = dx[i] + m.h * d[i]; }
-    jvp_cont(m, sp + 24, th, arg, du, d);
+        for (int i = 0; i < NX; ++i) {
+            acc[i] = (st == 0) ? d[i] : acc[i] + w * d[i];
+            arg[i] = dx[i] + c * d[i];
+        }
+    }
     const T h6 = m.h / T(6);
 #pragma unroll
-    for (int i = 0; i < NX; ++i) col[i] = dx[i] + h6 * (acc[i] + d[i]);
+    for (int i = 0; i < NX; ++i) col[i] = dx[i] + h6 * acc[i];
 }
 
 // ------------------------------------------------------------- box QP ------
@@ -258,14 +253,16 @@ __device__ __forceinline__ void tangent_column(const Model<T>& m, const T* sp, i
 __device__ __forceinline__ int lidx(int i, int j) { return i * (i + 1) / 2 + j; }
 
 // Cholesky of H with the rows/columns outside `mask` replaced by the identity:
-// the free block is factored exactly, clamped dimensions decouple.
+// the free block is factored exactly, clamped dimensions decouple.  L[10 + j]
+// holds 1 / L_jj so that the solves multiply instead of divide.
 template <typename T>
-__device__ __forceinline__ bool chol_masked(const T (&H)[4][4], int mask, T (&L)[10]) {
+__device__ __forceinline__ bool chol_masked(const T (&H)[4][4], int mask, T (&L)[NL]) {
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
         const bool fj = (mask >> j) & 1;
         if (!fj) {
             L[lidx(j, j)] = T(1);
+            L[10 + j] = T(1);
 #pragma unroll
             for (int i = j + 1; i < 4; ++i) L[lidx(i, j)] = T(0);
             continue;
@@ -275,14 +272,16 @@ __device__ __forceinline__ bool chol_masked(const T (&H)[4][4], int mask, T (&L)
         for (int k = 0; k < j; ++k) s -= L[lidx(j, k)] * L[lidx(j, k)];
         if (!(s > T(0))) return false;
         const T ljj = sqrt(s);
+        const T ij = T(1) / ljj;
         L[lidx(j, j)] = ljj;
+        L[10 + j] = ij;
 #pragma unroll
         for (int i = j + 1; i < 4; ++i) {
             if ((mask >> i) & 1) {
                 T t = H[i][j];
 #pragma unroll
                 for (int k = 0; k < j; ++k) t -= L[lidx(i, k)] * L[lidx(j, k)];
-                L[lidx(i, j)] = t / ljj;
+                L[lidx(i, j)] = t * ij;
             } else {
                 L[lidx(i, j)] = T(0);
             }
@@ -300,14 +299,14 @@ __device__ __forceinline__ void chol_solve4(const T* L, const T (&b)[4], T (&y)[
         T s = b[i];
 #pragma unroll
         for (int k = 0; k < i; ++k) s -= L[lidx(i, k)] * z[k];
-        z[i] = s / L[lidx(i, i)];
+        z[i] = s * L[10 + i];
     }
 #pragma unroll
     for (int i = 3; i >= 0; --i) {
         T s = z[i];
 #pragma unroll
         for (int k = i + 1; k < 4; ++k) s -= L[lidx(k, i)] * y[k];
-        y[i] = s / L[lidx(i, i)];
+        y[i] = s * L[10 + i];
     }
 }
 
@@ -334,14 +333,14 @@ __device__ __forceinline__ T qp_value(const T (&H)[4][4], const T (&g)[4], const
 // a non-positive pivot.  `L` and `mask` describe the last factored free set.
 template <typename T>
 __device__ bool box_qp(const T (&H)[4][4], const T (&g)[4], const T (&lo)[4], const T (&hi)[4],
-                       T (&d)[4], T (&L)[10], int& mask_out) {
+                       T (&d)[4], T (&L)[NL], int& mask_out) {
 #pragma unroll
     for (int i = 0; i < 4; ++i) d[i] = clampT(T(0), lo[i], hi[i]);
     int free_prev = -1, mask_fact = 0;
     bool last_full = false;
 #pragma unroll
-    for (int i = 0; i < 10; ++i) L[i] = T(0);
-    L[0] = L[2] = L[5] = L[9] = T(1);
+    for (int i = 0; i < NL; ++i) L[i] = T(0);
+    L[0] = L[2] = L[5] = L[9] = L[10] = L[11] = L[12] = L[13] = T(1);
     for (int it = 0; it < QP_MAX_IT; ++it) {
         T grad[4];
 #pragma unroll
@@ -359,8 +358,8 @@ __device__ bool box_qp(const T (&H)[4][4], const T (&g)[4], const T (&lo)[4], co
         }
         if (fm == 0) {
 #pragma unroll
-            for (int i = 0; i < 10; ++i) L[i] = T(0);
-            L[0] = L[2] = L[5] = L[9] = T(1);
+            for (int i = 0; i < NL; ++i) L[i] = T(0);
+            L[0] = L[2] = L[5] = L[9] = L[10] = L[11] = L[12] = L[13] = T(1);
             mask_out = 0;
             return true;
         }
@@ -398,13 +397,20 @@ __device__ bool box_qp(const T (&H)[4][4], const T (&g)[4], const T (&lo)[4], co
             step *= T(0.6);
         }
         if (!acc) { mask_out = mask_fact; return true; }
-        bool inside = true;
+        bool inside = true, strict = true;
 #pragma unroll
-        for (int i = 0; i < 4; ++i) inside = inside && (trial[i] >= lo[i]) && (trial[i] <= hi[i]);
+        for (int i = 0; i < 4; ++i) {
+            inside = inside && (trial[i] >= lo[i]) && (trial[i] <= hi[i]);
+            strict = strict && (trial[i] > lo[i]) && (trial[i] < hi[i]);
+        }
         last_full = (step == T(1)) && inside;
         free_prev = fm;
 #pragma unroll
         for (int i = 0; i < 4; ++i) d[i] = dnew[i];
+        // A full step strictly inside the box with every dimension free: no
+        // dimension sits on a bound at the new point, so the next iteration
+        // would find the same (full) free set and stop here.
+        if (last_full && strict && fm == 15) { mask_out = fm; return true; }
     }
     mask_out = mask_fact;
     return true;
@@ -506,29 +512,25 @@ __device__ T initial_rollout(const Params<T>& P, const Inst<T>& I, const WarpSme
 }
 
 // ------------------------------------------------------ A2 linearization ----
-// F_t = [A_t B_t] at the nominal for t = 0..n-2 into Fdst ([t][221], column-major):
-// lanes first take one stage each for the RK4 stage points, then one
-// (stage, column) tangent each.
+// F_t = [A_t B_t] at the nominal for t = 0..n-2 into Fdst ([t][221], column-major;
+// only the 11 computed columns are written): lanes first take one stage each
+// for the RK4 stage points, then one (stage, column) tangent each.
 template <typename T>
 __device__ void linearize(const Params<T>& P, const Inst<T>& I, T* Fdst, int lane) {
     const int ns = I.n - 1;
     for (int t = lane; t < ns; t += 32) {
-        T xs[NX], us[NU], sp[SP_STRIDE];
+        T xs[NX], us[NU];
 #pragma unroll
         for (int i = 0; i < NX; ++i) xs[i] = I.xb[t * NX + i];
 #pragma unroll
         for (int a = 0; a < NU; ++a) us[a] = I.ub[t * NU + a];
-        rk4_stage_points(P.mdl, xs, us, sp);
-#pragma unroll
-        for (int i = 0; i < SP_STRIDE; ++i) I.sp[t * SP_STRIDE + i] = sp[i];
+        rk4_stage_points(P.mdl, xs, us, I.sp + t * SP_STRIDE);
     }
     __syncwarp();
-    for (int w = lane; w < ns * NZ; w += 32) {
-        const int t = w / NZ, j = w - t * NZ;
-        T sp[SP_STRIDE], col[NX];
-#pragma unroll
-        for (int i = 0; i < SP_STRIDE; ++i) sp[i] = I.sp[t * SP_STRIDE + i];
-        tangent_column(P.mdl, sp, j, col);
+    for (int w = lane; w < ns * NGC; w += 32) {
+        const int t = w / NGC, j = gcol(w - t * NGC);
+        T col[NX];
+        tangent_column(P.mdl, I.sp + t * SP_STRIDE, j, col);
         T* dst = Fdst + (size_t)t * NF + j * NX;
 #pragma unroll
         for (int i = 0; i < NX; ++i) dst[i] = col[i];
@@ -563,6 +565,34 @@ __device__ bool riccati(const Params<T>& P, const Inst<T>& I, WarpSmem<T>& S, in
     const int n = I.n;
     for (int e = lane; e < NX * NX; e += 32) S.V[e] = T(0);
     if (lane < NX) { S.v[lane] = T(0); S.vh[lane] = T(0); }
+    // Software pipeline: the next stage's F_t columns and cost inputs are
+    // loaded into registers while the current stage computes.
+    constexpr int FR = (NGC * NX + 31) / 32;
+    T fpre[FR], cq = T(0), cz = T(0), cr = T(0), cl = T(0);
+    auto load_f = [&](int tt) {
+#pragma unroll
+        for (int r = 0; r < FR; ++r) {
+            const int e = lane + 32 * r;
+            if (e < NGC * NX) {
+                const int jj = e / NX, i = e - jj * NX, j = gcol(jj);
+                fpre[r] = I.F[(size_t)tt * NF + j * NX + i];
+            }
+        }
+    };
+    auto load_c = [&](int tt) {
+        if (lane < NX) {
+            cq = Qrow(P, I, tt)[lane];
+            cz = I.xb[tt * NX + lane];
+            cr = I.xrefb[tt * NX + lane];
+            if (o.use_lo) cl = I.xlo[tt * NX + lane];
+        } else if (lane < NZ) {
+            cz = I.ub[tt * NU + lane - NX];
+        }
+    };
+    if (!o.replay) {
+        load_c(n - 1);
+        if (n >= 2) load_f(n - 2);
+    }
     __syncwarp();
     for (int t = n - 1; t >= 0; --t) {
         const bool dyn = (t < n - 1);
@@ -577,50 +607,92 @@ __device__ bool riccati(const Params<T>& P, const Inst<T>& I, WarpSmem<T>& S, in
             if (lane == 0) S.mask = (int)rec[TAPE_MASK];
             __syncwarp();
         } else {
-            const T* Qt = Qrow(P, I, t);
             if (lane < NZ) {
                 T cd, e;
                 if (lane < NX) {
-                    cd = Qt[lane];
-                    e = I.xb[t * NX + lane] - I.xrefb[t * NX + lane];
-                    if (o.use_lo) e += I.xlo[t * NX + lane];
+                    cd = cq;
+                    e = cz - cr;
+                    if (o.use_lo) e += cl;
                 } else {
                     const int a = lane - NX;
                     cd = S.R[a];
-                    e = I.ub[t * NU + a] - S.uref[a];
+                    e = cz - S.uref[a];
                 }
                 S.Cd[lane] = cd;
                 S.c[lane] = cd * e;
             }
             if (dyn) {
-                const T* Ft = I.F + (size_t)t * NF;
-                for (int e = lane; e < NF; e += 32) S.F[e] = Ft[e];
+#pragma unroll
+                for (int r = 0; r < FR; ++r) {
+                    const int e = lane + 32 * r;
+                    if (e < NGC * NX) {
+                        const int jj = e / NX, i = e - jj * NX, j = gcol(jj);
+                        S.F[j * NX + i] = fpre[r];
+                    }
+                }
+                const T hv = hv_coef(P.mdl);
+                for (int e = lane; e < NTC * NX; e += 32) {
+                    const int jj = e / NX, i = e - jj * NX, j = tcol(jj);
+                    S.F[j * NX + i] = (i == j) ? T(1) : ((j >= 7 && i == j - 7) ? hv : T(0));
+                }
+            }
+            if (t >= 1) {
+                load_c(t - 1);
+                load_f(t - 1);
             }
             __syncwarp();
             if (dyn) {
-                // W = V F (column-major)
-                for (int e = lane; e < NF; e += 32) {
-                    const int j = e / NX, i = e - j * NX;
-                    T s = T(0);
+                const T hv = hv_coef(P.mdl);
+                // W = V F (column-major): 11 computed columns, then the constant ones
 #pragma unroll
-                    for (int k = 0; k < NX; ++k) s += S.V[i * NX + k] * S.F[j * NX + k];
-                    S.W[e] = s;
+                for (int r = 0; r < FR; ++r) {
+                    const int e = lane + 32 * r;
+                    if (e < NGC * NX) {
+                        const int jj = e / NX, i = e - jj * NX, j = gcol(jj);
+                        T s = T(0);
+#pragma unroll
+                        for (int k = 0; k < NX; ++k) s += S.V[i * NX + k] * S.F[j * NX + k];
+                        S.W[j * NX + i] = s;
+                    }
+                }
+#pragma unroll
+                for (int r = 0; r < (NTC * NX + 31) / 32; ++r) {
+                    const int e = lane + 32 * r;
+                    if (e < NTC * NX) {
+                        const int jj = e / NX, i = e - jj * NX, j = tcol(jj);
+                        S.W[j * NX + i] = (j < 3) ? S.V[i * NX + j] : S.V[i * NX + j] + hv * S.V[i * NX + j - 7];
+                    }
                 }
                 __syncwarp();
-                // Q = C + F' W (upper triangle, mirrored), q = c + F' v
-                for (int p = lane; p < NTRI_Q + NZ; p += 32) {
+                // Q = C + F' W (upper triangle), q = c + F' v; rows of the
+                // constant columns first need one or two terms
+#pragma unroll
+                for (int r = 0; r < (NTRI_Q + NZ + 31) / 32; ++r) {
+                    const int p = lane + 32 * r;
+                    if (p >= NTRI_Q + NZ) break;
                     if (p < NTRI_Q) {
                         const int ab = triQ[p], a = ab >> 8, bb = ab & 0xff;
                         T s = (a == bb) ? S.Cd[a] : T(0);
+                        if (a < 3) {
+                            s += S.W[bb * NX + a];
+                        } else if (a >= 7 && a < 10) {
+                            s += S.W[bb * NX + a] + hv * S.W[bb * NX + a - 7];
+                        } else {
 #pragma unroll
-                        for (int k = 0; k < NX; ++k) s += S.F[a * NX + k] * S.W[bb * NX + k];
+                            for (int k = 0; k < NX; ++k) s += S.F[a * NX + k] * S.W[bb * NX + k];
+                        }
                         S.Qm[a * NZ + bb] = s;
-                        S.Qm[bb * NZ + a] = s;
                     } else {
                         const int a = p - NTRI_Q;
                         T s = S.c[a];
+                        if (a < 3) {
+                            s += S.v[a];
+                        } else if (a >= 7 && a < 10) {
+                            s += S.v[a] + hv * S.v[a - 7];
+                        } else {
 #pragma unroll
-                        for (int k = 0; k < NX; ++k) s += S.F[a * NX + k] * S.v[k];
+                            for (int k = 0; k < NX; ++k) s += S.F[a * NX + k] * S.v[k];
+                        }
                         S.q[a] = s;
                     }
                 }
@@ -633,12 +705,13 @@ __device__ bool riccati(const Params<T>& P, const Inst<T>& I, WarpSmem<T>& S, in
             }
             __syncwarp();
             if (lane == 0) {
-                T H[4][4], g[4], lo[4], hi[4], d[4], L[10];
+                T H[4][4], g[4], lo[4], hi[4], d[4], L[NL];
                 int mask = 0;
 #pragma unroll
                 for (int a = 0; a < 4; ++a) {
 #pragma unroll
-                    for (int bb = 0; bb < 4; ++bb) H[a][bb] = S.Qm[(NX + a) * NZ + NX + bb];
+                    for (int bb = 0; bb < 4; ++bb)
+                        H[a][bb] = a <= bb ? S.Qm[(NX + a) * NZ + NX + bb] : S.Qm[(NX + bb) * NZ + NX + a];
                     g[a] = S.q[NX + a];
                     const T ub = I.ub[t * NU + a];
                     lo[a] = S.ulo[a] - ub;
@@ -648,7 +721,7 @@ __device__ bool riccati(const Params<T>& P, const Inst<T>& I, WarpSmem<T>& S, in
 #pragma unroll
                 for (int a = 0; a < 4; ++a) S.k[a] = d[a];
 #pragma unroll
-                for (int i = 0; i < 10; ++i) S.L[i] = L[i];
+                for (int i = 0; i < NL; ++i) S.L[i] = L[i];
                 S.mask = mask;
                 S.ok = ok ? 1 : 0;
             }
@@ -659,14 +732,17 @@ __device__ bool riccati(const Params<T>& P, const Inst<T>& I, WarpSmem<T>& S, in
             if (lane < NX) {
                 T rhs[4], y[4];
 #pragma unroll
-                for (int a = 0; a < 4; ++a) rhs[a] = ((mask >> a) & 1) ? S.Qm[(NX + a) * NZ + lane] : T(0);
+                for (int a = 0; a < 4; ++a) rhs[a] = ((mask >> a) & 1) ? S.Qm[lane * NZ + NX + a] : T(0);
                 chol_solve4(S.L, rhs, y);
 #pragma unroll
                 for (int a = 0; a < 4; ++a) S.K[a * NX + lane] = ((mask >> a) & 1) ? -y[a] : T(0);
             }
             __syncwarp();
             // V_t, v_t
-            for (int p = lane; p < NTRI_V + NX; p += 32) {
+#pragma unroll
+            for (int r = 0; r < (NTRI_V + NX + 31) / 32; ++r) {
+                const int p = lane + 32 * r;
+                if (p >= NTRI_V + NX) break;
                 if (p < NTRI_V) {
                     const int ij = triV[p], i = ij >> 8, j = ij & 0xff;
                     T s = S.Qm[i * NZ + j];
@@ -744,29 +820,52 @@ __device__ bool riccati(const Params<T>& P, const Inst<T>& I, WarpSmem<T>& S, in
 // candidate becomes the next nominal (Sec. IV-3).  Returns 0 (step taken: du,
 // J updated) or 1 (no candidate with a finite cost: nominal kept).
 template <typename T>
+__device__ __forceinline__ void ls_stage_load(const Params<T>& P, const Inst<T>& I, T* dst, int t, int e0, int step) {
+    const T* Qt = Qrow(P, I, t);
+    for (int e = e0; e < 112; e += step) {
+        T v;
+        if (e < KREC) v = I.Kr[(size_t)t * KREC + e];
+        else if (e < KREC + NX) v = I.xb[t * NX + e - KREC];
+        else if (e < KREC + 2 * NX) v = I.xlo[t * NX + e - KREC - NX];
+        else if (e < KREC + 2 * NX + NU) v = I.ub[t * NU + e - KREC - 2 * NX];
+        else if (e < KREC + 3 * NX + NU) v = Qt[e - KREC - 2 * NX - NU];
+        else v = I.xrefb[t * NX + e - KREC - 3 * NX - NU];
+        dst[e] = v;
+    }
+}
+
+template <typename T>
 __device__ int line_search(const Params<T>& P, const Inst<T>& I, WarpSmem<T>& S, int lane, T& Jnom, T& du_out) {
     const int n = I.n;
-    if (lane < P.n_alpha) {
-        const T alpha = P.alpha[lane];
-        T xh[NX], xl[NX], uh[NU];
+    // Each stage's gains, nominal and cost rows are staged into shared memory
+    // one stage ahead by the lanes that roll out no candidate.
+    ls_stage_load(P, I, S.stg[0], 0, lane, 32);
+    __syncwarp();
+    const T alpha = lane < P.n_alpha ? P.alpha[lane] : T(0);
+    T xh[NX], xl[NX], uh[NU];
 #pragma unroll
-        for (int i = 0; i < NX; ++i) { xh[i] = S.x0[i]; xl[i] = T(0); }
-        T dJ = T(0), dJl = T(0);
-        T* cd = I.cand + (size_t)lane * P.N_ws * CREC;
-        for (int t = 0; t < n; ++t) {
-            const T* kr = I.Kr + (size_t)t * KREC;
-            const T* Qt = Qrow(P, I, t);
-            const T* xr = I.xrefb + t * NX;
+    for (int i = 0; i < NX; ++i) { xh[i] = S.x0[i]; xl[i] = T(0); }
+    T dJ = T(0), dJl = T(0);
+    T* cd = I.cand + (size_t)(lane & 3) * P.N_ws * CREC;
+    for (int t = 0; t < n; ++t) {
+        if (lane < P.n_alpha) {
+            const T* sb = S.stg[t & 1];
+            const T* kr = sb;
+            const T* xbt = sb + KREC;
+            const T* xlt = sb + KREC + NX;
+            const T* ubt = sb + KREC + 2 * NX;
+            const T* Qt = sb + KREC + 2 * NX + NU;
+            const T* xr = sb + KREC + 3 * NX + NU;
             T dxv[NX];
 #pragma unroll
-            for (int i = 0; i < NX; ++i) dxv[i] = (xh[i] - I.xb[t * NX + i]) + (xl[i] - I.xlo[t * NX + i]);
+            for (int i = 0; i < NX; ++i) dxv[i] = (xh[i] - xbt[i]) + (xl[i] - xlt[i]);
             T sx = T(0), su = T(0);
 #pragma unroll
             for (int a = 0; a < NU; ++a) {
                 T s = T(0);
 #pragma unroll
                 for (int i = 0; i < NX; ++i) s += kr[a * NX + i] * dxv[i];
-                const T ub = I.ub[t * NU + a];
+                const T ub = ubt[a];
                 const T un = ub + alpha * kr[NU * NX + a] + s;
                 uh[a] = clampT(un, S.ulo[a], S.uhi[a]);
                 const T d = uh[a] - ub;
@@ -774,7 +873,7 @@ __device__ int line_search(const Params<T>& P, const Inst<T>& I, WarpSmem<T>& S,
             }
 #pragma unroll
             for (int i = 0; i < NX; ++i) {
-                const T eb = (I.xb[t * NX + i] - xr[i]) + I.xlo[t * NX + i];
+                const T eb = (xbt[i] - xr[i]) + xlt[i];
                 sx += dxv[i] * (Qt[i] * (eb + T(0.5) * dxv[i]));
             }
             acc2(dJ, dJl, sx + su);
@@ -783,7 +882,12 @@ __device__ int line_search(const Params<T>& P, const Inst<T>& I, WarpSmem<T>& S,
 #pragma unroll
             for (int a = 0; a < NU; ++a) cd[t * CREC + 2 * NX + a] = uh[a];
             if (t < n - 1) rk4_step2(P.mdl, xh, xl, uh);
+        } else if (lane >= 4 && t + 1 < n) {
+            ls_stage_load(P, I, S.stg[(t + 1) & 1], t + 1, lane - 4, 28);
         }
+        __syncwarp();
+    }
+    if (lane < P.n_alpha) {
         dJ = dJ + dJl;
         S.Jc[lane] = finiteT(dJ) ? dJ : T(INFINITY);
     }
@@ -793,11 +897,11 @@ __device__ int line_search(const Params<T>& P, const Inst<T>& I, WarpSmem<T>& S,
     for (int c = 1; c < P.n_alpha; ++c)
         if (S.Jc[c] < Jb) { Jb = S.Jc[c]; best = c; }
     if (!finiteT(Jb)) return 1;
-    const T* cd = I.cand + (size_t)best * P.N_ws * CREC;
+    const T* cb = I.cand + (size_t)best * P.N_ws * CREC;
     T dmax = T(0);
     for (int e = lane; e < n * CREC; e += 32) {
         const int t = e / CREC, j = e - t * CREC;
-        const T val = cd[e];
+        const T val = cb[e];
         if (j < NX) {
             I.xb[t * NX + j] = val;
         } else if (j < 2 * NX) {
@@ -854,10 +958,15 @@ __device__ void adjoint_forward(const Params<T>& P, const Inst<T>& I, WarpSmem<T
             const T* Ft = Fsrc + (size_t)t * fs;
             T s = T(0);
             if (lane < NX) {
+                // dx_{t+1} = F_t [dx_t; du_t]: the 11 computed columns, then the
+                // constant p and v columns
 #pragma unroll
-                for (int k = 0; k < NX; ++k) s += Ft[k * NX + lane] * S.dx[k];
-#pragma unroll
-                for (int a = 0; a < NU; ++a) s += Ft[(NX + a) * NX + lane] * S.du[a];
+                for (int jj = 0; jj < NGC; ++jj) {
+                    const int j = gcol(jj);
+                    s += Ft[j * NX + lane] * (j < NX ? S.dx[j] : S.du[j - NX]);
+                }
+                if (lane < 3) s += S.dx[lane] + hv_coef(P.mdl) * S.dx[lane + 7];
+                else if (lane >= 7 && lane < 10) s += S.dx[lane];
             }
             __syncwarp();
             if (lane < NX) S.dx[lane] = s;

@@ -38,11 +38,23 @@ enum Phase {
 };
 constexpr int MODE_FWD = -1, MODE_BWD = -2;
 
+// Upper-triangle index tables.  Q's entries are ordered rows of the computed
+// columns of F first (13-term dot products), then the rows of the constant
+// p and v columns (one or two terms), so that a round of lanes mostly runs
+// the same branch.
 __device__ void init_tables(int* triQ, int* triV) {
     for (int p = threadIdx.x; p < NTRI_Q; p += blockDim.x) {
-        int a = 0, r = p;
-        while (r >= NZ - a) { r -= NZ - a; ++a; }
-        triQ[p] = (a << 8) | (a + r);
+        int r = p, q = 0;
+        for (int pass = 0; pass < 2; ++pass) {
+            for (int a = 0; a < NZ; ++a) {
+                const bool constant_row = a < 3 || (a >= 7 && a < 10);
+                if (constant_row != (pass == 1)) continue;
+                const int len = NZ - a;
+                if (r < len) { triQ[p] = (a << 8) | (a + r); q = 1; break; }
+                r -= len;
+            }
+            if (q) break;
+        }
     }
     for (int p = threadIdx.x; p < NTRI_V; p += blockDim.x) {
         int a = 0, r = p;
@@ -74,7 +86,7 @@ __device__ void zero_grads(const Params<T>& P, const AdjArgs<T>& A, int b, int l
 // mode == MODE_FWD / MODE_BWD: persistent forward / backward over the work queue.
 // `last`: the plain line-search launch of the final iteration.
 template <typename T>
-__global__ void __launch_bounds__(256, 3) k_mpc(Params<T> P, AdjArgs<T> A, int mode, int last) {
+__global__ void __launch_bounds__(256, 2) k_mpc(Params<T> P, AdjArgs<T> A, int mode, int last) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int triQ[NTRI_Q], triV[NTRI_V];
     init_tables(triQ, triV);

@@ -51,7 +51,7 @@ def run_gpu(prob, dtype, max_iter, tol, grad_u=None, grad_x=None, store_mode="st
     s = solver.solve(p)
     out = dict(u=s.u, x=s.x, cost=s.cost, iters=s.iters, status=s.status)
     if s.tape is not None:
-        out["masks"] = s.tape.view(B, N, 288)[:, :, 283].to(torch.int32)
+        out["masks"] = s.tape.view(B, N, 288)[:, :, 287].to(torch.int32)
     if grad_u is not None:
         gu = torch.as_tensor(grad_u, dtype=dtype, device="cuda")
         gx = None if grad_x is None else torch.as_tensor(grad_x, dtype=dtype, device="cuda")
