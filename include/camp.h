@@ -88,8 +88,9 @@ typedef struct mpc_config {
     double alpha[4];        /* coefficients in (0, 1], default {1, .5, .25, .1}        */
     int    store_mode;      /* MPC_STORE_ALL or MPC_RECOMPUTE                          */
     int    exec_mode;       /* MPC_EXEC_PERSISTENT or MPC_EXEC_PLAIN                   */
-    int    tpi;             /* threads per instance: 0 (auto) or 32                    */
-    int    ipb;             /* instances per block: 0 (auto) or 1, 2, 4, 8             */
+    int    tpi;             /* threads per instance: 0 (auto = 16), 8, 16 or 32        */
+    int    ipb;             /* instances per block: 0 (auto) or 1..32 (power of 2),    */
+                            /* with tpi * ipb a multiple of 32 between 32 and 256       */
 } mpc_config;
 
 typedef struct mpc_problem {
@@ -153,9 +154,11 @@ int mpc_solve_bwd(mpc_handle *h, const mpc_problem *p, const mpc_solution *s,
                   const void *grad_u, const void *grad_x,
                   void *dQ, void *dx_ref, void *dx0, cudaStream_t stream);
 
-/* Time the persistent forward for each instances-per-block choice on this
- * problem (overwriting *s), keep the fastest in the handle and report it in
- * *ipb_out (may be NULL).  Synchronises `stream`; not capturable. */
+/* Time the persistent forward for each launch shape (threads per instance x
+ * instances per block; a nonzero tpi or ipb in the config pins that value) on
+ * this problem (overwriting *s), keep the fastest in the handle and report its
+ * ipb in *ipb_out (may be NULL; mpc_launch_shape gives the whole shape).
+ * Synchronises `stream`; not capturable. */
 int mpc_autotune(mpc_handle *h, const mpc_problem *p, mpc_solution *s,
                  cudaStream_t stream, int *ipb_out);
 

@@ -19,7 +19,8 @@ struct mpc_handle {
     void *wsF, *wsK, *wsCand, *wsSP, *wsKh, *wsXlo;
     int* queue;             // [2] work-queue tickets (forward, backward)
     int* order;             // [B_max] longest-horizon-first order
-    int ipb;                // instances per block of the persistent kernels
+    int tpi;                // threads per instance
+    int ipb;                // instances per block
 };
 
 static size_t elem_size(int dtype) { return dtype == MPC_F64 ? sizeof(double) : sizeof(float); }
@@ -72,8 +73,10 @@ static int validate_config(const mpc_config* c) {
         if (!(c->alpha[i] > 0.0 && c->alpha[i] <= 1.0)) return MPC_ERR_ARG;
     if (c->store_mode != MPC_STORE_ALL && c->store_mode != MPC_RECOMPUTE) return MPC_ERR_ARG;
     if (c->exec_mode != MPC_EXEC_PERSISTENT && c->exec_mode != MPC_EXEC_PLAIN) return MPC_ERR_ARG;
-    if (c->tpi != 0 && c->tpi != 32) return MPC_ERR_ARG;
-    if (c->ipb != 0 && c->ipb != 1 && c->ipb != 2 && c->ipb != 4 && c->ipb != 8) return MPC_ERR_ARG;
+    if (c->tpi != 0 && c->tpi != 8 && c->tpi != 16 && c->tpi != 32) return MPC_ERR_ARG;
+    if (c->ipb != 0 && c->ipb != 1 && c->ipb != 2 && c->ipb != 4 && c->ipb != 8 && c->ipb != 16 && c->ipb != 32)
+        return MPC_ERR_ARG;
+    if (c->tpi && c->ipb && !shape_ok(c->tpi, c->ipb)) return MPC_ERR_ARG;
     return MPC_OK;
 }
 
@@ -85,7 +88,9 @@ extern "C" int mpc_create(const mpc_config* cfg, mpc_handle** out) {
     mpc_handle* h = (mpc_handle*)calloc(1, sizeof(mpc_handle));
     if (!h) return MPC_ERR_CUDA;
     h->cfg = *cfg;
-    h->ipb = cfg->ipb ? cfg->ipb : 4;
+    h->tpi = cfg->tpi ? cfg->tpi : 16;
+    h->ipb = cfg->ipb ? cfg->ipb : 128 / h->tpi;
+    if (!shape_ok(h->tpi, h->ipb)) h->ipb = 64 / h->tpi;
     if (cudaGetDevice(&h->device) != cudaSuccess) { free(h); return MPC_ERR_CUDA; }
     if (cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device) != cudaSuccess) {
         free(h);
@@ -93,7 +98,7 @@ extern "C" int mpc_create(const mpc_config* cfg, mpc_handle** out) {
     }
     const cudaError_t pe = cfg->dtype == MPC_F64 ? prepare_kernels<double>() : prepare_kernels<float>();
     if (pe != cudaSuccess) { free(h); return MPC_ERR_CUDA; }
-    const int resident = h->num_sms * 64;
+    const int resident = h->num_sms * 64;        // instances resident at once (128 registers, 8 lanes each)
     h->slots = cfg->B_max > resident ? cfg->B_max : resident;
     const size_t es = elem_size(cfg->dtype);
     const size_t S = (size_t)h->slots, Nw = (size_t)cfg->N_max;
@@ -135,9 +140,9 @@ extern "C" size_t mpc_tape_bytes(const mpc_handle* h, int B, int N) {
     return (size_t)B * N * TAPE_STRIDE * elem_size(h->cfg.dtype);
 }
 
-static int grid_for(const mpc_handle* h, int B, int which) {
-    const int bps = h->cfg.dtype == MPC_F64 ? persistent_blocks_per_sm<double>(h->ipb, which)
-                                            : persistent_blocks_per_sm<float>(h->ipb, which);
+static int grid_for(const mpc_handle* h, int B) {
+    const int bps = h->cfg.dtype == MPC_F64 ? persistent_blocks_per_sm<double>(h->tpi, h->ipb)
+                                            : persistent_blocks_per_sm<float>(h->tpi, h->ipb);
     long long g = (long long)(bps > 0 ? bps : 1) * h->num_sms;
     const long long need = (B + h->ipb - 1) / h->ipb;
     if (g > need) g = need;
@@ -229,10 +234,10 @@ extern "C" int mpc_solve_fwd(mpc_handle* h, const mpc_problem* p, mpc_solution* 
     cudaError_t e;
     if (h->cfg.dtype == MPC_F64) {
         const Params<double> P = make_params<double>(h, p, s);
-        e = launch_forward<double>(P, h->cfg.exec_mode, h->ipb, grid_for(h, p->B, 0), h->order, stream);
+        e = launch_forward<double>(P, h->cfg.exec_mode, h->tpi, h->ipb, grid_for(h, p->B), h->order, stream);
     } else {
         const Params<float> P = make_params<float>(h, p, s);
-        e = launch_forward<float>(P, h->cfg.exec_mode, h->ipb, grid_for(h, p->B, 0), h->order, stream);
+        e = launch_forward<float>(P, h->cfg.exec_mode, h->tpi, h->ipb, grid_for(h, p->B), h->order, stream);
     }
     return e == cudaSuccess ? MPC_OK : MPC_ERR_CUDA;
 }
@@ -251,12 +256,12 @@ extern "C" int mpc_solve_bwd(mpc_handle* h, const mpc_problem* p, const mpc_solu
         const Params<double> P = make_params<double>(h, p, s);
         AdjArgs<double> A{(const double*)grad_u, (const double*)grad_x, (double*)dQ, (double*)dx_ref,
                           (double*)dx0, recompute};
-        e = launch_backward<double>(P, A, h->ipb, grid_for(h, p->B, 1), h->order, stream);
+        e = launch_backward<double>(P, A, h->tpi, h->ipb, grid_for(h, p->B), h->order, stream);
     } else {
         const Params<float> P = make_params<float>(h, p, s);
         AdjArgs<float> A{(const float*)grad_u, (const float*)grad_x, (float*)dQ, (float*)dx_ref, (float*)dx0,
                          recompute};
-        e = launch_backward<float>(P, A, h->ipb, grid_for(h, p->B, 1), h->order, stream);
+        e = launch_backward<float>(P, A, h->tpi, h->ipb, grid_for(h, p->B), h->order, stream);
     }
     return e == cudaSuccess ? MPC_OK : MPC_ERR_CUDA;
 }
@@ -267,36 +272,42 @@ extern "C" int mpc_autotune(mpc_handle* h, const mpc_problem* p, mpc_solution* s
     if (r != MPC_OK) return r;
     if (h->cfg.exec_mode != MPC_EXEC_PERSISTENT) return MPC_ERR_STATE;
     if (p->B == 0) { if (ipb_out) *ipb_out = h->ipb; return MPC_OK; }
-    const int cands[4] = {1, 2, 4, 8};
-    const int keep = h->ipb;
+    const int keep_tpi = h->tpi, keep_ipb = h->ipb;
+    const int tpis[3] = {8, 16, 32};
     float best_ms = 3.0e38f;
-    int best = keep;
+    int best_tpi = keep_tpi, best_ipb = keep_ipb;
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess) return MPC_ERR_CUDA;
     if (cudaEventCreate(&e1) != cudaSuccess) { cudaEventDestroy(e0); return MPC_ERR_CUDA; }
-    for (int ci = 0; ci < 4; ++ci) {
-        h->ipb = cands[ci];
-        if ((r = mpc_solve_fwd(h, p, s, stream)) != MPC_OK) break;          // warm-up
-        cudaEventRecord(e0, stream);
-        for (int rep = 0; rep < 3 && r == MPC_OK; ++rep) r = mpc_solve_fwd(h, p, s, stream);
-        cudaEventRecord(e1, stream);
-        if (r != MPC_OK || cudaEventSynchronize(e1) != cudaSuccess) { r = MPC_ERR_CUDA; break; }
-        float ms = 0.f;
-        cudaEventElapsedTime(&ms, e0, e1);
-        if (ms < best_ms) { best_ms = ms; best = cands[ci]; }
+    for (int ti = 0; ti < 3 && r == MPC_OK; ++ti) {
+        if (h->cfg.tpi && h->cfg.tpi != tpis[ti]) continue;
+        for (int ipb = 1; ipb <= 32 && r == MPC_OK; ipb *= 2) {
+            if (!shape_ok(tpis[ti], ipb) || (h->cfg.ipb && h->cfg.ipb != ipb)) continue;
+            h->tpi = tpis[ti];
+            h->ipb = ipb;
+            if ((r = mpc_solve_fwd(h, p, s, stream)) != MPC_OK) break;          // warm-up
+            cudaEventRecord(e0, stream);
+            for (int rep = 0; rep < 3 && r == MPC_OK; ++rep) r = mpc_solve_fwd(h, p, s, stream);
+            cudaEventRecord(e1, stream);
+            if (r != MPC_OK || cudaEventSynchronize(e1) != cudaSuccess) { r = MPC_ERR_CUDA; break; }
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (ms < best_ms) { best_ms = ms; best_tpi = tpis[ti]; best_ipb = ipb; }
+        }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    h->ipb = (r == MPC_OK) ? best : keep;
+    h->tpi = r == MPC_OK ? best_tpi : keep_tpi;
+    h->ipb = r == MPC_OK ? best_ipb : keep_ipb;
     if (ipb_out) *ipb_out = h->ipb;
     return r;
 }
 
 extern "C" int mpc_launch_shape(const mpc_handle* h, int B, int N, int* tpi, int* ipb, int* grid) {
     if (!h || B < 0 || N < 1 || N > h->cfg.N_max) return MPC_ERR_ARG;
-    if (tpi) *tpi = 32;
+    if (tpi) *tpi = h->tpi;
     if (ipb) *ipb = h->ipb;
-    if (grid) *grid = B > 0 ? grid_for(h, B, 0) : 0;
+    if (grid) *grid = B > 0 ? grid_for(h, B) : 0;
     return MPC_OK;
 }
 

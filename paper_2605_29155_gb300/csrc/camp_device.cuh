@@ -2,12 +2,13 @@
 // layer (box-constrained iLQR forward, adjoint LQR backward), templated on the
 // working precision T (float on the product path, double for logic checks).
 //
-// Mapping: one warp (32 lanes) owns one MPC instance at a time.  The warp's
-// matrices live in a per-warp shared-memory record (WarpSmem); every matrix
-// product of the Riccati recursion is split over the lanes by output entry;
-// the per-stage box QP runs on lane 0; the line search rolls out each alpha on
-// its own lane.  Per-instance trajectories, gains and Jacobians that outlive a
-// phase live in a global scratch "slot" owned by the warp (L2-resident).
+// Mapping: a group of TPI lanes (8, 16 or 32) owns one MPC instance; a warp
+// runs 32 / TPI instances in lockstep.  Each instance's matrices live in its
+// shared-memory record (WarpSmem); every matrix product of the Riccati
+// recursion is split over the group's lanes by output entry; the per-stage box
+// QP runs on one lane; the line search rolls out each alpha on its own lane.
+// Per-instance trajectories, gains and Jacobians that outlive a phase live in
+// a global scratch "slot" owned by the group (L2-resident).
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -57,7 +58,7 @@ template <typename T> struct AdjArgs {
     int recompute;
 };
 
-// Per-warp shared-memory record.
+// Per-instance shared-memory record.
 template <typename T> struct WarpSmem {
     T V[NX * NX];      // value Hessian V_{t+1} (full symmetric storage)
     T v[NX];           // value gradient v_{t+1}
@@ -416,6 +417,35 @@ __device__ bool box_qp(const T (&H)[4][4], const T (&g)[4], const T (&lo)[4], co
     return true;
 }
 
+// ------------------------------------------------------------ lanes --------
+// An instance is owned by a group of TPI consecutive lanes of a warp; a warp
+// holds PACK = 32 / TPI instances and runs them in lockstep.  Every loop that
+// contains a warp barrier runs a warp-uniform number of times (the largest
+// horizon in the pack); each group does its own instance's share under a
+// per-group predicate.  Per-instance arithmetic is the same for every TPI:
+// each output entry is produced by one lane, in the same order of operations.
+template <int TPI> struct Lanes {
+    static constexpr int PACK = 32 / TPI;
+    int lane, g, l;
+    __device__ __forceinline__ Lanes() {
+        lane = threadIdx.x & 31;
+        g = lane / TPI;
+        l = lane - g * TPI;
+    }
+    __device__ __forceinline__ int src(int sub) const { return g * TPI + sub; }
+};
+
+__device__ __forceinline__ void wsync() { __syncwarp(); }
+
+__device__ __forceinline__ int warp_max(int v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const int w = __shfl_xor_sync(FULL, v, o);
+        v = w > v ? w : v;
+    }
+    return v;
+}
+
 // ------------------------------------------------------------ helpers -------
 template <typename T> struct Inst {
     int b, n, slot;
@@ -425,19 +455,21 @@ template <typename T> struct Inst {
     T* xb;            // nominal / output x  [N][13]
     T* F;             // slot scratch: F_t   [N_ws][221]
     T* Kr;            // slot scratch: K_t,k_t [N_ws][56]
-    T* cand;          // slot scratch: candidates [4][N_ws][17]
+    T* cand;          // slot scratch: candidates [4][N_ws][30]
     T* sp;            // slot scratch: stage points [N_ws][32]
     T* kh;            // slot scratch: adjoint k-hat [N_ws][4]
     T* xlo;           // slot scratch: low part of the nominal state [N_ws][13]
 };
 
+// Instance b in scratch slot `slot`; `valid` false gives an empty instance
+// (n = 0) whose pointers are never dereferenced.
 template <typename T>
-__device__ __forceinline__ Inst<T> make_inst(const Params<T>& P, int b, int slot) {
+__device__ __forceinline__ Inst<T> make_inst(const Params<T>& P, int b, int slot, bool valid) {
     Inst<T> I;
     I.b = b;
     int n = P.horizon ? P.horizon[b] : P.N;
     n = n < 1 ? 1 : (n > P.N ? P.N : n);
-    I.n = n;
+    I.n = valid ? n : 0;
     I.slot = slot;
     I.Qb = P.Q + (size_t)b * P.Nq * NX;
     I.xrefb = P.xref + (size_t)b * P.N * NX;
@@ -458,67 +490,74 @@ __device__ __forceinline__ const T* Qrow(const Params<T>& P, const Inst<T>& I, i
     return I.Qb + (P.Nq > 1 ? t : 0) * NX;
 }
 
-template <typename T>
-__device__ __forceinline__ void load_instance(const Params<T>& P, const Inst<T>& I, WarpSmem<T>& S, int lane) {
-    if (lane < NX) S.x0[lane] = P.x0[(size_t)I.b * NX + lane];
-    if (lane < NU) {
-        S.R[lane] = P.R[I.b * NU + lane];
-        S.uref[lane] = P.uref[I.b * NU + lane];
-        S.ulo[lane] = P.ulo[I.b * NU + lane];
-        S.uhi[lane] = P.uhi[I.b * NU + lane];
+template <typename T, int TPI>
+__device__ __forceinline__ void load_instance(const Params<T>& P, const Inst<T>& I, WarpSmem<T>& S,
+                                              const Lanes<TPI>& L, bool act) {
+    if (act) {
+        for (int e = L.l; e < NX; e += TPI) S.x0[e] = P.x0[(size_t)I.b * NX + e];
+        for (int e = L.l; e < 4 * NU; e += TPI) {
+            const int w = e >> 2, a = e & 3;
+            const T* src = w == 0 ? P.R : (w == 1 ? P.uref : (w == 2 ? P.ulo : P.uhi));
+            T* dst = w == 0 ? S.R : (w == 1 ? S.uref : (w == 2 ? S.ulo : S.uhi));
+            dst[a] = src[I.b * NU + a];
+        }
     }
-    __syncwarp();
+    wsync();
 }
 
 // --------------------------------------------------------- A1 rollout -------
-// U^0 = clamp(u_init or u_ref), X^0 by RK4 from x_init (lane 0), J^0.  States
+// U^0 = clamp(u_init or u_ref), X^0 by RK4 from x_init (one lane), J^0.  States
 // are carried as hi + lo (rk4_step2); hi is the output x, lo stays in the slot.
-// Stages past the horizon are zero-filled.  Returns J^0 on every lane.
-template <typename T>
-__device__ T initial_rollout(const Params<T>& P, const Inst<T>& I, const WarpSmem<T>& S, int lane) {
-    const int n = I.n;
-    for (int e = n * NU + lane; e < P.N * NU; e += 32) I.ub[e] = T(0);
-    for (int e = n * NX + lane; e < P.N * NX; e += 32) I.xb[e] = T(0);
+// Stages past the horizon are zero-filled.  Returns J^0 on every lane of the group.
+template <typename T, int TPI>
+__device__ T initial_rollout(const Params<T>& P, const Inst<T>& I, const WarpSmem<T>& S, const Lanes<TPI>& L,
+                             bool act) {
     T J = T(0);
-    if (lane == 0) {
-        T xh[NX], xl[NX], us[NU];
+    if (act) {
+        const int n = I.n;
+        for (int e = n * NU + L.l; e < P.N * NU; e += TPI) I.ub[e] = T(0);
+        for (int e = n * NX + L.l; e < P.N * NX; e += TPI) I.xb[e] = T(0);
+        if (L.l == 0) {
+            T xh[NX], xl[NX], us[NU];
 #pragma unroll
-        for (int i = 0; i < NX; ++i) { xh[i] = S.x0[i]; xl[i] = T(0); }
-        for (int t = 0; t < n; ++t) {
+            for (int i = 0; i < NX; ++i) { xh[i] = S.x0[i]; xl[i] = T(0); }
+            for (int t = 0; t < n; ++t) {
 #pragma unroll
-            for (int a = 0; a < NU; ++a) {
-                const T u0 = P.uinit ? P.uinit[((size_t)I.b * P.N + t) * NU + a] : S.uref[a];
-                us[a] = clampT(u0, S.ulo[a], S.uhi[a]);
-                I.ub[t * NU + a] = us[a];
+                for (int a = 0; a < NU; ++a) {
+                    const T u0 = P.uinit ? P.uinit[((size_t)I.b * P.N + t) * NU + a] : S.uref[a];
+                    us[a] = clampT(u0, S.ulo[a], S.uhi[a]);
+                    I.ub[t * NU + a] = us[a];
+                }
+                const T* Qt = Qrow(P, I, t);
+                const T* xr = I.xrefb + t * NX;
+                T sx = T(0), su = T(0);
+#pragma unroll
+                for (int i = 0; i < NX; ++i) {
+                    I.xb[t * NX + i] = xh[i];
+                    I.xlo[t * NX + i] = xl[i];
+                    const T e = (xh[i] - xr[i]) + xl[i];
+                    sx += e * (Qt[i] * e);
+                }
+#pragma unroll
+                for (int a = 0; a < NU; ++a) { const T e = us[a] - S.uref[a]; su += e * (S.R[a] * e); }
+                J += T(0.5) * sx + T(0.5) * su;
+                if (t < n - 1) rk4_step2(P.mdl, xh, xl, us);
             }
-            const T* Qt = Qrow(P, I, t);
-            const T* xr = I.xrefb + t * NX;
-            T sx = T(0), su = T(0);
-#pragma unroll
-            for (int i = 0; i < NX; ++i) {
-                I.xb[t * NX + i] = xh[i];
-                I.xlo[t * NX + i] = xl[i];
-                const T e = (xh[i] - xr[i]) + xl[i];
-                sx += e * (Qt[i] * e);
-            }
-#pragma unroll
-            for (int a = 0; a < NU; ++a) { const T e = us[a] - S.uref[a]; su += e * (S.R[a] * e); }
-            J += T(0.5) * sx + T(0.5) * su;
-            if (t < n - 1) rk4_step2(P.mdl, xh, xl, us);
         }
     }
-    __syncwarp();
-    return __shfl_sync(FULL, J, 0);
+    wsync();
+    return __shfl_sync(FULL, J, L.src(0));
 }
 
 // ------------------------------------------------------ A2 linearization ----
-// F_t = [A_t B_t] at the nominal for t = 0..n-2 into Fdst ([t][221], column-major;
-// only the 11 computed columns are written): lanes first take one stage each
-// for the RK4 stage points, then one (stage, column) tangent each.
-template <typename T>
-__device__ void linearize(const Params<T>& P, const Inst<T>& I, T* Fdst, int lane) {
-    const int ns = I.n - 1;
-    for (int t = lane; t < ns; t += 32) {
+// F_t = [A_t B_t] at the nominal for t = 0..n-2 into the slot ([t][221],
+// column-major; only the 11 computed columns are written): the group's lanes
+// first take one stage each for the RK4 stage points, then one
+// (stage, column) tangent each.
+template <typename T, int TPI>
+__device__ void linearize(const Params<T>& P, const Inst<T>& I, const Lanes<TPI>& L, bool act) {
+    const int ns = act ? I.n - 1 : 0;
+    for (int t = L.l; t < ns; t += TPI) {
         T xs[NX], us[NU];
 #pragma unroll
         for (int i = 0; i < NX; ++i) xs[i] = I.xb[t * NX + i];
@@ -526,16 +565,16 @@ __device__ void linearize(const Params<T>& P, const Inst<T>& I, T* Fdst, int lan
         for (int a = 0; a < NU; ++a) us[a] = I.ub[t * NU + a];
         rk4_stage_points(P.mdl, xs, us, I.sp + t * SP_STRIDE);
     }
-    __syncwarp();
-    for (int w = lane; w < ns * NGC; w += 32) {
+    wsync();
+    for (int w = L.l; w < ns * NGC; w += TPI) {
         const int t = w / NGC, j = gcol(w - t * NGC);
         T col[NX];
         tangent_column(P.mdl, I.sp + t * SP_STRIDE, j, col);
-        T* dst = Fdst + (size_t)t * NF + j * NX;
+        T* dst = I.F + (size_t)t * NF + j * NX;
 #pragma unroll
         for (int i = 0; i < NX; ++i) dst[i] = col[i];
     }
-    __syncwarp();
+    wsync();
 }
 
 // ---------------------------------------------- A3 Riccati with box QP ------
@@ -552,6 +591,8 @@ __device__ void linearize(const Params<T>& P, const Inst<T>& I, T* Fdst, int lan
 //   adj      after each stage, the adjoint backward step (Sec. IV implicit
 //            differentiation) on that stage's factorization:
 //              qh = g_t + F_t' vh_{t+1};  kh_t = -(Q_uu,ff)^-1 qh_u,f;  vh_t = qh_x + K_t' qh_u
+// Returns false (for the group) when a free block of Q_uu is not positive
+// definite; the group's remaining stages are then skipped.
 template <typename T> struct RicOpts {
     T* tape;
     const AdjArgs<T>* adj;
@@ -559,117 +600,81 @@ template <typename T> struct RicOpts {
     bool use_lo;
 };
 
-template <typename T>
-__device__ bool riccati(const Params<T>& P, const Inst<T>& I, WarpSmem<T>& S, int lane,
-                        const int* triQ, const int* triV, const RicOpts<T> o) {
-    const int n = I.n;
-    for (int e = lane; e < NX * NX; e += 32) S.V[e] = T(0);
-    if (lane < NX) { S.v[lane] = T(0); S.vh[lane] = T(0); }
-    // Software pipeline: the next stage's F_t columns and cost inputs are
-    // loaded into registers while the current stage computes.
-    constexpr int FR = (NGC * NX + 31) / 32;
-    T fpre[FR], cq = T(0), cz = T(0), cr = T(0), cl = T(0);
-    auto load_f = [&](int tt) {
-#pragma unroll
-        for (int r = 0; r < FR; ++r) {
-            const int e = lane + 32 * r;
-            if (e < NGC * NX) {
-                const int jj = e / NX, i = e - jj * NX, j = gcol(jj);
-                fpre[r] = I.F[(size_t)tt * NF + j * NX + i];
-            }
-        }
-    };
-    auto load_c = [&](int tt) {
-        if (lane < NX) {
-            cq = Qrow(P, I, tt)[lane];
-            cz = I.xb[tt * NX + lane];
-            cr = I.xrefb[tt * NX + lane];
-            if (o.use_lo) cl = I.xlo[tt * NX + lane];
-        } else if (lane < NZ) {
-            cz = I.ub[tt * NU + lane - NX];
-        }
-    };
-    if (!o.replay) {
-        load_c(n - 1);
-        if (n >= 2) load_f(n - 2);
-    }
-    __syncwarp();
-    for (int t = n - 1; t >= 0; --t) {
-        const bool dyn = (t < n - 1);
+template <typename T, int TPI>
+__device__ bool riccati(const Params<T>& P, const Inst<T>& I, WarpSmem<T>& S, const Lanes<TPI>& L,
+                        const int* triQ, const int* triV, const RicOpts<T> o, bool act) {
+    const int n = act ? I.n : 0;
+    const int nmax = warp_max(n);
+    for (int e = L.l; e < NX * NX; e += TPI) S.V[e] = T(0);
+    for (int e = L.l; e < NX; e += TPI) { S.v[e] = T(0); S.vh[e] = T(0); }
+    if (L.l == 0) S.ok = 1;
+    const T hv = hv_coef(P.mdl);
+    bool alive = true;
+    wsync();
+    for (int t = nmax - 1; t >= 0; --t) {
+        const bool on = alive && t < n;
+        const bool dyn = on && t < n - 1;
+        bool go = on;
         if (o.replay) {
-            const T* rec = P.tape + ((size_t)I.b * P.N + t) * TAPE_STRIDE;
-            for (int e = lane; e < TAPE_MASK; e += 32) {
-                const T val = rec[e];
-                if (e < TAPE_K) S.F[e] = val;
-                else if (e < TAPE_L) S.K[e - TAPE_K] = val;
-                else S.L[e - TAPE_L] = val;
-            }
-            if (lane == 0) S.mask = (int)rec[TAPE_MASK];
-            __syncwarp();
-        } else {
-            if (lane < NZ) {
-                T cd, e;
-                if (lane < NX) {
-                    cd = cq;
-                    e = cz - cr;
-                    if (o.use_lo) e += cl;
-                } else {
-                    const int a = lane - NX;
-                    cd = S.R[a];
-                    e = cz - S.uref[a];
+            if (on) {
+                const T* rec = P.tape + ((size_t)I.b * P.N + t) * TAPE_STRIDE;
+                for (int e = L.l; e < TAPE_MASK; e += TPI) {
+                    const T val = rec[e];
+                    if (e < TAPE_K) S.F[e] = val;
+                    else if (e < TAPE_L) S.K[e - TAPE_K] = val;
+                    else S.L[e - TAPE_L] = val;
                 }
-                S.Cd[lane] = cd;
-                S.c[lane] = cd * e;
+                if (L.l == 0) S.mask = (int)rec[TAPE_MASK];
+            }
+            wsync();
+        } else {
+            if (on) {
+                const T* Qt = Qrow(P, I, t);
+                for (int a = L.l; a < NZ; a += TPI) {
+                    T cd, e;
+                    if (a < NX) {
+                        cd = Qt[a];
+                        e = I.xb[t * NX + a] - I.xrefb[t * NX + a];
+                        if (o.use_lo) e += I.xlo[t * NX + a];
+                    } else {
+                        cd = S.R[a - NX];
+                        e = I.ub[t * NU + a - NX] - S.uref[a - NX];
+                    }
+                    S.Cd[a] = cd;
+                    S.c[a] = cd * e;
+                }
             }
             if (dyn) {
-#pragma unroll
-                for (int r = 0; r < FR; ++r) {
-                    const int e = lane + 32 * r;
-                    if (e < NGC * NX) {
-                        const int jj = e / NX, i = e - jj * NX, j = gcol(jj);
-                        S.F[j * NX + i] = fpre[r];
-                    }
+                const T* Ft = I.F + (size_t)t * NF;
+                for (int e = L.l; e < NGC * NX; e += TPI) {
+                    const int jj = e / NX, i = e - jj * NX, j = gcol(jj);
+                    S.F[j * NX + i] = Ft[j * NX + i];
                 }
-                const T hv = hv_coef(P.mdl);
-                for (int e = lane; e < NTC * NX; e += 32) {
+                for (int e = L.l; e < NTC * NX; e += TPI) {
                     const int jj = e / NX, i = e - jj * NX, j = tcol(jj);
                     S.F[j * NX + i] = (i == j) ? T(1) : ((j >= 7 && i == j - 7) ? hv : T(0));
                 }
             }
-            if (t >= 1) {
-                load_c(t - 1);
-                load_f(t - 1);
-            }
-            __syncwarp();
+            wsync();
             if (dyn) {
-                const T hv = hv_coef(P.mdl);
                 // W = V F (column-major): 11 computed columns, then the constant ones
+                for (int e = L.l; e < NGC * NX; e += TPI) {
+                    const int jj = e / NX, i = e - jj * NX, j = gcol(jj);
+                    T s = T(0);
 #pragma unroll
-                for (int r = 0; r < FR; ++r) {
-                    const int e = lane + 32 * r;
-                    if (e < NGC * NX) {
-                        const int jj = e / NX, i = e - jj * NX, j = gcol(jj);
-                        T s = T(0);
-#pragma unroll
-                        for (int k = 0; k < NX; ++k) s += S.V[i * NX + k] * S.F[j * NX + k];
-                        S.W[j * NX + i] = s;
-                    }
+                    for (int k = 0; k < NX; ++k) s += S.V[i * NX + k] * S.F[j * NX + k];
+                    S.W[j * NX + i] = s;
                 }
-#pragma unroll
-                for (int r = 0; r < (NTC * NX + 31) / 32; ++r) {
-                    const int e = lane + 32 * r;
-                    if (e < NTC * NX) {
-                        const int jj = e / NX, i = e - jj * NX, j = tcol(jj);
-                        S.W[j * NX + i] = (j < 3) ? S.V[i * NX + j] : S.V[i * NX + j] + hv * S.V[i * NX + j - 7];
-                    }
+                for (int e = L.l; e < NTC * NX; e += TPI) {
+                    const int jj = e / NX, i = e - jj * NX, j = tcol(jj);
+                    S.W[j * NX + i] = (j < 3) ? S.V[i * NX + j] : S.V[i * NX + j] + hv * S.V[i * NX + j - 7];
                 }
-                __syncwarp();
+            }
+            wsync();
+            if (dyn) {
                 // Q = C + F' W (upper triangle), q = c + F' v; rows of the
-                // constant columns first need one or two terms
-#pragma unroll
-                for (int r = 0; r < (NTRI_Q + NZ + 31) / 32; ++r) {
-                    const int p = lane + 32 * r;
-                    if (p >= NTRI_Q + NZ) break;
+                // constant columns need one or two terms
+                for (int p = L.l; p < NTRI_Q + NZ; p += TPI) {
                     if (p < NTRI_Q) {
                         const int ab = triQ[p], a = ab >> 8, bb = ab & 0xff;
                         T s = (a == bb) ? S.Cd[a] : T(0);
@@ -696,16 +701,16 @@ __device__ bool riccati(const Params<T>& P, const Inst<T>& I, WarpSmem<T>& S, in
                         S.q[a] = s;
                     }
                 }
-            } else {
-                for (int e = lane; e < NZ * NZ; e += 32) {
+            } else if (on) {
+                for (int e = L.l; e < NZ * NZ; e += TPI) {
                     const int a = e / NZ, bb = e - a * NZ;
                     S.Qm[e] = (a == bb) ? S.Cd[a] : T(0);
                 }
-                if (lane < NZ) S.q[lane] = S.c[lane];
+                for (int a = L.l; a < NZ; a += TPI) S.q[a] = S.c[a];
             }
-            __syncwarp();
-            if (lane == 0) {
-                T H[4][4], g[4], lo[4], hi[4], d[4], L[NL];
+            wsync();
+            if (on && L.l == 0) {
+                T H[4][4], g[4], lo[4], hi[4], d[4], Lf[NL];
                 int mask = 0;
 #pragma unroll
                 for (int a = 0; a < 4; ++a) {
@@ -717,99 +722,105 @@ __device__ bool riccati(const Params<T>& P, const Inst<T>& I, WarpSmem<T>& S, in
                     lo[a] = S.ulo[a] - ub;
                     hi[a] = S.uhi[a] - ub;
                 }
-                const bool ok = box_qp(H, g, lo, hi, d, L, mask);
+                const bool ok = box_qp(H, g, lo, hi, d, Lf, mask);
 #pragma unroll
                 for (int a = 0; a < 4; ++a) S.k[a] = d[a];
 #pragma unroll
-                for (int i = 0; i < NL; ++i) S.L[i] = L[i];
+                for (int i = 0; i < NL; ++i) S.L[i] = Lf[i];
                 S.mask = mask;
                 S.ok = ok ? 1 : 0;
             }
-            __syncwarp();
-            if (!S.ok) return false;
+            wsync();
+            if (on && !S.ok) alive = false;
+            go = on && alive;
             const int mask = S.mask;
             // K_t columns
-            if (lane < NX) {
-                T rhs[4], y[4];
+            if (go) {
+                for (int c = L.l; c < NX; c += TPI) {
+                    T rhs[4], y[4];
 #pragma unroll
-                for (int a = 0; a < 4; ++a) rhs[a] = ((mask >> a) & 1) ? S.Qm[lane * NZ + NX + a] : T(0);
-                chol_solve4(S.L, rhs, y);
+                    for (int a = 0; a < 4; ++a) rhs[a] = ((mask >> a) & 1) ? S.Qm[c * NZ + NX + a] : T(0);
+                    chol_solve4(S.L, rhs, y);
 #pragma unroll
-                for (int a = 0; a < 4; ++a) S.K[a * NX + lane] = ((mask >> a) & 1) ? -y[a] : T(0);
-            }
-            __syncwarp();
-            // V_t, v_t
-#pragma unroll
-            for (int r = 0; r < (NTRI_V + NX + 31) / 32; ++r) {
-                const int p = lane + 32 * r;
-                if (p >= NTRI_V + NX) break;
-                if (p < NTRI_V) {
-                    const int ij = triV[p], i = ij >> 8, j = ij & 0xff;
-                    T s = S.Qm[i * NZ + j];
-#pragma unroll
-                    for (int a = 0; a < NU; ++a) s += S.Qm[i * NZ + NX + a] * S.K[a * NX + j];
-                    S.V[i * NX + j] = s;
-                    S.V[j * NX + i] = s;
-                } else {
-                    const int i = p - NTRI_V;
-                    T s = S.q[i];
-#pragma unroll
-                    for (int a = 0; a < NU; ++a) s += S.Qm[i * NZ + NX + a] * S.k[a];
-                    S.v[i] = s;
+                    for (int a = 0; a < 4; ++a) S.K[a * NX + c] = ((mask >> a) & 1) ? -y[a] : T(0);
                 }
             }
-            // gains to the slot scratch (and tape)
-            T* kr = I.Kr + (size_t)t * KREC;
-            for (int e = lane; e < KREC; e += 32) kr[e] = (e < NU * NX) ? S.K[e] : S.k[e - NU * NX];
-            if (o.tape) {
-                T* rec = o.tape + ((size_t)I.b * P.N + t) * TAPE_STRIDE;
-                for (int e = lane; e < TAPE_STRIDE; e += 32) {
-                    T val;
-                    if (e < TAPE_K) val = dyn ? S.F[e] : T(0);
-                    else if (e < TAPE_L) val = S.K[e - TAPE_K];
-                    else if (e < TAPE_MASK) val = S.L[e - TAPE_L];
-                    else if (e == TAPE_MASK) val = T(mask);
-                    else val = T(0);
-                    rec[e] = val;
+            wsync();
+            if (go) {
+                // V_t, v_t
+                for (int p = L.l; p < NTRI_V + NX; p += TPI) {
+                    if (p < NTRI_V) {
+                        const int ij = triV[p], i = ij >> 8, j = ij & 0xff;
+                        T s = S.Qm[i * NZ + j];
+#pragma unroll
+                        for (int a = 0; a < NU; ++a) s += S.Qm[i * NZ + NX + a] * S.K[a * NX + j];
+                        S.V[i * NX + j] = s;
+                        S.V[j * NX + i] = s;
+                    } else {
+                        const int i = p - NTRI_V;
+                        T s = S.q[i];
+#pragma unroll
+                        for (int a = 0; a < NU; ++a) s += S.Qm[i * NZ + NX + a] * S.k[a];
+                        S.v[i] = s;
+                    }
+                }
+                // gains to the slot scratch (and tape)
+                T* kr = I.Kr + (size_t)t * KREC;
+                for (int e = L.l; e < KREC; e += TPI) kr[e] = (e < NU * NX) ? S.K[e] : S.k[e - NU * NX];
+                if (o.tape) {
+                    T* rec = o.tape + ((size_t)I.b * P.N + t) * TAPE_STRIDE;
+                    for (int e = L.l; e < TAPE_STRIDE; e += TPI) {
+                        T val;
+                        if (e < TAPE_K) val = dyn ? S.F[e] : T(0);
+                        else if (e < TAPE_L) val = S.K[e - TAPE_K];
+                        else if (e < TAPE_MASK) val = S.L[e - TAPE_L];
+                        else val = T(mask);
+                        rec[e] = val;
+                    }
                 }
             }
         }
         if (o.adj) {
             const AdjArgs<T>* adj = o.adj;
-            __syncwarp();
-            if (lane < NZ) {
-                T g;
-                if (lane < NX) g = adj->gx ? adj->gx[((size_t)I.b * P.N + t) * NX + lane] : T(0);
-                else g = adj->gu[((size_t)I.b * P.N + t) * NU + lane - NX];
-                if (dyn) {
+            wsync();
+            if (go) {
+                for (int a = L.l; a < NZ; a += TPI) {
+                    T g;
+                    if (a < NX) g = adj->gx ? adj->gx[((size_t)I.b * P.N + t) * NX + a] : T(0);
+                    else g = adj->gu[((size_t)I.b * P.N + t) * NU + a - NX];
+                    if (dyn) {
 #pragma unroll
-                    for (int k = 0; k < NX; ++k) g += S.F[lane * NX + k] * S.vh[k];
+                        for (int k = 0; k < NX; ++k) g += S.F[a * NX + k] * S.vh[k];
+                    }
+                    S.qh[a] = g;
                 }
-                S.qh[lane] = g;
             }
-            __syncwarp();
-            const int mask = S.mask;
-            if (lane < NX) {
-                T s = S.qh[lane];
+            wsync();
+            if (go) {
+                const int mask = S.mask;
+                for (int i = L.l; i < NX; i += TPI) {
+                    T s = S.qh[i];
 #pragma unroll
-                for (int a = 0; a < NU; ++a) s += S.K[a * NX + lane] * S.qh[NX + a];
-                S.vh[lane] = s;
-            } else if (lane == 16) {
-                T rhs[4], y[4];
+                    for (int a = 0; a < NU; ++a) s += S.K[a * NX + i] * S.qh[NX + a];
+                    S.vh[i] = s;
+                }
+                if (L.l == TPI - 1) {
+                    T rhs[4], y[4];
 #pragma unroll
-                for (int a = 0; a < 4; ++a) rhs[a] = ((mask >> a) & 1) ? S.qh[NX + a] : T(0);
-                chol_solve4(S.L, rhs, y);
+                    for (int a = 0; a < 4; ++a) rhs[a] = ((mask >> a) & 1) ? S.qh[NX + a] : T(0);
+                    chol_solve4(S.L, rhs, y);
 #pragma unroll
-                for (int a = 0; a < 4; ++a) I.kh[t * NU + a] = ((mask >> a) & 1) ? -y[a] : T(0);
+                    for (int a = 0; a < 4; ++a) I.kh[t * NU + a] = ((mask >> a) & 1) ? -y[a] : T(0);
+                }
             }
         }
-        __syncwarp();
+        wsync();
     }
-    return true;
+    return alive;
 }
 
 // ------------------------------------------------- A4 line search ----------
-// Sec. IV-3: every alpha rolled out on its own lane,
+// Sec. IV-3: each alpha rolled out on its own lane of the group,
 //   u_hat_t = clamp(u_t + alpha k_t + K_t (x_hat_t - x_t)),  x_hat_{t+1} = RK4.
 // The candidates are compared through their cost change with respect to the
 // nominal, accumulated stage by stage from the differences themselves,
@@ -817,8 +828,10 @@ __device__ bool riccati(const Params<T>& P, const Inst<T>& I, WarpSmem<T>& S, in
 // which equals J(alpha) - J exactly for the quadratic cost but does not cancel
 // against J's magnitude; with the hi + lo states it resolves differences far
 // below the working precision of J.  alpha* = first argmin, and the best
-// candidate becomes the next nominal (Sec. IV-3).  Returns 0 (step taken: du,
-// J updated) or 1 (no candidate with a finite cost: nominal kept).
+// candidate becomes the next nominal (Sec. IV-3).  Each stage's gains, nominal
+// and cost rows are staged into shared memory one stage ahead by the group's
+// other lanes.  Returns 0 (step taken: du, J updated) or 1 (no candidate with
+// a finite cost: nominal kept).
 template <typename T>
 __device__ __forceinline__ void ls_stage_load(const Params<T>& P, const Inst<T>& I, T* dst, int t, int e0, int step) {
     const T* Qt = Qrow(P, I, t);
@@ -834,21 +847,23 @@ __device__ __forceinline__ void ls_stage_load(const Params<T>& P, const Inst<T>&
     }
 }
 
-template <typename T>
-__device__ int line_search(const Params<T>& P, const Inst<T>& I, WarpSmem<T>& S, int lane, T& Jnom, T& du_out) {
-    const int n = I.n;
-    // Each stage's gains, nominal and cost rows are staged into shared memory
-    // one stage ahead by the lanes that roll out no candidate.
-    ls_stage_load(P, I, S.stg[0], 0, lane, 32);
-    __syncwarp();
-    const T alpha = lane < P.n_alpha ? P.alpha[lane] : T(0);
+template <typename T, int TPI>
+__device__ int line_search(const Params<T>& P, const Inst<T>& I, WarpSmem<T>& S, const Lanes<TPI>& L, bool act,
+                           T& Jnom, T& du_out) {
+    static_assert(TPI >= 8, "line search needs 4 candidate lanes and at least 4 staging lanes");
+    const int n = act ? I.n : 0;
+    const int nmax = warp_max(n);
+    if (act) ls_stage_load(P, I, S.stg[0], 0, L.l, TPI);
+    wsync();
+    const bool cl = act && L.l < P.n_alpha;
+    const T alpha = cl ? P.alpha[L.l] : T(0);
     T xh[NX], xl[NX], uh[NU];
 #pragma unroll
-    for (int i = 0; i < NX; ++i) { xh[i] = S.x0[i]; xl[i] = T(0); }
+    for (int i = 0; i < NX; ++i) { xh[i] = act ? S.x0[i] : T(0); xl[i] = T(0); }
     T dJ = T(0), dJl = T(0);
-    T* cd = I.cand + (size_t)(lane & 3) * P.N_ws * CREC;
-    for (int t = 0; t < n; ++t) {
-        if (lane < P.n_alpha) {
+    T* cd = I.cand + (size_t)(L.l & 3) * P.N_ws * CREC;
+    for (int t = 0; t < nmax; ++t) {
+        if (cl && t < n) {
             const T* sb = S.stg[t & 1];
             const T* kr = sb;
             const T* xbt = sb + KREC;
@@ -882,46 +897,54 @@ __device__ int line_search(const Params<T>& P, const Inst<T>& I, WarpSmem<T>& S,
 #pragma unroll
             for (int a = 0; a < NU; ++a) cd[t * CREC + 2 * NX + a] = uh[a];
             if (t < n - 1) rk4_step2(P.mdl, xh, xl, uh);
-        } else if (lane >= 4 && t + 1 < n) {
-            ls_stage_load(P, I, S.stg[(t + 1) & 1], t + 1, lane - 4, 28);
+        } else if (act && L.l >= 4 && t + 1 < n) {
+            ls_stage_load(P, I, S.stg[(t + 1) & 1], t + 1, L.l - 4, TPI - 4);
         }
-        __syncwarp();
+        wsync();
     }
-    if (lane < P.n_alpha) {
+    if (cl) {
         dJ = dJ + dJl;
-        S.Jc[lane] = finiteT(dJ) ? dJ : T(INFINITY);
+        S.Jc[L.l] = finiteT(dJ) ? dJ : T(INFINITY);
     }
-    __syncwarp();
-    int best = 0;
-    T Jb = S.Jc[0];
-    for (int c = 1; c < P.n_alpha; ++c)
-        if (S.Jc[c] < Jb) { Jb = S.Jc[c]; best = c; }
-    if (!finiteT(Jb)) return 1;
-    const T* cb = I.cand + (size_t)best * P.N_ws * CREC;
-    T dmax = T(0);
-    for (int e = lane; e < n * CREC; e += 32) {
-        const int t = e / CREC, j = e - t * CREC;
-        const T val = cb[e];
-        if (j < NX) {
-            I.xb[t * NX + j] = val;
-        } else if (j < 2 * NX) {
-            I.xlo[t * NX + j - NX] = val;
+    wsync();
+    int r = 0;
+    T dmax = T(0), Jb = T(0);
+    if (act) {
+        int best = 0;
+        Jb = S.Jc[0];
+        for (int c = 1; c < P.n_alpha; ++c)
+            if (S.Jc[c] < Jb) { Jb = S.Jc[c]; best = c; }
+        if (!finiteT(Jb)) {
+            r = 1;
         } else {
-            T* up = I.ub + t * NU + (j - 2 * NX);
-            const T d = fabs(val - *up);
-            dmax = d > dmax ? d : dmax;
-            *up = val;
+            const T* cb = I.cand + (size_t)best * P.N_ws * CREC;
+            for (int e = L.l; e < n * CREC; e += TPI) {
+                const int t = e / CREC, j = e - t * CREC;
+                const T val = cb[e];
+                if (j < NX) {
+                    I.xb[t * NX + j] = val;
+                } else if (j < 2 * NX) {
+                    I.xlo[t * NX + j - NX] = val;
+                } else {
+                    T* up = I.ub + t * NU + (j - 2 * NX);
+                    const T d = fabs(val - *up);
+                    dmax = d > dmax ? d : dmax;
+                    *up = val;
+                }
+            }
         }
     }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
+    for (int o = TPI / 2; o > 0; o >>= 1) {
         const T other = __shfl_xor_sync(FULL, dmax, o);
         dmax = other > dmax ? other : dmax;
     }
-    __syncwarp();
-    Jnom = Jnom + Jb;
-    du_out = dmax;
-    return 0;
+    wsync();
+    if (act && r == 0) {
+        Jnom = Jnom + Jb;
+        du_out = dmax;
+    }
+    return r;
 }
 
 // ---------------------------------------------- A8 adjoint forward sweep ----
@@ -929,58 +952,89 @@ __device__ int line_search(const Params<T>& P, const Inst<T>& I, WarpSmem<T>& S,
 // d_tau_t = [dx_t; du_t]:  dQ_t = dx_t * (x*_t - x_ref,t),  dx_ref,t = -Q_t * dx_t,
 // dx0 = vh_0 (value gradient of the adjoint LQR).  Fsrc / Ksrc: per-stage F_t
 // and K_t with strides fs / ks (tape records or slot scratch).
-template <typename T>
-__device__ void adjoint_forward(const Params<T>& P, const Inst<T>& I, WarpSmem<T>& S, int lane,
-                                const T* Fsrc, size_t fs, const T* Ksrc, size_t ks, const AdjArgs<T>& A) {
-    const int n = I.n;
+template <typename T, int TPI>
+__device__ void adjoint_forward(const Params<T>& P, const Inst<T>& I, WarpSmem<T>& S, const Lanes<TPI>& L,
+                                bool act, const T* Fsrc, size_t fs, const T* Ksrc, size_t ks,
+                                const AdjArgs<T>& A) {
+    const int n = act ? I.n : 0;
+    const int nmax = warp_max(n);
     const size_t b = I.b;
-    if (lane < NX) { S.dx[lane] = T(0); S.dQacc[lane] = T(0); A.dx0[b * NX + lane] = S.vh[lane]; }
-    __syncwarp();
-    for (int t = 0; t < n; ++t) {
-        const T* Kt = Ksrc + (size_t)t * ks;
-        if (lane < NU) {
-            T s = I.kh[t * NU + lane];
+    constexpr int RX = (NX + TPI - 1) / TPI;
+    if (act) {
+        for (int i = L.l; i < NX; i += TPI) { S.dx[i] = T(0); S.dQacc[i] = T(0); A.dx0[b * NX + i] = S.vh[i]; }
+    }
+    wsync();
+    for (int t = 0; t < nmax; ++t) {
+        const bool on = t < n;
+        if (on) {
+            const T* Kt = Ksrc + (size_t)t * ks;
+            for (int a = L.l; a < NU; a += TPI) {
+                T s = I.kh[t * NU + a];
 #pragma unroll
-            for (int i = 0; i < NX; ++i) s += Kt[lane * NX + i] * S.dx[i];
-            S.du[lane] = s;
-        }
-        if (lane >= 16 && lane < 16 + NX) {
-            const int i = lane - 16;
-            const T* Qt = Qrow(P, I, t);
-            const T dxi = S.dx[i];
-            const T e = I.xb[t * NX + i] - I.xrefb[t * NX + i];
-            if (P.Nq > 1) A.dQ[(b * P.Nq + t) * NX + i] = dxi * e;
-            else S.dQacc[i] += dxi * e;
-            A.dxref[(b * P.N + t) * NX + i] = -Qt[i] * dxi;
-        }
-        __syncwarp();
-        if (t < n - 1) {
-            const T* Ft = Fsrc + (size_t)t * fs;
-            T s = T(0);
-            if (lane < NX) {
-                // dx_{t+1} = F_t [dx_t; du_t]: the 11 computed columns, then the
-                // constant p and v columns
-#pragma unroll
-                for (int jj = 0; jj < NGC; ++jj) {
-                    const int j = gcol(jj);
-                    s += Ft[j * NX + lane] * (j < NX ? S.dx[j] : S.du[j - NX]);
-                }
-                if (lane < 3) s += S.dx[lane] + hv_coef(P.mdl) * S.dx[lane + 7];
-                else if (lane >= 7 && lane < 10) s += S.dx[lane];
+                for (int i = 0; i < NX; ++i) s += Kt[a * NX + i] * S.dx[i];
+                S.du[a] = s;
             }
-            __syncwarp();
-            if (lane < NX) S.dx[lane] = s;
-            __syncwarp();
+            const T* Qt = Qrow(P, I, t);
+            for (int i = L.l; i < NX; i += TPI) {
+                const T dxi = S.dx[i];
+                const T e = I.xb[t * NX + i] - I.xrefb[t * NX + i];
+                if (P.Nq > 1) A.dQ[(b * P.Nq + t) * NX + i] = dxi * e;
+                else S.dQacc[i] += dxi * e;
+                A.dxref[(b * P.N + t) * NX + i] = -Qt[i] * dxi;
+            }
+        }
+        wsync();
+        T snew[RX];
+        if (on && t < n - 1) {
+            // dx_{t+1} = F_t [dx_t; du_t]: the 11 computed columns, then the
+            // constant p and v columns
+            const T* Ft = Fsrc + (size_t)t * fs;
+#pragma unroll
+            for (int r = 0; r < RX; ++r) {
+                const int i = L.l + r * TPI;
+                if (i < NX) {
+                    T s = T(0);
+#pragma unroll
+                    for (int jj = 0; jj < NGC; ++jj) {
+                        const int j = gcol(jj);
+                        s += Ft[j * NX + i] * (j < NX ? S.dx[j] : S.du[j - NX]);
+                    }
+                    if (i < 3) s += S.dx[i] + hv_coef(P.mdl) * S.dx[i + 7];
+                    else if (i >= 7 && i < 10) s += S.dx[i];
+                    snew[r] = s;
+                }
+            }
+        }
+        wsync();
+        if (on && t < n - 1) {
+#pragma unroll
+            for (int r = 0; r < RX; ++r) {
+                const int i = L.l + r * TPI;
+                if (i < NX) S.dx[i] = snew[r];
+            }
+        }
+        wsync();
+    }
+    if (act) {
+        // zero the stages past the horizon, write the shared-Q sum
+        for (int e = n * NX + L.l; e < P.N * NX; e += TPI) A.dxref[b * P.N * NX + e] = T(0);
+        if (P.Nq > 1) {
+            for (int e = n * NX + L.l; e < P.Nq * NX; e += TPI) A.dQ[b * P.Nq * NX + e] = T(0);
+        } else {
+            for (int i = L.l; i < NX; i += TPI) A.dQ[b * NX + i] = S.dQacc[i];
         }
     }
-    // zero the stages past the horizon, write the shared-Q sum
-    for (int e = n * NX + lane; e < P.N * NX; e += 32) A.dxref[b * P.N * NX + e] = T(0);
-    if (P.Nq > 1) {
-        for (int e = n * NX + lane; e < P.Nq * NX; e += 32) A.dQ[b * P.Nq * NX + e] = T(0);
-    } else if (lane < NX) {
-        A.dQ[b * NX + lane] = S.dQacc[lane];
+    wsync();
+}
+
+template <typename T, int TPI>
+__device__ void zero_grads(const Params<T>& P, const AdjArgs<T>& A, int b, const Lanes<TPI>& L, bool act) {
+    if (act) {
+        for (int e = L.l; e < P.Nq * NX; e += TPI) A.dQ[(size_t)b * P.Nq * NX + e] = T(0);
+        for (int e = L.l; e < P.N * NX; e += TPI) A.dxref[(size_t)b * P.N * NX + e] = T(0);
+        for (int i = L.l; i < NX; i += TPI) A.dx0[(size_t)b * NX + i] = T(0);
     }
-    __syncwarp();
+    wsync();
 }
 
 }  // namespace camp

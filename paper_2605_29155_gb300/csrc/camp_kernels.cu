@@ -1,15 +1,19 @@
 // camp_kernels.cu -- the kernel and launch sequences of the batched MPC layer.
 //
-// One kernel, k_mpc, runs every phase of the method through a per-instance
-// phase machine; each phase has exactly one call site, so every launch form
-// executes the same machine code for it and gives bit-identical results.
+// One kernel template, k_mpc<T, TPI>, runs every phase of the method through a
+// phase machine over a pack of 32 / TPI instances (a group of TPI lanes per
+// instance, the pack in lockstep).  Every phase has exactly one call site, so
+// every launch form executes the same machine code for it and gives
+// bit-identical results.
 //
 // Forward (Sec. IV, Algorithm 2's inner loop):
-//   persistent form (one launch): each warp pulls instances from an atomic work
-//     queue (longest horizon first when horizons differ) and runs the whole
-//     solve of that instance -- rollout, then per iteration linearization,
+//   persistent form (one launch): each warp pulls packs of instances from an
+//     atomic work queue (longest horizon first when horizons differ) and runs
+//     their whole solves -- rollout, then per iteration linearization,
 //     Riccati + box QP, line search, convergence test -- and the final
-//     factorization at the returned iterate, with no host round trip.
+//     factorization at the returned iterates, with no host round trip.  An
+//     instance that converges stops updating while the rest of its pack
+//     iterates.
 //   plain form: Sec. IV's structure, three launches per iteration
 //     (rollout + linearization, Riccati backward pass with bounds, forward
 //     pass + line search) over all instances, the per-instance convergence
@@ -74,117 +78,127 @@ __device__ __forceinline__ bool plain_applies(int ph, int st) {
     return finished_ok(st);
 }
 
-template <typename T>
-__device__ void zero_grads(const Params<T>& P, const AdjArgs<T>& A, int b, int lane) {
-    for (int e = lane; e < P.Nq * NX; e += 32) A.dQ[(size_t)b * P.Nq * NX + e] = T(0);
-    for (int e = lane; e < P.N * NX; e += 32) A.dxref[(size_t)b * P.N * NX + e] = T(0);
-    if (lane < NX) A.dx0[(size_t)b * NX + lane] = T(0);
-    __syncwarp();
-}
+__device__ __forceinline__ bool warp_any(bool v) { return __any_sync(FULL, v) != 0; }
 
-// mode >= 0: plain form, run phase `mode` once for instance = global warp index.
+// mode >= 0: plain form, run phase `mode` once for the pack = global warp index.
 // mode == MODE_FWD / MODE_BWD: persistent forward / backward over the work queue.
 // `last`: the plain line-search launch of the final iteration.
-template <typename T>
+template <typename T, int TPI>
 __global__ void __launch_bounds__(256, 2) k_mpc(Params<T> P, AdjArgs<T> A, int mode, int last) {
+    constexpr int PACK = 32 / TPI;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int triQ[NTRI_Q], triV[NTRI_V];
     init_tables(triQ, triV);
     __syncthreads();
-    WarpSmem<T>& S = reinterpret_cast<WarpSmem<T>*>(smem_raw)[threadIdx.x >> 5];
-    const int lane = threadIdx.x & 31;
-    const int wslot = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const Lanes<TPI> L;
+    const int wib = threadIdx.x >> 5;
+    WarpSmem<T>& S = reinterpret_cast<WarpSmem<T>*>(smem_raw)[wib * PACK + L.g];
+    const int wglob = blockIdx.x * (blockDim.x >> 5) + wib;
     const bool plain = mode >= 0;
     bool first = true;
     for (;;) {
-        int b;
+        int base;
         if (plain) {
             if (!first) break;
             first = false;
-            b = wslot;
-            if (b >= P.B) break;
+            base = wglob * PACK;
+            if (base >= P.B) break;
         } else {
-            int idx = 0;
-            if (lane == 0) idx = atomicAdd(P.queue + (mode == MODE_BWD ? 1 : 0), 1);
-            idx = __shfl_sync(FULL, idx, 0);
-            if (idx >= P.B) break;
-            b = P.order ? P.order[idx] : idx;
+            int tk = 0;
+            if (L.lane == 0) tk = atomicAdd(P.queue + (mode == MODE_BWD ? 1 : 0), PACK);
+            base = __shfl_sync(FULL, tk, 0);
+            if (base >= P.B) break;
         }
-        const Inst<T> I = make_inst(P, b, plain ? b : wslot);
-        int ph, status, iters;
-        T J;
+        const int idx = base + L.g;
+        const bool valid = idx < P.B;
+        const int b = valid ? (P.order ? P.order[idx] : idx) : 0;
+        const Inst<T> I = make_inst(P, b, plain ? (valid ? b : 0) : wglob * PACK + L.g, valid);
+
+        // per-instance state (uniform within the group)
+        int status = ST_RUNNING, iters = 0;
+        T J = T(0);
+        bool ok_bwd = false;
+        int ph;
         if (plain) {
             ph = mode;
-            status = ph == PH_INIT ? ST_RUNNING : P.status[b];
-            iters = ph == PH_INIT ? 0 : P.iters[b];
-            J = ph == PH_INIT ? T(0) : P.cost[b];
-            if (!plain_applies(ph, status)) continue;
+            if (valid && ph != PH_INIT) {
+                status = P.status[b];
+                iters = P.iters[b];
+                J = P.cost[b];
+            }
         } else if (mode == MODE_FWD) {
             ph = PH_INIT;
-            status = ST_RUNNING;
-            iters = 0;
-            J = T(0);
         } else {
-            status = P.status[b];
-            iters = 0;
-            J = T(0);
-            ph = finished_ok(status) ? (A.recompute ? PH_BLIN : PH_BTAPE) : PH_BZERO;
+            status = valid ? P.status[b] : ST_NONFINITE;
+            ok_bwd = valid && finished_ok(status);
+            ph = warp_any(ok_bwd) ? (A.recompute ? PH_BLIN : PH_BTAPE) : PH_BZERO;
         }
-        load_instance(P, I, S, lane);
+        const bool applies = plain ? (valid && plain_applies(mode, status)) : valid;
+        load_instance(P, I, S, L, applies);
         const int after_fwd = P.store_all ? PH_FLIN : PH_END;
         while (ph != PH_DONE) {
             int next = PH_DONE;
             if (ph == PH_INIT) {
-                J = initial_rollout(P, I, S, lane);
-                if (!finiteT(J)) { status = ST_NONFINITE; next = PH_END; }
-                else if (P.max_iter > 0) next = PH_LIN;
-                else { status = ST_MAX_ITER; next = after_fwd; }
+                const bool act = applies;
+                J = initial_rollout(P, I, S, L, act);
+                if (act) {
+                    if (!finiteT(J)) status = ST_NONFINITE;
+                    else if (P.max_iter == 0) status = ST_MAX_ITER;
+                }
+                next = warp_any(act && status == ST_RUNNING) ? PH_LIN : after_fwd;
             } else if (ph == PH_LIN || ph == PH_FLIN || ph == PH_BLIN) {
-                if (ph == PH_LIN) ++iters;
-                linearize(P, I, I.F, lane);
+                const bool act = ph == PH_LIN ? (applies && status == ST_RUNNING)
+                                : (ph == PH_FLIN ? (applies && finished_ok(status)) : ok_bwd);
+                if (ph == PH_LIN && act) ++iters;
+                linearize(P, I, L, act);
                 next = ph + 1;
             } else if (ph == PH_RIC || ph == PH_FRIC || ph == PH_BRIC || ph == PH_BTAPE) {
+                const bool act = ph == PH_RIC ? (applies && status == ST_RUNNING)
+                                : (ph == PH_FRIC ? (applies && finished_ok(status)) : ok_bwd);
                 RicOpts<T> o;
                 o.tape = ph == PH_FRIC ? P.tape : (T*)nullptr;
                 o.adj = (ph == PH_BRIC || ph == PH_BTAPE) ? &A : (const AdjArgs<T>*)nullptr;
                 o.replay = ph == PH_BTAPE;
                 o.use_lo = ph == PH_RIC;
-                const bool ok = riccati(P, I, S, lane, triQ, triV, o);
+                const bool ok = riccati(P, I, S, L, triQ, triV, o, act);
                 if (ph == PH_RIC) {
-                    if (ok) next = PH_LS;
-                    else { status = ST_NONPD; next = PH_END; }
+                    if (act && !ok) status = ST_NONPD;
+                    next = warp_any(act && ok) ? PH_LS : after_fwd;
                 } else if (ph == PH_FRIC) {
-                    if (!ok) status = ST_NONPD;
+                    if (act && !ok) status = ST_NONPD;
                     next = PH_END;
                 } else {
-                    next = ok ? PH_BFWD : PH_BZERO;
+                    ok_bwd = ok_bwd && ok;
+                    next = PH_BFWD;
                 }
             } else if (ph == PH_LS) {
+                const bool act = applies && status == ST_RUNNING;
                 T du = T(0);
-                const int r = line_search(P, I, S, lane, J, du);
-                if (r) { status = ST_STALLED; next = after_fwd; }
-                else if (du < P.tol) { status = ST_CONVERGED; next = after_fwd; }
-                else if (plain ? (last != 0) : (iters >= P.max_iter)) { status = ST_MAX_ITER; next = after_fwd; }
-                else next = PH_LIN;
+                const int r = line_search(P, I, S, L, act, J, du);
+                if (act) {
+                    if (r) status = ST_STALLED;
+                    else if (du < P.tol) status = ST_CONVERGED;
+                    else if (plain ? (last != 0) : (iters >= P.max_iter)) status = ST_MAX_ITER;
+                }
+                next = warp_any(act && status == ST_RUNNING) ? PH_LIN : after_fwd;
             } else if (ph == PH_BFWD) {
                 const T* tb = A.recompute ? (const T*)nullptr : P.tape + (size_t)I.b * P.N * TAPE_STRIDE;
                 const T* Fs = A.recompute ? (const T*)I.F : tb + TAPE_F;
                 const T* Ks = A.recompute ? (const T*)I.Kr : tb + TAPE_K;
                 const size_t fs = A.recompute ? (size_t)NF : (size_t)TAPE_STRIDE;
                 const size_t ks = A.recompute ? (size_t)KREC : (size_t)TAPE_STRIDE;
-                adjoint_forward(P, I, S, lane, Fs, fs, Ks, ks, A);
-                next = PH_DONE;
+                adjoint_forward(P, I, S, L, ok_bwd, Fs, fs, Ks, ks, A);
+                next = PH_BZERO;
             } else if (ph == PH_BZERO) {
-                zero_grads(P, A, b, lane);
+                zero_grads(P, A, b, L, valid && !ok_bwd);
                 next = PH_DONE;
             } else if (ph == PH_END) {
                 next = PH_DONE;
             }
             if (plain) break;
-            if (next == PH_DONE && mode == MODE_FWD) break;
             ph = next;
         }
-        if (mode != MODE_BWD && lane == 0) {
+        if (mode != MODE_BWD && applies && L.l == 0) {
             P.cost[b] = J;
             P.iters[b] = iters;
             P.status[b] = status;
@@ -219,25 +233,53 @@ __global__ void k_lpt_order(const int* horizon, int B, int N, int* order) {
 // ------------------------------------------------------------ host side ----
 template <typename T> size_t warp_smem_bytes() { return sizeof(WarpSmem<T>); }
 
-template <typename T> cudaError_t prepare_kernels() {
-    return cudaFuncSetAttribute(k_mpc<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)(8 * sizeof(WarpSmem<T>)));
+template <typename T> static const void* kernel_for(int tpi) {
+    if (tpi == 8) return (const void*)k_mpc<T, 8>;
+    if (tpi == 16) return (const void*)k_mpc<T, 16>;
+    return (const void*)k_mpc<T, 32>;
 }
 
-template <typename T> int persistent_blocks_per_sm(int ipb, int /*which*/) {
+// Allow the largest dynamic shared memory a block may need (32 instances),
+// capped by the device's opt-in limit less the kernel's static tables.
+template <typename T> cudaError_t prepare_kernels() {
+    int dev = 0, optin = 0;
+    cudaError_t e;
+    if ((e = cudaGetDevice(&dev))) return e;
+    if ((e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev))) return e;
+    for (int tpi = 8; tpi <= 32; tpi *= 2) {
+        cudaFuncAttributes fa;
+        if ((e = cudaFuncGetAttributes(&fa, kernel_for<T>(tpi)))) return e;
+        size_t want = (size_t)(256 / tpi) * sizeof(WarpSmem<T>);
+        const size_t cap = (size_t)optin > fa.sharedSizeBytes ? (size_t)optin - fa.sharedSizeBytes : 0;
+        if (want > cap) want = cap;
+        if ((e = cudaFuncSetAttribute(kernel_for<T>(tpi), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)want)))
+            return e;
+    }
+    return cudaSuccess;
+}
+
+template <typename T> int persistent_blocks_per_sm(int tpi, int ipb) {
     int nb = 0;
     const size_t smem = (size_t)ipb * sizeof(WarpSmem<T>);
-    const cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_mpc<T>, 32 * ipb, smem);
+    const cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel_for<T>(tpi), tpi * ipb, smem);
     return e == cudaSuccess ? nb : 0;
 }
 
 template <typename T>
-cudaError_t launch_forward(const Params<T>& Pin, int exec_mode, int ipb, int grid, int* order_ws,
+static void launch_tpi(int tpi, int grid, int threads, size_t smem, cudaStream_t st, const Params<T>& P,
+                       const AdjArgs<T>& A, int mode, int last) {
+    if (tpi == 8) k_mpc<T, 8><<<grid, threads, smem, st>>>(P, A, mode, last);
+    else if (tpi == 16) k_mpc<T, 16><<<grid, threads, smem, st>>>(P, A, mode, last);
+    else k_mpc<T, 32><<<grid, threads, smem, st>>>(P, A, mode, last);
+}
+
+template <typename T>
+cudaError_t launch_forward(const Params<T>& Pin, int exec_mode, int tpi, int ipb, int grid, int* order_ws,
                            cudaStream_t st) {
     Params<T> P = Pin;
     AdjArgs<T> A{};
     const size_t smem = (size_t)ipb * sizeof(WarpSmem<T>);
-    const int threads = 32 * ipb;
+    const int threads = tpi * ipb;
     cudaError_t e;
     P.order = nullptr;
     if (exec_mode == 0) {
@@ -246,25 +288,25 @@ cudaError_t launch_forward(const Params<T>& Pin, int exec_mode, int ipb, int gri
             k_lpt_order<<<1, 1024, 0, st>>>(P.horizon, P.B, P.N, order_ws);
             P.order = order_ws;
         }
-        k_mpc<T><<<grid, threads, smem, st>>>(P, A, MODE_FWD, 0);
+        launch_tpi<T>(tpi, grid, threads, smem, st, P, A, MODE_FWD, 0);
         return cudaGetLastError();
     }
     const int blocks = (P.B + ipb - 1) / ipb;
-    k_mpc<T><<<blocks, threads, smem, st>>>(P, A, PH_INIT, 0);
+    launch_tpi<T>(tpi, blocks, threads, smem, st, P, A, PH_INIT, 0);
     for (int it = 0; it < P.max_iter; ++it) {
-        k_mpc<T><<<blocks, threads, smem, st>>>(P, A, PH_LIN, 0);
-        k_mpc<T><<<blocks, threads, smem, st>>>(P, A, PH_RIC, 0);
-        k_mpc<T><<<blocks, threads, smem, st>>>(P, A, PH_LS, it == P.max_iter - 1);
+        launch_tpi<T>(tpi, blocks, threads, smem, st, P, A, PH_LIN, 0);
+        launch_tpi<T>(tpi, blocks, threads, smem, st, P, A, PH_RIC, 0);
+        launch_tpi<T>(tpi, blocks, threads, smem, st, P, A, PH_LS, it == P.max_iter - 1);
     }
     if (P.store_all) {
-        k_mpc<T><<<blocks, threads, smem, st>>>(P, A, PH_FLIN, 0);
-        k_mpc<T><<<blocks, threads, smem, st>>>(P, A, PH_FRIC, 0);
+        launch_tpi<T>(tpi, blocks, threads, smem, st, P, A, PH_FLIN, 0);
+        launch_tpi<T>(tpi, blocks, threads, smem, st, P, A, PH_FRIC, 0);
     }
     return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t launch_backward(const Params<T>& Pin, const AdjArgs<T>& A, int ipb, int grid, int* order_ws,
+cudaError_t launch_backward(const Params<T>& Pin, const AdjArgs<T>& A, int tpi, int ipb, int grid, int* order_ws,
                             cudaStream_t st) {
     Params<T> P = Pin;
     const size_t smem = (size_t)ipb * sizeof(WarpSmem<T>);
@@ -275,7 +317,7 @@ cudaError_t launch_backward(const Params<T>& Pin, const AdjArgs<T>& A, int ipb, 
         k_lpt_order<<<1, 1024, 0, st>>>(P.horizon, P.B, P.N, order_ws);
         P.order = order_ws;
     }
-    k_mpc<T><<<grid, 32 * ipb, smem, st>>>(P, A, MODE_BWD, 0);
+    launch_tpi<T>(tpi, grid, tpi * ipb, smem, st, P, A, MODE_BWD, 0);
     return cudaGetLastError();
 }
 
@@ -283,8 +325,8 @@ cudaError_t launch_backward(const Params<T>& Pin, const AdjArgs<T>& A, int ipb, 
     template size_t warp_smem_bytes<T>();                                                                \
     template cudaError_t prepare_kernels<T>();                                                           \
     template int persistent_blocks_per_sm<T>(int, int);                                                  \
-    template cudaError_t launch_forward<T>(const Params<T>&, int, int, int, int*, cudaStream_t);         \
-    template cudaError_t launch_backward<T>(const Params<T>&, const AdjArgs<T>&, int, int, int*, cudaStream_t);
+    template cudaError_t launch_forward<T>(const Params<T>&, int, int, int, int, int*, cudaStream_t);    \
+    template cudaError_t launch_backward<T>(const Params<T>&, const AdjArgs<T>&, int, int, int, int*, cudaStream_t);
 
 CAMP_INSTANTIATE(float)
 CAMP_INSTANTIATE(double)

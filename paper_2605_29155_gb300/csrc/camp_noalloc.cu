@@ -32,7 +32,7 @@ using namespace camp;
 
 namespace {
 
-constexpr int NA_IPB = 4;                                   // instances per block
+constexpr int NA_TPI = 32, NA_IPB = 4;                      // threads per instance, instances per block
 constexpr int NA_SLOTS = MPC_NOALLOC_B_MAX + NA_IPB;        // warp slots the grid can use
 constexpr size_t NA_STAGES = (size_t)NA_SLOTS * MPC_NOALLOC_N_MAX;
 
@@ -169,10 +169,10 @@ extern "C" int mpc_solve_fwd_noalloc(const mpc_config* cfg, const mpc_problem* p
     P.queue = (int*)(ws + OFF_Q);
     int* order = (int*)(ws + OFF_O);
 
-    int bps = persistent_blocks_per_sm<float>(NA_IPB, 0);
+    int bps = persistent_blocks_per_sm<float>(NA_TPI, NA_IPB);
     long long grid = (long long)(bps > 0 ? bps : 1) * sms;
     const long long need = (p->B + NA_IPB - 1) / NA_IPB;
     if (grid > need) grid = need;
-    const cudaError_t e = launch_forward<float>(P, MPC_EXEC_PERSISTENT, NA_IPB, (int)grid, order, stream);
+    const cudaError_t e = launch_forward<float>(P, MPC_EXEC_PERSISTENT, NA_TPI, NA_IPB, (int)grid, order, stream);
     return e == cudaSuccess ? MPC_OK : MPC_ERR_CUDA;
 }

@@ -74,7 +74,7 @@ class DiffMPC:
 
     def __init__(self, N_max=40, B_max=8192, dtype=torch.float32, max_iter=8, tol=1e-6,
                  store_mode="store_all", exec_mode="persistent", ipb=0, model=None, alphas=None,
-                 device=None):
+                 device=None, tpi=0):
         if not torch.cuda.is_available():
             raise RuntimeError("DiffMPC needs a CUDA device (libcamp.so has no CPU path)")
         self.device = torch.device(device or "cuda")
@@ -85,6 +85,7 @@ class DiffMPC:
         cfg.store_mode = camp.MPC_STORE_ALL if store_mode == "store_all" else camp.MPC_RECOMPUTE
         cfg.exec_mode = camp.MPC_EXEC_PERSISTENT if exec_mode == "persistent" else camp.MPC_EXEC_PLAIN
         cfg.ipb = int(ipb)
+        cfg.tpi = int(tpi)
         if model is not None:
             cfg.dt, cfg.mass, cfg.arm, cfg.kappa_yaw, cfg.gravity = model.dt, model.mass, model.arm, model.kappa, model.gravity
             for i in range(3):

@@ -38,7 +38,7 @@ TIE64 = 1e-9
 
 
 def run_gpu(prob, dtype, max_iter, tol, grad_u=None, grad_x=None, store_mode="store_all",
-            exec_mode="persistent", ipb=0, N_max=None, B_max=None, solver=None):
+            exec_mode="persistent", ipb=0, N_max=None, B_max=None, solver=None, tpi=0):
     import torch
     from paper_2605_29155_gb300 import DiffMPC, Problem
 
@@ -46,7 +46,7 @@ def run_gpu(prob, dtype, max_iter, tol, grad_u=None, grad_x=None, store_mode="st
     own = solver is None
     if own:
         solver = DiffMPC(N_max=N_max or N, B_max=B_max or max(B, 1), dtype=dtype, max_iter=max_iter, tol=tol,
-                         store_mode=store_mode, exec_mode=exec_mode, ipb=ipb)
+                         store_mode=store_mode, exec_mode=exec_mode, ipb=ipb, tpi=tpi)
     p = Problem.from_numpy(prob, dtype=dtype)
     s = solver.solve(p)
     out = dict(u=s.u, x=s.x, cost=s.cost, iters=s.iters, status=s.status)

@@ -99,8 +99,8 @@ def test_plain_form_is_bit_identical_to_persistent(dtype):
     dt = getattr(torch, dtype)
     prob = cached_problem("track", 48, 20, 1, True)
     gu, _ = _grads(48, 20, 3)
-    a = run_gpu(prob, dt, 8, 1e-6, gu, exec_mode="persistent", ipb=4)
-    b = run_gpu(prob, dt, 8, 1e-6, gu, exec_mode="plain", ipb=2)
+    a = run_gpu(prob, dt, 8, 1e-6, gu, exec_mode="persistent", tpi=16, ipb=8)
+    b = run_gpu(prob, dt, 8, 1e-6, gu, exec_mode="plain", tpi=16, ipb=4)
     assert set(a) == set(b)
     for k in a:
         np.testing.assert_array_equal(a[k], b[k], err_msg=k)
@@ -118,14 +118,30 @@ def test_recompute_backward_is_bit_identical_to_store_all(dtype):
         np.testing.assert_array_equal(a[k], b[k], err_msg=k)
 
 
-@pytest.mark.parametrize("ipb", [1, 2, 8])
-def test_launch_shapes_agree(ipb):
+@pytest.mark.parametrize("dtype,tpi,ipb", [("float32", 16, 2), ("float32", 16, 16), ("float32", 8, 4),
+                                            ("float32", 8, 32), ("float32", 32, 1), ("float32", 32, 8),
+                                            ("float64", 8, 8), ("float64", 32, 4)])
+def test_launch_shapes_agree(dtype, tpi, ipb):
+    """Every launch shape runs the same per-instance arithmetic.  Results are
+    bit-identical across instances per block, and across threads per instance
+    in FP64; in FP32 a different threads-per-instance count is a different
+    compiled kernel whose rounding can differ (fused multiply-add choices),
+    so there converged instances must agree to the parity tolerance."""
+    dt = getattr(torch, dtype)
     prob = cached_problem("track", 70, 20, 4, True)
-    ref = run_gpu(prob, torch.float32, 8, 1e-6, ipb=4)
-    got = run_gpu(prob, torch.float32, 8, 1e-6, ipb=ipb)
+    gu, gx = _grads(70, 20, 9)
+    ref_tpi = 16 if dtype == "float32" else 8
+    ref = run_gpu(prob, dt, 8, 1e-6, gu, gx, tpi=ref_tpi, ipb=4)
+    got = run_gpu(prob, dt, 8, 1e-6, gu, gx, tpi=tpi, ipb=ipb)
     assert set(ref) == set(got)
-    for k in ref:
-        np.testing.assert_array_equal(ref[k], got[k], err_msg=k)
+    if dtype == "float64" or tpi == ref_tpi:
+        for k in ref:
+            np.testing.assert_array_equal(ref[k], got[k], err_msg=k)
+    else:
+        conv = (ref["status"] == 0) & (got["status"] == 0)
+        assert conv.sum() >= 10
+        err = np.linalg.norm(got["u"][conv] - ref["u"][conv], axis=(1, 2)) / np.linalg.norm(ref["u"][conv], axis=(1, 2))
+        assert err.max() <= U_TOL32
 
 
 # ------------------------------------------------------------- edge cases --
