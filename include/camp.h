@@ -175,7 +175,7 @@ int mpc_launch_count(const mpc_handle *h, int has_horizon, int *fwd, int *bwd);
  * control loop that must not allocate after start-up, a plug-in whose host
  * application owns every device allocation).  Same problem, outputs and
  * per-instance statuses as mpc_solve_fwd in the persistent form, without a
- * handle: the scratch is one statically allocated device array (18.6 MB,
+ * handle: the scratch is one statically allocated device array (15.5 MB,
  * held on every device the library runs on until the process exits).
  *   cfg    as for mpc_create, dtype must be MPC_F32 (exec_mode, tpi, ipb,
  *          N_max and B_max are ignored); MPC_STORE_ALL writes the tape.

@@ -102,7 +102,7 @@ extern "C" int mpc_create(const mpc_config* cfg, mpc_handle** out) {
     h->slots = cfg->B_max > resident ? cfg->B_max : resident;
     const size_t es = elem_size(cfg->dtype);
     const size_t S = (size_t)h->slots, Nw = (size_t)cfg->N_max;
-    const size_t bF = align256(S * Nw * NF * es);
+    const size_t bF = align256(S * Nw * NFC * es);
     const size_t bK = align256(S * Nw * KREC * es);
     const size_t bC = align256(S * 4 * Nw * CREC * es);
     const size_t bX = align256(S * Nw * NX * es);

@@ -17,6 +17,7 @@ namespace camp {
 
 constexpr int NX = 13, NU = 4, NZ = 17;
 constexpr int NF = NX * NZ;            // entries of F_t = [A_t B_t], stored column-major
+constexpr int NFC = 11 * NX;           // scratch copy of F_t: only its 11 computed columns
 constexpr int TAPE_STRIDE = 288;       // tape record per stage (elements)
 constexpr int TAPE_F = 0, TAPE_K = 221, TAPE_L = 273, TAPE_MASK = 287;
 constexpr int NL = 14;                 // factor: packed lower 4x4 (10) + reciprocal diagonal (4)
@@ -253,6 +254,20 @@ __device__ __forceinline__ void tangent_column(const Model<T>& m, const T* __res
 // Packed lower-triangular index of a 4x4 factor.
 __device__ __forceinline__ int lidx(int i, int j) { return i * (i + 1) / 2 + j; }
 
+// Pivot of the Cholesky factor: l = sqrt(s) and 1 / l.  In FP32 from the
+// hardware reciprocal square root refined by one Newton step (about 1 ulp, as
+// accurate as the correctly rounded pair for the gradients, and a much shorter
+// serial chain in the box QP); in FP64 correctly rounded.
+__device__ __forceinline__ void pivot(float s, float& l, float& il) {
+    il = rsqrtf(s);
+    il = il * (1.5f - 0.5f * s * il * il);
+    l = s * il;
+}
+__device__ __forceinline__ void pivot(double s, double& l, double& il) {
+    l = sqrt(s);
+    il = 1.0 / l;
+}
+
 // Cholesky of H with the rows/columns outside `mask` replaced by the identity:
 // the free block is factored exactly, clamped dimensions decouple.  L[10 + j]
 // holds 1 / L_jj so that the solves multiply instead of divide.
@@ -272,8 +287,8 @@ __device__ __forceinline__ bool chol_masked(const T (&H)[4][4], int mask, T (&L)
 #pragma unroll
         for (int k = 0; k < j; ++k) s -= L[lidx(j, k)] * L[lidx(j, k)];
         if (!(s > T(0))) return false;
-        const T ljj = sqrt(s);
-        const T ij = T(1) / ljj;
+        T ljj, ij;
+        pivot(s, ljj, ij);
         L[lidx(j, j)] = ljj;
         L[10 + j] = ij;
 #pragma unroll
@@ -453,7 +468,7 @@ template <typename T> struct Inst {
     const T* xrefb;
     T* ub;            // nominal / output u  [N][4]
     T* xb;            // nominal / output x  [N][13]
-    T* F;             // slot scratch: F_t   [N_ws][221]
+    T* F;             // slot scratch: computed columns of F_t [N_ws][11][13]
     T* Kr;            // slot scratch: K_t,k_t [N_ws][56]
     T* cand;          // slot scratch: candidates [4][N_ws][30]
     T* sp;            // slot scratch: stage points [N_ws][32]
@@ -476,7 +491,7 @@ __device__ __forceinline__ Inst<T> make_inst(const Params<T>& P, int b, int slot
     I.ub = P.u + (size_t)b * P.N * NU;
     I.xb = P.x + (size_t)b * P.N * NX;
     const size_t s = (size_t)slot;
-    I.F = P.wsF + s * P.N_ws * NF;
+    I.F = P.wsF + s * P.N_ws * NFC;
     I.Kr = P.wsK + s * P.N_ws * KREC;
     I.cand = P.wsCand + s * 4 * P.N_ws * CREC;
     I.sp = P.wsSP + s * P.N_ws * SP_STRIDE;
@@ -550,8 +565,8 @@ __device__ T initial_rollout(const Params<T>& P, const Inst<T>& I, const WarpSme
 }
 
 // ------------------------------------------------------ A2 linearization ----
-// F_t = [A_t B_t] at the nominal for t = 0..n-2 into the slot ([t][221],
-// column-major; only the 11 computed columns are written): the group's lanes
+// F_t = [A_t B_t] at the nominal for t = 0..n-2 into the slot (its 11
+// computed columns, [t][11][13]): the group's lanes
 // first take one stage each for the RK4 stage points, then one
 // (stage, column) tangent each.
 template <typename T, int TPI>
@@ -567,10 +582,10 @@ __device__ void linearize(const Params<T>& P, const Inst<T>& I, const Lanes<TPI>
     }
     wsync();
     for (int w = L.l; w < ns * NGC; w += TPI) {
-        const int t = w / NGC, j = gcol(w - t * NGC);
+        const int t = w / NGC, jj = w - t * NGC;
         T col[NX];
-        tangent_column(P.mdl, I.sp + t * SP_STRIDE, j, col);
-        T* dst = I.F + (size_t)t * NF + j * NX;
+        tangent_column(P.mdl, I.sp + t * SP_STRIDE, gcol(jj), col);
+        T* dst = I.F + (size_t)t * NFC + jj * NX;
 #pragma unroll
         for (int i = 0; i < NX; ++i) dst[i] = col[i];
     }
@@ -610,6 +625,35 @@ __device__ bool riccati(const Params<T>& P, const Inst<T>& I, WarpSmem<T>& S, co
     if (L.l == 0) S.ok = 1;
     const T hv = hv_coef(P.mdl);
     bool alive = true;
+    // Software pipeline: the next stage's F_t columns and cost inputs are
+    // loaded into registers before the current stage computes.
+    constexpr int FR = (NFC + TPI - 1) / TPI;
+    constexpr int CR = (NZ + TPI - 1) / TPI;
+    T fpre[FR], cq[CR], cz[CR], cr[CR];
+    auto prefetch = [&](int tt) {
+        if (tt < 0 || tt >= n || o.replay) return;
+        if (tt < n - 1) {
+            const T* Ft = I.F + (size_t)tt * NFC;
+#pragma unroll
+            for (int r = 0; r < FR; ++r) {
+                const int e = L.l + r * TPI;
+                if (e < NFC) fpre[r] = Ft[e];
+            }
+        }
+        const T* Qt = Qrow(P, I, tt);
+#pragma unroll
+        for (int r = 0; r < CR; ++r) {
+            const int a = L.l + r * TPI;
+            if (a < NX) {
+                cq[r] = Qt[a];
+                cz[r] = I.xb[tt * NX + a] - I.xrefb[tt * NX + a];
+                cr[r] = o.use_lo ? I.xlo[tt * NX + a] : T(0);
+            } else if (a < NZ) {
+                cz[r] = I.ub[tt * NU + a - NX];
+            }
+        }
+    };
+    prefetch(n - 1);
     wsync();
     for (int t = nmax - 1; t >= 0; --t) {
         const bool on = alive && t < n;
@@ -629,32 +673,34 @@ __device__ bool riccati(const Params<T>& P, const Inst<T>& I, WarpSmem<T>& S, co
             wsync();
         } else {
             if (on) {
-                const T* Qt = Qrow(P, I, t);
-                for (int a = L.l; a < NZ; a += TPI) {
-                    T cd, e;
+#pragma unroll
+                for (int r = 0; r < CR; ++r) {
+                    const int a = L.l + r * TPI;
                     if (a < NX) {
-                        cd = Qt[a];
-                        e = I.xb[t * NX + a] - I.xrefb[t * NX + a];
-                        if (o.use_lo) e += I.xlo[t * NX + a];
-                    } else {
-                        cd = S.R[a - NX];
-                        e = I.ub[t * NU + a - NX] - S.uref[a - NX];
+                        S.Cd[a] = cq[r];
+                        S.c[a] = cq[r] * (o.use_lo ? cz[r] + cr[r] : cz[r]);
+                    } else if (a < NZ) {
+                        const T cd = S.R[a - NX];
+                        S.Cd[a] = cd;
+                        S.c[a] = cd * (cz[r] - S.uref[a - NX]);
                     }
-                    S.Cd[a] = cd;
-                    S.c[a] = cd * e;
                 }
             }
             if (dyn) {
-                const T* Ft = I.F + (size_t)t * NF;
-                for (int e = L.l; e < NGC * NX; e += TPI) {
-                    const int jj = e / NX, i = e - jj * NX, j = gcol(jj);
-                    S.F[j * NX + i] = Ft[j * NX + i];
+#pragma unroll
+                for (int r = 0; r < FR; ++r) {
+                    const int e = L.l + r * TPI;
+                    if (e < NFC) {
+                        const int jj = e / NX, i = e - jj * NX;
+                        S.F[gcol(jj) * NX + i] = fpre[r];
+                    }
                 }
                 for (int e = L.l; e < NTC * NX; e += TPI) {
                     const int jj = e / NX, i = e - jj * NX, j = tcol(jj);
                     S.F[j * NX + i] = (i == j) ? T(1) : ((j >= 7 && i == j - 7) ? hv : T(0));
                 }
             }
+            if (on) prefetch(t - 1);
             wsync();
             if (dyn) {
                 // W = V F (column-major): 11 computed columns, then the constant ones
@@ -829,31 +875,49 @@ __device__ bool riccati(const Params<T>& P, const Inst<T>& I, WarpSmem<T>& S, co
 // against J's magnitude; with the hi + lo states it resolves differences far
 // below the working precision of J.  alpha* = first argmin, and the best
 // candidate becomes the next nominal (Sec. IV-3).  Each stage's gains, nominal
-// and cost rows are staged into shared memory one stage ahead by the group's
-// other lanes.  Returns 0 (step taken: du, J updated) or 1 (no candidate with
-// a finite cost: nominal kept).
+// and cost rows are fetched into registers two stages ahead by all lanes of
+// the group and staged into shared memory one stage ahead.  Returns 0 (step
+// taken: du, J updated) or 1 (no candidate with a finite cost: nominal kept).
+// Entry e of stage t's staged record: K_t, k_t (56), x (13), x lo (13), u (4),
+// Q_t (13), x_ref,t (13).
 template <typename T>
-__device__ __forceinline__ void ls_stage_load(const Params<T>& P, const Inst<T>& I, T* dst, int t, int e0, int step) {
-    const T* Qt = Qrow(P, I, t);
-    for (int e = e0; e < 112; e += step) {
-        T v;
-        if (e < KREC) v = I.Kr[(size_t)t * KREC + e];
-        else if (e < KREC + NX) v = I.xb[t * NX + e - KREC];
-        else if (e < KREC + 2 * NX) v = I.xlo[t * NX + e - KREC - NX];
-        else if (e < KREC + 2 * NX + NU) v = I.ub[t * NU + e - KREC - 2 * NX];
-        else if (e < KREC + 3 * NX + NU) v = Qt[e - KREC - 2 * NX - NU];
-        else v = I.xrefb[t * NX + e - KREC - 3 * NX - NU];
-        dst[e] = v;
-    }
+__device__ __forceinline__ T ls_stage_value(const Params<T>& P, const Inst<T>& I, int t, int e) {
+    if (e < KREC) return I.Kr[(size_t)t * KREC + e];
+    if (e < KREC + NX) return I.xb[t * NX + e - KREC];
+    if (e < KREC + 2 * NX) return I.xlo[t * NX + e - KREC - NX];
+    if (e < KREC + 2 * NX + NU) return I.ub[t * NU + e - KREC - 2 * NX];
+    if (e < KREC + 3 * NX + NU) return Qrow(P, I, t)[e - KREC - 2 * NX - NU];
+    return I.xrefb[t * NX + e - KREC - 3 * NX - NU];
 }
 
 template <typename T, int TPI>
 __device__ int line_search(const Params<T>& P, const Inst<T>& I, WarpSmem<T>& S, const Lanes<TPI>& L, bool act,
                            T& Jnom, T& du_out) {
-    static_assert(TPI >= 8, "line search needs 4 candidate lanes and at least 4 staging lanes");
+    static_assert(TPI >= 4, "line search needs 4 candidate lanes");
     const int n = act ? I.n : 0;
     const int nmax = warp_max(n);
-    if (act) ls_stage_load(P, I, S.stg[0], 0, L.l, TPI);
+    constexpr int SR = (112 + TPI - 1) / TPI;
+    T pre[SR];
+    auto fetch = [&](int tt) {
+        if (tt >= n) return;
+#pragma unroll
+        for (int r = 0; r < SR; ++r) {
+            const int e = L.l + r * TPI;
+            if (e < 112) pre[r] = ls_stage_value(P, I, tt, e);
+        }
+    };
+    auto stash = [&](int tt) {
+        if (tt >= n) return;
+        T* dst = S.stg[tt & 1];
+#pragma unroll
+        for (int r = 0; r < SR; ++r) {
+            const int e = L.l + r * TPI;
+            if (e < 112) dst[e] = pre[r];
+        }
+    };
+    fetch(0);
+    stash(0);
+    fetch(1);
     wsync();
     const bool cl = act && L.l < P.n_alpha;
     const T alpha = cl ? P.alpha[L.l] : T(0);
@@ -897,8 +961,11 @@ __device__ int line_search(const Params<T>& P, const Inst<T>& I, WarpSmem<T>& S,
 #pragma unroll
             for (int a = 0; a < NU; ++a) cd[t * CREC + 2 * NX + a] = uh[a];
             if (t < n - 1) rk4_step2(P.mdl, xh, xl, uh);
-        } else if (act && L.l >= 4 && t + 1 < n) {
-            ls_stage_load(P, I, S.stg[(t + 1) & 1], t + 1, L.l - 4, TPI - 4);
+        }
+        // stage t + 1 was fetched during stage t's work; stash it, fetch t + 2
+        if (act) {
+            stash(t + 1);
+            fetch(t + 2);
         }
         wsync();
     }
@@ -951,10 +1018,11 @@ __device__ int line_search(const Params<T>& P, const Inst<T>& I, WarpSmem<T>& S,
 // dx_0 = 0; du_t = K_t dx_t + kh_t; dx_{t+1} = F_t [dx_t; du_t]; with
 // d_tau_t = [dx_t; du_t]:  dQ_t = dx_t * (x*_t - x_ref,t),  dx_ref,t = -Q_t * dx_t,
 // dx0 = vh_0 (value gradient of the adjoint LQR).  Fsrc / Ksrc: per-stage F_t
-// and K_t with strides fs / ks (tape records or slot scratch).
+// and K_t with strides fs / ks: tape records (full F_t) or slot scratch (its
+// 11 computed columns, fcompact).
 template <typename T, int TPI>
 __device__ void adjoint_forward(const Params<T>& P, const Inst<T>& I, WarpSmem<T>& S, const Lanes<TPI>& L,
-                                bool act, const T* Fsrc, size_t fs, const T* Ksrc, size_t ks,
+                                bool act, const T* Fsrc, size_t fs, bool fcompact, const T* Ksrc, size_t ks,
                                 const AdjArgs<T>& A) {
     const int n = act ? I.n : 0;
     const int nmax = warp_max(n);
@@ -997,7 +1065,7 @@ __device__ void adjoint_forward(const Params<T>& P, const Inst<T>& I, WarpSmem<T
 #pragma unroll
                     for (int jj = 0; jj < NGC; ++jj) {
                         const int j = gcol(jj);
-                        s += Ft[j * NX + i] * (j < NX ? S.dx[j] : S.du[j - NX]);
+                        s += Ft[(fcompact ? jj : j) * NX + i] * (j < NX ? S.dx[j] : S.du[j - NX]);
                     }
                     if (i < 3) s += S.dx[i] + hv_coef(P.mdl) * S.dx[i + 7];
                     else if (i >= 7 && i < 10) s += S.dx[i];

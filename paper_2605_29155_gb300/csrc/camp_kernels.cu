@@ -185,9 +185,9 @@ __global__ void __launch_bounds__(256, 2) k_mpc(Params<T> P, AdjArgs<T> A, int m
                 const T* tb = A.recompute ? (const T*)nullptr : P.tape + (size_t)I.b * P.N * TAPE_STRIDE;
                 const T* Fs = A.recompute ? (const T*)I.F : tb + TAPE_F;
                 const T* Ks = A.recompute ? (const T*)I.Kr : tb + TAPE_K;
-                const size_t fs = A.recompute ? (size_t)NF : (size_t)TAPE_STRIDE;
+                const size_t fs = A.recompute ? (size_t)NFC : (size_t)TAPE_STRIDE;
                 const size_t ks = A.recompute ? (size_t)KREC : (size_t)TAPE_STRIDE;
-                adjoint_forward(P, I, S, L, ok_bwd, Fs, fs, Ks, ks, A);
+                adjoint_forward(P, I, S, L, ok_bwd, Fs, fs, A.recompute != 0, Ks, ks, A);
                 next = PH_BZERO;
             } else if (ph == PH_BZERO) {
                 zero_grads(P, A, b, L, valid && !ok_bwd);

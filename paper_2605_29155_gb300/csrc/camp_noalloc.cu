@@ -32,13 +32,13 @@ using namespace camp;
 
 namespace {
 
-constexpr int NA_TPI = 32, NA_IPB = 4;                      // threads per instance, instances per block
+constexpr int NA_TPI = 16, NA_IPB = 8;                      // the handle's default launch shape
 constexpr int NA_SLOTS = MPC_NOALLOC_B_MAX + NA_IPB;        // warp slots the grid can use
 constexpr size_t NA_STAGES = (size_t)NA_SLOTS * MPC_NOALLOC_N_MAX;
 
 constexpr size_t a256(size_t floats) { return (floats + 63) & ~(size_t)63; }   // 64 floats = 256 bytes
 constexpr size_t OFF_F = 0;
-constexpr size_t OFF_K = OFF_F + a256(NA_STAGES * NF);
+constexpr size_t OFF_K = OFF_F + a256(NA_STAGES * NFC);
 constexpr size_t OFF_C = OFF_K + a256(NA_STAGES * KREC);
 constexpr size_t OFF_P = OFF_C + a256(NA_STAGES * 4 * CREC);
 constexpr size_t OFF_H = OFF_P + a256(NA_STAGES * SP_STRIDE);
@@ -49,7 +49,7 @@ constexpr size_t NA_FLOATS = OFF_O + a256(MPC_NOALLOC_B_MAX);
 
 }  // namespace
 
-// The scratch array (4,638,752 floats, 18.6 MB).  In host code this name is only a host-side
+// The scratch array (3,886,400 floats, 15.5 MB).  In host code this name is only a host-side
 // stand-in: kernels get the device address looked up below.
 static __device__ __align__(256) float g_noalloc_scratch[NA_FLOATS];
 
