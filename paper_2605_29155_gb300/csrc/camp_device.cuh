@@ -64,7 +64,6 @@ template <typename T> struct WarpSmem {
     T V[NX * NX];      // value Hessian V_{t+1} (full symmetric storage)
     T v[NX];           // value gradient v_{t+1}
     T F[NF];           // F_t column-major: F[j*13 + i] = dx+_i / dz_j
-    T W[NF];           // V_{t+1} F_t, column-major
     T Qm[NZ * NZ];     // Q_t (row-major, full)
     T q[NZ];           // q_t
     T c[NZ];           // C_t z_t + c_t at the nominal
@@ -74,6 +73,7 @@ template <typename T> struct WarpSmem {
     T L[NL];           // Cholesky of Q_uu on the free set (packed lower, masked) + 1/diag
     T x0[NX];
     T R[NU], uref[NU], ulo[NU], uhi[NU];
+    T ut[NU];          // the nominal u_t of the current Riccati stage
     T Jc[4];
     T stg[2][112];     // line search: next stage's K, k, x, x lo, u, Q, x_ref (double buffered)
     T vh[NX];          // adjoint value gradient
@@ -683,6 +683,7 @@ __device__ bool riccati(const Params<T>& P, const Inst<T>& I, WarpSmem<T>& S, co
                         const T cd = S.R[a - NX];
                         S.Cd[a] = cd;
                         S.c[a] = cd * (cz[r] - S.uref[a - NX]);
+                        S.ut[a - NX] = cz[r];
                     }
                 }
             }
@@ -703,48 +704,56 @@ __device__ bool riccati(const Params<T>& P, const Inst<T>& I, WarpSmem<T>& S, co
             if (on) prefetch(t - 1);
             wsync();
             if (dyn) {
-                // W = V F (column-major): 11 computed columns, then the constant ones
-                for (int e = L.l; e < NGC * NX; e += TPI) {
-                    const int jj = e / NX, i = e - jj * NX, j = gcol(jj);
-                    T s = T(0);
+                // Column products.  Item c < NTC is the constant column tcol(c),
+                // item c >= NTC the computed column gcol(c - NTC); its lane forms
+                //   W[:, j] = V F[:, j]            (in registers)
+                //   Q[r, j] = C_rj + F[:, r]' W[:, j] for every row r (rows of the
+                //             constant columns take one or two entries of W[:, j])
+                //   q[j]    = c_j + F[:, j]' v
+                // and, for a computed column, mirrors its entries in the constant
+                // rows into Q[j, r], so the upper triangle of Q is complete.
+                for (int c = L.l; c < NZ; c += TPI) {
+                    const bool cc = c < NTC;
+                    const int j = cc ? tcol(c) : gcol(c - NTC);
+                    T w[NX];
+                    T qj;
+                    if (cc) {
 #pragma unroll
-                    for (int k = 0; k < NX; ++k) s += S.V[i * NX + k] * S.F[j * NX + k];
-                    S.W[j * NX + i] = s;
-                }
-                for (int e = L.l; e < NTC * NX; e += TPI) {
-                    const int jj = e / NX, i = e - jj * NX, j = tcol(jj);
-                    S.W[j * NX + i] = (j < 3) ? S.V[i * NX + j] : S.V[i * NX + j] + hv * S.V[i * NX + j - 7];
-                }
-            }
-            wsync();
-            if (dyn) {
-                // Q = C + F' W (upper triangle), q = c + F' v; rows of the
-                // constant columns need one or two terms
-                for (int p = L.l; p < NTRI_Q + NZ; p += TPI) {
-                    if (p < NTRI_Q) {
-                        const int ab = triQ[p], a = ab >> 8, bb = ab & 0xff;
-                        T s = (a == bb) ? S.Cd[a] : T(0);
-                        if (a < 3) {
-                            s += S.W[bb * NX + a];
-                        } else if (a >= 7 && a < 10) {
-                            s += S.W[bb * NX + a] + hv * S.W[bb * NX + a - 7];
-                        } else {
-#pragma unroll
-                            for (int k = 0; k < NX; ++k) s += S.F[a * NX + k] * S.W[bb * NX + k];
-                        }
-                        S.Qm[a * NZ + bb] = s;
+                        for (int i = 0; i < NX; ++i)
+                            w[i] = (j < 3) ? S.V[i * NX + j] : S.V[i * NX + j] + hv * S.V[i * NX + j - 7];
+                        qj = S.c[j] + ((j < 3) ? S.v[j] : S.v[j] + hv * S.v[j - 7]);
                     } else {
-                        const int a = p - NTRI_Q;
-                        T s = S.c[a];
-                        if (a < 3) {
-                            s += S.v[a];
-                        } else if (a >= 7 && a < 10) {
-                            s += S.v[a] + hv * S.v[a - 7];
+                        T f[NX];
+#pragma unroll
+                        for (int k = 0; k < NX; ++k) f[k] = S.F[j * NX + k];
+#pragma unroll
+                        for (int i = 0; i < NX; ++i) {
+                            T s = T(0);
+#pragma unroll
+                            for (int k = 0; k < NX; ++k) s += S.V[i * NX + k] * f[k];
+                            w[i] = s;
+                        }
+                        T s = S.c[j];
+#pragma unroll
+                        for (int k = 0; k < NX; ++k) s += f[k] * S.v[k];
+                        qj = s;
+                    }
+                    S.q[j] = qj;
+#pragma unroll
+                    for (int r = 0; r < NZ; ++r) {
+                        const bool rc = r < 3 || (r >= 7 && r < 10);
+                        if (cc && !rc) continue;          // filled by the computed column's mirror
+                        T s = (r == j) ? S.Cd[j] : T(0);
+                        if (r < 3) {
+                            s += w[r];
+                        } else if (r >= 7 && r < 10) {
+                            s += w[r] + hv * w[r - 7];
                         } else {
 #pragma unroll
-                            for (int k = 0; k < NX; ++k) s += S.F[a * NX + k] * S.v[k];
+                            for (int k = 0; k < NX; ++k) s += S.F[r * NX + k] * w[k];
                         }
-                        S.q[a] = s;
+                        S.Qm[r * NZ + j] = s;
+                        if (!cc && rc) S.Qm[j * NZ + r] = s;
                     }
                 }
             } else if (on) {
@@ -764,7 +773,7 @@ __device__ bool riccati(const Params<T>& P, const Inst<T>& I, WarpSmem<T>& S, co
                     for (int bb = 0; bb < 4; ++bb)
                         H[a][bb] = a <= bb ? S.Qm[(NX + a) * NZ + NX + bb] : S.Qm[(NX + bb) * NZ + NX + a];
                     g[a] = S.q[NX + a];
-                    const T ub = I.ub[t * NU + a];
+                    const T ub = S.ut[a];
                     lo[a] = S.ulo[a] - ub;
                     hi[a] = S.uhi[a] - ub;
                 }

@@ -4,7 +4,9 @@ FP64 oracle on the same seeded inputs, and compare them instance by instance.
 Tolerances (FP32 path vs FP64 oracle, per instance):
   controls   |u - u_or|_2 / max(|u_or|_2, 1e-6)            <= 1e-4
   cost       |J - J_or| / max(|J_or|, 1e-12)                 <= 1e-5
-  gradients  |g - g_or|_2 / max(|g_or|_2, 1e-9) per block   <= 1e-3
+  gradients  |g - g_or|_2 / max(|g_or|_2, 1e-9) per block   <= 1e-3, where for
+             a Q shared over the stages the denominator is at least 0.1 x the
+             size of the per-stage terms its gradient sums (dq_term_scale)
 Instances the oracle solves to convergence are compared with its solution.
 Instances still iterating at max_iter follow a path that rounding-level
 decisions steer (reading R12), so for them the returned iterate is checked
@@ -204,8 +206,20 @@ def compare32(gpu, prob, orc, idx, grad_u, grad_x=None):
                 ref2.X = ref.X
                 ref_gr = adjoint.adjoint(pr, ref2, gx, grad_u[i])
         for name, r in (("dQ", ref_gr.dQ), ("dx_ref", ref_gr.dx_ref), ("dx0", ref_gr.dx0)):
-            eg = rel(gpu[name][i], r, 1e-9)
+            floor = 1e-9
+            if name == "dQ" and pr.Q.shape[0] == 1:
+                floor = max(floor, 0.1 * dq_term_scale(pr, ref, ref_gr))
+            eg = rel(gpu[name][i], r, floor)
             rep["max_g"] = max(rep["max_g"], eg)
             if eg > G_TOL32:
                 fails.append((i, name, eg))
     return rep, fails
+
+
+def dq_term_scale(pr, sol, gr):
+    """|| sum_t |d_x,t * (x*_t - x_ref,t)| ||: the size of the terms a shared
+    Q's gradient sums over the stages.  Those terms can cancel (the sum can be
+    ~60x smaller than their magnitudes), and a rounding error of the sum is
+    relative to them, not to the sum."""
+    terms = np.array([gr.dX[t] * (sol.X[t] - pr.x_ref[t]) for t in range(pr.n)])
+    return float(np.linalg.norm(np.abs(terms).sum(0)))
