@@ -18,14 +18,13 @@ namespace camp {
 constexpr int NX = 13, NU = 4, NZ = 17;
 constexpr int NF = NX * NZ;            // entries of F_t = [A_t B_t], stored column-major
 constexpr int NFC = 11 * NX;           // scratch copy of F_t: only its 11 computed columns
+constexpr int LD = 16;                 // row / column stride of V_t and F_t in shared memory (128-bit aligned)
 constexpr int TAPE_STRIDE = 288;       // tape record per stage (elements)
 constexpr int TAPE_F = 0, TAPE_K = 221, TAPE_L = 273, TAPE_MASK = 287;
 constexpr int NL = 14;                 // factor: packed lower 4x4 (10) + reciprocal diagonal (4)
 constexpr int KREC = 56;               // K_t (52, row-major) + k_t (4)
 constexpr int SP_STRIDE = 32;          // RK4 stage points per stage: 4 x (q, w, pad)
 constexpr int CREC = 30;               // line-search candidate per stage: x hi (13), x lo (13), u (4)
-constexpr int NTRI_Q = NZ * (NZ + 1) / 2;   // 153 upper-triangle entries of Q_t
-constexpr int NTRI_V = NX * (NX + 1) / 2;   // 91 upper-triangle entries of V_t
 constexpr int QP_MAX_IT = 20, QP_MAX_LS = 30;
 constexpr unsigned FULL = 0xffffffffu;
 
@@ -60,10 +59,13 @@ template <typename T> struct AdjArgs {
 };
 
 // Per-instance shared-memory record.
-template <typename T> struct WarpSmem {
-    T V[NX * NX];      // value Hessian V_{t+1} (full symmetric storage)
-    T v[NX];           // value gradient v_{t+1}
-    T F[NF];           // F_t column-major: F[j*13 + i] = dx+_i / dz_j
+template <typename T> struct alignas(16) WarpSmem {
+    T V[NX * LD];      // value Hessian V_{t+1}: V[i*LD + j] (full symmetric storage)
+    T F[2][NZ * LD];   // F_t column-major, F[t & 1][j*LD + i] = dx+_i / dz_j (double buffered)
+    T Qxu[NX * NU];    // x-u block of Q_t again, Qxu[i*4 + a] = Q[i][13 + a]
+    T v[LD];           // value gradient v_{t+1} (13 used)
+    T stg[2][112];     // a stage's inputs, prefetched (double buffered): K_t, k_t (56), then
+                       // x_t, x lo_t, u_t, Q_t, x_ref,t (SIN entries)
     T Qm[NZ * NZ];     // Q_t (row-major, full)
     T q[NZ];           // q_t
     T c[NZ];           // C_t z_t + c_t at the nominal
@@ -75,7 +77,6 @@ template <typename T> struct WarpSmem {
     T R[NU], uref[NU], ulo[NU], uhi[NU];
     T ut[NU];          // the nominal u_t of the current Riccati stage
     T Jc[4];
-    T stg[2][112];     // line search: next stage's K, k, x, x lo, u, Q, x_ref (double buffered)
     T vh[NX];          // adjoint value gradient
     T qh[NZ];          // adjoint q-hat
     T dx[NX];          // adjoint forward-sweep state
@@ -90,6 +91,52 @@ template <typename T> __device__ __forceinline__ T clampT(T v, T lo, T hi) {
 }
 
 template <typename T> __device__ __forceinline__ bool finiteT(T v) { return isfinite(v); }
+
+// 13 (or 4) consecutive entries of a 16-byte aligned shared-memory row, read
+// with 128-bit loads.
+__device__ __forceinline__ void ld13(const float* p, float (&o)[NX]) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const float4 u = reinterpret_cast<const float4*>(p)[k];
+        o[4 * k] = u.x; o[4 * k + 1] = u.y; o[4 * k + 2] = u.z; o[4 * k + 3] = u.w;
+    }
+    o[12] = p[12];
+}
+__device__ __forceinline__ void ld13(const double* p, double (&o)[NX]) {
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+        const double2 u = reinterpret_cast<const double2*>(p)[k];
+        o[2 * k] = u.x; o[2 * k + 1] = u.y;
+    }
+    o[12] = p[12];
+}
+__device__ __forceinline__ void ld4(const float* p, float (&o)[4]) {
+    const float4 u = *reinterpret_cast<const float4*>(p);
+    o[0] = u.x; o[1] = u.y; o[2] = u.z; o[3] = u.w;
+}
+__device__ __forceinline__ void ld4(const double* p, double (&o)[4]) {
+    const double2 u = reinterpret_cast<const double2*>(p)[0], w = reinterpret_cast<const double2*>(p)[1];
+    o[0] = u.x; o[1] = u.y; o[2] = w.x; o[3] = w.y;
+}
+
+// Asynchronous global -> shared copies (cp.async): the data lands in shared
+// memory without passing through registers; a lane waits for its own copies
+// with cp_async_wait_all, and a warp barrier after that makes every lane's
+// copies visible to the group.
+template <typename T> __device__ __forceinline__ void cp_async(T* dst, const T* src) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    if constexpr (sizeof(T) == 4)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src) : "memory");
+}
+// 16 bytes; both addresses 16-byte aligned.
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
 // ------------------------------------------------------------------ model ----
 // Continuous quadrotor model x' = f_c(x, u):
@@ -505,6 +552,31 @@ __device__ __forceinline__ const T* Qrow(const Params<T>& P, const Inst<T>& I, i
     return I.Qb + (P.Nq > 1 ? t : 0) * NX;
 }
 
+// A stage's nominal and cost inputs as staged in shared memory (after K_t, k_t
+// in the line search's record): x_t, x lo_t, u_t, Q_t, x_ref,t.
+constexpr int SI_X = 0, SI_XL = NX, SI_U = 2 * NX, SI_Q = 2 * NX + NU, SI_R = 3 * NX + NU, SIN = 4 * NX + NU;
+
+template <typename T>
+__device__ __forceinline__ const T* stage_input_src(const Params<T>& P, const Inst<T>& I, int t, int e) {
+    if (e < SI_XL) return I.xb + t * NX + e;
+    if (e < SI_U) return I.xlo + t * NX + e - SI_XL;
+    if (e < SI_Q) return I.ub + t * NU + e - SI_U;
+    if (e < SI_R) return Qrow(P, I, t) + e - SI_Q;
+    return I.xrefb + t * NX + e - SI_R;
+}
+
+// Starts the asynchronous copy of stage t's inputs to dst[0..SIN).
+template <typename T, int TPI>
+__device__ __forceinline__ void stage_inputs_async(const Params<T>& P, const Inst<T>& I, const Lanes<TPI>& L, int t,
+                                                   T* dst) {
+    constexpr int R = (SIN + TPI - 1) / TPI;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int e = L.l + r * TPI;
+        if (e < SIN) cp_async(dst + e, stage_input_src(P, I, t, e));
+    }
+}
+
 template <typename T, int TPI>
 __device__ __forceinline__ void load_instance(const Params<T>& P, const Inst<T>& I, WarpSmem<T>& S,
                                               const Lanes<TPI>& L, bool act) {
@@ -617,125 +689,125 @@ template <typename T> struct RicOpts {
 
 template <typename T, int TPI>
 __device__ bool riccati(const Params<T>& P, const Inst<T>& I, WarpSmem<T>& S, const Lanes<TPI>& L,
-                        const int* triQ, const int* triV, const RicOpts<T> o, bool act) {
+                        const RicOpts<T> o, bool act) {
     const int n = act ? I.n : 0;
     const int nmax = warp_max(n);
-    for (int e = L.l; e < NX * NX; e += TPI) S.V[e] = T(0);
+    for (int e = L.l; e < NX * LD; e += TPI) S.V[e] = T(0);
     for (int e = L.l; e < NX; e += TPI) { S.v[e] = T(0); S.vh[e] = T(0); }
     if (L.l == 0) S.ok = 1;
     const T hv = hv_coef(P.mdl);
+    // The six constant columns of F_t (p and v: identity, plus hv on the p
+    // rows of the v columns) are the same at every stage: both buffers.
+    for (int e = L.l; e < NTC * NX; e += TPI) {
+        const int jj = e / NX, i = e - jj * NX, j = tcol(jj);
+        const T val = (i == j) ? T(1) : ((j >= 7 && i == j - 7) ? hv : T(0));
+        S.F[0][j * LD + i] = val;
+        S.F[1][j * LD + i] = val;
+    }
     bool alive = true;
-    // Software pipeline: the next stage's F_t columns and cost inputs are
-    // loaded into registers before the current stage computes.
-    constexpr int FR = (NFC + TPI - 1) / TPI;
-    constexpr int CR = (NZ + TPI - 1) / TPI;
-    T fpre[FR], cq[CR], cz[CR], cr[CR];
+    // Software pipeline: while stage t computes, stage t - 1's F_t columns and
+    // cost inputs are copied asynchronously into the other buffers.
     auto prefetch = [&](int tt) {
         if (tt < 0 || tt >= n || o.replay) return;
         if (tt < n - 1) {
             const T* Ft = I.F + (size_t)tt * NFC;
+            T* Fd = S.F[tt & 1];
+            constexpr int FR = (NFC + TPI - 1) / TPI;
 #pragma unroll
             for (int r = 0; r < FR; ++r) {
                 const int e = L.l + r * TPI;
-                if (e < NFC) fpre[r] = Ft[e];
+                if (e < NFC) {
+                    const int jj = e / NX;
+                    cp_async(Fd + gcol(jj) * LD + e - jj * NX, Ft + e);
+                }
             }
         }
-        const T* Qt = Qrow(P, I, tt);
-#pragma unroll
-        for (int r = 0; r < CR; ++r) {
-            const int a = L.l + r * TPI;
-            if (a < NX) {
-                cq[r] = Qt[a];
-                cz[r] = I.xb[tt * NX + a] - I.xrefb[tt * NX + a];
-                cr[r] = o.use_lo ? I.xlo[tt * NX + a] : T(0);
-            } else if (a < NZ) {
-                cz[r] = I.ub[tt * NU + a - NX];
-            }
-        }
+        stage_inputs_async(P, I, L, tt, S.stg[tt & 1] + KREC);
+        cp_async_commit();
     };
     prefetch(n - 1);
-    wsync();
     for (int t = nmax - 1; t >= 0; --t) {
         const bool on = alive && t < n;
         const bool dyn = on && t < n - 1;
         bool go = on;
+        T* Fc = S.F[t & 1];
         if (o.replay) {
+            wsync();
             if (on) {
                 const T* rec = P.tape + ((size_t)I.b * P.N + t) * TAPE_STRIDE;
                 for (int e = L.l; e < TAPE_MASK; e += TPI) {
                     const T val = rec[e];
-                    if (e < TAPE_K) S.F[e] = val;
-                    else if (e < TAPE_L) S.K[e - TAPE_K] = val;
-                    else S.L[e - TAPE_L] = val;
+                    if (e < TAPE_K) {
+                        const int j = e / NX;
+                        Fc[j * LD + e - j * NX] = val;
+                    } else if (e < TAPE_L) {
+                        S.K[e - TAPE_K] = val;
+                    } else {
+                        S.L[e - TAPE_L] = val;
+                    }
                 }
                 if (L.l == 0) S.mask = (int)rec[TAPE_MASK];
             }
             wsync();
         } else {
+            cp_async_wait_all();
+            wsync();
             if (on) {
-#pragma unroll
-                for (int r = 0; r < CR; ++r) {
-                    const int a = L.l + r * TPI;
+                const T* si = S.stg[t & 1] + KREC;
+                for (int a = L.l; a < NZ; a += TPI) {
                     if (a < NX) {
-                        S.Cd[a] = cq[r];
-                        S.c[a] = cq[r] * (o.use_lo ? cz[r] + cr[r] : cz[r]);
-                    } else if (a < NZ) {
-                        const T cd = S.R[a - NX];
+                        const T qa = si[SI_Q + a], ea = si[SI_X + a] - si[SI_R + a];
+                        S.Cd[a] = qa;
+                        S.c[a] = qa * (o.use_lo ? ea + si[SI_XL + a] : ea);
+                    } else {
+                        const T cd = S.R[a - NX], ua = si[SI_U + a - NX];
                         S.Cd[a] = cd;
-                        S.c[a] = cd * (cz[r] - S.uref[a - NX]);
-                        S.ut[a - NX] = cz[r];
+                        S.c[a] = cd * (ua - S.uref[a - NX]);
+                        S.ut[a - NX] = ua;
                     }
                 }
+                prefetch(t - 1);
             }
-            if (dyn) {
-#pragma unroll
-                for (int r = 0; r < FR; ++r) {
-                    const int e = L.l + r * TPI;
-                    if (e < NFC) {
-                        const int jj = e / NX, i = e - jj * NX;
-                        S.F[gcol(jj) * NX + i] = fpre[r];
-                    }
-                }
-                for (int e = L.l; e < NTC * NX; e += TPI) {
-                    const int jj = e / NX, i = e - jj * NX, j = tcol(jj);
-                    S.F[j * NX + i] = (i == j) ? T(1) : ((j >= 7 && i == j - 7) ? hv : T(0));
-                }
-            }
-            if (on) prefetch(t - 1);
             wsync();
             if (dyn) {
-                // Column products.  Item c < NTC is the constant column tcol(c),
-                // item c >= NTC the computed column gcol(c - NTC); its lane forms
+                // Column products.  Item c < NGC is the computed column gcol(c),
+                // item c >= NGC the constant column tcol(c - NGC) (the costly
+                // items first, so that no lane takes two of them while others
+                // idle); its lane forms
                 //   W[:, j] = V F[:, j]            (in registers)
                 //   Q[r, j] = C_rj + F[:, r]' W[:, j] for every row r (rows of the
                 //             constant columns take one or two entries of W[:, j])
                 //   q[j]    = c_j + F[:, j]' v
                 // and, for a computed column, mirrors its entries in the constant
-                // rows into Q[j, r], so the upper triangle of Q is complete.
+                // rows into Q[j, r], so the upper triangle of Q is complete; the
+                // lanes of the u columns also fill Qxu.
                 for (int c = L.l; c < NZ; c += TPI) {
-                    const bool cc = c < NTC;
-                    const int j = cc ? tcol(c) : gcol(c - NTC);
+                    const bool cc = c >= NGC;
+                    const int j = cc ? tcol(c - NGC) : gcol(c);
                     T w[NX];
                     T qj;
                     if (cc) {
 #pragma unroll
                         for (int i = 0; i < NX; ++i)
-                            w[i] = (j < 3) ? S.V[i * NX + j] : S.V[i * NX + j] + hv * S.V[i * NX + j - 7];
+                            w[i] = (j < 3) ? S.V[i * LD + j] : S.V[i * LD + j] + hv * S.V[i * LD + j - 7];
                         qj = S.c[j] + ((j < 3) ? S.v[j] : S.v[j] + hv * S.v[j - 7]);
                     } else {
                         T f[NX];
-#pragma unroll
-                        for (int k = 0; k < NX; ++k) f[k] = S.F[j * NX + k];
+                        ld13(Fc + j * LD, f);
 #pragma unroll
                         for (int i = 0; i < NX; ++i) {
+                            T vr[NX];
+                            ld13(S.V + i * LD, vr);
                             T s = T(0);
 #pragma unroll
-                            for (int k = 0; k < NX; ++k) s += S.V[i * NX + k] * f[k];
+                            for (int k = 0; k < NX; ++k) s += vr[k] * f[k];
                             w[i] = s;
                         }
+                        T vv[NX];
+                        ld13(S.v, vv);
                         T s = S.c[j];
 #pragma unroll
-                        for (int k = 0; k < NX; ++k) s += f[k] * S.v[k];
+                        for (int k = 0; k < NX; ++k) s += f[k] * vv[k];
                         qj = s;
                     }
                     S.q[j] = qj;
@@ -749,11 +821,14 @@ __device__ bool riccati(const Params<T>& P, const Inst<T>& I, WarpSmem<T>& S, co
                         } else if (r >= 7 && r < 10) {
                             s += w[r] + hv * w[r - 7];
                         } else {
+                            T fr[NX];
+                            ld13(Fc + r * LD, fr);
 #pragma unroll
-                            for (int k = 0; k < NX; ++k) s += S.F[r * NX + k] * w[k];
+                            for (int k = 0; k < NX; ++k) s += fr[k] * w[k];
                         }
                         S.Qm[r * NZ + j] = s;
                         if (!cc && rc) S.Qm[j * NZ + r] = s;
+                        if (!cc && r < NX && j >= NX) S.Qxu[r * NU + j - NX] = s;
                     }
                 }
             } else if (on) {
@@ -761,6 +836,7 @@ __device__ bool riccati(const Params<T>& P, const Inst<T>& I, WarpSmem<T>& S, co
                     const int a = e / NZ, bb = e - a * NZ;
                     S.Qm[e] = (a == bb) ? S.Cd[a] : T(0);
                 }
+                for (int e = L.l; e < NX * NU; e += TPI) S.Qxu[e] = T(0);
                 for (int a = L.l; a < NZ; a += TPI) S.q[a] = S.c[a];
             }
             wsync();
@@ -789,47 +865,61 @@ __device__ bool riccati(const Params<T>& P, const Inst<T>& I, WarpSmem<T>& S, co
             if (on && !S.ok) alive = false;
             go = on && alive;
             const int mask = S.mask;
-            // K_t columns
             if (go) {
+                // Column c of K_t (to shared memory and the slot scratch), then,
+                // from it in registers, the upper part of column c of
+                //   V_t = Q_xx + Q_xu K_t   (mirrored: V_t is stored in full)
+                // and v_t[c] = q_x[c] + Q_xu[c, :] k_t.
+                T* kr = I.Kr + (size_t)t * KREC;
                 for (int c = L.l; c < NX; c += TPI) {
-                    T rhs[4], y[4];
+                    T qc[4], rhs[4], y[4], kc[4];
+                    ld4(S.Qxu + c * NU, qc);
 #pragma unroll
-                    for (int a = 0; a < 4; ++a) rhs[a] = ((mask >> a) & 1) ? S.Qm[c * NZ + NX + a] : T(0);
+                    for (int a = 0; a < 4; ++a) rhs[a] = ((mask >> a) & 1) ? qc[a] : T(0);
                     chol_solve4(S.L, rhs, y);
 #pragma unroll
-                    for (int a = 0; a < 4; ++a) S.K[a * NX + c] = ((mask >> a) & 1) ? -y[a] : T(0);
+                    for (int a = 0; a < 4; ++a) {
+                        kc[a] = ((mask >> a) & 1) ? -y[a] : T(0);
+                        S.K[a * NX + c] = kc[a];
+                        kr[a * NX + c] = kc[a];
+                    }
+#pragma unroll
+                    for (int i = 0; i < NX; ++i) {
+                        if (i > c) break;
+                        T qi[4];
+                        ld4(S.Qxu + i * NU, qi);
+                        T s = S.Qm[i * NZ + c];
+#pragma unroll
+                        for (int a = 0; a < NU; ++a) s += qi[a] * kc[a];
+                        S.V[i * LD + c] = s;
+                        S.V[c * LD + i] = s;
+                    }
+                    T s = S.q[c];
+#pragma unroll
+                    for (int a = 0; a < NU; ++a) s += qc[a] * S.k[a];
+                    S.v[c] = s;
+                }
+                if (L.l == 0) {
+#pragma unroll
+                    for (int a = 0; a < NU; ++a) kr[NU * NX + a] = S.k[a];
                 }
             }
-            wsync();
-            if (go) {
-                // V_t, v_t
-                for (int p = L.l; p < NTRI_V + NX; p += TPI) {
-                    if (p < NTRI_V) {
-                        const int ij = triV[p], i = ij >> 8, j = ij & 0xff;
-                        T s = S.Qm[i * NZ + j];
-#pragma unroll
-                        for (int a = 0; a < NU; ++a) s += S.Qm[i * NZ + NX + a] * S.K[a * NX + j];
-                        S.V[i * NX + j] = s;
-                        S.V[j * NX + i] = s;
-                    } else {
-                        const int i = p - NTRI_V;
-                        T s = S.q[i];
-#pragma unroll
-                        for (int a = 0; a < NU; ++a) s += S.Qm[i * NZ + NX + a] * S.k[a];
-                        S.v[i] = s;
-                    }
-                }
-                // gains to the slot scratch (and tape)
-                T* kr = I.Kr + (size_t)t * KREC;
-                for (int e = L.l; e < KREC; e += TPI) kr[e] = (e < NU * NX) ? S.K[e] : S.k[e - NU * NX];
-                if (o.tape) {
+            if (o.tape) {
+                wsync();
+                if (go) {
                     T* rec = o.tape + ((size_t)I.b * P.N + t) * TAPE_STRIDE;
                     for (int e = L.l; e < TAPE_STRIDE; e += TPI) {
                         T val;
-                        if (e < TAPE_K) val = dyn ? S.F[e] : T(0);
-                        else if (e < TAPE_L) val = S.K[e - TAPE_K];
-                        else if (e < TAPE_MASK) val = S.L[e - TAPE_L];
-                        else val = T(mask);
+                        if (e < TAPE_K) {
+                            const int j = e / NX;
+                            val = dyn ? Fc[j * LD + e - j * NX] : T(0);
+                        } else if (e < TAPE_L) {
+                            val = S.K[e - TAPE_K];
+                        } else if (e < TAPE_MASK) {
+                            val = S.L[e - TAPE_L];
+                        } else {
+                            val = T(mask);
+                        }
                         rec[e] = val;
                     }
                 }
@@ -845,7 +935,7 @@ __device__ bool riccati(const Params<T>& P, const Inst<T>& I, WarpSmem<T>& S, co
                     else g = adj->gu[((size_t)I.b * P.N + t) * NU + a - NX];
                     if (dyn) {
 #pragma unroll
-                        for (int k = 0; k < NX; ++k) g += S.F[a * NX + k] * S.vh[k];
+                        for (int k = 0; k < NX; ++k) g += Fc[a * LD + k] * S.vh[k];
                     }
                     S.qh[a] = g;
                 }
@@ -884,49 +974,27 @@ __device__ bool riccati(const Params<T>& P, const Inst<T>& I, WarpSmem<T>& S, co
 // against J's magnitude; with the hi + lo states it resolves differences far
 // below the working precision of J.  alpha* = first argmin, and the best
 // candidate becomes the next nominal (Sec. IV-3).  Each stage's gains, nominal
-// and cost rows are fetched into registers two stages ahead by all lanes of
-// the group and staged into shared memory one stage ahead.  Returns 0 (step
-// taken: du, J updated) or 1 (no candidate with a finite cost: nominal kept).
-// Entry e of stage t's staged record: K_t, k_t (56), x (13), x lo (13), u (4),
-// Q_t (13), x_ref,t (13).
-template <typename T>
-__device__ __forceinline__ T ls_stage_value(const Params<T>& P, const Inst<T>& I, int t, int e) {
-    if (e < KREC) return I.Kr[(size_t)t * KREC + e];
-    if (e < KREC + NX) return I.xb[t * NX + e - KREC];
-    if (e < KREC + 2 * NX) return I.xlo[t * NX + e - KREC - NX];
-    if (e < KREC + 2 * NX + NU) return I.ub[t * NU + e - KREC - 2 * NX];
-    if (e < KREC + 3 * NX + NU) return Qrow(P, I, t)[e - KREC - 2 * NX - NU];
-    return I.xrefb[t * NX + e - KREC - 3 * NX - NU];
-}
-
+// and cost rows are copied into shared memory by all lanes of the group
+// (asynchronous copies) one stage ahead.  Returns 0 (step taken: du, J
+// updated) or 1 (no candidate with a finite cost: nominal kept).
+// Stage t's staged record: K_t, k_t (KREC), then the stage inputs (SIN).
 template <typename T, int TPI>
 __device__ int line_search(const Params<T>& P, const Inst<T>& I, WarpSmem<T>& S, const Lanes<TPI>& L, bool act,
                            T& Jnom, T& du_out) {
     static_assert(TPI >= 4, "line search needs 4 candidate lanes");
     const int n = act ? I.n : 0;
     const int nmax = warp_max(n);
-    constexpr int SR = (112 + TPI - 1) / TPI;
-    T pre[SR];
-    auto fetch = [&](int tt) {
-        if (tt >= n) return;
-#pragma unroll
-        for (int r = 0; r < SR; ++r) {
-            const int e = L.l + r * TPI;
-            if (e < 112) pre[r] = ls_stage_value(P, I, tt, e);
-        }
-    };
-    auto stash = [&](int tt) {
+    auto issue = [&](int tt) {
         if (tt >= n) return;
         T* dst = S.stg[tt & 1];
-#pragma unroll
-        for (int r = 0; r < SR; ++r) {
-            const int e = L.l + r * TPI;
-            if (e < 112) dst[e] = pre[r];
-        }
+        const T* kr = I.Kr + (size_t)tt * KREC;
+        constexpr int PER = 16 / sizeof(T), NCH = KREC / PER;
+        for (int e = L.l; e < NCH; e += TPI) cp_async16(dst + e * PER, kr + e * PER);
+        stage_inputs_async(P, I, L, tt, dst + KREC);
+        cp_async_commit();
     };
-    fetch(0);
-    stash(0);
-    fetch(1);
+    issue(0);
+    cp_async_wait_all();
     wsync();
     const bool cl = act && L.l < P.n_alpha;
     const T alpha = cl ? P.alpha[L.l] : T(0);
@@ -936,14 +1004,15 @@ __device__ int line_search(const Params<T>& P, const Inst<T>& I, WarpSmem<T>& S,
     T dJ = T(0), dJl = T(0);
     T* cd = I.cand + (size_t)(L.l & 3) * P.N_ws * CREC;
     for (int t = 0; t < nmax; ++t) {
+        issue(t + 1);
         if (cl && t < n) {
             const T* sb = S.stg[t & 1];
             const T* kr = sb;
-            const T* xbt = sb + KREC;
-            const T* xlt = sb + KREC + NX;
-            const T* ubt = sb + KREC + 2 * NX;
-            const T* Qt = sb + KREC + 2 * NX + NU;
-            const T* xr = sb + KREC + 3 * NX + NU;
+            const T* xbt = sb + KREC + SI_X;
+            const T* xlt = sb + KREC + SI_XL;
+            const T* ubt = sb + KREC + SI_U;
+            const T* Qt = sb + KREC + SI_Q;
+            const T* xr = sb + KREC + SI_R;
             T dxv[NX];
 #pragma unroll
             for (int i = 0; i < NX; ++i) dxv[i] = (xh[i] - xbt[i]) + (xl[i] - xlt[i]);
@@ -971,11 +1040,7 @@ __device__ int line_search(const Params<T>& P, const Inst<T>& I, WarpSmem<T>& S,
             for (int a = 0; a < NU; ++a) cd[t * CREC + 2 * NX + a] = uh[a];
             if (t < n - 1) rk4_step2(P.mdl, xh, xl, uh);
         }
-        // stage t + 1 was fetched during stage t's work; stash it, fetch t + 2
-        if (act) {
-            stash(t + 1);
-            fetch(t + 2);
-        }
+        cp_async_wait_all();
         wsync();
     }
     if (cl) {

@@ -42,31 +42,6 @@ enum Phase {
 };
 constexpr int MODE_FWD = -1, MODE_BWD = -2;
 
-// Upper-triangle index tables.  Q's entries are ordered rows of the computed
-// columns of F first (13-term dot products), then the rows of the constant
-// p and v columns (one or two terms), so that a round of lanes mostly runs
-// the same branch.
-__device__ void init_tables(int* triQ, int* triV) {
-    for (int p = threadIdx.x; p < NTRI_Q; p += blockDim.x) {
-        int r = p, q = 0;
-        for (int pass = 0; pass < 2; ++pass) {
-            for (int a = 0; a < NZ; ++a) {
-                const bool constant_row = a < 3 || (a >= 7 && a < 10);
-                if (constant_row != (pass == 1)) continue;
-                const int len = NZ - a;
-                if (r < len) { triQ[p] = (a << 8) | (a + r); q = 1; break; }
-                r -= len;
-            }
-            if (q) break;
-        }
-    }
-    for (int p = threadIdx.x; p < NTRI_V; p += blockDim.x) {
-        int a = 0, r = p;
-        while (r >= NX - a) { r -= NX - a; ++a; }
-        triV[p] = (a << 8) | (a + r);
-    }
-}
-
 __device__ __forceinline__ bool finished_ok(int st) {
     return st == ST_CONVERGED || st == ST_STALLED || st == ST_MAX_ITER;
 }
@@ -87,9 +62,6 @@ template <typename T, int TPI>
 __global__ void __launch_bounds__(256, 2) k_mpc(Params<T> P, AdjArgs<T> A, int mode, int last) {
     constexpr int PACK = 32 / TPI;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ int triQ[NTRI_Q], triV[NTRI_V];
-    init_tables(triQ, triV);
-    __syncthreads();
     const Lanes<TPI> L;
     const int wib = threadIdx.x >> 5;
     WarpSmem<T>& S = reinterpret_cast<WarpSmem<T>*>(smem_raw)[wib * PACK + L.g];
@@ -160,7 +132,7 @@ __global__ void __launch_bounds__(256, 2) k_mpc(Params<T> P, AdjArgs<T> A, int m
                 o.adj = (ph == PH_BRIC || ph == PH_BTAPE) ? &A : (const AdjArgs<T>*)nullptr;
                 o.replay = ph == PH_BTAPE;
                 o.use_lo = ph == PH_RIC;
-                const bool ok = riccati(P, I, S, L, triQ, triV, o, act);
+                const bool ok = riccati(P, I, S, L, o, act);
                 if (ph == PH_RIC) {
                     if (act && !ok) status = ST_NONPD;
                     next = warp_any(act && ok) ? PH_LS : after_fwd;
