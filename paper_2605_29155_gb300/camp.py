@@ -17,7 +17,6 @@ MPC_F32, MPC_F64 = 0, 1
 MPC_STORE_ALL, MPC_RECOMPUTE = 0, 1
 MPC_EXEC_PERSISTENT, MPC_EXEC_PLAIN = 0, 1
 MPC_ST_CONVERGED, MPC_ST_STALLED, MPC_ST_MAX_ITER, MPC_ST_NONFINITE, MPC_ST_NONPD = 0, 1, 2, 3, 4
-TAPE_STRIDE = 288
 
 EXPORTED = ("mpc_config_default", "mpc_create", "mpc_destroy", "mpc_tape_bytes", "mpc_solve_fwd",
             "mpc_solve_bwd", "mpc_autotune", "mpc_launch_shape", "mpc_launch_count", "mpc_strerror",

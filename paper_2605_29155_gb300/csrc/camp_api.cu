@@ -13,14 +13,14 @@ struct mpc_handle {
     mpc_config cfg;
     int device;
     int num_sms;
-    int slots;              // scratch slots (>= B_max and >= resident warps)
+    int slots;              // scratch positions (= B_max)
     void* ws;               // one allocation holding every scratch region
     size_t ws_bytes;
-    void *wsF, *wsK, *wsCand, *wsSP, *wsKh, *wsXlo;
+    void *stg, *cand, *kh;  // per-stage records, line-search candidates, adjoint k-hat
     int* queue;             // [2] work-queue tickets (forward, backward)
     int* order;             // [B_max] longest-horizon-first order
-    int tpi;                // threads per instance
-    int ipb;                // instances per block
+    int tpi;                // threads per instance (warps per block): 4 or 8
+    int ipb;                // instances per block, 0 = as many as fill one block per SM
 };
 
 static size_t elem_size(int dtype) { return dtype == MPC_F64 ? sizeof(double) : sizeof(float); }
@@ -73,10 +73,8 @@ static int validate_config(const mpc_config* c) {
         if (!(c->alpha[i] > 0.0 && c->alpha[i] <= 1.0)) return MPC_ERR_ARG;
     if (c->store_mode != MPC_STORE_ALL && c->store_mode != MPC_RECOMPUTE) return MPC_ERR_ARG;
     if (c->exec_mode != MPC_EXEC_PERSISTENT && c->exec_mode != MPC_EXEC_PLAIN) return MPC_ERR_ARG;
-    if (c->tpi != 0 && c->tpi != 8 && c->tpi != 16 && c->tpi != 32) return MPC_ERR_ARG;
-    if (c->ipb != 0 && c->ipb != 1 && c->ipb != 2 && c->ipb != 4 && c->ipb != 8 && c->ipb != 16 && c->ipb != 32)
-        return MPC_ERR_ARG;
-    if (c->tpi && c->ipb && !shape_ok(c->tpi, c->ipb)) return MPC_ERR_ARG;
+    if (c->tpi != 0 && c->tpi != 4 && c->tpi != 8) return MPC_ERR_ARG;
+    if (c->ipb < 0 || c->ipb > 32) return MPC_ERR_ARG;
     return MPC_OK;
 }
 
@@ -88,9 +86,8 @@ extern "C" int mpc_create(const mpc_config* cfg, mpc_handle** out) {
     mpc_handle* h = (mpc_handle*)calloc(1, sizeof(mpc_handle));
     if (!h) return MPC_ERR_CUDA;
     h->cfg = *cfg;
-    h->tpi = cfg->tpi ? cfg->tpi : 16;
-    h->ipb = cfg->ipb ? cfg->ipb : 128 / h->tpi;
-    if (!shape_ok(h->tpi, h->ipb)) h->ipb = 64 / h->tpi;
+    h->tpi = cfg->tpi ? cfg->tpi : 4;
+    h->ipb = cfg->ipb;
     if (cudaGetDevice(&h->device) != cudaSuccess) { free(h); return MPC_ERR_CUDA; }
     if (cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device) != cudaSuccess) {
         free(h);
@@ -98,30 +95,24 @@ extern "C" int mpc_create(const mpc_config* cfg, mpc_handle** out) {
     }
     const cudaError_t pe = cfg->dtype == MPC_F64 ? prepare_kernels<double>() : prepare_kernels<float>();
     if (pe != cudaSuccess) { free(h); return MPC_ERR_CUDA; }
-    const int resident = h->num_sms * 64;        // instances resident at once (128 registers, 8 lanes each)
-    h->slots = cfg->B_max > resident ? cfg->B_max : resident;
+    h->slots = cfg->B_max;
     const size_t es = elem_size(cfg->dtype);
-    const size_t S = (size_t)h->slots, Nw = (size_t)cfg->N_max;
-    const size_t bF = align256(S * Nw * NFC * es);
-    const size_t bK = align256(S * Nw * KREC * es);
-    const size_t bC = align256(S * 4 * Nw * CREC * es);
-    const size_t bX = align256(S * Nw * NX * es);
-    const size_t bP = align256(S * Nw * SP_STRIDE * es);
-    const size_t bH = align256(S * Nw * NU * es);
+    const size_t S = (size_t)h->slots;
+    const int Nw = cfg->N_max;
+    const size_t bS = align256(stg_elems(S, Nw) * es);
+    const size_t bC = align256(cand_elems(S, Nw) * es);
+    const size_t bH = align256(kh_elems(S, Nw) * es);
     const size_t bQ = align256(2 * sizeof(int));
     const size_t bO = align256((size_t)cfg->B_max * sizeof(int));
-    h->ws_bytes = bF + bK + bC + bP + bH + bX + bQ + bO;
+    h->ws_bytes = bS + bC + bH + bQ + bO;
     if (cudaMalloc(&h->ws, h->ws_bytes) != cudaSuccess) { free(h); return MPC_ERR_CUDA; }
     // All-ones bytes are NaN in float and double: a read of scratch that no
     // phase wrote surfaces as a NaN result instead of stale data.
     if (cudaMemset(h->ws, 0xff, h->ws_bytes) != cudaSuccess) { cudaFree(h->ws); free(h); return MPC_ERR_CUDA; }
     char* p = (char*)h->ws;
-    h->wsF = p; p += bF;
-    h->wsK = p; p += bK;
-    h->wsCand = p; p += bC;
-    h->wsSP = p; p += bP;
-    h->wsKh = p; p += bH;
-    h->wsXlo = p; p += bX;
+    h->stg = p; p += bS;
+    h->cand = p; p += bC;
+    h->kh = p; p += bH;
     h->queue = (int*)p; p += bQ;
     h->order = (int*)p;
     *out = h;
@@ -137,39 +128,24 @@ extern "C" int mpc_destroy(mpc_handle* h) {
 
 extern "C" size_t mpc_tape_bytes(const mpc_handle* h, int B, int N) {
     if (!h || B <= 0 || N <= 0 || h->cfg.store_mode != MPC_STORE_ALL) return 0;
-    return (size_t)B * N * TAPE_STRIDE * elem_size(h->cfg.dtype);
+    return tape_elems(B, N) * elem_size(h->cfg.dtype);
 }
 
-static int grid_for(const mpc_handle* h, int B) {
-    const int bps = h->cfg.dtype == MPC_F64 ? persistent_blocks_per_sm<double>(h->tpi, h->ipb)
-                                            : persistent_blocks_per_sm<float>(h->tpi, h->ipb);
+// Instances per block for a batch of B: the handle's fixed value, or as many
+// as spread the batch over one block per SM.
+static int ipb_for(const mpc_handle* h, int B) {
+    if (h->ipb) return h->ipb;
+    const int per_sm = (B + h->num_sms - 1) / h->num_sms;
+    return per_sm < 1 ? 1 : (per_sm > 32 ? 32 : per_sm);
+}
+
+static int grid_for(const mpc_handle* h, int B, int ipb) {
+    const int bps = h->cfg.dtype == MPC_F64 ? persistent_blocks_per_sm<double>(h->tpi)
+                                            : persistent_blocks_per_sm<float>(h->tpi);
     long long g = (long long)(bps > 0 ? bps : 1) * h->num_sms;
-    const long long need = (B + h->ipb - 1) / h->ipb;
+    const long long need = (B + ipb - 1) / ipb;
     if (g > need) g = need;
-    if (g * h->ipb > h->slots) g = h->slots / h->ipb;
     return (int)(g > 0 ? g : 1);
-}
-
-template <typename T>
-static void fill_model(const mpc_config& c, Model<T>& m) {
-    m.h = (T)c.dt;
-    m.inv_m = (T)(1.0 / c.mass);
-    m.g = (T)c.gravity;
-    m.Jx = (T)c.inertia[0];
-    m.Jy = (T)c.inertia[1];
-    m.Jz = (T)c.inertia[2];
-    m.iJx = (T)(1.0 / c.inertia[0]);
-    m.iJy = (T)(1.0 / c.inertia[1]);
-    m.iJz = (T)(1.0 / c.inertia[2]);
-    // X layout, rotors FR, RL, FL, RR at (+-d, +-d), spins (+1, +1, -1, -1):
-    // tau_x = sum y_i u_i, tau_y = -sum x_i u_i, tau_z = kappa sum s_i u_i
-    const double d = c.arm / sqrt(2.0);
-    const double rx[4] = {d, -d, d, -d}, ry[4] = {-d, d, d, -d}, sp[4] = {1, 1, -1, -1};
-    for (int i = 0; i < 4; ++i) {
-        m.M[0][i] = (T)ry[i];
-        m.M[1][i] = (T)(-rx[i]);
-        m.M[2][i] = (T)(c.kappa_yaw * sp[i]);
-    }
 }
 
 static int check_problem(const mpc_handle* h, const mpc_problem* p) {
@@ -183,10 +159,11 @@ static int check_problem(const mpc_handle* h, const mpc_problem* p) {
 }
 
 template <typename T>
-static Params<T> make_params(const mpc_handle* h, const mpc_problem* p, const mpc_solution* s) {
+static Params<T> make_params(const mpc_handle* h, const mpc_problem* p, const mpc_solution* s, int ipb) {
     Params<T> P;
     memset(&P, 0, sizeof(P));
-    fill_model(h->cfg, P.mdl);
+    const mpc_config& c = h->cfg;
+    fill_model(P.mdl, c.dt, c.mass, c.inertia, c.arm, c.kappa_yaw, c.gravity);
     P.B = p->B;
     P.N = p->N;
     P.Nq = p->Nq;
@@ -194,6 +171,7 @@ static Params<T> make_params(const mpc_handle* h, const mpc_problem* p, const mp
     P.n_alpha = h->cfg.n_alpha;
     P.store_all = h->cfg.store_mode == MPC_STORE_ALL;
     P.N_ws = h->cfg.N_max;
+    P.ipb = ipb;
     P.tol = (T)h->cfg.tol;
     for (int i = 0; i < 4; ++i) P.alpha[i] = (T)h->cfg.alpha[i];
     P.horizon = p->horizon;
@@ -212,12 +190,9 @@ static Params<T> make_params(const mpc_handle* h, const mpc_problem* p, const mp
     P.iters = s->iters;
     P.status = s->status;
     P.tape = (T*)s->tape;
-    P.wsF = (T*)h->wsF;
-    P.wsK = (T*)h->wsK;
-    P.wsCand = (T*)h->wsCand;
-    P.wsSP = (T*)h->wsSP;
-    P.wsKh = (T*)h->wsKh;
-    P.wsXlo = (T*)h->wsXlo;
+    P.stg = (T*)h->stg;
+    P.cand = (T*)h->cand;
+    P.kh = (T*)h->kh;
     P.queue = h->queue;
     return P;
 }
@@ -232,12 +207,14 @@ extern "C" int mpc_solve_fwd(mpc_handle* h, const mpc_problem* p, mpc_solution* 
         if (!s->tape || s->tape_bytes < mpc_tape_bytes(h, p->B, p->N)) return MPC_ERR_ARG;
     }
     cudaError_t e;
+    const int ipb = ipb_for(h, p->B);
+    const int grid = grid_for(h, p->B, ipb);
     if (h->cfg.dtype == MPC_F64) {
-        const Params<double> P = make_params<double>(h, p, s);
-        e = launch_forward<double>(P, h->cfg.exec_mode, h->tpi, h->ipb, grid_for(h, p->B), h->order, stream);
+        const Params<double> P = make_params<double>(h, p, s, ipb);
+        e = launch_forward<double>(P, h->cfg.exec_mode, h->tpi, grid, h->order, stream);
     } else {
-        const Params<float> P = make_params<float>(h, p, s);
-        e = launch_forward<float>(P, h->cfg.exec_mode, h->tpi, h->ipb, grid_for(h, p->B), h->order, stream);
+        const Params<float> P = make_params<float>(h, p, s, ipb);
+        e = launch_forward<float>(P, h->cfg.exec_mode, h->tpi, grid, h->order, stream);
     }
     return e == cudaSuccess ? MPC_OK : MPC_ERR_CUDA;
 }
@@ -252,16 +229,18 @@ extern "C" int mpc_solve_bwd(mpc_handle* h, const mpc_problem* p, const mpc_solu
     const int recompute = h->cfg.store_mode == MPC_RECOMPUTE;
     if (!recompute && (!s->tape || s->tape_bytes < mpc_tape_bytes(h, p->B, p->N))) return MPC_ERR_ARG;
     cudaError_t e;
+    const int ipb = ipb_for(h, p->B);
+    const int grid = grid_for(h, p->B, ipb);
     if (h->cfg.dtype == MPC_F64) {
-        const Params<double> P = make_params<double>(h, p, s);
+        const Params<double> P = make_params<double>(h, p, s, ipb);
         AdjArgs<double> A{(const double*)grad_u, (const double*)grad_x, (double*)dQ, (double*)dx_ref,
                           (double*)dx0, recompute};
-        e = launch_backward<double>(P, A, h->tpi, h->ipb, grid_for(h, p->B), h->order, stream);
+        e = launch_backward<double>(P, A, h->tpi, grid, h->order, stream);
     } else {
-        const Params<float> P = make_params<float>(h, p, s);
+        const Params<float> P = make_params<float>(h, p, s, ipb);
         AdjArgs<float> A{(const float*)grad_u, (const float*)grad_x, (float*)dQ, (float*)dx_ref, (float*)dx0,
                          recompute};
-        e = launch_backward<float>(P, A, h->tpi, h->ipb, grid_for(h, p->B), h->order, stream);
+        e = launch_backward<float>(P, A, h->tpi, grid, h->order, stream);
     }
     return e == cudaSuccess ? MPC_OK : MPC_ERR_CUDA;
 }
@@ -271,18 +250,28 @@ extern "C" int mpc_autotune(mpc_handle* h, const mpc_problem* p, mpc_solution* s
     int r = check_problem(h, p);
     if (r != MPC_OK) return r;
     if (h->cfg.exec_mode != MPC_EXEC_PERSISTENT) return MPC_ERR_STATE;
-    if (p->B == 0) { if (ipb_out) *ipb_out = h->ipb; return MPC_OK; }
+    if (p->B == 0) { if (ipb_out) *ipb_out = ipb_for(h, 0); return MPC_OK; }
     const int keep_tpi = h->tpi, keep_ipb = h->ipb;
-    const int tpis[3] = {8, 16, 32};
+    // candidate instances per block: one, two, three or four blocks' worth per SM
+    int cands[4], nc = 0;
+    for (int k = 1; k <= 4; ++k) {
+        int v = (p->B + k * h->num_sms - 1) / (k * h->num_sms);
+        v = v < 1 ? 1 : (v > 32 ? 32 : v);
+        bool dup = false;
+        for (int i = 0; i < nc; ++i) dup = dup || cands[i] == v;
+        if (!dup) cands[nc++] = v;
+    }
+    const int tpis[2] = {4, 8};
     float best_ms = 3.0e38f;
     int best_tpi = keep_tpi, best_ipb = keep_ipb;
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess) return MPC_ERR_CUDA;
     if (cudaEventCreate(&e1) != cudaSuccess) { cudaEventDestroy(e0); return MPC_ERR_CUDA; }
-    for (int ti = 0; ti < 3 && r == MPC_OK; ++ti) {
+    for (int ti = 0; ti < 2 && r == MPC_OK; ++ti) {
         if (h->cfg.tpi && h->cfg.tpi != tpis[ti]) continue;
-        for (int ipb = 1; ipb <= 32 && r == MPC_OK; ipb *= 2) {
-            if (!shape_ok(tpis[ti], ipb) || (h->cfg.ipb && h->cfg.ipb != ipb)) continue;
+        for (int ci = 0; ci < nc && r == MPC_OK; ++ci) {
+            const int ipb = h->cfg.ipb ? h->cfg.ipb : cands[ci];
+            if (h->cfg.ipb && ci > 0) break;
             h->tpi = tpis[ti];
             h->ipb = ipb;
             if ((r = mpc_solve_fwd(h, p, s, stream)) != MPC_OK) break;          // warm-up
@@ -299,15 +288,16 @@ extern "C" int mpc_autotune(mpc_handle* h, const mpc_problem* p, mpc_solution* s
     cudaEventDestroy(e1);
     h->tpi = r == MPC_OK ? best_tpi : keep_tpi;
     h->ipb = r == MPC_OK ? best_ipb : keep_ipb;
-    if (ipb_out) *ipb_out = h->ipb;
+    if (ipb_out) *ipb_out = ipb_for(h, p->B);
     return r;
 }
 
 extern "C" int mpc_launch_shape(const mpc_handle* h, int B, int N, int* tpi, int* ipb, int* grid) {
     if (!h || B < 0 || N < 1 || N > h->cfg.N_max) return MPC_ERR_ARG;
+    const int i = ipb_for(h, B);
     if (tpi) *tpi = h->tpi;
-    if (ipb) *ipb = h->ipb;
-    if (grid) *grid = B > 0 ? grid_for(h, B) : 0;
+    if (ipb) *ipb = i;
+    if (grid) *grid = B > 0 ? grid_for(h, B, i) : 0;
     return MPC_OK;
 }
 
@@ -316,7 +306,7 @@ extern "C" int mpc_launch_count(const mpc_handle* h, int has_horizon, int* fwd, 
     const int hz = has_horizon ? 1 : 0;
     if (fwd) {
         if (h->cfg.exec_mode == MPC_EXEC_PERSISTENT) *fwd = 1 + hz;
-        else *fwd = 1 + 3 * h->cfg.max_iter + (h->cfg.store_mode == MPC_STORE_ALL ? 2 : 0);
+        else *fwd = hz + 2 + 2 * h->cfg.max_iter + (h->cfg.store_mode == MPC_STORE_ALL ? 1 : 0);
     }
     if (bwd) *bwd = 1 + hz;
     return MPC_OK;

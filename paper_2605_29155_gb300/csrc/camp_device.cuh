@@ -1,32 +1,42 @@
-// camp_device.cuh -- per-instance device code of the batched differentiable MPC
-// layer (box-constrained iLQR forward, adjoint LQR backward), templated on the
+// camp_device.cuh -- device code of the batched differentiable MPC layer
+// (box-constrained iLQR forward, adjoint LQR backward), templated on the
 // working precision T (float on the product path, double for logic checks).
 //
-// Mapping: a group of TPI lanes (8, 16 or 32) owns one MPC instance; a warp
-// runs 32 / TPI instances in lockstep.  Each instance's matrices live in its
-// shared-memory record (WarpSmem); every matrix product of the Riccati
-// recursion is split over the group's lanes by output entry; the per-stage box
-// QP runs on one lane; the line search rolls out each alpha on its own lane.
-// Per-instance trajectories, gains and Jacobians that outlive a phase live in
-// a global scratch "slot" owned by the group (L2-resident).
+// Mapping: a block of NW warps serves a pack of up to 32 instances, one
+// instance per lane: lane l of every warp works on instance l of the pack, and
+// the warps split each instance's work between them.  The serial parts of the
+// method (the per-stage box QP, each line-search rollout, the adjoint forward
+// sweep) thus run 32 instances per warp instruction, and the parallel parts
+// (the 11 computed columns of the RK4 Jacobian, the 13x13 / 17x17 Riccati
+// products, the gain columns) are divided between the warps.  Per-instance
+// matrices live in shared memory as [row][lane] arrays (conflict-free: lane l
+// reads word l of a row); per-instance trajectories, gains and line-search
+// candidates live in a global scratch laid out the same way ([row][32
+// positions]), so every warp access to them is one or two 128-byte lines.
 #pragma once
 #include <cuda_runtime.h>
+#include <math.h>
 #include <stdint.h>
 
 namespace camp {
 
 constexpr int NX = 13, NU = 4, NZ = 17;
-constexpr int NF = NX * NZ;            // entries of F_t = [A_t B_t], stored column-major
-constexpr int NFC = 11 * NX;           // scratch copy of F_t: only its 11 computed columns
-constexpr int LD = 16;                 // row / column stride of V_t and F_t in shared memory (128-bit aligned)
-constexpr int TAPE_STRIDE = 288;       // tape record per stage (elements)
-constexpr int TAPE_F = 0, TAPE_K = 221, TAPE_L = 273, TAPE_MASK = 287;
-constexpr int NL = 14;                 // factor: packed lower 4x4 (10) + reciprocal diagonal (4)
-constexpr int KREC = 56;               // K_t (52, row-major) + k_t (4)
-constexpr int SP_STRIDE = 32;          // RK4 stage points per stage: 4 x (q, w, pad)
-constexpr int CREC = 30;               // line-search candidate per stage: x hi (13), x lo (13), u (4)
+constexpr int NGC = 11, NTC = 6;       // computed / constant columns of F_t = [A_t B_t]
+constexpr int NFC = NGC * NX;          // entries of the computed columns
+constexpr int NV = NX * (NX + 1) / 2;  // packed upper triangle of V (13 x 13)
+constexpr int NQ = NZ * (NZ + 1) / 2;  // packed upper triangle of Q (17 x 17)
+constexpr int NL = 14;                 // masked Cholesky factor of Q_uu: packed lower 4x4 (10) + 1/diag (4)
+constexpr int LW = 32;                 // lanes of a warp = instances of a pack at most
 constexpr int QP_MAX_IT = 20, QP_MAX_LS = 30;
 constexpr unsigned FULL = 0xffffffffu;
+
+// Per-stage record of the global scratch (rows of 32 positions):
+// nominal x (hi, lo), u, the cost rows Q_t, x_ref,t, then the gains K_t, k_t.
+constexpr int R_X = 0, R_XL = 13, R_U = 26, R_Q = 30, R_XR = 43, CST = 56, R_K = 56, R_KK = 108, SREC = 112;
+constexpr int CREC = 30;               // line-search candidate per stage: x hi, x lo, u
+// Tape record per stage (rows of 32 instances): computed columns of F_t,
+// K_t (row-major), masked factor, free mask.
+constexpr int T_F = 0, T_K = 143, T_L = 195, T_M = 209, TREC = 210;
 
 enum { ST_CONVERGED = 0, ST_STALLED = 1, ST_MAX_ITER = 2, ST_NONFINITE = 3, ST_NONPD = 4,
        ST_RUNNING = -1 };
@@ -35,20 +45,51 @@ template <typename T> struct Model {
     T h, inv_m, g;
     T Jx, Jy, Jz, iJx, iJy, iJz;
     T M[3][4];                          // torque map tau = M u
+    T TJ[3][4];                         // J^-1 M: body-rate rows of B_c
+    T gyr[3];                           // (Jz - Jy)/Jx, (Jx - Jz)/Jy, (Jy - Jx)/Jz
 };
+
+// The quadrotor constants in the working precision.  X layout, rotors FR, RL,
+// FL, RR at (+-d, +-d) with d = arm / sqrt(2), spins (+1, +1, -1, -1):
+// tau_x = sum y_i u_i, tau_y = -sum x_i u_i, tau_z = kappa sum s_i u_i.
+template <typename T>
+inline void fill_model(Model<T>& m, double dt, double mass, const double* inertia, double arm, double kappa,
+                       double gravity) {
+    m.h = (T)dt;
+    m.inv_m = (T)(1.0 / mass);
+    m.g = (T)gravity;
+    m.Jx = (T)inertia[0];
+    m.Jy = (T)inertia[1];
+    m.Jz = (T)inertia[2];
+    m.iJx = (T)(1.0 / inertia[0]);
+    m.iJy = (T)(1.0 / inertia[1]);
+    m.iJz = (T)(1.0 / inertia[2]);
+    const double d = arm / sqrt(2.0);
+    const double rx[4] = {d, -d, d, -d}, ry[4] = {-d, d, d, -d}, sp[4] = {1, 1, -1, -1};
+    for (int i = 0; i < 4; ++i) {
+        const double Mi[3] = {ry[i], -rx[i], kappa * sp[i]};
+        for (int r = 0; r < 3; ++r) {
+            m.M[r][i] = (T)Mi[r];
+            m.TJ[r][i] = (T)(Mi[r] / inertia[r]);
+        }
+    }
+    m.gyr[0] = (T)((inertia[2] - inertia[1]) / inertia[0]);
+    m.gyr[1] = (T)((inertia[0] - inertia[2]) / inertia[1]);
+    m.gyr[2] = (T)((inertia[1] - inertia[0]) / inertia[2]);
+}
 
 template <typename T> struct Params {
     Model<T> mdl;
-    int B, N, Nq, max_iter, n_alpha, store_all, N_ws;
+    int B, N, Nq, max_iter, n_alpha, store_all, N_ws, ipb;
     T tol;
     T alpha[4];
     const int* horizon;
-    const int* order;                   // LPT order of instances (or NULL)
+    const int* order;                   // processing order of the instances (or NULL)
     const T *x0, *Q, *xref, *R, *uref, *ulo, *uhi, *uinit;
     T *u, *x, *cost;
     int *iters, *status;
     T* tape;
-    T *wsF, *wsK, *wsCand, *wsSP, *wsKh, *wsXlo;
+    T *stg, *cand, *kh;                 // global scratch, by position in the processing order
     int* queue;
 };
 
@@ -58,82 +99,68 @@ template <typename T> struct AdjArgs {
     int recompute;
 };
 
-// Per-instance shared-memory record.
-template <typename T> struct alignas(16) WarpSmem {
-    T V[NX * LD];      // value Hessian V_{t+1}: V[i*LD + j] (full symmetric storage)
-    T F[2][NZ * LD];   // F_t column-major, F[t & 1][j*LD + i] = dx+_i / dz_j (double buffered)
-    T Qxu[NX * NU];    // x-u block of Q_t again, Qxu[i*4 + a] = Q[i][13 + a]
-    T v[LD];           // value gradient v_{t+1} (13 used)
-    T stg[2][112];     // a stage's inputs, prefetched (double buffered): K_t, k_t (56), then
-                       // x_t, x lo_t, u_t, Q_t, x_ref,t (SIN entries)
-    T Qm[NZ * NZ];     // Q_t (row-major, full)
-    T q[NZ];           // q_t
-    T c[NZ];           // C_t z_t + c_t at the nominal
-    T Cd[NZ];          // diag C_t
-    T K[NU * NX];      // K_t row-major
-    T k[NU];           // k_t
-    T L[NL];           // Cholesky of Q_uu on the free set (packed lower, masked) + 1/diag
-    T x0[NX];
-    T R[NU], uref[NU], ulo[NU], uhi[NU];
-    T ut[NU];          // the nominal u_t of the current Riccati stage
-    T Jc[4];
-    T vh[NX];          // adjoint value gradient
-    T qh[NZ];          // adjoint q-hat
-    T dx[NX];          // adjoint forward-sweep state
-    T du[NU];
-    T dQacc[NX];
-    int mask;
-    int ok;
+// Packed upper-triangular indices (row <= column) of V (13 x 13) and Q (17 x 17).
+__host__ __device__ constexpr int vidx(int i, int j) {
+    return i <= j ? i * NX - i * (i - 1) / 2 + (j - i) : j * NX - j * (j - 1) / 2 + (i - j);
+}
+__host__ __device__ constexpr int qidx(int i, int j) {
+    return i <= j ? i * NZ - i * (i - 1) / 2 + (j - i) : j * NZ - j * (j - 1) / 2 + (i - j);
+}
+
+// The 6 columns of F_t for p and v are constant: position enters nothing
+// (F[:, p_i] = e_{p_i}) and velocity only the position (F[:, v_i] = e_{v_i} +
+// h e_{p_i}, h written as (h/6) * 6 as the RK4 combination forms it).  The
+// other 11 columns (q, w, u) are computed; gcol maps 0..10 to them.
+__host__ __device__ constexpr int gcol(int jj) { return jj < 4 ? 3 + jj : 6 + jj; }
+
+// ------------------------------------------------------- shared memory ----
+template <typename T> struct RicSmem {
+    T F[2][NFC][LW];       // computed columns of F_t, F[t & 1][jj * 13 + i]
+    T Q[NQ][LW];           // Q_t, packed upper triangle
+    T q[NZ][LW];           // q_t
+    T cst[2][CST][LW];     // a stage's nominal and cost rows (double buffered)
+};
+template <typename T> struct LsSmem {
+    T stg[2][SREC][LW];    // a stage's nominal, cost and gain rows (double buffered)
+};
+template <typename T> struct TapeSmem {
+    T rec[2][TREC][LW];    // a stage's tape record (double buffered)
+};
+template <typename T> struct alignas(16) BlockSmem {
+    T V[NV][LW];           // value Hessian V_{t+1} (packed upper)
+    T v[NX][LW];           // value gradient v_{t+1}
+    T K[NU * NX][LW];      // K_t, row-major
+    T k[NU][LW];
+    T L[NL][LW];
+    T x0[NX][LW];
+    T R[NU][LW], uref[NU][LW], ulo[NU][LW], uhi[NU][LW];
+    T Jc[4][LW];           // line search: cost change of each candidate
+    T dmax[4][LW];         // line search: max |u_hat - u| of each candidate
+    T vh[NX][LW];          // adjoint value gradient
+    T qh[NZ][LW];          // adjoint q-hat
+    int mask[LW];
+    int ok[LW];
+    union {
+        RicSmem<T> r;
+        LsSmem<T> s;
+        TapeSmem<T> tp;
+    } u;
 };
 
 template <typename T> __device__ __forceinline__ T clampT(T v, T lo, T hi) {
     return v < lo ? lo : (v > hi ? hi : v);
 }
-
 template <typename T> __device__ __forceinline__ bool finiteT(T v) { return isfinite(v); }
 
-// 13 (or 4) consecutive entries of a 16-byte aligned shared-memory row, read
-// with 128-bit loads.
-__device__ __forceinline__ void ld13(const float* p, float (&o)[NX]) {
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        const float4 u = reinterpret_cast<const float4*>(p)[k];
-        o[4 * k] = u.x; o[4 * k + 1] = u.y; o[4 * k + 2] = u.z; o[4 * k + 3] = u.w;
-    }
-    o[12] = p[12];
-}
-__device__ __forceinline__ void ld13(const double* p, double (&o)[NX]) {
-#pragma unroll
-    for (int k = 0; k < 6; ++k) {
-        const double2 u = reinterpret_cast<const double2*>(p)[k];
-        o[2 * k] = u.x; o[2 * k + 1] = u.y;
-    }
-    o[12] = p[12];
-}
-__device__ __forceinline__ void ld4(const float* p, float (&o)[4]) {
-    const float4 u = *reinterpret_cast<const float4*>(p);
-    o[0] = u.x; o[1] = u.y; o[2] = u.z; o[3] = u.w;
-}
-__device__ __forceinline__ void ld4(const double* p, double (&o)[4]) {
-    const double2 u = reinterpret_cast<const double2*>(p)[0], w = reinterpret_cast<const double2*>(p)[1];
-    o[0] = u.x; o[1] = u.y; o[2] = w.x; o[3] = w.y;
-}
-
-// Asynchronous global -> shared copies (cp.async): the data lands in shared
-// memory without passing through registers; a lane waits for its own copies
-// with cp_async_wait_all, and a warp barrier after that makes every lane's
-// copies visible to the group.
+// Asynchronous 4- or 8-byte global -> shared copies (cp.async): a thread waits
+// for its own copies with cp_async_wait_all; a barrier after that makes them
+// visible to the block.
 template <typename T> __device__ __forceinline__ void cp_async(T* dst, const T* src) {
     const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
     if constexpr (sizeof(T) == 4)
         asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
     else
         asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src) : "memory");
-}
-// 16 bytes; both addresses 16-byte aligned.
-__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
-    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
@@ -204,9 +231,10 @@ __device__ __forceinline__ void rk4_step2(const Model<T>& m, T* xh, T* xl, const
 }
 
 // RK4 stage points of one step: for s = 1..4 the (q, w) of xi_s (xi_1 = x,
-// xi_2 = x + h/2 k1, xi_3 = x + h/2 k2, xi_4 = x + h k3) and the thrust.
+// xi_2 = x + h/2 k1, xi_3 = x + h/2 k2, xi_4 = x + h k3) in sp[8 s .. 8 s + 6],
+// and the total thrust in sp[7].
 template <typename T>
-__device__ __forceinline__ void rk4_stage_points(const Model<T>& m, const T* x, const T* u, T* __restrict__ sp) {
+__device__ __forceinline__ void rk4_stage_points(const Model<T>& m, const T* x, const T* u, T* sp) {
     T k[NX], xs[NX];
     const T hh = T(0.5) * m.h;
 #pragma unroll
@@ -227,63 +255,73 @@ __device__ __forceinline__ void rk4_stage_points(const Model<T>& m, const T* x, 
     sp[7] = u[0] + u[1] + u[2] + u[3];
 }
 
-// Jacobian-vector product of f_c at a stage point (q, w given in sp8, thrust th):
-// out = A_c dx + B_c du.
+// Coefficients of the continuous Jacobian J_c = [A_c B_c] at one RK4 stage
+// point (q, w, total thrust th), so that J_c [dx; du] costs about one
+// multiply-add per nonzero entry and the coefficients are shared by every
+// direction pushed through the same stage point.
+template <typename T> struct JcCoef {
+    T hq[4], hw[3];                     // quaternion rows: 1/2 q, 1/2 w
+    T c7[4], c8[4], c9[4];              // velocity rows, d/dq of (th/m) R(q) e3
+    T r7, r8, r9;                       // velocity rows, R(q) e3 / m per unit of total thrust
+    T g10y, g10z, g11x, g11z, g12x, g12y;   // body-rate rows, gyroscopic terms
+};
+
 template <typename T>
-__device__ __forceinline__ void jvp_cont(const Model<T>& m, const T* sp8, T th, const T* dx, const T* du,
-                                         T* out) {
+__device__ __forceinline__ void jc_coef(const Model<T>& m, const T* sp8, T th, JcCoef<T>& c) {
     const T qw = sp8[0], qx = sp8[1], qy = sp8[2], qz = sp8[3];
     const T wx = sp8[4], wy = sp8[5], wz = sp8[6];
+    c.hq[0] = T(0.5) * qw; c.hq[1] = T(0.5) * qx; c.hq[2] = T(0.5) * qy; c.hq[3] = T(0.5) * qz;
+    c.hw[0] = T(0.5) * wx; c.hw[1] = T(0.5) * wy; c.hw[2] = T(0.5) * wz;
+    const T a2 = T(2) * (th * m.inv_m);
+    c.c7[0] = a2 * qy;  c.c7[1] = a2 * qz;  c.c7[2] = a2 * qw;  c.c7[3] = a2 * qx;
+    c.c8[0] = -a2 * qx; c.c8[1] = -a2 * qw; c.c8[2] = a2 * qz;  c.c8[3] = a2 * qy;
+    c.c9[0] = a2 * qw;  c.c9[1] = -a2 * qx; c.c9[2] = -a2 * qy; c.c9[3] = a2 * qz;
+    c.r7 = (T(2) * (qx * qz + qw * qy)) * m.inv_m;
+    c.r8 = (T(2) * (qy * qz - qw * qx)) * m.inv_m;
+    c.r9 = (qw * qw - qx * qx - qy * qy + qz * qz) * m.inv_m;
+    c.g10y = -m.gyr[0] * wz; c.g10z = -m.gyr[0] * wy;
+    c.g11x = -m.gyr[1] * wz; c.g11z = -m.gyr[1] * wx;
+    c.g12x = -m.gyr[2] * wy; c.g12y = -m.gyr[2] * wx;
+}
+
+// out = J_c [dx; du] with the precomputed coefficients.
+template <typename T>
+__device__ __forceinline__ void jc_apply(const Model<T>& m, const JcCoef<T>& c, const T* dx, const T* du, T* out) {
     const T dqw = dx[3], dqx = dx[4], dqy = dx[5], dqz = dx[6];
     const T dwx = dx[10], dwy = dx[11], dwz = dx[12];
     out[0] = dx[7]; out[1] = dx[8]; out[2] = dx[9];
-    out[3] = T(0.5) * (-wx * dqx - wy * dqy - wz * dqz) + T(0.5) * (-qx * dwx - qy * dwy - qz * dwz);
-    out[4] = T(0.5) * (wx * dqw + wz * dqy - wy * dqz) + T(0.5) * (qw * dwx - qz * dwy + qy * dwz);
-    out[5] = T(0.5) * (wy * dqw - wz * dqx + wx * dqz) + T(0.5) * (qz * dwx + qw * dwy - qx * dwz);
-    out[6] = T(0.5) * (wz * dqw + wy * dqx - wx * dqy) + T(0.5) * (-qy * dwx + qx * dwy + qw * dwz);
-    const T a = th * m.inv_m;
+    out[3] = -c.hw[0] * dqx - c.hw[1] * dqy - c.hw[2] * dqz - c.hq[1] * dwx - c.hq[2] * dwy - c.hq[3] * dwz;
+    out[4] = c.hw[0] * dqw + c.hw[2] * dqy - c.hw[1] * dqz + c.hq[0] * dwx - c.hq[3] * dwy + c.hq[2] * dwz;
+    out[5] = c.hw[1] * dqw - c.hw[2] * dqx + c.hw[0] * dqz + c.hq[3] * dwx + c.hq[0] * dwy - c.hq[1] * dwz;
+    out[6] = c.hw[2] * dqw + c.hw[1] * dqx - c.hw[0] * dqy - c.hq[2] * dwx + c.hq[1] * dwy + c.hq[0] * dwz;
     const T dth = du[0] + du[1] + du[2] + du[3];
-    const T b = dth * m.inv_m;
-    out[7] = a * (T(2) * qy * dqw + T(2) * qz * dqx + T(2) * qw * dqy + T(2) * qx * dqz)
-           + b * (T(2) * (qx * qz + qw * qy));
-    out[8] = a * (-T(2) * qx * dqw - T(2) * qw * dqx + T(2) * qz * dqy + T(2) * qy * dqz)
-           + b * (T(2) * (qy * qz - qw * qx));
-    out[9] = a * (T(2) * qw * dqw - T(2) * qx * dqx - T(2) * qy * dqy + T(2) * qz * dqz)
-           + b * (qw * qw - qx * qx - qy * qy + qz * qz);
-    const T gx = (m.Jz - m.Jy) * (wz * dwy + wy * dwz);
-    const T gy = (m.Jx - m.Jz) * (wz * dwx + wx * dwz);
-    const T gz = (m.Jy - m.Jx) * (wy * dwx + wx * dwy);
-    const T tx = m.M[0][0] * du[0] + m.M[0][1] * du[1] + m.M[0][2] * du[2] + m.M[0][3] * du[3];
-    const T ty = m.M[1][0] * du[0] + m.M[1][1] * du[1] + m.M[1][2] * du[2] + m.M[1][3] * du[3];
-    const T tz = m.M[2][0] * du[0] + m.M[2][1] * du[1] + m.M[2][2] * du[2] + m.M[2][3] * du[3];
-    out[10] = (tx - gx) * m.iJx;
-    out[11] = (ty - gy) * m.iJy;
-    out[12] = (tz - gz) * m.iJz;
+    out[7] = c.c7[0] * dqw + c.c7[1] * dqx + c.c7[2] * dqy + c.c7[3] * dqz + c.r7 * dth;
+    out[8] = c.c8[0] * dqw + c.c8[1] * dqx + c.c8[2] * dqy + c.c8[3] * dqz + c.r8 * dth;
+    out[9] = c.c9[0] * dqw + c.c9[1] * dqx + c.c9[2] * dqy + c.c9[3] * dqz + c.r9 * dth;
+    out[10] = m.TJ[0][0] * du[0] + m.TJ[0][1] * du[1] + m.TJ[0][2] * du[2] + m.TJ[0][3] * du[3]
+            + c.g10y * dwy + c.g10z * dwz;
+    out[11] = m.TJ[1][0] * du[0] + m.TJ[1][1] * du[1] + m.TJ[1][2] * du[2] + m.TJ[1][3] * du[3]
+            + c.g11x * dwx + c.g11z * dwz;
+    out[12] = m.TJ[2][0] * du[0] + m.TJ[2][1] * du[1] + m.TJ[2][2] * du[2] + m.TJ[2][3] * du[3]
+            + c.g12x * dwx + c.g12y * dwy;
 }
 
-// The 6 columns of F_t for p and v are constant: position enters nothing
-// (F[:, p_i] = e_{p_i}) and velocity only the position (F[:, v_i] = e_{v_i} +
-// h e_{p_i}, h written as (h/6) * 6 as the RK4 combination forms it).  The
-// other 11 columns (q, w, u) are computed; GCOL maps 0..10 to them.
-__device__ __forceinline__ int gcol(int jj) { return jj < 4 ? 3 + jj : 6 + jj; }
-__device__ __forceinline__ int tcol(int jj) { return jj < 3 ? jj : jj + 4; }
-constexpr int NGC = 11, NTC = 6;
-template <typename T> __device__ __forceinline__ T hv_coef(const Model<T>& m) { return (m.h / T(6)) * T(6); }
-
-// Column j of F_t = d RK4 / d(x, u): forward tangent through the four stages,
-// d_s = J_c(xi_s) [dx + c_s d_{s-1}; du],  col = dx + h/6 (d1 + 2 d2 + 2 d3 + d4).
+// Directional derivative of the RK4 step, F_t [dx; du], by a forward tangent
+// through the four stages: d_s = J_c(xi_s) [dx + c_s d_{s-1}; du],
+// out = dx + h/6 (d1 + 2 d2 + 2 d3 + d4).  With a unit direction it is one
+// column of F_t.
 template <typename T>
-__device__ __forceinline__ void tangent_column(const Model<T>& m, const T* __restrict__ sp, int j, T* col) {
-    T dx[NX], du[NU], arg[NX], d[NX], acc[NX];
+__device__ __forceinline__ void rk4_tangent(const Model<T>& m, const T* sp, const T* dx, const T* du, T* out) {
+    T arg[NX], d[NX], acc[NX];
 #pragma unroll
-    for (int i = 0; i < NX; ++i) { dx[i] = (i == j) ? T(1) : T(0); arg[i] = dx[i]; }
-#pragma unroll
-    for (int a = 0; a < NU; ++a) du[a] = (NX + a == j) ? T(1) : T(0);
+    for (int i = 0; i < NX; ++i) arg[i] = dx[i];
     const T th = sp[7];
     const T hh = T(0.5) * m.h;
 #pragma unroll
     for (int st = 0; st < 4; ++st) {
-        jvp_cont(m, sp + 8 * st, th, arg, du, d);
+        JcCoef<T> jc;
+        jc_coef(m, sp + 8 * st, th, jc);
+        jc_apply(m, jc, arg, du, d);
         const T w = (st == 0 || st == 3) ? T(1) : T(2);
         const T c = (st < 2) ? hh : m.h;
 #pragma unroll
@@ -294,12 +332,55 @@ __device__ __forceinline__ void tangent_column(const Model<T>& m, const T* __res
     }
     const T h6 = m.h / T(6);
 #pragma unroll
-    for (int i = 0; i < NX; ++i) col[i] = dx[i] + h6 * acc[i];
+    for (int i = 0; i < NX; ++i) out[i] = dx[i] + h6 * acc[i];
 }
+
+// Columns j[0..NC) of F_t together: unit directions pushed through the four
+// RK4 stages side by side (d_s = J_c(xi_s) [e_j + c_s d_{s-1}; e_u],
+// col = e_j + h/6 (d1 + 2 d2 + 2 d3 + d4)), so each stage's Jacobian
+// coefficients are formed once and the NC chains interleave.  j = -1 gives
+// a column of zeros' tangent (unused).
+template <typename T, int NC>
+__device__ __forceinline__ void tangent_columns(const Model<T>& m, const T* sp, const int (&j)[NC],
+                                                T (&col)[NC][NX]) {
+    T arg[NC][NX], acc[NC][NX], du[NC][NU];
+#pragma unroll
+    for (int k = 0; k < NC; ++k) {
+#pragma unroll
+        for (int i = 0; i < NX; ++i) arg[k][i] = (i == j[k]) ? T(1) : T(0);
+#pragma unroll
+        for (int a = 0; a < NU; ++a) du[k][a] = (NX + a == j[k]) ? T(1) : T(0);
+    }
+    const T hh = T(0.5) * m.h;
+#pragma unroll
+    for (int st = 0; st < 4; ++st) {
+        JcCoef<T> c;
+        jc_coef(m, sp + 8 * st, sp[7], c);
+        const T w = (st == 0 || st == 3) ? T(1) : T(2);
+        const T cs = (st < 2) ? hh : m.h;
+#pragma unroll
+        for (int k = 0; k < NC; ++k) {
+            T d[NX];
+            jc_apply(m, c, arg[k], du[k], d);
+#pragma unroll
+            for (int i = 0; i < NX; ++i) {
+                acc[k][i] = (st == 0) ? d[i] : acc[k][i] + w * d[i];
+                arg[k][i] = ((i == j[k]) ? T(1) : T(0)) + cs * d[i];
+            }
+        }
+    }
+    const T h6 = m.h / T(6);
+#pragma unroll
+    for (int k = 0; k < NC; ++k)
+#pragma unroll
+        for (int i = 0; i < NX; ++i) col[k][i] = ((i == j[k]) ? T(1) : T(0)) + h6 * acc[k][i];
+}
+
+template <typename T> __device__ __forceinline__ T hv_coef(const Model<T>& m) { return (m.h / T(6)) * T(6); }
 
 // ------------------------------------------------------------- box QP ------
 // Packed lower-triangular index of a 4x4 factor.
-__device__ __forceinline__ int lidx(int i, int j) { return i * (i + 1) / 2 + j; }
+__host__ __device__ constexpr int lidx(int i, int j) { return i * (i + 1) / 2 + j; }
 
 // Pivot of the Cholesky factor: l = sqrt(s) and 1 / l.  In FP32 from the
 // hardware reciprocal square root refined by one Newton step (about 1 ulp, as
@@ -317,45 +398,39 @@ __device__ __forceinline__ void pivot(double s, double& l, double& il) {
 
 // Cholesky of H with the rows/columns outside `mask` replaced by the identity:
 // the free block is factored exactly, clamped dimensions decouple.  L[10 + j]
-// holds 1 / L_jj so that the solves multiply instead of divide.
+// holds 1 / L_jj so that the solves multiply instead of divide.  Straight-line
+// code (selects, no branches), so the lanes of a warp -- different instances
+// with different free sets -- never diverge here.  Returns false when a free
+// pivot is not positive (the factor is then meaningless).
 template <typename T>
 __device__ __forceinline__ bool chol_masked(const T (&H)[4][4], int mask, T (&L)[NL]) {
+    bool ok = true;
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
         const bool fj = (mask >> j) & 1;
-        if (!fj) {
-            L[lidx(j, j)] = T(1);
-            L[10 + j] = T(1);
-#pragma unroll
-            for (int i = j + 1; i < 4; ++i) L[lidx(i, j)] = T(0);
-            continue;
-        }
         T s = H[j][j];
 #pragma unroll
         for (int k = 0; k < j; ++k) s -= L[lidx(j, k)] * L[lidx(j, k)];
-        if (!(s > T(0))) return false;
+        const bool pos = s > T(0);
+        ok = ok && (pos || !fj);
         T ljj, ij;
-        pivot(s, ljj, ij);
-        L[lidx(j, j)] = ljj;
-        L[10 + j] = ij;
+        pivot(fj && pos ? s : T(1), ljj, ij);
+        L[lidx(j, j)] = fj ? ljj : T(1);
+        L[10 + j] = fj ? ij : T(1);
 #pragma unroll
         for (int i = j + 1; i < 4; ++i) {
-            if ((mask >> i) & 1) {
-                T t = H[i][j];
+            T t = H[i][j];
 #pragma unroll
-                for (int k = 0; k < j; ++k) t -= L[lidx(i, k)] * L[lidx(j, k)];
-                L[lidx(i, j)] = t * ij;
-            } else {
-                L[lidx(i, j)] = T(0);
-            }
+            for (int k = 0; k < j; ++k) t -= L[lidx(i, k)] * L[lidx(j, k)];
+            L[lidx(i, j)] = (fj && ((mask >> i) & 1)) ? t * ij : T(0);
         }
     }
-    return true;
+    return ok;
 }
 
 // Solve (L L') y = b with a masked factor (b must be 0 on clamped dimensions).
 template <typename T>
-__device__ __forceinline__ void chol_solve4(const T* L, const T (&b)[4], T (&y)[4]) {
+__device__ __forceinline__ void chol_solve4(const T (&L)[NL], const T (&b)[4], T (&y)[4]) {
     T z[4];
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
@@ -387,6 +462,12 @@ __device__ __forceinline__ T qp_value(const T (&H)[4][4], const T (&g)[4], const
     return lin + T(0.5) * quad;
 }
 
+template <typename T> __device__ __forceinline__ void identity_factor(T (&L)[NL]) {
+#pragma unroll
+    for (int i = 0; i < NL; ++i) L[i] = T(0);
+    L[0] = L[2] = L[5] = L[9] = L[10] = L[11] = L[12] = L[13] = T(1);
+}
+
 // Projected-Newton box QP (Tassa et al. 2014, Bertsekas 1982):
 //   min 1/2 d'Hd + g'd  s.t. lo <= d <= hi,  start d = clamp(0).
 // Clamped set: at a bound with the gradient pointing out of the box.  Newton
@@ -394,17 +475,22 @@ __device__ __forceinline__ T qp_value(const T (&H)[4][4], const T (&g)[4], const
 // Stops with no free dimension, or when the free set repeats after a full step
 // the projection did not cut, or after QP_MAX_IT iterations.  Returns false on
 // a non-positive pivot.  `L` and `mask` describe the last factored free set.
+//
+// Called by all 32 lanes of a warp (one instance each; `on` false for lanes
+// without a problem).  Every lane runs the same straight-line iteration and
+// keeps or discards its result by selects; the loop ends when every lane has
+// stopped, and only the rare backtracking beyond the full step branches.
 template <typename T>
-__device__ bool box_qp(const T (&H)[4][4], const T (&g)[4], const T (&lo)[4], const T (&hi)[4],
+__device__ bool box_qp(bool on, const T (&H)[4][4], const T (&g)[4], const T (&lo)[4], const T (&hi)[4],
                        T (&d)[4], T (&L)[NL], int& mask_out) {
 #pragma unroll
     for (int i = 0; i < 4; ++i) d[i] = clampT(T(0), lo[i], hi[i]);
     int free_prev = -1, mask_fact = 0;
-    bool last_full = false;
-#pragma unroll
-    for (int i = 0; i < NL; ++i) L[i] = T(0);
-    L[0] = L[2] = L[5] = L[9] = L[10] = L[11] = L[12] = L[13] = T(1);
+    bool last_full = false, done = !on, ok = true;
+    identity_factor(L);
+    mask_out = 0;
     for (int it = 0; it < QP_MAX_IT; ++it) {
+        if (__all_sync(FULL, done)) break;
         T grad[4];
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
@@ -417,251 +503,313 @@ __device__ bool box_qp(const T (&H)[4][4], const T (&g)[4], const T (&lo)[4], co
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
             const bool cl = (d[i] <= lo[i] && grad[i] > T(0)) || (d[i] >= hi[i] && grad[i] < T(0));
-            if (!cl) fm |= 1 << i;
+            fm |= cl ? 0 : (1 << i);
         }
-        if (fm == 0) {
-#pragma unroll
-            for (int i = 0; i < NL; ++i) L[i] = T(0);
-            L[0] = L[2] = L[5] = L[9] = L[10] = L[11] = L[12] = L[13] = T(1);
-            mask_out = 0;
-            return true;
-        }
-        if (last_full && fm == free_prev) { mask_out = fm; return true; }
-        if (!chol_masked(H, fm, L)) { mask_out = fm; return false; }
-        mask_fact = fm;
+        const bool none_free = fm == 0;
+        const bool repeat = last_full && fm == free_prev;
+        T Ln[NL];
+        const bool pd = chol_masked(H, fm, Ln);
         T rhs[4], dn[4], dir[4];
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
-            if ((fm >> i) & 1) {
-                T s = g[i];
+            T s = g[i];
 #pragma unroll
-                for (int k = 0; k < 4; ++k)
-                    if (!((fm >> k) & 1)) s += H[i][k] * d[k];
-                rhs[i] = -s;
-            } else {
-                rhs[i] = T(0);
-            }
+            for (int k = 0; k < 4; ++k) s = ((fm >> k) & 1) ? s : s + H[i][k] * d[k];
+            rhs[i] = ((fm >> i) & 1) ? -s : T(0);
         }
-        chol_solve4(L, rhs, dn);
+        chol_solve4(Ln, rhs, dn);
 #pragma unroll
         for (int i = 0; i < 4; ++i) dir[i] = ((fm >> i) & 1) ? dn[i] - d[i] : T(0);
         const T phi0 = qp_value(H, g, d);
-        T step = T(1);
-        bool acc = false;
-        T trial[4], dnew[4];
-        for (int ls = 0; ls < QP_MAX_LS; ++ls) {
+        T step = T(1), trial[4], dnew[4];
 #pragma unroll
-            for (int i = 0; i < 4; ++i) { trial[i] = d[i] + step * dir[i]; dnew[i] = clampT(trial[i], lo[i], hi[i]); }
-            const T phin = qp_value(H, g, dnew);
-            T gd = T(0);
+        for (int i = 0; i < 4; ++i) { trial[i] = d[i] + dir[i]; dnew[i] = clampT(trial[i], lo[i], hi[i]); }
+        T gd = T(0);
 #pragma unroll
-            for (int i = 0; i < 4; ++i) gd += grad[i] * (dnew[i] - d[i]);
-            if (phin - phi0 <= T(0.1) * gd) { acc = true; break; }
-            step *= T(0.6);
+        for (int i = 0; i < 4; ++i) gd += grad[i] * (dnew[i] - d[i]);
+        bool acc = qp_value(H, g, dnew) - phi0 <= T(0.1) * gd;
+        const bool live = !done && !none_free && !repeat && pd;
+        if (__any_sync(FULL, live && !acc)) {
+            for (int ls = 1; ls < QP_MAX_LS; ++ls) {
+                if (!__any_sync(FULL, live && !acc)) break;
+                if (live && !acc) {
+                    step *= T(0.6);
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) { trial[i] = d[i] + step * dir[i]; dnew[i] = clampT(trial[i], lo[i], hi[i]); }
+                    T gd2 = T(0);
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) gd2 += grad[i] * (dnew[i] - d[i]);
+                    acc = qp_value(H, g, dnew) - phi0 <= T(0.1) * gd2;
+                }
+            }
         }
-        if (!acc) { mask_out = mask_fact; return true; }
         bool inside = true, strict = true;
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
             inside = inside && (trial[i] >= lo[i]) && (trial[i] <= hi[i]);
             strict = strict && (trial[i] > lo[i]) && (trial[i] < hi[i]);
         }
-        last_full = (step == T(1)) && inside;
-        free_prev = fm;
+        // outcome of this iteration for a lane still running
+        if (!done) {
+            if (none_free) {
+                identity_factor(L);
+                mask_out = 0;
+                done = true;
+            } else if (repeat) {
+                mask_out = fm;
+                done = true;
+            } else {
 #pragma unroll
-        for (int i = 0; i < 4; ++i) d[i] = dnew[i];
-        // A full step strictly inside the box with every dimension free: no
-        // dimension sits on a bound at the new point, so the next iteration
-        // would find the same (full) free set and stop here.
-        if (last_full && strict && fm == 15) { mask_out = fm; return true; }
-    }
-    mask_out = mask_fact;
-    return true;
-}
-
-// ------------------------------------------------------------ lanes --------
-// An instance is owned by a group of TPI consecutive lanes of a warp; a warp
-// holds PACK = 32 / TPI instances and runs them in lockstep.  Every loop that
-// contains a warp barrier runs a warp-uniform number of times (the largest
-// horizon in the pack); each group does its own instance's share under a
-// per-group predicate.  Per-instance arithmetic is the same for every TPI:
-// each output entry is produced by one lane, in the same order of operations.
-template <int TPI> struct Lanes {
-    static constexpr int PACK = 32 / TPI;
-    int lane, g, l;
-    __device__ __forceinline__ Lanes() {
-        lane = threadIdx.x & 31;
-        g = lane / TPI;
-        l = lane - g * TPI;
-    }
-    __device__ __forceinline__ int src(int sub) const { return g * TPI + sub; }
-};
-
-__device__ __forceinline__ void wsync() { __syncwarp(); }
-
-__device__ __forceinline__ int warp_max(int v) {
+                for (int i = 0; i < NL; ++i) L[i] = Ln[i];
+                mask_fact = fm;
+                if (!pd) {
+                    mask_out = fm;
+                    ok = false;
+                    done = true;
+                } else if (!acc) {
+                    mask_out = fm;
+                    done = true;
+                } else {
+                    last_full = (step == T(1)) && inside;
+                    free_prev = fm;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        const int w = __shfl_xor_sync(FULL, v, o);
-        v = w > v ? w : v;
-    }
-    return v;
-}
-
-// ------------------------------------------------------------ helpers -------
-template <typename T> struct Inst {
-    int b, n, slot;
-    const T* Qb;      // Q rows of this instance
-    const T* xrefb;
-    T* ub;            // nominal / output u  [N][4]
-    T* xb;            // nominal / output x  [N][13]
-    T* F;             // slot scratch: computed columns of F_t [N_ws][11][13]
-    T* Kr;            // slot scratch: K_t,k_t [N_ws][56]
-    T* cand;          // slot scratch: candidates [4][N_ws][30]
-    T* sp;            // slot scratch: stage points [N_ws][32]
-    T* kh;            // slot scratch: adjoint k-hat [N_ws][4]
-    T* xlo;           // slot scratch: low part of the nominal state [N_ws][13]
-};
-
-// Instance b in scratch slot `slot`; `valid` false gives an empty instance
-// (n = 0) whose pointers are never dereferenced.
-template <typename T>
-__device__ __forceinline__ Inst<T> make_inst(const Params<T>& P, int b, int slot, bool valid) {
-    Inst<T> I;
-    I.b = b;
-    int n = P.horizon ? P.horizon[b] : P.N;
-    n = n < 1 ? 1 : (n > P.N ? P.N : n);
-    I.n = valid ? n : 0;
-    I.slot = slot;
-    I.Qb = P.Q + (size_t)b * P.Nq * NX;
-    I.xrefb = P.xref + (size_t)b * P.N * NX;
-    I.ub = P.u + (size_t)b * P.N * NU;
-    I.xb = P.x + (size_t)b * P.N * NX;
-    const size_t s = (size_t)slot;
-    I.F = P.wsF + s * P.N_ws * NFC;
-    I.Kr = P.wsK + s * P.N_ws * KREC;
-    I.cand = P.wsCand + s * 4 * P.N_ws * CREC;
-    I.sp = P.wsSP + s * P.N_ws * SP_STRIDE;
-    I.kh = P.wsKh + s * P.N_ws * NU;
-    I.xlo = P.wsXlo + s * P.N_ws * NX;
-    return I;
-}
-
-template <typename T>
-__device__ __forceinline__ const T* Qrow(const Params<T>& P, const Inst<T>& I, int t) {
-    return I.Qb + (P.Nq > 1 ? t : 0) * NX;
-}
-
-// A stage's nominal and cost inputs as staged in shared memory (after K_t, k_t
-// in the line search's record): x_t, x lo_t, u_t, Q_t, x_ref,t.
-constexpr int SI_X = 0, SI_XL = NX, SI_U = 2 * NX, SI_Q = 2 * NX + NU, SI_R = 3 * NX + NU, SIN = 4 * NX + NU;
-
-template <typename T>
-__device__ __forceinline__ const T* stage_input_src(const Params<T>& P, const Inst<T>& I, int t, int e) {
-    if (e < SI_XL) return I.xb + t * NX + e;
-    if (e < SI_U) return I.xlo + t * NX + e - SI_XL;
-    if (e < SI_Q) return I.ub + t * NU + e - SI_U;
-    if (e < SI_R) return Qrow(P, I, t) + e - SI_Q;
-    return I.xrefb + t * NX + e - SI_R;
-}
-
-// Starts the asynchronous copy of stage t's inputs to dst[0..SIN).
-template <typename T, int TPI>
-__device__ __forceinline__ void stage_inputs_async(const Params<T>& P, const Inst<T>& I, const Lanes<TPI>& L, int t,
-                                                   T* dst) {
-    constexpr int R = (SIN + TPI - 1) / TPI;
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-        const int e = L.l + r * TPI;
-        if (e < SIN) cp_async(dst + e, stage_input_src(P, I, t, e));
-    }
-}
-
-template <typename T, int TPI>
-__device__ __forceinline__ void load_instance(const Params<T>& P, const Inst<T>& I, WarpSmem<T>& S,
-                                              const Lanes<TPI>& L, bool act) {
-    if (act) {
-        for (int e = L.l; e < NX; e += TPI) S.x0[e] = P.x0[(size_t)I.b * NX + e];
-        for (int e = L.l; e < 4 * NU; e += TPI) {
-            const int w = e >> 2, a = e & 3;
-            const T* src = w == 0 ? P.R : (w == 1 ? P.uref : (w == 2 ? P.ulo : P.uhi));
-            T* dst = w == 0 ? S.R : (w == 1 ? S.uref : (w == 2 ? S.ulo : S.uhi));
-            dst[a] = src[I.b * NU + a];
-        }
-    }
-    wsync();
-}
-
-// --------------------------------------------------------- A1 rollout -------
-// U^0 = clamp(u_init or u_ref), X^0 by RK4 from x_init (one lane), J^0.  States
-// are carried as hi + lo (rk4_step2); hi is the output x, lo stays in the slot.
-// Stages past the horizon are zero-filled.  Returns J^0 on every lane of the group.
-template <typename T, int TPI>
-__device__ T initial_rollout(const Params<T>& P, const Inst<T>& I, const WarpSmem<T>& S, const Lanes<TPI>& L,
-                             bool act) {
-    T J = T(0);
-    if (act) {
-        const int n = I.n;
-        for (int e = n * NU + L.l; e < P.N * NU; e += TPI) I.ub[e] = T(0);
-        for (int e = n * NX + L.l; e < P.N * NX; e += TPI) I.xb[e] = T(0);
-        if (L.l == 0) {
-            T xh[NX], xl[NX], us[NU];
-#pragma unroll
-            for (int i = 0; i < NX; ++i) { xh[i] = S.x0[i]; xl[i] = T(0); }
-            for (int t = 0; t < n; ++t) {
-#pragma unroll
-                for (int a = 0; a < NU; ++a) {
-                    const T u0 = P.uinit ? P.uinit[((size_t)I.b * P.N + t) * NU + a] : S.uref[a];
-                    us[a] = clampT(u0, S.ulo[a], S.uhi[a]);
-                    I.ub[t * NU + a] = us[a];
+                    for (int i = 0; i < 4; ++i) d[i] = dnew[i];
+                    // A full step strictly inside the box with every dimension free:
+                    // the next iteration would find the same free set and stop.
+                    if (last_full && strict && fm == 15) {
+                        mask_out = fm;
+                        done = true;
+                    }
                 }
-                const T* Qt = Qrow(P, I, t);
-                const T* xr = I.xrefb + t * NX;
-                T sx = T(0), su = T(0);
-#pragma unroll
-                for (int i = 0; i < NX; ++i) {
-                    I.xb[t * NX + i] = xh[i];
-                    I.xlo[t * NX + i] = xl[i];
-                    const T e = (xh[i] - xr[i]) + xl[i];
-                    sx += e * (Qt[i] * e);
-                }
-#pragma unroll
-                for (int a = 0; a < NU; ++a) { const T e = us[a] - S.uref[a]; su += e * (S.R[a] * e); }
-                J += T(0.5) * sx + T(0.5) * su;
-                if (t < n - 1) rk4_step2(P.mdl, xh, xl, us);
             }
         }
     }
-    wsync();
-    return __shfl_sync(FULL, J, L.src(0));
+    if (!done) mask_out = mask_fact;
+    return ok;
 }
 
-// ------------------------------------------------------ A2 linearization ----
-// F_t = [A_t B_t] at the nominal for t = 0..n-2 into the slot (its 11
-// computed columns, [t][11][13]): the group's lanes
-// first take one stage each for the RK4 stage points, then one
-// (stage, column) tangent each.
-template <typename T, int TPI>
-__device__ void linearize(const Params<T>& P, const Inst<T>& I, const Lanes<TPI>& L, bool act) {
-    const int ns = act ? I.n - 1 : 0;
-    for (int t = L.l; t < ns; t += TPI) {
-        T xs[NX], us[NU];
-#pragma unroll
-        for (int i = 0; i < NX; ++i) xs[i] = I.xb[t * NX + i];
-#pragma unroll
-        for (int a = 0; a < NU; ++a) us[a] = I.ub[t * NU + a];
-        rk4_stage_points(P.mdl, xs, us, I.sp + t * SP_STRIDE);
+// ------------------------------------------------------------ work split ----
+// Which warp does what, for NW = 4 or 8 warps per block.  Computed columns
+// are numbered jj = 0..10 (gcol(jj) is the column of F_t / Q_t).
+//   pcol(w, s)   the computed columns whose W = V F column and Q entries warp w
+//                forms in the products (s = 0..2, -1 = none); the entries of
+//                column j in rows of computed columns jj_r <= jj cost jj + 1
+//                dot products, so large and small columns are paired
+//   CONST_W      the warp that forms the block of the constant p, v rows/columns
+//   tcol(w, s)   the tangent columns of F_{t-1} warp w computes while warp 0
+//                runs the box QP (so warp 0 takes fewer)
+//   kcol(w, s)   the columns c of K_t (and of V_t, v_t) warp w forms; column c
+//                of V_t has c + 1 entries
+// The tables, by warp: 4-warp split first, then the 8-warp split.
+__constant__ int c_pcol4[4][3] = {{10, 9, 0}, {8, 7, 1}, {6, 5, 2}, {4, 3, -1}};
+__constant__ int c_tcol4[4][3] = {{0, 1, -1}, {2, 3, 4}, {5, 6, 7}, {8, 9, 10}};
+__constant__ int c_kcol4[4][4] = {{12, 0, 6, -1}, {11, 1, 7, -1}, {10, 2, 8, -1}, {9, 3, 4, 5}};
+__constant__ int c_pcol8[8][2] = {{10, 0}, {9, 1}, {8, 2}, {7, 3}, {6, 4}, {5, -1}, {-1, -1}, {-1, -1}};
+__constant__ int c_tcol8[8][2] = {{0, -1}, {1, 2}, {3, 4}, {5, 6}, {7, 8}, {9, 10}, {-1, -1}, {-1, -1}};
+__constant__ int c_kcol8[8][2] = {{12, 0}, {11, 1}, {10, 2}, {9, 3}, {8, 4}, {7, 5}, {6, -1}, {-1, -1}};
+
+template <int NW> struct Split;
+template <> struct Split<4> {
+    static constexpr int NP = 3, NT = 3, NK = 4, CONST_W = 3;
+    __device__ static int pcol(int w, int s) { return c_pcol4[w][s]; }
+    __device__ static int tcol(int w, int s) { return c_tcol4[w][s]; }
+    __device__ static int kcol(int w, int s) { return c_kcol4[w][s]; }
+};
+template <> struct Split<8> {
+    static constexpr int NP = 2, NT = 2, NK = 2, CONST_W = 7;
+    __device__ static int pcol(int w, int s) { return c_pcol8[w][s]; }
+    __device__ static int tcol(int w, int s) { return c_tcol8[w][s]; }
+    __device__ static int kcol(int w, int s) { return c_kcol8[w][s]; }
+};
+
+// ------------------------------------------------------------ lanes --------
+// The calling thread's place: warp w of NW, lane l = instance l of the pack,
+// its position pos in the processing order (scratch index) and instance b.
+struct Lane {
+    int w, l, pos, b;
+    bool valid;
+};
+
+// Scratch row e of stage t for position pos ([group][stage][row][32]).
+template <typename T>
+__device__ __forceinline__ size_t srow(const Params<T>& P, int pos, int t, int e) {
+    return (((size_t)(pos >> 5) * P.N_ws + t) * SREC + e) * LW + (pos & 31);
+}
+template <typename T>
+__device__ __forceinline__ size_t crow(const Params<T>& P, int c, int pos, int t, int e) {
+    const size_t groups = ((size_t)P.B + 31) >> 5;
+    return ((((size_t)c * groups + (pos >> 5)) * P.N_ws + t) * CREC + e) * LW + (pos & 31);
+}
+template <typename T>
+__device__ __forceinline__ size_t khrow(const Params<T>& P, int pos, int t, int a) {
+    return (((size_t)(pos >> 5) * P.N_ws + t) * NU + a) * LW + (pos & 31);
+}
+// Tape row e of stage t for instance b ([group of 32 instances][stage][row][32]).
+template <typename T>
+__device__ __forceinline__ size_t trow(const Params<T>& P, int b, int t, int e) {
+    return (((size_t)(b >> 5) * P.N + t) * TREC + e) * LW + (b & 31);
+}
+
+template <typename T>
+__device__ __forceinline__ const T* Qrow(const Params<T>& P, int b, int t) {
+    return P.Q + ((size_t)b * P.Nq + (P.Nq > 1 ? t : 0)) * NX;
+}
+
+// The pack's per-instance constants into shared memory (rows split by warp).
+template <typename T, int NW>
+__device__ void load_constants(const Params<T>& P, BlockSmem<T>& S, const Lane& L) {
+    if (L.valid) {
+        for (int e = L.w; e < NX + 4 * NU; e += NW) {
+            if (e < NX) {
+                S.x0[e][L.l] = P.x0[(size_t)L.b * NX + e];
+            } else {
+                const int r = e - NX, q = r >> 2, a = r & 3;
+                const T* src = q == 0 ? P.R : (q == 1 ? P.uref : (q == 2 ? P.ulo : P.uhi));
+                T(*dst)[LW] = q == 0 ? S.R : (q == 1 ? S.uref : (q == 2 ? S.ulo : S.uhi));
+                dst[a][L.l] = src[(size_t)L.b * NU + a];
+            }
+        }
     }
-    wsync();
-    for (int w = L.l; w < ns * NGC; w += TPI) {
-        const int t = w / NGC, jj = w - t * NGC;
-        T col[NX];
-        tangent_column(P.mdl, I.sp + t * SP_STRIDE, gcol(jj), col);
-        T* dst = I.F + (size_t)t * NFC + jj * NX;
+}
+
+// The cost rows Q_t, x_ref,t of every stage t < n into the scratch records
+// (stages split by warp).  With `nominal` also x*, u* from the solution
+// outputs as the nominal (x lo = 0): the backward's re-factorization point.
+template <typename T, int NW>
+__device__ void load_stage_rows(const Params<T>& P, const Lane& L, int n, bool nominal) {
+    if (!L.valid) return;
+    for (int t = L.w; t < n; t += NW) {
+        const T* q = Qrow(P, L.b, t);
+        const T* xr = P.xref + ((size_t)L.b * P.N + t) * NX;
+        T* dr = P.stg + srow(P, L.pos, t, 0);
+        T buf[2 * NX];
 #pragma unroll
-        for (int i = 0; i < NX; ++i) dst[i] = col[i];
+        for (int i = 0; i < NX; ++i) { buf[i] = q[i]; buf[NX + i] = xr[i]; }
+        if (nominal) {
+            const T* xs = P.x + ((size_t)L.b * P.N + t) * NX;
+            const T* us = P.u + ((size_t)L.b * P.N + t) * NU;
+            T nb[NX + NU];
+#pragma unroll
+            for (int i = 0; i < NX; ++i) nb[i] = xs[i];
+#pragma unroll
+            for (int a = 0; a < NU; ++a) nb[NX + a] = us[a];
+#pragma unroll
+            for (int i = 0; i < NX; ++i) { dr[(R_X + i) * LW] = nb[i]; dr[(R_XL + i) * LW] = T(0); }
+#pragma unroll
+            for (int a = 0; a < NU; ++a) dr[(R_U + a) * LW] = nb[NX + a];
+        }
+#pragma unroll
+        for (int i = 0; i < NX; ++i) { dr[(R_Q + i) * LW] = buf[i]; dr[(R_XR + i) * LW] = buf[NX + i]; }
     }
-    wsync();
+}
+
+// --------------------------------------------------------- A1 rollout -------
+// U^0 = clamp(u_init or u_ref), X^0 by RK4 from x_init, J^0 (warp 0; the
+// state is carried as hi + lo).  Writes the nominal records; returns J^0 in
+// S.Jc[0] for the block (after the caller's barrier).
+template <typename T, int NW>
+__device__ void initial_rollout(const Params<T>& P, BlockSmem<T>& S, const Lane& L, int n) {
+    if (L.w != 0) return;
+    T J = T(0);
+    if (n > 0) {
+        T xh[NX], xl[NX], us[NU], R[NU], ur[NU], lo[NU], hi[NU];
+#pragma unroll
+        for (int i = 0; i < NX; ++i) { xh[i] = S.x0[i][L.l]; xl[i] = T(0); }
+#pragma unroll
+        for (int a = 0; a < NU; ++a) {
+            R[a] = S.R[a][L.l]; ur[a] = S.uref[a][L.l]; lo[a] = S.ulo[a][L.l]; hi[a] = S.uhi[a][L.l];
+        }
+        for (int t = 0; t < n; ++t) {
+            T* sr = P.stg + srow(P, L.pos, t, 0);
+            T qv[NX], xr[NX], u0[NU];
+#pragma unroll
+            for (int i = 0; i < NX; ++i) { qv[i] = sr[(R_Q + i) * LW]; xr[i] = sr[(R_XR + i) * LW]; }
+#pragma unroll
+            for (int a = 0; a < NU; ++a) u0[a] = P.uinit ? P.uinit[((size_t)L.b * P.N + t) * NU + a] : ur[a];
+            T sx = T(0), su = T(0);
+#pragma unroll
+            for (int a = 0; a < NU; ++a) {
+                us[a] = clampT(u0[a], lo[a], hi[a]);
+                sr[(R_U + a) * LW] = us[a];
+                const T e = us[a] - ur[a];
+                su += e * (R[a] * e);
+            }
+#pragma unroll
+            for (int i = 0; i < NX; ++i) {
+                sr[(R_X + i) * LW] = xh[i];
+                sr[(R_XL + i) * LW] = xl[i];
+                const T e = (xh[i] - xr[i]) + xl[i];
+                sx += e * (qv[i] * e);
+            }
+            J += T(0.5) * sx + T(0.5) * su;
+            if (t < n - 1) rk4_step2(P.mdl, xh, xl, us);
+        }
+    }
+    S.Jc[0][L.l] = J;
+}
+
+
+// --------------------------------------------- A8 adjoint backward step ----
+// One stage of the adjoint LQR's backward sweep (Sec. IV implicit
+// differentiation, Amos et al. 2018) on the stage's frozen factorization:
+//   qh = g_t + F_t' vh_{t+1};  kh_t = -(Q_uu,ff)^-1 qh_u,f (0 on clamped rows);
+//   vh_t = qh_x + K_t' qh_u.
+// Fp, Kp, Lp point at row 0 of the stage's computed F columns, K_t and masked
+// factor in shared memory (this lane's column, rows LW apart).  Two
+// barrier-separated steps: qh (columns split like the products), then kh
+// (warp 0) and vh (rows split).
+template <typename T, int NW>
+__device__ __forceinline__ void adjoint_step(const Params<T>& P, BlockSmem<T>& S, const Lane& L, int t, bool go,
+                                             const AdjArgs<T>& A, const T* Fp, const T* Kp, const T* Lp, int mask) {
+    const int l = L.l;
+    const T hv = hv_coef(P.mdl);
+    const size_t gxo = ((size_t)L.b * P.N + t) * NX, guo = ((size_t)L.b * P.N + t) * NU;
+    if (go) {
+        T vh[NX];
+#pragma unroll
+        for (int i = 0; i < NX; ++i) vh[i] = S.vh[i][l];
+#pragma unroll
+        for (int s = 0; s < Split<NW>::NP; ++s) {
+            const int jj = Split<NW>::pcol(L.w, s);
+            if (jj < 0) continue;
+            const int j = gcol(jj);
+            T g = j < NX ? (A.gx ? A.gx[gxo + j] : T(0)) : A.gu[guo + j - NX];
+#pragma unroll
+            for (int k = 0; k < NX; ++k) g += Fp[(jj * NX + k) * LW] * vh[k];
+            S.qh[j][l] = g;
+        }
+        if (L.w == Split<NW>::CONST_W) {
+#pragma unroll
+            for (int b = 0; b < 3; ++b) {
+                const T gp = A.gx ? A.gx[gxo + b] : T(0), gv = A.gx ? A.gx[gxo + 7 + b] : T(0);
+                S.qh[b][l] = gp + vh[b];
+                S.qh[7 + b][l] = gv + (vh[7 + b] + hv * vh[b]);
+            }
+        }
+    }
+    __syncthreads();
+    if (go) {
+        T qu[NU];
+#pragma unroll
+        for (int a = 0; a < NU; ++a) qu[a] = S.qh[NX + a][l];
+        if (L.w == 0) {
+            T Lf[NL], rhs[4], y[4];
+#pragma unroll
+            for (int i = 0; i < NL; ++i) Lf[i] = Lp[i * LW];
+#pragma unroll
+            for (int a = 0; a < 4; ++a) rhs[a] = ((mask >> a) & 1) ? qu[a] : T(0);
+            chol_solve4(Lf, rhs, y);
+#pragma unroll
+            for (int a = 0; a < 4; ++a) P.kh[khrow(P, L.pos, t, a)] = ((mask >> a) & 1) ? -y[a] : T(0);
+        }
+        for (int i = L.w; i < NX; i += NW) {
+            T s = S.qh[i][l];
+#pragma unroll
+            for (int a = 0; a < NU; ++a) s += Kp[(a * NX + i) * LW] * qu[a];
+            S.vh[i][l] = s;
+        }
+    }
+    __syncthreads();
 }
 
 // ---------------------------------------------- A3 Riccati with box QP ------
@@ -670,302 +818,408 @@ __device__ void linearize(const Params<T>& P, const Inst<T>& I, const Lanes<TPI>
 //   k_t, free set <- box QP(Q_uu, q_u, u_lo - u_t, u_hi - u_t)
 //   K_t = -Q_uu,ff^-1 Q_ux,f on free rows, 0 on clamped rows
 //   V_t = Q_xx + Q_xu K_t,   v_t = q_x + Q_xu k_t
-// K_t, k_t go to the slot scratch.  Options:
+// with the linearization of Sec. IV-1 fused in: F_{t-1} = [A B] at the
+// nominal (one forward tangent through the RK4 stages per computed column) is
+// formed while warp 0 solves stage t's box QP.  Stage t runs in three steps
+// separated by block barriers:
+//   (A) products: every warp forms its columns of W = V_{t+1} F_t and their
+//       entries of Q_t, q_t (the constant p, v columns take one warp);
+//   (B) warp 0: box QP of stage t; all warps: tangent columns of F_{t-1};
+//   (C) columns of K_t with the matching columns of V_t, v_t; gains to the
+//       scratch (for the line search); on request the tape record and the
+//       adjoint step.
+// Options:
 //   use_lo   cost gradient at the hi + lo nominal (iterations); otherwise at
 //            x* as returned (the factorization the backward differentiates)
 //   tape     also store F_t, K_t, the masked factor and the free mask
-//   replay   skip the recursion and read F_t, K_t, factor and mask from the tape
-//   adj      after each stage, the adjoint backward step (Sec. IV implicit
-//            differentiation) on that stage's factorization:
-//              qh = g_t + F_t' vh_{t+1};  kh_t = -(Q_uu,ff)^-1 qh_u,f;  vh_t = qh_x + K_t' qh_u
-// Returns false (for the group) when a free block of Q_uu is not positive
-// definite; the group's remaining stages are then skipped.
+//   adj      the adjoint backward step after each stage
+//   replay   no recursion: each stage's F_t, K_t, factor and free mask come
+//            from the tape (copied to shared memory one stage ahead) for the
+//            adjoint step
+// Every sweep of the method -- iterations, final factorization, backward
+// re-factorization, tape replay -- runs through this one function from one
+// call site, so the same arithmetic gives the same bits in every mode.
+// Returns false for an instance whose free block of Q_uu is not positive
+// definite; its remaining stages are skipped.
 template <typename T> struct RicOpts {
     T* tape;
     const AdjArgs<T>* adj;
-    bool replay;
     bool use_lo;
+    bool replay;
 };
 
-template <typename T, int TPI>
-__device__ bool riccati(const Params<T>& P, const Inst<T>& I, WarpSmem<T>& S, const Lanes<TPI>& L,
-                        const RicOpts<T> o, bool act) {
-    const int n = act ? I.n : 0;
-    const int nmax = warp_max(n);
-    for (int e = L.l; e < NX * LD; e += TPI) S.V[e] = T(0);
-    for (int e = L.l; e < NX; e += TPI) { S.v[e] = T(0); S.vh[e] = T(0); }
-    if (L.l == 0) S.ok = 1;
-    const T hv = hv_coef(P.mdl);
-    // The six constant columns of F_t (p and v: identity, plus hv on the p
-    // rows of the v columns) are the same at every stage: both buffers.
-    for (int e = L.l; e < NTC * NX; e += TPI) {
-        const int jj = e / NX, i = e - jj * NX, j = tcol(jj);
-        const T val = (i == j) ? T(1) : ((j >= 7 && i == j - 7) ? hv : T(0));
-        S.F[0][j * LD + i] = val;
-        S.F[1][j * LD + i] = val;
-    }
-    bool alive = true;
-    // Software pipeline: while stage t computes, stage t - 1's F_t columns and
-    // cost inputs are copied asynchronously into the other buffers.
-    auto prefetch = [&](int tt) {
-        if (tt < 0 || tt >= n || o.replay) return;
-        if (tt < n - 1) {
-            const T* Ft = I.F + (size_t)tt * NFC;
-            T* Fd = S.F[tt & 1];
-            constexpr int FR = (NFC + TPI - 1) / TPI;
+// Writes the tangent columns of F_s this warp owns, or zeros when s is the
+// instance's last stage (no dynamics: with F = 0 and V_{s+1} = 0 the products
+// reduce to Q = C, q = c).
+template <typename T, int NW>
+__device__ __forceinline__ void tangent_step(const Params<T>& P, BlockSmem<T>& S, const Lane& L, int s, int n,
+                                             bool on) {
+    if (s < 0) return;
+    const bool dyn = on && s < n - 1;
+    const bool last = on && s == n - 1;
+    T* Fd = &S.u.r.F[s & 1][0][L.l];
+    if (dyn) {
+        const T* cs = &S.u.r.cst[s & 1][0][L.l];
+        T xs[NX], us[NU], sp[32];
 #pragma unroll
-            for (int r = 0; r < FR; ++r) {
-                const int e = L.l + r * TPI;
-                if (e < NFC) {
-                    const int jj = e / NX;
-                    cp_async(Fd + gcol(jj) * LD + e - jj * NX, Ft + e);
+        for (int i = 0; i < NX; ++i) xs[i] = cs[(R_X + i) * LW];
+#pragma unroll
+        for (int a = 0; a < NU; ++a) us[a] = cs[(R_U + a) * LW];
+        rk4_stage_points(P.mdl, xs, us, sp);
+        constexpr int NT = Split<NW>::NT;
+        int jj[NT], jc[NT];
+#pragma unroll
+        for (int k = 0; k < NT; ++k) {
+            jj[k] = Split<NW>::tcol(L.w, k);
+            jc[k] = jj[k] < 0 ? -1 : gcol(jj[k]);
+        }
+        T col[NT][NX];
+        tangent_columns<T, NT>(P.mdl, sp, jc, col);
+#pragma unroll
+        for (int k = 0; k < NT; ++k) {
+            if (jj[k] < 0) continue;
+#pragma unroll
+            for (int i = 0; i < NX; ++i) Fd[(jj[k] * NX + i) * LW] = col[k][i];
+        }
+    } else if (last) {
+#pragma unroll
+        for (int k = 0; k < Split<NW>::NT; ++k) {
+            const int jj = Split<NW>::tcol(L.w, k);
+            if (jj < 0) continue;
+#pragma unroll
+            for (int i = 0; i < NX; ++i) Fd[(jj * NX + i) * LW] = T(0);
+        }
+    }
+}
+
+// Cost row j of stage t: C_jj and (C z + c)_j at the nominal.
+template <typename T>
+__device__ __forceinline__ void cost_row(const BlockSmem<T>& S, const T* cs, int l, int j, bool use_lo, T& Cd,
+                                         T& c) {
+    if (j < NX) {
+        const T q = cs[(R_Q + j) * LW];
+        const T e = cs[(R_X + j) * LW] - cs[(R_XR + j) * LW];
+        Cd = q;
+        c = q * (use_lo ? e + cs[(R_XL + j) * LW] : e);
+    } else {
+        const int a = j - NX;
+        Cd = S.R[a][l];
+        c = Cd * (cs[(R_U + a) * LW] - S.uref[a][l]);
+    }
+}
+
+// (A): this warp's entries of Q_t and q_t.  Everything it reads (its F
+// columns, V_{t+1}, v_{t+1}, its cost rows) is loaded before the arithmetic,
+// and the rows of the other computed columns are loaded one row ahead, so the
+// shared-memory latency overlaps the multiply-adds.
+template <typename T, int NW>
+__device__ __forceinline__ void products(const Params<T>& P, BlockSmem<T>& S, const Lane& L, int t, bool use_lo) {
+    constexpr int NP = Split<NW>::NP;
+    const int l = L.l;
+    const T hv = hv_coef(P.mdl);
+    const T* cs = &S.u.r.cst[t & 1][0][l];
+    const T* Fb = &S.u.r.F[t & 1][0][l];
+    T* Qs = &S.u.r.Q[0][l];
+    T* qs = &S.u.r.q[0][l];
+    int jj[NP], col[NP];
+    int jmax = -1;
+#pragma unroll
+    for (int s = 0; s < NP; ++s) {
+        jj[s] = Split<NW>::pcol(L.w, s);
+        col[s] = jj[s] < 0 ? 0 : jj[s];
+        jmax = jj[s] > jmax ? jj[s] : jmax;
+    }
+    const bool cw = L.w == Split<NW>::CONST_W;
+    if (jmax < 0 && !cw) return;
+    T V[NV], vv[NX], f[NP][NX], Cd[NP], cj[NP];
+#pragma unroll
+    for (int e = 0; e < NV; ++e) V[e] = S.V[e][l];
+#pragma unroll
+    for (int i = 0; i < NX; ++i) vv[i] = S.v[i][l];
+#pragma unroll
+    for (int s = 0; s < NP; ++s) {
+#pragma unroll
+        for (int i = 0; i < NX; ++i) f[s][i] = Fb[(col[s] * NX + i) * LW];
+        cost_row(S, cs, l, gcol(col[s]), use_lo, Cd[s], cj[s]);
+    }
+    if (cw) {
+        // the block of the constant rows/columns p_a = a, v_a = 7 + a:
+        //   Q[p_a][p_b] = V[p_a][p_b] (+ C),  Q[p_a][v_b] = V[p_a][v_b] + hv V[p_a][p_b],
+        //   Q[v_a][v_b] = (V[v_a][v_b] + hv V[v_a][p_b]) + hv (V[p_a][v_b] + hv V[p_a][p_b]) (+ C),
+        //   q[p_b] = c + v[p_b],  q[v_b] = c + (v[v_b] + hv v[p_b])
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            T Cp, cp, Cv, cv;
+            cost_row(S, cs, l, b, use_lo, Cp, cp);
+            cost_row(S, cs, l, 7 + b, use_lo, Cv, cv);
+            qs[b * LW] = cp + vv[b];
+            qs[(7 + b) * LW] = cv + (vv[7 + b] + hv * vv[b]);
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                const T Vpp = V[vidx(a, b)];
+                const T Wpv = V[vidx(a, 7 + b)] + hv * Vpp;
+                Qs[qidx(a, 7 + b) * LW] = Wpv;
+                if (a <= b) {
+                    Qs[qidx(a, b) * LW] = a == b ? Cp + Vpp : Vpp;
+                    const T s = (V[vidx(7 + a, 7 + b)] + hv * V[vidx(7 + a, b)]) + hv * Wpv;
+                    Qs[qidx(7 + a, 7 + b) * LW] = a == b ? Cv + s : s;
                 }
             }
         }
-        stage_inputs_async(P, I, L, tt, S.stg[tt & 1] + KREC);
+    }
+    if (jmax < 0) return;
+    // W[:, j] = V f_j, the reduction index outermost so that the 13 x NP
+    // accumulators advance side by side
+    T W[NP][NX];
+#pragma unroll
+    for (int s = 0; s < NP; ++s)
+#pragma unroll
+        for (int i = 0; i < NX; ++i) W[s][i] = T(0);
+#pragma unroll
+    for (int k = 0; k < NX; ++k)
+#pragma unroll
+        for (int i = 0; i < NX; ++i) {
+            const T vik = V[vidx(i, k)];
+#pragma unroll
+            for (int s = 0; s < NP; ++s) W[s][i] += vik * f[s][k];
+        }
+    // q_j, the diagonal entry, and the rows of the constant columns
+    // (p_a takes W[p_a], v_a takes W[v_a] + hv W[p_a])
+    T qj[NP], dsum[NP];
+#pragma unroll
+    for (int s = 0; s < NP; ++s) { qj[s] = cj[s]; dsum[s] = Cd[s]; }
+#pragma unroll
+    for (int k = 0; k < NX; ++k)
+#pragma unroll
+        for (int s = 0; s < NP; ++s) {
+            qj[s] += f[s][k] * vv[k];
+            dsum[s] += f[s][k] * W[s][k];
+        }
+#pragma unroll
+    for (int s = 0; s < NP; ++s) {
+        if (jj[s] < 0) continue;
+        const int j = gcol(jj[s]);
+        qs[j * LW] = qj[s];
+        Qs[qidx(j, j) * LW] = dsum[s];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            Qs[qidx(a, j) * LW] = W[s][a];
+            Qs[qidx(7 + a, j) * LW] = W[s][7 + a] + hv * W[s][a];
+        }
+    }
+    // rows of the computed columns jj_r < jj, two rows at a time:
+    // Q[r][j] = F[:, r]' W[:, j]
+#pragma unroll
+    for (int r0 = 0; r0 < NGC - 1; r0 += 2) {
+        if (r0 < jmax) {
+            T fr[2][NX];
+#pragma unroll
+            for (int rr = 0; rr < 2; ++rr)
+#pragma unroll
+                for (int i = 0; i < NX; ++i) fr[rr][i] = Fb[((r0 + rr) * NX + i) * LW];
+            T acc[2][NP];
+#pragma unroll
+            for (int rr = 0; rr < 2; ++rr)
+#pragma unroll
+                for (int s = 0; s < NP; ++s) acc[rr][s] = T(0);
+#pragma unroll
+            for (int k = 0; k < NX; ++k)
+#pragma unroll
+                for (int rr = 0; rr < 2; ++rr)
+#pragma unroll
+                    for (int s = 0; s < NP; ++s) acc[rr][s] += fr[rr][k] * W[s][k];
+#pragma unroll
+            for (int rr = 0; rr < 2; ++rr)
+#pragma unroll
+                for (int s = 0; s < NP; ++s)
+                    if (r0 + rr < jj[s]) Qs[qidx(gcol(r0 + rr), gcol(jj[s])) * LW] = acc[rr][s];
+        }
+    }
+}
+
+template <typename T, int NW>
+__device__ bool riccati(const Params<T>& P, BlockSmem<T>& S, const Lane& L, int n, const RicOpts<T>& o) {
+    const int l = L.l;
+    const int nmax = __reduce_max_sync(FULL, n);
+    for (int e = L.w; e < NV; e += NW) S.V[e][l] = T(0);
+    for (int e = L.w; e < NX; e += NW) { S.v[e][l] = T(0); S.vh[e][l] = T(0); }
+    bool alive = true;
+    // copy of stage tt's nominal and cost rows into cst[tt & 1] (rows split by warp)
+    auto stage_copy = [&](int tt) {
+        if (tt >= 0 && tt < n) {
+            T* dst = &S.u.r.cst[tt & 1][0][l];
+            const T* src = P.stg + srow(P, L.pos, tt, 0);
+            for (int e = L.w; e < CST; e += NW) cp_async(dst + e * LW, src + e * LW);
+        }
         cp_async_commit();
     };
-    prefetch(n - 1);
+    // copy of stage tt's tape record into rec[tt & 1] (replay)
+    auto rec_copy = [&](int tt) {
+        if (tt >= 0 && tt < n) {
+            T* dst = &S.u.tp.rec[tt & 1][0][l];
+            const T* src = P.tape + trow(P, L.b, tt, 0);
+            for (int e = L.w; e < TREC; e += NW) cp_async(dst + e * LW, src + e * LW);
+        }
+        cp_async_commit();
+    };
+    if (o.replay) {
+        rec_copy(nmax - 1);
+    } else {
+        stage_copy(nmax - 1);
+        stage_copy(nmax - 2);
+        cp_async_wait_all();
+        __syncthreads();
+        tangent_step<T, NW>(P, S, L, nmax - 1, n, n > 0);
+        __syncthreads();
+    }
     for (int t = nmax - 1; t >= 0; --t) {
         const bool on = alive && t < n;
-        const bool dyn = on && t < n - 1;
-        bool go = on;
-        T* Fc = S.F[t & 1];
+        // the stage's factorization for the adjoint step: replayed or just formed
+        const T *Fp, *Kp, *Lp;
+        int amask;
+        bool ago;
         if (o.replay) {
-            wsync();
-            if (on) {
-                const T* rec = P.tape + ((size_t)I.b * P.N + t) * TAPE_STRIDE;
-                for (int e = L.l; e < TAPE_MASK; e += TPI) {
-                    const T val = rec[e];
-                    if (e < TAPE_K) {
-                        const int j = e / NX;
-                        Fc[j * LD + e - j * NX] = val;
-                    } else if (e < TAPE_L) {
-                        S.K[e - TAPE_K] = val;
-                    } else {
-                        S.L[e - TAPE_L] = val;
-                    }
-                }
-                if (L.l == 0) S.mask = (int)rec[TAPE_MASK];
-            }
-            wsync();
-        } else {
             cp_async_wait_all();
-            wsync();
-            if (on) {
-                const T* si = S.stg[t & 1] + KREC;
-                for (int a = L.l; a < NZ; a += TPI) {
-                    if (a < NX) {
-                        const T qa = si[SI_Q + a], ea = si[SI_X + a] - si[SI_R + a];
-                        S.Cd[a] = qa;
-                        S.c[a] = qa * (o.use_lo ? ea + si[SI_XL + a] : ea);
-                    } else {
-                        const T cd = S.R[a - NX], ua = si[SI_U + a - NX];
-                        S.Cd[a] = cd;
-                        S.c[a] = cd * (ua - S.uref[a - NX]);
-                        S.ut[a - NX] = ua;
-                    }
-                }
-                prefetch(t - 1);
-            }
-            wsync();
-            if (dyn) {
-                // Column products.  Item c < NGC is the computed column gcol(c),
-                // item c >= NGC the constant column tcol(c - NGC) (the costly
-                // items first, so that no lane takes two of them while others
-                // idle); its lane forms
-                //   W[:, j] = V F[:, j]            (in registers)
-                //   Q[r, j] = C_rj + F[:, r]' W[:, j] for every row r (rows of the
-                //             constant columns take one or two entries of W[:, j])
-                //   q[j]    = c_j + F[:, j]' v
-                // and, for a computed column, mirrors its entries in the constant
-                // rows into Q[j, r], so the upper triangle of Q is complete; the
-                // lanes of the u columns also fill Qxu.
-                for (int c = L.l; c < NZ; c += TPI) {
-                    const bool cc = c >= NGC;
-                    const int j = cc ? tcol(c - NGC) : gcol(c);
-                    T w[NX];
-                    T qj;
-                    if (cc) {
-#pragma unroll
-                        for (int i = 0; i < NX; ++i)
-                            w[i] = (j < 3) ? S.V[i * LD + j] : S.V[i * LD + j] + hv * S.V[i * LD + j - 7];
-                        qj = S.c[j] + ((j < 3) ? S.v[j] : S.v[j] + hv * S.v[j - 7]);
-                    } else {
-                        T f[NX];
-                        ld13(Fc + j * LD, f);
-#pragma unroll
-                        for (int i = 0; i < NX; ++i) {
-                            T vr[NX];
-                            ld13(S.V + i * LD, vr);
-                            T s = T(0);
-#pragma unroll
-                            for (int k = 0; k < NX; ++k) s += vr[k] * f[k];
-                            w[i] = s;
-                        }
-                        T vv[NX];
-                        ld13(S.v, vv);
-                        T s = S.c[j];
-#pragma unroll
-                        for (int k = 0; k < NX; ++k) s += f[k] * vv[k];
-                        qj = s;
-                    }
-                    S.q[j] = qj;
-#pragma unroll
-                    for (int r = 0; r < NZ; ++r) {
-                        const bool rc = r < 3 || (r >= 7 && r < 10);
-                        if (cc && !rc) continue;          // filled by the computed column's mirror
-                        T s = (r == j) ? S.Cd[j] : T(0);
-                        if (r < 3) {
-                            s += w[r];
-                        } else if (r >= 7 && r < 10) {
-                            s += w[r] + hv * w[r - 7];
-                        } else {
-                            T fr[NX];
-                            ld13(Fc + r * LD, fr);
-#pragma unroll
-                            for (int k = 0; k < NX; ++k) s += fr[k] * w[k];
-                        }
-                        S.Qm[r * NZ + j] = s;
-                        if (!cc && rc) S.Qm[j * NZ + r] = s;
-                        if (!cc && r < NX && j >= NX) S.Qxu[r * NU + j - NX] = s;
-                    }
-                }
-            } else if (on) {
-                for (int e = L.l; e < NZ * NZ; e += TPI) {
-                    const int a = e / NZ, bb = e - a * NZ;
-                    S.Qm[e] = (a == bb) ? S.Cd[a] : T(0);
-                }
-                for (int e = L.l; e < NX * NU; e += TPI) S.Qxu[e] = T(0);
-                for (int a = L.l; a < NZ; a += TPI) S.q[a] = S.c[a];
-            }
-            wsync();
-            if (on && L.l == 0) {
+            __syncthreads();
+            rec_copy(t - 1);
+            const T* R = &S.u.tp.rec[t & 1][0][l];
+            Fp = R + T_F * LW;
+            Kp = R + T_K * LW;
+            Lp = R + T_L * LW;
+            amask = on ? (int)R[T_M * LW] : 0;
+            ago = on;
+        } else {
+            // (A) products
+            products<T, NW>(P, S, L, t, o.use_lo);
+            cp_async_wait_all();
+            __syncthreads();
+            // (B) box QP of stage t (warp 0); tangent columns of F_{t-1}
+            if (L.w == 0) {
+                const T* cs = &S.u.r.cst[t & 1][0][l];
                 T H[4][4], g[4], lo[4], hi[4], d[4], Lf[NL];
                 int mask = 0;
 #pragma unroll
                 for (int a = 0; a < 4; ++a) {
 #pragma unroll
-                    for (int bb = 0; bb < 4; ++bb)
-                        H[a][bb] = a <= bb ? S.Qm[(NX + a) * NZ + NX + bb] : S.Qm[(NX + bb) * NZ + NX + a];
-                    g[a] = S.q[NX + a];
-                    const T ub = S.ut[a];
-                    lo[a] = S.ulo[a] - ub;
-                    hi[a] = S.uhi[a] - ub;
+                    for (int bb = 0; bb < 4; ++bb) H[a][bb] = S.u.r.Q[qidx(NX + a, NX + bb)][l];
+                    g[a] = S.u.r.q[NX + a][l];
+                    const T ub = cs[(R_U + a) * LW];
+                    lo[a] = S.ulo[a][l] - ub;
+                    hi[a] = S.uhi[a][l] - ub;
                 }
-                const bool ok = box_qp(H, g, lo, hi, d, Lf, mask);
+                const bool ok = box_qp(on, H, g, lo, hi, d, Lf, mask);
+                if (on) {
 #pragma unroll
-                for (int a = 0; a < 4; ++a) S.k[a] = d[a];
+                    for (int a = 0; a < 4; ++a) S.k[a][l] = d[a];
 #pragma unroll
-                for (int i = 0; i < NL; ++i) S.L[i] = Lf[i];
-                S.mask = mask;
-                S.ok = ok ? 1 : 0;
+                    for (int i = 0; i < NL; ++i) S.L[i][l] = Lf[i];
+                    S.mask[l] = mask;
+                    S.ok[l] = ok ? 1 : 0;
+                }
             }
-            wsync();
-            if (on && !S.ok) alive = false;
-            go = on && alive;
-            const int mask = S.mask;
+            tangent_step<T, NW>(P, S, L, t - 1, n, alive && n > 0);
+            __syncthreads();
+            if (on && !S.ok[l]) alive = false;
+            const bool go = on && alive;
+            // (C) K_t, V_t, v_t
+            stage_copy(t - 2);
             if (go) {
-                // Column c of K_t (to shared memory and the slot scratch), then,
-                // from it in registers, the upper part of column c of
-                //   V_t = Q_xx + Q_xu K_t   (mirrored: V_t is stored in full)
-                // and v_t[c] = q_x[c] + Q_xu[c, :] k_t.
-                T* kr = I.Kr + (size_t)t * KREC;
-                for (int c = L.l; c < NX; c += TPI) {
-                    T qc[4], rhs[4], y[4], kc[4];
-                    ld4(S.Qxu + c * NU, qc);
+                // every operand first (factor, k_t, Q_xu, and for each of this
+                // warp's columns c its column of Q_xx and row of Q_xu), then the
+                // columns' solves and updates side by side
+                constexpr int NK = Split<NW>::NK;
+                T Lf[NL], kk[NU], qxu[NX][NU], qxx[NK][NX], qc[NK][NU], qv[NK];
+                int cs_[NK];
+                const int mask = S.mask[l];
 #pragma unroll
-                    for (int a = 0; a < 4; ++a) rhs[a] = ((mask >> a) & 1) ? qc[a] : T(0);
-                    chol_solve4(S.L, rhs, y);
+                for (int i = 0; i < NL; ++i) Lf[i] = S.L[i][l];
 #pragma unroll
-                    for (int a = 0; a < 4; ++a) {
-                        kc[a] = ((mask >> a) & 1) ? -y[a] : T(0);
-                        S.K[a * NX + c] = kc[a];
-                        kr[a * NX + c] = kc[a];
-                    }
+                for (int a = 0; a < NU; ++a) kk[a] = S.k[a][l];
 #pragma unroll
-                    for (int i = 0; i < NX; ++i) {
-                        if (i > c) break;
-                        T qi[4];
-                        ld4(S.Qxu + i * NU, qi);
-                        T s = S.Qm[i * NZ + c];
+                for (int i = 0; i < NX; ++i)
 #pragma unroll
-                        for (int a = 0; a < NU; ++a) s += qi[a] * kc[a];
-                        S.V[i * LD + c] = s;
-                        S.V[c * LD + i] = s;
-                    }
-                    T s = S.q[c];
+                    for (int a = 0; a < NU; ++a) qxu[i][a] = S.u.r.Q[qidx(i, NX + a)][l];
 #pragma unroll
-                    for (int a = 0; a < NU; ++a) s += qc[a] * S.k[a];
-                    S.v[c] = s;
+                for (int s = 0; s < NK; ++s) {
+                    const int c = Split<NW>::kcol(L.w, s);
+                    cs_[s] = c;
+                    const int cc = c < 0 ? 0 : c;
+#pragma unroll
+                    for (int i = 0; i < NX; ++i) qxx[s][i] = S.u.r.Q[qidx(i, cc)][l];
+#pragma unroll
+                    for (int a = 0; a < NU; ++a) qc[s][a] = S.u.r.Q[qidx(cc, NX + a)][l];
+                    qv[s] = S.u.r.q[cc][l];
                 }
-                if (L.l == 0) {
+                T* grow = P.stg + srow(P, L.pos, t, 0);
+                // the columns' solves side by side (no branch between them)
+                T kc[NK][NU];
 #pragma unroll
-                    for (int a = 0; a < NU; ++a) kr[NU * NX + a] = S.k[a];
-                }
-            }
-            if (o.tape) {
-                wsync();
-                if (go) {
-                    T* rec = o.tape + ((size_t)I.b * P.N + t) * TAPE_STRIDE;
-                    for (int e = L.l; e < TAPE_STRIDE; e += TPI) {
-                        T val;
-                        if (e < TAPE_K) {
-                            const int j = e / NX;
-                            val = dyn ? Fc[j * LD + e - j * NX] : T(0);
-                        } else if (e < TAPE_L) {
-                            val = S.K[e - TAPE_K];
-                        } else if (e < TAPE_MASK) {
-                            val = S.L[e - TAPE_L];
-                        } else {
-                            val = T(mask);
-                        }
-                        rec[e] = val;
-                    }
-                }
-            }
-        }
-        if (o.adj) {
-            const AdjArgs<T>* adj = o.adj;
-            wsync();
-            if (go) {
-                for (int a = L.l; a < NZ; a += TPI) {
-                    T g;
-                    if (a < NX) g = adj->gx ? adj->gx[((size_t)I.b * P.N + t) * NX + a] : T(0);
-                    else g = adj->gu[((size_t)I.b * P.N + t) * NU + a - NX];
-                    if (dyn) {
-#pragma unroll
-                        for (int k = 0; k < NX; ++k) g += Fc[a * LD + k] * S.vh[k];
-                    }
-                    S.qh[a] = g;
-                }
-            }
-            wsync();
-            if (go) {
-                const int mask = S.mask;
-                for (int i = L.l; i < NX; i += TPI) {
-                    T s = S.qh[i];
-#pragma unroll
-                    for (int a = 0; a < NU; ++a) s += S.K[a * NX + i] * S.qh[NX + a];
-                    S.vh[i] = s;
-                }
-                if (L.l == TPI - 1) {
+                for (int s = 0; s < NK; ++s) {
                     T rhs[4], y[4];
 #pragma unroll
-                    for (int a = 0; a < 4; ++a) rhs[a] = ((mask >> a) & 1) ? S.qh[NX + a] : T(0);
-                    chol_solve4(S.L, rhs, y);
+                    for (int a = 0; a < 4; ++a) rhs[a] = ((mask >> a) & 1) ? qc[s][a] : T(0);
+                    chol_solve4(Lf, rhs, y);
 #pragma unroll
-                    for (int a = 0; a < 4; ++a) I.kh[t * NU + a] = ((mask >> a) & 1) ? -y[a] : T(0);
+                    for (int a = 0; a < 4; ++a) kc[s][a] = ((mask >> a) & 1) ? -y[a] : T(0);
+                }
+#pragma unroll
+                for (int s = 0; s < NK; ++s) {
+                    const int c = cs_[s];
+                    const bool has = c >= 0;
+                    const int cc = has ? c : 0;
+                    T vcol[NX];
+#pragma unroll
+                    for (int i = 0; i < NX; ++i) {
+                        T s2 = qxx[s][i];
+#pragma unroll
+                        for (int a = 0; a < NU; ++a) s2 += qxu[i][a] * kc[s][a];
+                        vcol[i] = s2;
+                    }
+                    T s3 = qv[s];
+#pragma unroll
+                    for (int a = 0; a < NU; ++a) s3 += qc[s][a] * kk[a];
+                    if (has) {
+#pragma unroll
+                        for (int a = 0; a < 4; ++a) {
+                            S.K[a * NX + cc][l] = kc[s][a];
+                            grow[(R_K + a * NX + cc) * LW] = kc[s][a];
+                        }
+#pragma unroll
+                        for (int i = 0; i < NX; ++i)
+                            if (i <= cc) S.V[vidx(i, cc)][l] = vcol[i];
+                        S.v[cc][l] = s3;
+                    }
+                }
+                if (L.w == 0) {
+#pragma unroll
+                    for (int a = 0; a < NU; ++a) grow[(R_KK + a) * LW] = kk[a];
                 }
             }
+            __syncthreads();
+            if (o.tape && go) {
+                const int mask = S.mask[l];
+                for (int e = L.w; e < TREC; e += NW) {
+                    T val;
+                    if (e < T_K) val = S.u.r.F[t & 1][e][l];
+                    else if (e < T_L) val = S.K[e - T_K][l];
+                    else if (e < T_M) val = S.L[e - T_L][l];
+                    else val = T(mask);
+                    o.tape[trow(P, L.b, t, e)] = val;
+                }
+            }
+            Fp = &S.u.r.F[t & 1][0][l];
+            Kp = &S.K[0][l];
+            Lp = &S.L[0][l];
+            amask = S.mask[l];
+            ago = go;
         }
-        wsync();
+        if (o.adj) adjoint_step<T, NW>(P, S, L, t, ago, *o.adj, Fp, Kp, Lp, amask);
     }
     return alive;
 }
 
 // ------------------------------------------------- A4 line search ----------
-// Sec. IV-3: each alpha rolled out on its own lane of the group,
+// Sec. IV-3: warp c rolls out candidate alpha_c for every instance of the pack,
 //   u_hat_t = clamp(u_t + alpha k_t + K_t (x_hat_t - x_t)),  x_hat_{t+1} = RK4.
 // The candidates are compared through their cost change with respect to the
 // nominal, accumulated stage by stage from the differences themselves,
@@ -973,210 +1227,202 @@ __device__ bool riccati(const Params<T>& P, const Inst<T>& I, WarpSmem<T>& S, co
 // which equals J(alpha) - J exactly for the quadratic cost but does not cancel
 // against J's magnitude; with the hi + lo states it resolves differences far
 // below the working precision of J.  alpha* = first argmin, and the best
-// candidate becomes the next nominal (Sec. IV-3).  Each stage's gains, nominal
-// and cost rows are copied into shared memory by all lanes of the group
-// (asynchronous copies) one stage ahead.  Returns 0 (step taken: du, J
-// updated) or 1 (no candidate with a finite cost: nominal kept).
-// Stage t's staged record: K_t, k_t (KREC), then the stage inputs (SIN).
-template <typename T, int TPI>
-__device__ int line_search(const Params<T>& P, const Inst<T>& I, WarpSmem<T>& S, const Lanes<TPI>& L, bool act,
-                           T& Jnom, T& du_out) {
-    static_assert(TPI >= 4, "line search needs 4 candidate lanes");
-    const int n = act ? I.n : 0;
-    const int nmax = warp_max(n);
+// candidate becomes the next nominal (Sec. IV-3).  Each stage's gains,
+// nominal and cost rows are copied into shared memory by all warps one stage
+// ahead.  Returns 0 (step taken: du, J updated) or 1 (no candidate with a
+// finite cost: nominal kept).
+template <typename T, int NW>
+__device__ int line_search(const Params<T>& P, BlockSmem<T>& S, const Lane& L, int n, T& Jnom, T& du_out) {
+    const int l = L.l;
+    const int nmax = __reduce_max_sync(FULL, n);
+    const bool cl = n > 0 && L.w < P.n_alpha;
+    const T alpha = L.w == 0 ? P.alpha[0] : (L.w == 1 ? P.alpha[1] : (L.w == 2 ? P.alpha[2] : P.alpha[3]));
     auto issue = [&](int tt) {
-        if (tt >= n) return;
-        T* dst = S.stg[tt & 1];
-        const T* kr = I.Kr + (size_t)tt * KREC;
-        constexpr int PER = 16 / sizeof(T), NCH = KREC / PER;
-        for (int e = L.l; e < NCH; e += TPI) cp_async16(dst + e * PER, kr + e * PER);
-        stage_inputs_async(P, I, L, tt, dst + KREC);
+        if (tt < n) {
+            T* dst = &S.u.s.stg[tt & 1][0][l];
+            const T* src = P.stg + srow(P, L.pos, tt, 0);
+            for (int e = L.w; e < SREC; e += NW) cp_async(dst + e * LW, src + e * LW);
+        }
         cp_async_commit();
     };
     issue(0);
     cp_async_wait_all();
-    wsync();
-    const bool cl = act && L.l < P.n_alpha;
-    const T alpha = cl ? P.alpha[L.l] : T(0);
-    T xh[NX], xl[NX], uh[NU];
+    __syncthreads();
+    T xh[NX], xl[NX], R[NU], ur[NU], ulo[NU], uhi[NU];
 #pragma unroll
-    for (int i = 0; i < NX; ++i) { xh[i] = act ? S.x0[i] : T(0); xl[i] = T(0); }
-    T dJ = T(0), dJl = T(0);
-    T* cd = I.cand + (size_t)(L.l & 3) * P.N_ws * CREC;
+    for (int i = 0; i < NX; ++i) { xh[i] = S.x0[i][l]; xl[i] = T(0); }
+#pragma unroll
+    for (int a = 0; a < NU; ++a) { R[a] = S.R[a][l]; ur[a] = S.uref[a][l]; ulo[a] = S.ulo[a][l]; uhi[a] = S.uhi[a][l]; }
+    T dJ = T(0), dJl = T(0), dmx = T(0);
+    const int c = L.w & 3;
     for (int t = 0; t < nmax; ++t) {
         issue(t + 1);
         if (cl && t < n) {
-            const T* sb = S.stg[t & 1];
-            const T* kr = sb;
-            const T* xbt = sb + KREC + SI_X;
-            const T* xlt = sb + KREC + SI_XL;
-            const T* ubt = sb + KREC + SI_U;
-            const T* Qt = sb + KREC + SI_Q;
-            const T* xr = sb + KREC + SI_R;
-            T dxv[NX];
+            const T* sb = &S.u.s.stg[t & 1][0][l];
+            T dxv[NX], uh[NU];
 #pragma unroll
-            for (int i = 0; i < NX; ++i) dxv[i] = (xh[i] - xbt[i]) + (xl[i] - xlt[i]);
+            for (int i = 0; i < NX; ++i) dxv[i] = (xh[i] - sb[(R_X + i) * LW]) + (xl[i] - sb[(R_XL + i) * LW]);
             T sx = T(0), su = T(0);
 #pragma unroll
             for (int a = 0; a < NU; ++a) {
                 T s = T(0);
 #pragma unroll
-                for (int i = 0; i < NX; ++i) s += kr[a * NX + i] * dxv[i];
-                const T ub = ubt[a];
-                const T un = ub + alpha * kr[NU * NX + a] + s;
-                uh[a] = clampT(un, S.ulo[a], S.uhi[a]);
+                for (int i = 0; i < NX; ++i) s += sb[(R_K + a * NX + i) * LW] * dxv[i];
+                const T ub = sb[(R_U + a) * LW];
+                const T un = ub + alpha * sb[(R_KK + a) * LW] + s;
+                uh[a] = clampT(un, ulo[a], uhi[a]);
                 const T d = uh[a] - ub;
-                su += d * (S.R[a] * ((ub - S.uref[a]) + T(0.5) * d));
+                su += d * (R[a] * ((ub - ur[a]) + T(0.5) * d));
+                const T ad = fabs(d);
+                dmx = ad > dmx ? ad : dmx;
             }
 #pragma unroll
             for (int i = 0; i < NX; ++i) {
-                const T eb = (xbt[i] - xr[i]) + xlt[i];
-                sx += dxv[i] * (Qt[i] * (eb + T(0.5) * dxv[i]));
+                const T eb = (sb[(R_X + i) * LW] - sb[(R_XR + i) * LW]) + sb[(R_XL + i) * LW];
+                sx += dxv[i] * (sb[(R_Q + i) * LW] * (eb + T(0.5) * dxv[i]));
             }
             acc2(dJ, dJl, sx + su);
+            T* cr = P.cand + crow(P, c, L.pos, t, 0);
 #pragma unroll
-            for (int i = 0; i < NX; ++i) { cd[t * CREC + i] = xh[i]; cd[t * CREC + NX + i] = xl[i]; }
+            for (int i = 0; i < NX; ++i) {
+                cr[i * LW] = xh[i];
+                cr[(NX + i) * LW] = xl[i];
+            }
 #pragma unroll
-            for (int a = 0; a < NU; ++a) cd[t * CREC + 2 * NX + a] = uh[a];
+            for (int a = 0; a < NU; ++a) cr[(2 * NX + a) * LW] = uh[a];
             if (t < n - 1) rk4_step2(P.mdl, xh, xl, uh);
         }
         cp_async_wait_all();
-        wsync();
+        __syncthreads();
     }
     if (cl) {
         dJ = dJ + dJl;
-        S.Jc[L.l] = finiteT(dJ) ? dJ : T(INFINITY);
+        S.Jc[L.w][l] = finiteT(dJ) ? dJ : T(INFINITY);
+        S.dmax[L.w][l] = dmx;
     }
-    wsync();
+    __syncthreads();
     int r = 0;
-    T dmax = T(0), Jb = T(0);
-    if (act) {
+    if (n > 0) {
         int best = 0;
-        Jb = S.Jc[0];
-        for (int c = 1; c < P.n_alpha; ++c)
-            if (S.Jc[c] < Jb) { Jb = S.Jc[c]; best = c; }
+        T Jb = S.Jc[0][l];
+        for (int k = 1; k < P.n_alpha; ++k)
+            if (S.Jc[k][l] < Jb) { Jb = S.Jc[k][l]; best = k; }
         if (!finiteT(Jb)) {
             r = 1;
         } else {
-            const T* cb = I.cand + (size_t)best * P.N_ws * CREC;
-            for (int e = L.l; e < n * CREC; e += TPI) {
-                const int t = e / CREC, j = e - t * CREC;
-                const T val = cb[e];
-                if (j < NX) {
-                    I.xb[t * NX + j] = val;
-                } else if (j < 2 * NX) {
-                    I.xlo[t * NX + j - NX] = val;
-                } else {
-                    T* up = I.ub + t * NU + (j - 2 * NX);
-                    const T d = fabs(val - *up);
-                    dmax = d > dmax ? d : dmax;
-                    *up = val;
-                }
+            // the best candidate becomes the nominal: all of a stage's loads, then its stores
+            for (int t = L.w; t < n; t += NW) {
+                const T* cr = P.cand + crow(P, best, L.pos, t, 0);
+                T* dr = P.stg + srow(P, L.pos, t, R_X);
+                T buf[CREC];
+#pragma unroll
+                for (int e = 0; e < CREC; ++e) buf[e] = cr[e * LW];
+#pragma unroll
+                for (int e = 0; e < CREC; ++e) dr[e * LW] = buf[e];
             }
+            Jnom = Jnom + Jb;
+            du_out = S.dmax[best][l];
         }
     }
-#pragma unroll
-    for (int o = TPI / 2; o > 0; o >>= 1) {
-        const T other = __shfl_xor_sync(FULL, dmax, o);
-        dmax = other > dmax ? other : dmax;
-    }
-    wsync();
-    if (act && r == 0) {
-        Jnom = Jnom + Jb;
-        du_out = dmax;
-    }
+    __syncthreads();
     return r;
 }
 
 // ---------------------------------------------- A8 adjoint forward sweep ----
-// dx_0 = 0; du_t = K_t dx_t + kh_t; dx_{t+1} = F_t [dx_t; du_t]; with
-// d_tau_t = [dx_t; du_t]:  dQ_t = dx_t * (x*_t - x_ref,t),  dx_ref,t = -Q_t * dx_t,
-// dx0 = vh_0 (value gradient of the adjoint LQR).  Fsrc / Ksrc: per-stage F_t
-// and K_t with strides fs / ks: tape records (full F_t) or slot scratch (its
-// 11 computed columns, fcompact).
-template <typename T, int TPI>
-__device__ void adjoint_forward(const Params<T>& P, const Inst<T>& I, WarpSmem<T>& S, const Lanes<TPI>& L,
-                                bool act, const T* Fsrc, size_t fs, bool fcompact, const T* Ksrc, size_t ks,
+// dx_0 = 0; du_t = K_t dx_t + kh_t; dx_{t+1} = F_t [dx_t; du_t], formed as the
+// directional derivative of the RK4 step at (x*_t, u*_t) (one forward tangent
+// instead of 17 columns); with d_tau_t = [dx_t; du_t]:
+//   dQ_t = dx_t * (x*_t - x_ref,t),  dx_ref,t = -Q_t * dx_t,  dx0 = vh_0.
+// Warp 0, one instance per lane.  K_t comes from the tape (store-all) or the
+// gain records the re-factorization wrote (recompute).
+template <typename T, int NW>
+__device__ void adjoint_forward(const Params<T>& P, const BlockSmem<T>& S, const Lane& L, int n,
                                 const AdjArgs<T>& A) {
-    const int n = act ? I.n : 0;
-    const int nmax = warp_max(n);
-    const size_t b = I.b;
-    constexpr int RX = (NX + TPI - 1) / TPI;
-    if (act) {
-        for (int i = L.l; i < NX; i += TPI) { S.dx[i] = T(0); S.dQacc[i] = T(0); A.dx0[b * NX + i] = S.vh[i]; }
-    }
-    wsync();
-    for (int t = 0; t < nmax; ++t) {
-        const bool on = t < n;
-        if (on) {
-            const T* Kt = Ksrc + (size_t)t * ks;
-            for (int a = L.l; a < NU; a += TPI) {
-                T s = I.kh[t * NU + a];
+    if (L.w != 0 || n <= 0) return;
+    const size_t b = L.b;
+    T dx[NX], dq[NX];
 #pragma unroll
-                for (int i = 0; i < NX; ++i) s += Kt[a * NX + i] * S.dx[i];
-                S.du[a] = s;
-            }
-            const T* Qt = Qrow(P, I, t);
-            for (int i = L.l; i < NX; i += TPI) {
-                const T dxi = S.dx[i];
-                const T e = I.xb[t * NX + i] - I.xrefb[t * NX + i];
-                if (P.Nq > 1) A.dQ[(b * P.Nq + t) * NX + i] = dxi * e;
-                else S.dQacc[i] += dxi * e;
-                A.dxref[(b * P.N + t) * NX + i] = -Qt[i] * dxi;
-            }
+    for (int i = 0; i < NX; ++i) { dx[i] = T(0); dq[i] = T(0); A.dx0[b * NX + i] = S.vh[i][L.l]; }
+    for (int t = 0; t < n; ++t) {
+        // the stage's operands first
+        const T* kr = A.recompute ? P.stg + srow(P, L.pos, t, R_K) : P.tape + trow(P, L.b, t, T_K);
+        const T* xs = P.x + (b * P.N + t) * NX;
+        const T* xr = P.xref + (b * P.N + t) * NX;
+        const T* Qt = Qrow(P, L.b, t);
+        T K[NU * NX], kh[NU], xv[NX], xrv[NX], qv[NX], us[NU];
+#pragma unroll
+        for (int e = 0; e < NU * NX; ++e) K[e] = kr[e * LW];
+#pragma unroll
+        for (int a = 0; a < NU; ++a) {
+            kh[a] = P.kh[khrow(P, L.pos, t, a)];
+            us[a] = P.u[(b * P.N + t) * NU + a];
         }
-        wsync();
-        T snew[RX];
-        if (on && t < n - 1) {
-            // dx_{t+1} = F_t [dx_t; du_t]: the 11 computed columns, then the
-            // constant p and v columns
-            const T* Ft = Fsrc + (size_t)t * fs;
 #pragma unroll
-            for (int r = 0; r < RX; ++r) {
-                const int i = L.l + r * TPI;
-                if (i < NX) {
-                    T s = T(0);
+        for (int i = 0; i < NX; ++i) { xv[i] = xs[i]; xrv[i] = xr[i]; qv[i] = Qt[i]; }
+        T du[NU];
 #pragma unroll
-                    for (int jj = 0; jj < NGC; ++jj) {
-                        const int j = gcol(jj);
-                        s += Ft[(fcompact ? jj : j) * NX + i] * (j < NX ? S.dx[j] : S.du[j - NX]);
-                    }
-                    if (i < 3) s += S.dx[i] + hv_coef(P.mdl) * S.dx[i + 7];
-                    else if (i >= 7 && i < 10) s += S.dx[i];
-                    snew[r] = s;
-                }
-            }
+        for (int a = 0; a < NU; ++a) {
+            T s = kh[a];
+#pragma unroll
+            for (int i = 0; i < NX; ++i) s += K[a * NX + i] * dx[i];
+            du[a] = s;
         }
-        wsync();
-        if (on && t < n - 1) {
 #pragma unroll
-            for (int r = 0; r < RX; ++r) {
-                const int i = L.l + r * TPI;
-                if (i < NX) S.dx[i] = snew[r];
-            }
+        for (int i = 0; i < NX; ++i) {
+            const T e = xv[i] - xrv[i];
+            if (P.Nq > 1) A.dQ[(b * P.Nq + t) * NX + i] = dx[i] * e;
+            else dq[i] += dx[i] * e;
+            A.dxref[(b * P.N + t) * NX + i] = -qv[i] * dx[i];
         }
-        wsync();
-    }
-    if (act) {
-        // zero the stages past the horizon, write the shared-Q sum
-        for (int e = n * NX + L.l; e < P.N * NX; e += TPI) A.dxref[b * P.N * NX + e] = T(0);
-        if (P.Nq > 1) {
-            for (int e = n * NX + L.l; e < P.Nq * NX; e += TPI) A.dQ[b * P.Nq * NX + e] = T(0);
-        } else {
-            for (int i = L.l; i < NX; i += TPI) A.dQ[b * NX + i] = S.dQacc[i];
+        if (t < n - 1) {
+            T sp[32], nx[NX];
+            rk4_stage_points(P.mdl, xv, us, sp);
+            rk4_tangent(P.mdl, sp, dx, du, nx);
+#pragma unroll
+            for (int i = 0; i < NX; ++i) dx[i] = nx[i];
         }
     }
-    wsync();
+    for (int e = n * NX; e < P.N * NX; ++e) A.dxref[b * P.N * NX + e] = T(0);
+    if (P.Nq > 1) {
+        for (int e = n * NX; e < P.Nq * NX; ++e) A.dQ[b * P.Nq * NX + e] = T(0);
+    } else {
+#pragma unroll
+        for (int i = 0; i < NX; ++i) A.dQ[b * NX + i] = dq[i];
+    }
 }
 
-template <typename T, int TPI>
-__device__ void zero_grads(const Params<T>& P, const AdjArgs<T>& A, int b, const Lanes<TPI>& L, bool act) {
-    if (act) {
-        for (int e = L.l; e < P.Nq * NX; e += TPI) A.dQ[(size_t)b * P.Nq * NX + e] = T(0);
-        for (int e = L.l; e < P.N * NX; e += TPI) A.dxref[(size_t)b * P.N * NX + e] = T(0);
-        for (int i = L.l; i < NX; i += TPI) A.dx0[(size_t)b * NX + i] = T(0);
+template <typename T, int NW>
+__device__ void zero_grads(const Params<T>& P, const AdjArgs<T>& A, const Lane& L, bool act) {
+    if (!act) return;
+    const size_t b = L.b;
+    for (int e = L.w; e < P.Nq * NX; e += NW) A.dQ[b * P.Nq * NX + e] = T(0);
+    for (int e = L.w; e < P.N * NX; e += NW) A.dxref[b * P.N * NX + e] = T(0);
+    for (int i = L.w; i < NX; i += NW) A.dx0[b * NX + i] = T(0);
+}
+
+// A7: the nominal trajectory into the caller's u*, x* (zero past the horizon).
+template <typename T, int NW>
+__device__ void write_solution(const Params<T>& P, const Lane& L, int n) {
+    if (!L.valid) return;
+    const size_t b = L.b;
+    for (int t = L.w; t < P.N; t += NW) {
+        T* xo = P.x + (b * P.N + t) * NX;
+        T* uo = P.u + (b * P.N + t) * NU;
+        T buf[NX + NU];
+#pragma unroll
+        for (int e = 0; e < NX + NU; ++e) buf[e] = T(0);
+        if (t < n) {
+            const T* sr = P.stg + srow(P, L.pos, t, 0);
+#pragma unroll
+            for (int i = 0; i < NX; ++i) buf[i] = sr[(R_X + i) * LW];
+#pragma unroll
+            for (int a = 0; a < NU; ++a) buf[NX + a] = sr[(R_U + a) * LW];
+        }
+#pragma unroll
+        for (int i = 0; i < NX; ++i) xo[i] = buf[i];
+#pragma unroll
+        for (int a = 0; a < NU; ++a) uo[a] = buf[NX + a];
     }
-    wsync();
 }
 
 }  // namespace camp

@@ -32,24 +32,21 @@ using namespace camp;
 
 namespace {
 
-constexpr int NA_TPI = 16, NA_IPB = 8;                      // the handle's default launch shape
-constexpr int NA_SLOTS = MPC_NOALLOC_B_MAX + NA_IPB;        // warp slots the grid can use
-constexpr size_t NA_STAGES = (size_t)NA_SLOTS * MPC_NOALLOC_N_MAX;
+constexpr int NA_TPI = 4;                                   // the handle's default threads per instance
+constexpr size_t NA_SLOTS = MPC_NOALLOC_B_MAX;
 
 constexpr size_t a256(size_t floats) { return (floats + 63) & ~(size_t)63; }   // 64 floats = 256 bytes
-constexpr size_t OFF_F = 0;
-constexpr size_t OFF_K = OFF_F + a256(NA_STAGES * NFC);
-constexpr size_t OFF_C = OFF_K + a256(NA_STAGES * KREC);
-constexpr size_t OFF_P = OFF_C + a256(NA_STAGES * 4 * CREC);
-constexpr size_t OFF_H = OFF_P + a256(NA_STAGES * SP_STRIDE);
-constexpr size_t OFF_X = OFF_H + a256(NA_STAGES * NU);
-constexpr size_t OFF_Q = OFF_X + a256(NA_STAGES * NX);      // 2 ints: work-queue tickets
-constexpr size_t OFF_O = OFF_Q + 64;                         // order: MPC_NOALLOC_B_MAX ints
+constexpr size_t NA_GROUPS = (NA_SLOTS + 31) / 32;
+constexpr size_t OFF_S = 0;                                                          // per-stage records
+constexpr size_t OFF_C = OFF_S + a256(NA_GROUPS * 32 * MPC_NOALLOC_N_MAX * SREC);    // line-search candidates
+constexpr size_t OFF_H = OFF_C + a256(4 * NA_GROUPS * 32 * MPC_NOALLOC_N_MAX * CREC);
+constexpr size_t OFF_Q = OFF_H + a256(NA_GROUPS * 32 * MPC_NOALLOC_N_MAX * NU);      // 2 ints: work-queue tickets
+constexpr size_t OFF_O = OFF_Q + 64;                                                 // order: MPC_NOALLOC_B_MAX ints
 constexpr size_t NA_FLOATS = OFF_O + a256(MPC_NOALLOC_B_MAX);
 
 }  // namespace
 
-// The scratch array (3,886,400 floats, 15.5 MB).  In host code this name is only a host-side
+// The scratch array (2,416,960 floats, 9.7 MB).  In host code this name is only a host-side
 // stand-in: kernels get the device address looked up below.
 static __device__ __align__(256) float g_noalloc_scratch[NA_FLOATS];
 
@@ -108,7 +105,7 @@ extern "C" int mpc_solve_fwd_noalloc(const mpc_config* cfg, const mpc_problem* p
     if (!p->x0 || !p->Q || !p->x_ref || !p->R || !p->u_ref || !p->u_lo || !p->u_hi) return MPC_ERR_ARG;
     if (!s->u || !s->x || !s->cost || !s->iters || !s->status) return MPC_ERR_ARG;
     const bool store_all = cfg->store_mode == MPC_STORE_ALL;
-    if (store_all && (!s->tape || s->tape_bytes < (size_t)p->B * p->N * TAPE_STRIDE * sizeof(float)))
+    if (store_all && (!s->tape || s->tape_bytes < tape_elems(p->B, p->N) * sizeof(float)))
         return MPC_ERR_ARG;
 
     int dev = 0;
@@ -119,23 +116,7 @@ extern "C" int mpc_solve_fwd_noalloc(const mpc_config* cfg, const mpc_problem* p
 
     Params<float> P;
     memset(&P, 0, sizeof(P));
-    Model<float>& m = P.mdl;
-    m.h = (float)cfg->dt;
-    m.inv_m = (float)(1.0 / cfg->mass);
-    m.g = (float)cfg->gravity;
-    m.Jx = (float)cfg->inertia[0];
-    m.Jy = (float)cfg->inertia[1];
-    m.Jz = (float)cfg->inertia[2];
-    m.iJx = (float)(1.0 / cfg->inertia[0]);
-    m.iJy = (float)(1.0 / cfg->inertia[1]);
-    m.iJz = (float)(1.0 / cfg->inertia[2]);
-    const double d = cfg->arm / sqrt(2.0);
-    const double rx[4] = {d, -d, d, -d}, ry[4] = {-d, d, d, -d}, sp[4] = {1, 1, -1, -1};
-    for (int i = 0; i < 4; ++i) {
-        m.M[0][i] = (float)ry[i];
-        m.M[1][i] = (float)(-rx[i]);
-        m.M[2][i] = (float)(cfg->kappa_yaw * sp[i]);
-    }
+    fill_model(P.mdl, cfg->dt, cfg->mass, cfg->inertia, cfg->arm, cfg->kappa_yaw, cfg->gravity);
     P.B = p->B;
     P.N = p->N;
     P.Nq = p->Nq;
@@ -160,19 +141,20 @@ extern "C" int mpc_solve_fwd_noalloc(const mpc_config* cfg, const mpc_problem* p
     P.iters = s->iters;
     P.status = s->status;
     P.tape = store_all ? (float*)s->tape : nullptr;
-    P.wsF = ws + OFF_F;
-    P.wsK = ws + OFF_K;
-    P.wsCand = ws + OFF_C;
-    P.wsSP = ws + OFF_P;
-    P.wsKh = ws + OFF_H;
-    P.wsXlo = ws + OFF_X;
+    P.stg = ws + OFF_S;
+    P.cand = ws + OFF_C;
+    P.kh = ws + OFF_H;
     P.queue = (int*)(ws + OFF_Q);
     int* order = (int*)(ws + OFF_O);
 
-    int bps = persistent_blocks_per_sm<float>(NA_TPI, NA_IPB);
+    // one block of up to 32 instances per SM
+    int ipb = (p->B + sms - 1) / sms;
+    ipb = ipb < 1 ? 1 : (ipb > 32 ? 32 : ipb);
+    P.ipb = ipb;
+    int bps = persistent_blocks_per_sm<float>(NA_TPI);
     long long grid = (long long)(bps > 0 ? bps : 1) * sms;
-    const long long need = (p->B + NA_IPB - 1) / NA_IPB;
+    const long long need = (p->B + ipb - 1) / ipb;
     if (grid > need) grid = need;
-    const cudaError_t e = launch_forward<float>(P, MPC_EXEC_PERSISTENT, NA_TPI, NA_IPB, (int)grid, order, stream);
+    const cudaError_t e = launch_forward<float>(P, MPC_EXEC_PERSISTENT, NA_TPI, (int)grid, order, stream);
     return e == cudaSuccess ? MPC_OK : MPC_ERR_CUDA;
 }

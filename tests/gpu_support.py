@@ -39,6 +39,24 @@ LS_MARGIN32, QP_MARGIN32 = 1e-5, 1e-5
 TIE64 = 1e-9
 
 
+# Tape layout (opaque to callers, read here only to compare free sets): per
+# group of 32 instances and per stage, 210 rows of 32 values -- the computed
+# columns of F_t (143), K_t (52), the masked factor (14), the free mask (1).
+TAPE_REC, TAPE_MASK_ROW = 210, 209
+
+
+def tape_rows(tape, B, N, row):
+    """Row `row` of every instance's tape record, as a [B, N] tensor."""
+    G = (B + 31) // 32
+    return tape[: G * N * TAPE_REC * 32].view(G, N, TAPE_REC, 32)[:, :, row, :].permute(0, 2, 1).reshape(G * 32, N)[:B]
+
+
+def tape_records(tape, B, N):
+    """Every instance's tape records as a [B, N, 210] tensor."""
+    G = (B + 31) // 32
+    return tape[: G * N * TAPE_REC * 32].view(G, N, TAPE_REC, 32).permute(0, 3, 1, 2).reshape(G * 32, N, TAPE_REC)[:B]
+
+
 def run_gpu(prob, dtype, max_iter, tol, grad_u=None, grad_x=None, store_mode="store_all",
             exec_mode="persistent", ipb=0, N_max=None, B_max=None, solver=None, tpi=0):
     import torch
@@ -53,7 +71,7 @@ def run_gpu(prob, dtype, max_iter, tol, grad_u=None, grad_x=None, store_mode="st
     s = solver.solve(p)
     out = dict(u=s.u, x=s.x, cost=s.cost, iters=s.iters, status=s.status)
     if s.tape is not None:
-        out["masks"] = s.tape.view(B, N, 288)[:, :, 287].to(torch.int32)
+        out["masks"] = tape_rows(s.tape, B, N, TAPE_MASK_ROW).to(torch.int32)
     if grad_u is not None:
         gu = torch.as_tensor(grad_u, dtype=dtype, device="cuda")
         gx = None if grad_x is None else torch.as_tensor(grad_x, dtype=dtype, device="cuda")

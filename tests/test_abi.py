@@ -37,7 +37,7 @@ def test_config_validation_without_gpu(lib):
     assert (cfg.nx, cfg.nu, cfg.N_max, cfg.max_iter) == (13, 4, 40, 8)
     assert list(cfg.alpha) == [1.0, 0.5, 0.25, 0.1]
     for field, bad in (("nx", 12), ("N_max", 0), ("N_max", 65), ("B_max", 0), ("dtype", 7), ("max_iter", -1),
-                       ("n_alpha", 5), ("store_mode", 3), ("exec_mode", 9), ("tpi", 12), ("ipb", 3)):
+                       ("n_alpha", 5), ("store_mode", 3), ("exec_mode", 9), ("tpi", 12), ("tpi", 16), ("ipb", 33), ("ipb", -1)):
         c = lib.mpc_config_default()
         setattr(c, field, bad)
         code, h = lib.mpc_create(c)
@@ -49,7 +49,7 @@ def test_config_validation_without_gpu(lib):
     c = lib.mpc_config_default()
     c.alpha[1] = 1.5
     assert lib.mpc_create(c)[0] == lib.MPC_ERR_ARG
-    for tpi, ipb in ((8, 2), (32, 16), (16, 1)):        # blocks must be 1..8 whole warps
+    for tpi, ipb in ((2, 8), (32, 1), (4, 64)):         # 4 or 8 warps per block, at most 32 instances
         c = lib.mpc_config_default()
         c.tpi, c.ipb = tpi, ipb
         assert lib.mpc_create(c)[0] == lib.MPC_ERR_ARG, (tpi, ipb)

@@ -61,7 +61,9 @@ def _check(out):
     assert np.max(np.abs(x_na - x_ref)) <= U_TOL32 * max(1.0, np.abs(x_ref).max())
     # the tape holds one record per stage inside each instance's horizon
     B, N = out["shape"]
-    t_ref, t_na = (t[: B * N * 288].reshape(B, N, 288) for t in out["tape"])
+    G = (B + 31) // 32
+    t_ref, t_na = (t[: G * N * 210 * 32].reshape(G, N, 210, 32).transpose(0, 3, 1, 2).reshape(G * 32, N, 210)[:B]
+                   for t in out["tape"])
     for i in range(B):
         n = out["n"][i]
         assert np.isfinite(t_na[i, :n]).all()
