@@ -401,7 +401,7 @@ def run_kernels_only(args):
     prob = W.cfg_track(B=Bk)
     p = Problem.from_numpy(prob)
     gu = torch.as_tensor(W.loss_weights_u0(Bk, N, seed=1), dtype=torch.float32, device="cuda")
-    solver = DiffMPC(N_max=N, B_max=Bk, max_iter=MAX_ITER, tol=TOL)
+    solver = DiffMPC(N_max=N, B_max=Bk, max_iter=MAX_ITER, tol=TOL, tpi=args.tpi, ipb=args.ipb)
     s = solver.alloc_solution(Bk, N)
     grads = (torch.empty_like(p.Q), torch.empty_like(p.x_ref), torch.empty_like(p.x0))
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -429,6 +429,8 @@ def main():
     ap.add_argument("--mode", default="full", choices=["full", "kernels"],
                     help="kernels: only W + K eager forward+backward steps of the workload (for profilers)")
     ap.add_argument("--batch", type=int, default=B, help="instances (kernels mode only)")
+    ap.add_argument("--tpi", type=int, default=0, help="threads per instance, 0 = default (kernels mode only)")
+    ap.add_argument("--ipb", type=int, default=0, help="instances per block, 0 = default (kernels mode only)")
     args = ap.parse_args()
     if args.mode == "kernels":
         run_kernels_only(args)

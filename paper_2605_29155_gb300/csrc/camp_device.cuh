@@ -335,27 +335,33 @@ __device__ __forceinline__ void rk4_tangent(const Model<T>& m, const T* sp, cons
     for (int i = 0; i < NX; ++i) out[i] = dx[i] + h6 * acc[i];
 }
 
-// Columns j[0..NC) of F_t together: unit directions pushed through the four
-// RK4 stages side by side (d_s = J_c(xi_s) [e_j + c_s d_{s-1}; e_u],
-// col = e_j + h/6 (d1 + 2 d2 + 2 d3 + d4)), so each stage's Jacobian
-// coefficients are formed once and the NC chains interleave.  j = -1 gives
-// a column of zeros' tangent (unused).
+// Columns j[0..NC) of F_t = d RK4 / d(x, u) at (x, u) together: unit
+// directions pushed through the four RK4 stages side by side,
+//   d_s = J_c(xi_s) [e_j + c_s d_{s-1}; e_u],  col = e_j + h/6 (d1 + 2 d2 + 2 d3 + d4),
+// with the stage points xi_1 = x, xi_{s+1} = x + c_{s+1} f_c(xi_s, u) formed
+// on the way.  One loop trip per stage keeps the code small; each stage's
+// Jacobian coefficients are formed once for all NC columns, whose chains
+// interleave.  j = -1 gives an unused column.
 template <typename T, int NC>
-__device__ __forceinline__ void tangent_columns(const Model<T>& m, const T* sp, const int (&j)[NC],
-                                                T (&col)[NC][NX]) {
-    T arg[NC][NX], acc[NC][NX], du[NC][NU];
+__device__ __forceinline__ void tangent_columns(const Model<T>& m, const T (&x)[NX], const T (&u)[NU],
+                                                const int (&j)[NC], T (&col)[NC][NX]) {
+    T xi[NX], arg[NC][NX], acc[NC][NX], du[NC][NU];
+#pragma unroll
+    for (int i = 0; i < NX; ++i) xi[i] = x[i];
 #pragma unroll
     for (int k = 0; k < NC; ++k) {
 #pragma unroll
-        for (int i = 0; i < NX; ++i) arg[k][i] = (i == j[k]) ? T(1) : T(0);
+        for (int i = 0; i < NX; ++i) { arg[k][i] = (i == j[k]) ? T(1) : T(0); acc[k][i] = T(0); }
 #pragma unroll
         for (int a = 0; a < NU; ++a) du[k][a] = (NX + a == j[k]) ? T(1) : T(0);
     }
+    const T th = u[0] + u[1] + u[2] + u[3];
     const T hh = T(0.5) * m.h;
-#pragma unroll
+#pragma unroll 1
     for (int st = 0; st < 4; ++st) {
         JcCoef<T> c;
-        jc_coef(m, sp + 8 * st, sp[7], c);
+        const T sp8[8] = {xi[3], xi[4], xi[5], xi[6], xi[10], xi[11], xi[12], th};
+        jc_coef(m, sp8, th, c);
         const T w = (st == 0 || st == 3) ? T(1) : T(2);
         const T cs = (st < 2) ? hh : m.h;
 #pragma unroll
@@ -367,6 +373,12 @@ __device__ __forceinline__ void tangent_columns(const Model<T>& m, const T* sp, 
                 acc[k][i] = (st == 0) ? d[i] : acc[k][i] + w * d[i];
                 arg[k][i] = ((i == j[k]) ? T(1) : T(0)) + cs * d[i];
             }
+        }
+        if (st < 3) {
+            T kf[NX];
+            f_cont(m, xi, u, kf);
+#pragma unroll
+            for (int i = 0; i < NX; ++i) xi[i] = x[i] + cs * kf[i];
         }
     }
     const T h6 = m.h / T(6);
@@ -597,20 +609,20 @@ __device__ bool box_qp(bool on, const T (&H)[4][4], const T (&g)[4], const T (&l
 //                dot products, so large and small columns are paired
 //   CONST_W      the warp that forms the block of the constant p, v rows/columns
 //   tcol(w, s)   the tangent columns of F_{t-1} warp w computes while warp 0
-//                runs the box QP (so warp 0 takes fewer)
+//                runs the box QP (warp 0 takes none)
 //   kcol(w, s)   the columns c of K_t (and of V_t, v_t) warp w forms; column c
 //                of V_t has c + 1 entries
 // The tables, by warp: 4-warp split first, then the 8-warp split.
 __constant__ int c_pcol4[4][3] = {{10, 9, 0}, {8, 7, 1}, {6, 5, 2}, {4, 3, -1}};
-__constant__ int c_tcol4[4][3] = {{0, 1, -1}, {2, 3, 4}, {5, 6, 7}, {8, 9, 10}};
+__constant__ int c_tcol4[4][4] = {{-1, -1, -1, -1}, {0, 1, 2, 3}, {4, 5, 6, 7}, {8, 9, 10, -1}};
 __constant__ int c_kcol4[4][4] = {{12, 0, 6, -1}, {11, 1, 7, -1}, {10, 2, 8, -1}, {9, 3, 4, 5}};
 __constant__ int c_pcol8[8][2] = {{10, 0}, {9, 1}, {8, 2}, {7, 3}, {6, 4}, {5, -1}, {-1, -1}, {-1, -1}};
-__constant__ int c_tcol8[8][2] = {{0, -1}, {1, 2}, {3, 4}, {5, 6}, {7, 8}, {9, 10}, {-1, -1}, {-1, -1}};
+__constant__ int c_tcol8[8][2] = {{-1, -1}, {0, 1}, {2, 3}, {4, 5}, {6, 7}, {8, 9}, {10, -1}, {-1, -1}};
 __constant__ int c_kcol8[8][2] = {{12, 0}, {11, 1}, {10, 2}, {9, 3}, {8, 4}, {7, 5}, {6, -1}, {-1, -1}};
 
 template <int NW> struct Split;
 template <> struct Split<4> {
-    static constexpr int NP = 3, NT = 3, NK = 4, CONST_W = 3;
+    static constexpr int NP = 3, NT = 4, NK = 4, CONST_W = 3;
     __device__ static int pcol(int w, int s) { return c_pcol4[w][s]; }
     __device__ static int tcol(int w, int s) { return c_tcol4[w][s]; }
     __device__ static int kcol(int w, int s) { return c_kcol4[w][s]; }
@@ -859,22 +871,24 @@ __device__ __forceinline__ void tangent_step(const Params<T>& P, BlockSmem<T>& S
     const bool last = on && s == n - 1;
     T* Fd = &S.u.r.F[s & 1][0][L.l];
     if (dyn) {
-        const T* cs = &S.u.r.cst[s & 1][0][L.l];
-        T xs[NX], us[NU], sp[32];
-#pragma unroll
-        for (int i = 0; i < NX; ++i) xs[i] = cs[(R_X + i) * LW];
-#pragma unroll
-        for (int a = 0; a < NU; ++a) us[a] = cs[(R_U + a) * LW];
-        rk4_stage_points(P.mdl, xs, us, sp);
         constexpr int NT = Split<NW>::NT;
         int jj[NT], jc[NT];
+        bool any = false;
 #pragma unroll
         for (int k = 0; k < NT; ++k) {
             jj[k] = Split<NW>::tcol(L.w, k);
             jc[k] = jj[k] < 0 ? -1 : gcol(jj[k]);
+            any = any || jj[k] >= 0;
         }
+        if (!any) return;
+        const T* cs = &S.u.r.cst[s & 1][0][L.l];
+        T xs[NX], us[NU];
+#pragma unroll
+        for (int i = 0; i < NX; ++i) xs[i] = cs[(R_X + i) * LW];
+#pragma unroll
+        for (int a = 0; a < NU; ++a) us[a] = cs[(R_U + a) * LW];
         T col[NT][NX];
-        tangent_columns<T, NT>(P.mdl, sp, jc, col);
+        tangent_columns<T, NT>(P.mdl, xs, us, jc, col);
 #pragma unroll
         for (int k = 0; k < NT; ++k) {
             if (jj[k] < 0) continue;
@@ -908,10 +922,25 @@ __device__ __forceinline__ void cost_row(const BlockSmem<T>& S, const T* cs, int
     }
 }
 
-// (A): this warp's entries of Q_t and q_t.  Everything it reads (its F
-// columns, V_{t+1}, v_{t+1}, its cost rows) is loaded before the arithmetic,
-// and the rows of the other computed columns are loaded one row ahead, so the
-// shared-memory latency overlaps the multiply-adds.
+// (A): this warp's entries of Q_t and q_t.  V_{t+1} is held in registers;
+// one loop trip per computed column j of this warp forms
+//   W[:, j] = V f_j  (the reduction index outermost: 13 accumulators side by side),
+//   q_j, the diagonal entry, the entries in the rows of the constant columns,
+//   and the entries F[:, r]' W[:, j] in the rows of the computed columns r < j,
+// two rows per trip with split accumulators.  Loops (not full unrolling) keep
+// the code of a stage small enough for the instruction cache.
+template <typename T>
+__device__ __forceinline__ T dot13(const T (&a)[NX], const T (&b)[NX]) {
+    T s0 = a[0] * b[0], s1 = a[1] * b[1], s2 = a[2] * b[2];
+#pragma unroll
+    for (int k = 3; k < NX; k += 3) {
+        s0 += a[k] * b[k];
+        if (k + 1 < NX) s1 += a[k + 1] * b[k + 1];
+        if (k + 2 < NX) s2 += a[k + 2] * b[k + 2];
+    }
+    return (s0 + s1) + s2;
+}
+
 template <typename T, int NW>
 __device__ __forceinline__ void products(const Params<T>& P, BlockSmem<T>& S, const Lane& L, int t, bool use_lo) {
     constexpr int NP = Split<NW>::NP;
@@ -921,27 +950,13 @@ __device__ __forceinline__ void products(const Params<T>& P, BlockSmem<T>& S, co
     const T* Fb = &S.u.r.F[t & 1][0][l];
     T* Qs = &S.u.r.Q[0][l];
     T* qs = &S.u.r.q[0][l];
-    int jj[NP], col[NP];
-    int jmax = -1;
-#pragma unroll
-    for (int s = 0; s < NP; ++s) {
-        jj[s] = Split<NW>::pcol(L.w, s);
-        col[s] = jj[s] < 0 ? 0 : jj[s];
-        jmax = jj[s] > jmax ? jj[s] : jmax;
-    }
     const bool cw = L.w == Split<NW>::CONST_W;
-    if (jmax < 0 && !cw) return;
-    T V[NV], vv[NX], f[NP][NX], Cd[NP], cj[NP];
+    if (Split<NW>::pcol(L.w, 0) < 0 && !cw) return;
+    T V[NV], vv[NX];
 #pragma unroll
     for (int e = 0; e < NV; ++e) V[e] = S.V[e][l];
 #pragma unroll
     for (int i = 0; i < NX; ++i) vv[i] = S.v[i][l];
-#pragma unroll
-    for (int s = 0; s < NP; ++s) {
-#pragma unroll
-        for (int i = 0; i < NX; ++i) f[s][i] = Fb[(col[s] * NX + i) * LW];
-        cost_row(S, cs, l, gcol(col[s]), use_lo, Cd[s], cj[s]);
-    }
     if (cw) {
         // the block of the constant rows/columns p_a = a, v_a = 7 + a:
         //   Q[p_a][p_b] = V[p_a][p_b] (+ C),  Q[p_a][v_b] = V[p_a][v_b] + hv V[p_a][p_b],
@@ -967,72 +982,36 @@ __device__ __forceinline__ void products(const Params<T>& P, BlockSmem<T>& S, co
             }
         }
     }
-    if (jmax < 0) return;
-    // W[:, j] = V f_j, the reduction index outermost so that the 13 x NP
-    // accumulators advance side by side
-    T W[NP][NX];
-#pragma unroll
-    for (int s = 0; s < NP; ++s)
-#pragma unroll
-        for (int i = 0; i < NX; ++i) W[s][i] = T(0);
-#pragma unroll
-    for (int k = 0; k < NX; ++k)
-#pragma unroll
-        for (int i = 0; i < NX; ++i) {
-            const T vik = V[vidx(i, k)];
-#pragma unroll
-            for (int s = 0; s < NP; ++s) W[s][i] += vik * f[s][k];
-        }
-    // q_j, the diagonal entry, and the rows of the constant columns
-    // (p_a takes W[p_a], v_a takes W[v_a] + hv W[p_a])
-    T qj[NP], dsum[NP];
-#pragma unroll
-    for (int s = 0; s < NP; ++s) { qj[s] = cj[s]; dsum[s] = Cd[s]; }
-#pragma unroll
-    for (int k = 0; k < NX; ++k)
-#pragma unroll
-        for (int s = 0; s < NP; ++s) {
-            qj[s] += f[s][k] * vv[k];
-            dsum[s] += f[s][k] * W[s][k];
-        }
-#pragma unroll
+#pragma unroll 1
     for (int s = 0; s < NP; ++s) {
-        if (jj[s] < 0) continue;
-        const int j = gcol(jj[s]);
-        qs[j * LW] = qj[s];
-        Qs[qidx(j, j) * LW] = dsum[s];
+        const int jj = Split<NW>::pcol(L.w, s);
+        if (jj < 0) break;
+        const int j = gcol(jj);
+        T f[NX], W[NX];
+#pragma unroll
+        for (int i = 0; i < NX; ++i) { f[i] = Fb[(jj * NX + i) * LW]; W[i] = T(0); }
+        T Cd, cj;
+        cost_row(S, cs, l, j, use_lo, Cd, cj);
+#pragma unroll
+        for (int k = 0; k < NX; ++k)
+#pragma unroll
+            for (int i = 0; i < NX; ++i) W[i] += V[vidx(i, k)] * f[k];
+        qs[j * LW] = cj + dot13(f, vv);
+        Qs[qidx(j, j) * LW] = Cd + dot13(f, W);
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-            Qs[qidx(a, j) * LW] = W[s][a];
-            Qs[qidx(7 + a, j) * LW] = W[s][7 + a] + hv * W[s][a];
+            Qs[qidx(a, j) * LW] = W[a];
+            Qs[qidx(7 + a, j) * LW] = W[7 + a] + hv * W[a];
         }
-    }
-    // rows of the computed columns jj_r < jj, two rows at a time:
-    // Q[r][j] = F[:, r]' W[:, j]
+#pragma unroll 1
+        for (int r = 0; r < jj; r += 2) {
+            const int r1 = r + 1 < jj ? r + 1 : r;
+            T f0[NX], f1[NX];
 #pragma unroll
-    for (int r0 = 0; r0 < NGC - 1; r0 += 2) {
-        if (r0 < jmax) {
-            T fr[2][NX];
-#pragma unroll
-            for (int rr = 0; rr < 2; ++rr)
-#pragma unroll
-                for (int i = 0; i < NX; ++i) fr[rr][i] = Fb[((r0 + rr) * NX + i) * LW];
-            T acc[2][NP];
-#pragma unroll
-            for (int rr = 0; rr < 2; ++rr)
-#pragma unroll
-                for (int s = 0; s < NP; ++s) acc[rr][s] = T(0);
-#pragma unroll
-            for (int k = 0; k < NX; ++k)
-#pragma unroll
-                for (int rr = 0; rr < 2; ++rr)
-#pragma unroll
-                    for (int s = 0; s < NP; ++s) acc[rr][s] += fr[rr][k] * W[s][k];
-#pragma unroll
-            for (int rr = 0; rr < 2; ++rr)
-#pragma unroll
-                for (int s = 0; s < NP; ++s)
-                    if (r0 + rr < jj[s]) Qs[qidx(gcol(r0 + rr), gcol(jj[s])) * LW] = acc[rr][s];
+            for (int i = 0; i < NX; ++i) { f0[i] = Fb[(r * NX + i) * LW]; f1[i] = Fb[(r1 * NX + i) * LW]; }
+            const T a0 = dot13(f0, W), a1 = dot13(f1, W);
+            Qs[qidx(gcol(r), j) * LW] = a0;
+            if (r1 != r) Qs[qidx(gcol(r1), j) * LW] = a1;
         }
     }
 }
@@ -1124,12 +1103,12 @@ __device__ bool riccati(const Params<T>& P, BlockSmem<T>& S, const Lane& L, int 
             // (C) K_t, V_t, v_t
             stage_copy(t - 2);
             if (go) {
-                // every operand first (factor, k_t, Q_xu, and for each of this
-                // warp's columns c its column of Q_xx and row of Q_xu), then the
-                // columns' solves and updates side by side
+                // the factor, k_t and Q_xu in registers, then two of this
+                // warp's columns c per loop trip: column c of K_t by the masked
+                // solve, the upper part of column c of V_t = Q_xx + Q_xu K_t and
+                // v_t[c] = q_x[c] + Q_xu[c, :] k_t
                 constexpr int NK = Split<NW>::NK;
-                T Lf[NL], kk[NU], qxu[NX][NU], qxx[NK][NX], qc[NK][NU], qv[NK];
-                int cs_[NK];
+                T Lf[NL], kk[NU], qxu[NX][NU];
                 const int mask = S.mask[l];
 #pragma unroll
                 for (int i = 0; i < NL; ++i) Lf[i] = S.L[i][l];
@@ -1139,55 +1118,50 @@ __device__ bool riccati(const Params<T>& P, BlockSmem<T>& S, const Lane& L, int 
                 for (int i = 0; i < NX; ++i)
 #pragma unroll
                     for (int a = 0; a < NU; ++a) qxu[i][a] = S.u.r.Q[qidx(i, NX + a)][l];
-#pragma unroll
-                for (int s = 0; s < NK; ++s) {
-                    const int c = Split<NW>::kcol(L.w, s);
-                    cs_[s] = c;
-                    const int cc = c < 0 ? 0 : c;
-#pragma unroll
-                    for (int i = 0; i < NX; ++i) qxx[s][i] = S.u.r.Q[qidx(i, cc)][l];
-#pragma unroll
-                    for (int a = 0; a < NU; ++a) qc[s][a] = S.u.r.Q[qidx(cc, NX + a)][l];
-                    qv[s] = S.u.r.q[cc][l];
-                }
                 T* grow = P.stg + srow(P, L.pos, t, 0);
-                // the columns' solves side by side (no branch between them)
-                T kc[NK][NU];
+#pragma unroll 1
+                for (int s0 = 0; s0 < NK; s0 += 2) {
+                    int cp[2];
+                    T kc[2][NU], qc[2][NU], qxx[2][NX], qv[2];
 #pragma unroll
-                for (int s = 0; s < NK; ++s) {
-                    T rhs[4], y[4];
+                    for (int h = 0; h < 2; ++h) {
+                        cp[h] = s0 + h < NK ? Split<NW>::kcol(L.w, s0 + h) : -1;
+                        const int cc = cp[h] < 0 ? 0 : cp[h];
 #pragma unroll
-                    for (int a = 0; a < 4; ++a) rhs[a] = ((mask >> a) & 1) ? qc[s][a] : T(0);
-                    chol_solve4(Lf, rhs, y);
+                        for (int a = 0; a < NU; ++a) qc[h][a] = S.u.r.Q[qidx(cc, NX + a)][l];
 #pragma unroll
-                    for (int a = 0; a < 4; ++a) kc[s][a] = ((mask >> a) & 1) ? -y[a] : T(0);
-                }
-#pragma unroll
-                for (int s = 0; s < NK; ++s) {
-                    const int c = cs_[s];
-                    const bool has = c >= 0;
-                    const int cc = has ? c : 0;
-                    T vcol[NX];
-#pragma unroll
-                    for (int i = 0; i < NX; ++i) {
-                        T s2 = qxx[s][i];
-#pragma unroll
-                        for (int a = 0; a < NU; ++a) s2 += qxu[i][a] * kc[s][a];
-                        vcol[i] = s2;
+                        for (int i = 0; i < NX; ++i) qxx[h][i] = S.u.r.Q[qidx(i, cc)][l];
+                        qv[h] = S.u.r.q[cc][l];
                     }
-                    T s3 = qv[s];
+                    if (cp[0] < 0) break;
 #pragma unroll
-                    for (int a = 0; a < NU; ++a) s3 += qc[s][a] * kk[a];
-                    if (has) {
+                    for (int h = 0; h < 2; ++h) {
+                        T rhs[4], y[4];
 #pragma unroll
-                        for (int a = 0; a < 4; ++a) {
-                            S.K[a * NX + cc][l] = kc[s][a];
-                            grow[(R_K + a * NX + cc) * LW] = kc[s][a];
+                        for (int a = 0; a < 4; ++a) rhs[a] = ((mask >> a) & 1) ? qc[h][a] : T(0);
+                        chol_solve4(Lf, rhs, y);
+#pragma unroll
+                        for (int a = 0; a < 4; ++a) kc[h][a] = ((mask >> a) & 1) ? -y[a] : T(0);
+                    }
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        const int c = cp[h];
+                        if (c < 0) continue;
+                        T s3 = qv[h];
+#pragma unroll
+                        for (int a = 0; a < NU; ++a) {
+                            s3 += qc[h][a] * kk[a];
+                            S.K[a * NX + c][l] = kc[h][a];
+                            grow[(R_K + a * NX + c) * LW] = kc[h][a];
                         }
+                        S.v[c][l] = s3;
 #pragma unroll
-                        for (int i = 0; i < NX; ++i)
-                            if (i <= cc) S.V[vidx(i, cc)][l] = vcol[i];
-                        S.v[cc][l] = s3;
+                        for (int i = 0; i < NX; ++i) {
+                            T s2 = qxx[h][i];
+#pragma unroll
+                            for (int a = 0; a < NU; ++a) s2 += qxu[i][a] * kc[h][a];
+                            if (i <= c) S.V[vidx(i, c)][l] = s2;
+                        }
                     }
                 }
                 if (L.w == 0) {
