@@ -74,7 +74,7 @@ static int validate_config(const mpc_config* c) {
     if (c->store_mode != MPC_STORE_ALL && c->store_mode != MPC_RECOMPUTE) return MPC_ERR_ARG;
     if (c->exec_mode != MPC_EXEC_PERSISTENT && c->exec_mode != MPC_EXEC_PLAIN) return MPC_ERR_ARG;
     if (c->tpi != 0 && c->tpi != 4 && c->tpi != 8) return MPC_ERR_ARG;
-    if (c->ipb < 0 || c->ipb > 32) return MPC_ERR_ARG;
+    if (c->ipb < 0 || c->ipb > (c->dtype == MPC_F64 ? 16 : 32)) return MPC_ERR_ARG;
     return MPC_OK;
 }
 
@@ -133,10 +133,13 @@ extern "C" size_t mpc_tape_bytes(const mpc_handle* h, int B, int N) {
 
 // Instances per block for a batch of B: the handle's fixed value, or as many
 // as spread the batch over one block per SM.
+static int ipb_cap(const mpc_handle* h) { return h->cfg.dtype == MPC_F64 ? 16 : 32; }
+
 static int ipb_for(const mpc_handle* h, int B) {
     if (h->ipb) return h->ipb;
     const int per_sm = (B + h->num_sms - 1) / h->num_sms;
-    return per_sm < 1 ? 1 : (per_sm > 32 ? 32 : per_sm);
+    const int cap = ipb_cap(h);
+    return per_sm < 1 ? 1 : (per_sm > cap ? cap : per_sm);
 }
 
 static int grid_for(const mpc_handle* h, int B, int ipb) {
@@ -256,7 +259,7 @@ extern "C" int mpc_autotune(mpc_handle* h, const mpc_problem* p, mpc_solution* s
     int cands[4], nc = 0;
     for (int k = 1; k <= 4; ++k) {
         int v = (p->B + k * h->num_sms - 1) / (k * h->num_sms);
-        v = v < 1 ? 1 : (v > 32 ? 32 : v);
+        v = v < 1 ? 1 : (v > ipb_cap(h) ? ipb_cap(h) : v);
         bool dup = false;
         for (int i = 0; i < nc; ++i) dup = dup || cands[i] == v;
         if (!dup) cands[nc++] = v;

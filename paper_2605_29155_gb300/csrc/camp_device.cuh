@@ -11,8 +11,9 @@
 // products, the gain columns) are divided between the warps.  Per-instance
 // matrices live in shared memory as [row][lane] arrays (conflict-free: lane l
 // reads word l of a row); per-instance trajectories, gains and line-search
-// candidates live in a global scratch laid out the same way ([row][32
-// positions]), so every warp access to them is one or two 128-byte lines.
+// candidates live in a global scratch laid out by groups of 32 positions
+// ([group][stage][row][32]), so every warp access to them is one or two
+// 128-byte lines.
 #pragma once
 #include <cuda_runtime.h>
 #include <math.h>
@@ -26,15 +27,15 @@ constexpr int NFC = NGC * NX;          // entries of the computed columns
 constexpr int NV = NX * (NX + 1) / 2;  // packed upper triangle of V (13 x 13)
 constexpr int NQ = NZ * (NZ + 1) / 2;  // packed upper triangle of Q (17 x 17)
 constexpr int NL = 14;                 // masked Cholesky factor of Q_uu: packed lower 4x4 (10) + 1/diag (4)
-constexpr int LW = 32;                 // lanes of a warp = instances of a pack at most
+constexpr int GW = 32;                 // positions per group of the global scratch and tape layouts
 constexpr int QP_MAX_IT = 20, QP_MAX_LS = 30;
 constexpr unsigned FULL = 0xffffffffu;
 
-// Per-stage record of the global scratch (rows of 32 positions):
+// Per-stage record of the global scratch (rows of GW positions):
 // nominal x (hi, lo), u, the cost rows Q_t, x_ref,t, then the gains K_t, k_t.
 constexpr int R_X = 0, R_XL = 13, R_U = 26, R_Q = 30, R_XR = 43, CST = 56, R_K = 56, R_KK = 108, SREC = 112;
 constexpr int CREC = 30;               // line-search candidate per stage: x hi, x lo, u
-// Tape record per stage (rows of 32 instances): computed columns of F_t,
+// Tape record per stage (rows of GW instances): computed columns of F_t,
 // K_t (row-major), masked factor, free mask.
 constexpr int T_F = 0, T_K = 143, T_L = 195, T_M = 209, TREC = 210;
 
@@ -114,32 +115,46 @@ __host__ __device__ constexpr int qidx(int i, int j) {
 __host__ __device__ constexpr int gcol(int jj) { return jj < 4 ? 3 + jj : 6 + jj; }
 
 // ------------------------------------------------------- shared memory ----
+// Lanes per pack in shared memory: 32 in FP32; 16 in FP64 (whose records are
+// twice as large), plus one spare column that the idle lanes 16..31 of an
+// FP64 warp read and write instead of a live instance's.
+template <typename T> struct SL {
+    static constexpr int W = sizeof(T) == 4 ? 32 : 16;
+    static constexpr int A = sizeof(T) == 4 ? 32 : 17;
+};
+
 template <typename T> struct RicSmem {
-    T F[2][NFC][LW];       // computed columns of F_t, F[t & 1][jj * 13 + i]
-    T Q[NQ][LW];           // Q_t, packed upper triangle
-    T q[NZ][LW];           // q_t
-    T cst[2][CST][LW];     // a stage's nominal and cost rows (double buffered)
+    static constexpr int A = SL<T>::A;
+    T F[2][NFC][A];        // computed columns of F_s, F[s & 1][jj * 13 + i]
+    T Q[2][NQ][A];         // P_s = C_s + F_s' Q_xx,s+1 F_s, completed in place to Q_s (packed upper)
+    T q[2][NZ][A];         // q_s
+    T M[NX * NU][A];       // M_t = Q_xu,t L_t^-T (row-major): V_t = Q_xx,t - M_t M_t'
+    T N[NZ * NU][A];       // N_s = F_s' M_s+1 (row-major)
+    T v[NX][A];            // v_t = q_x,t + Q_xu,t k_t
+    T cst[3][CST][A];      // nominal and cost rows of stages s (by s mod 3)
 };
 template <typename T> struct LsSmem {
-    T stg[2][SREC][LW];    // a stage's nominal, cost and gain rows (double buffered)
+    static constexpr int A = SL<T>::A;
+    T stg[2][SREC][A];     // a stage's nominal, cost and gain rows (double buffered)
 };
 template <typename T> struct TapeSmem {
-    T rec[2][TREC][LW];    // a stage's tape record (double buffered)
+    static constexpr int A = SL<T>::A;
+    T rec[2][TREC][A];     // a stage's tape record (double buffered)
 };
 template <typename T> struct alignas(16) BlockSmem {
-    T V[NV][LW];           // value Hessian V_{t+1} (packed upper)
-    T v[NX][LW];           // value gradient v_{t+1}
-    T K[NU * NX][LW];      // K_t, row-major
-    T k[NU][LW];
-    T L[NL][LW];
-    T x0[NX][LW];
-    T R[NU][LW], uref[NU][LW], ulo[NU][LW], uhi[NU][LW];
-    T Jc[4][LW];           // line search: cost change of each candidate
-    T dmax[4][LW];         // line search: max |u_hat - u| of each candidate
-    T vh[NX][LW];          // adjoint value gradient
-    T qh[NZ][LW];          // adjoint q-hat
-    int mask[LW];
-    int ok[LW];
+    static constexpr int A = SL<T>::A;
+    T K[NU * NX][A];       // K_t, row-major
+    T k[NU][A];
+    T L[NL][A];
+    T x0[NX][A];
+    T R[NU][A], uref[NU][A], ulo[NU][A], uhi[NU][A];
+    T Jc[4][A];            // line search: cost change of each candidate
+    T dmax[4][A];          // line search: max |u_hat - u| of each candidate
+    T vh[NX][A];           // adjoint value gradient
+    T qh[NZ][A];           // adjoint q-hat
+    T wa[NZ][A];           // adjoint F_t' vh_{t+1}, formed one stage ahead
+    int mask[A];
+    int ok[A];
     union {
         RicSmem<T> r;
         LsSmem<T> s;
@@ -600,66 +615,65 @@ __device__ bool box_qp(bool on, const T (&H)[4][4], const T (&g)[4], const T (&l
     return ok;
 }
 
+
 // ------------------------------------------------------------ work split ----
 // Which warp does what, for NW = 4 or 8 warps per block.  Computed columns
-// are numbered jj = 0..10 (gcol(jj) is the column of F_t / Q_t).
-//   pcol(w, s)   the computed columns whose W = V F column and Q entries warp w
-//                forms in the products (s = 0..2, -1 = none); the entries of
-//                column j in rows of computed columns jj_r <= jj cost jj + 1
-//                dot products, so large and small columns are paired
+// are numbered jj = 0..10 (gcol(jj) is the column of F_t / Q_t).  While warp 0
+// solves stage t's box QPs, warps 1..NW-1 form P_{t-1} and the tangent
+// columns of F_{t-2}:
+//   pcol(w, s)   the computed columns j of P_{t-1} warp w forms (its column
+//                of W = Q_xx F and the entries of P in rows of columns <= j);
+//                column jj costs about 169 + 13 jj multiply-adds
 //   CONST_W      the warp that forms the block of the constant p, v rows/columns
-//   tcol(w, s)   the tangent columns of F_{t-1} warp w computes while warp 0
-//                runs the box QP (warp 0 takes none)
-//   kcol(w, s)   the columns c of K_t (and of V_t, v_t) warp w forms; column c
-//                of V_t has c + 1 entries
-// The tables, by warp: 4-warp split first, then the 8-warp split.
-__constant__ int c_pcol4[4][3] = {{10, 9, 0}, {8, 7, 1}, {6, 5, 2}, {4, 3, -1}};
+//   tcol(w, s)   the tangent columns warp w computes
+// Warp 0 takes neither.  The steps after the QP split their columns / rows
+// round-robin over all NW warps.
+// The tables, by warp (warp 0 solves the box QPs and takes neither).
+__constant__ int c_pcol4[4][4] = {{-1, -1, -1, -1}, {10, 7, 4, 1}, {9, 6, 3, 0}, {8, 5, 2, -1}};
 __constant__ int c_tcol4[4][4] = {{-1, -1, -1, -1}, {0, 1, 2, 3}, {4, 5, 6, 7}, {8, 9, 10, -1}};
-__constant__ int c_kcol4[4][4] = {{12, 0, 6, -1}, {11, 1, 7, -1}, {10, 2, 8, -1}, {9, 3, 4, 5}};
-__constant__ int c_pcol8[8][2] = {{10, 0}, {9, 1}, {8, 2}, {7, 3}, {6, 4}, {5, -1}, {-1, -1}, {-1, -1}};
+__constant__ int c_pcol8[8][2] = {{-1, -1}, {10, 0}, {9, 1}, {8, 2}, {7, 3}, {6, 4}, {5, -1}, {-1, -1}};
 __constant__ int c_tcol8[8][2] = {{-1, -1}, {0, 1}, {2, 3}, {4, 5}, {6, 7}, {8, 9}, {10, -1}, {-1, -1}};
-__constant__ int c_kcol8[8][2] = {{12, 0}, {11, 1}, {10, 2}, {9, 3}, {8, 4}, {7, 5}, {6, -1}, {-1, -1}};
 
 template <int NW> struct Split;
 template <> struct Split<4> {
-    static constexpr int NP = 3, NT = 4, NK = 4, CONST_W = 3;
+    static constexpr int NP = 4, NT = 4, CONST_W = 3;
     __device__ static int pcol(int w, int s) { return c_pcol4[w][s]; }
     __device__ static int tcol(int w, int s) { return c_tcol4[w][s]; }
-    __device__ static int kcol(int w, int s) { return c_kcol4[w][s]; }
 };
 template <> struct Split<8> {
-    static constexpr int NP = 2, NT = 2, NK = 2, CONST_W = 7;
+    static constexpr int NP = 2, NT = 2, CONST_W = 7;
     __device__ static int pcol(int w, int s) { return c_pcol8[w][s]; }
     __device__ static int tcol(int w, int s) { return c_tcol8[w][s]; }
-    __device__ static int kcol(int w, int s) { return c_kcol8[w][s]; }
 };
 
 // ------------------------------------------------------------ lanes --------
 // The calling thread's place: warp w of NW, lane l = instance l of the pack,
-// its position pos in the processing order (scratch index) and instance b.
+// its shared-memory column sl (l, or the spare column for an FP64 lane past
+// the pack), its position pos in the processing order (scratch index) and
+// instance b.
 struct Lane {
-    int w, l, pos, b;
+    int w, l, sl, pos, b;
     bool valid;
 };
 
-// Scratch row e of stage t for position pos ([group][stage][row][32]).
+// Scratch row e of stage t for position pos ([group][stage][row][GW]).
 template <typename T>
 __device__ __forceinline__ size_t srow(const Params<T>& P, int pos, int t, int e) {
-    return (((size_t)(pos >> 5) * P.N_ws + t) * SREC + e) * LW + (pos & 31);
+    return (((size_t)(pos / GW) * P.N_ws + t) * SREC + e) * GW + (pos % GW);
 }
 template <typename T>
 __device__ __forceinline__ size_t crow(const Params<T>& P, int c, int pos, int t, int e) {
-    const size_t groups = ((size_t)P.B + 31) >> 5;
-    return ((((size_t)c * groups + (pos >> 5)) * P.N_ws + t) * CREC + e) * LW + (pos & 31);
+    const size_t groups = ((size_t)P.B + GW - 1) / GW;
+    return ((((size_t)c * groups + pos / GW) * P.N_ws + t) * CREC + e) * GW + (pos % GW);
 }
 template <typename T>
 __device__ __forceinline__ size_t khrow(const Params<T>& P, int pos, int t, int a) {
-    return (((size_t)(pos >> 5) * P.N_ws + t) * NU + a) * LW + (pos & 31);
+    return (((size_t)(pos / GW) * P.N_ws + t) * NU + a) * GW + (pos % GW);
 }
-// Tape row e of stage t for instance b ([group of 32 instances][stage][row][32]).
+// Tape row e of stage t for instance b ([group of GW instances][stage][row][GW]).
 template <typename T>
 __device__ __forceinline__ size_t trow(const Params<T>& P, int b, int t, int e) {
-    return (((size_t)(b >> 5) * P.N + t) * TREC + e) * LW + (b & 31);
+    return (((size_t)(b / GW) * P.N + t) * TREC + e) * GW + (b % GW);
 }
 
 template <typename T>
@@ -673,12 +687,12 @@ __device__ void load_constants(const Params<T>& P, BlockSmem<T>& S, const Lane& 
     if (L.valid) {
         for (int e = L.w; e < NX + 4 * NU; e += NW) {
             if (e < NX) {
-                S.x0[e][L.l] = P.x0[(size_t)L.b * NX + e];
+                S.x0[e][L.sl] = P.x0[(size_t)L.b * NX + e];
             } else {
                 const int r = e - NX, q = r >> 2, a = r & 3;
                 const T* src = q == 0 ? P.R : (q == 1 ? P.uref : (q == 2 ? P.ulo : P.uhi));
-                T(*dst)[LW] = q == 0 ? S.R : (q == 1 ? S.uref : (q == 2 ? S.ulo : S.uhi));
-                dst[a][L.l] = src[(size_t)L.b * NU + a];
+                T(*dst)[SL<T>::A] = q == 0 ? S.R : (q == 1 ? S.uref : (q == 2 ? S.ulo : S.uhi));
+                dst[a][L.sl] = src[(size_t)L.b * NU + a];
             }
         }
     }
@@ -706,12 +720,12 @@ __device__ void load_stage_rows(const Params<T>& P, const Lane& L, int n, bool n
 #pragma unroll
             for (int a = 0; a < NU; ++a) nb[NX + a] = us[a];
 #pragma unroll
-            for (int i = 0; i < NX; ++i) { dr[(R_X + i) * LW] = nb[i]; dr[(R_XL + i) * LW] = T(0); }
+            for (int i = 0; i < NX; ++i) { dr[(R_X + i) * GW] = nb[i]; dr[(R_XL + i) * GW] = T(0); }
 #pragma unroll
-            for (int a = 0; a < NU; ++a) dr[(R_U + a) * LW] = nb[NX + a];
+            for (int a = 0; a < NU; ++a) dr[(R_U + a) * GW] = nb[NX + a];
         }
 #pragma unroll
-        for (int i = 0; i < NX; ++i) { dr[(R_Q + i) * LW] = buf[i]; dr[(R_XR + i) * LW] = buf[NX + i]; }
+        for (int i = 0; i < NX; ++i) { dr[(R_Q + i) * GW] = buf[i]; dr[(R_XR + i) * GW] = buf[NX + i]; }
     }
 }
 
@@ -724,32 +738,33 @@ __device__ void initial_rollout(const Params<T>& P, BlockSmem<T>& S, const Lane&
     if (L.w != 0) return;
     T J = T(0);
     if (n > 0) {
+        const int sl = L.sl;
         T xh[NX], xl[NX], us[NU], R[NU], ur[NU], lo[NU], hi[NU];
 #pragma unroll
-        for (int i = 0; i < NX; ++i) { xh[i] = S.x0[i][L.l]; xl[i] = T(0); }
+        for (int i = 0; i < NX; ++i) { xh[i] = S.x0[i][sl]; xl[i] = T(0); }
 #pragma unroll
         for (int a = 0; a < NU; ++a) {
-            R[a] = S.R[a][L.l]; ur[a] = S.uref[a][L.l]; lo[a] = S.ulo[a][L.l]; hi[a] = S.uhi[a][L.l];
+            R[a] = S.R[a][sl]; ur[a] = S.uref[a][sl]; lo[a] = S.ulo[a][sl]; hi[a] = S.uhi[a][sl];
         }
         for (int t = 0; t < n; ++t) {
             T* sr = P.stg + srow(P, L.pos, t, 0);
             T qv[NX], xr[NX], u0[NU];
 #pragma unroll
-            for (int i = 0; i < NX; ++i) { qv[i] = sr[(R_Q + i) * LW]; xr[i] = sr[(R_XR + i) * LW]; }
+            for (int i = 0; i < NX; ++i) { qv[i] = sr[(R_Q + i) * GW]; xr[i] = sr[(R_XR + i) * GW]; }
 #pragma unroll
             for (int a = 0; a < NU; ++a) u0[a] = P.uinit ? P.uinit[((size_t)L.b * P.N + t) * NU + a] : ur[a];
             T sx = T(0), su = T(0);
 #pragma unroll
             for (int a = 0; a < NU; ++a) {
                 us[a] = clampT(u0[a], lo[a], hi[a]);
-                sr[(R_U + a) * LW] = us[a];
+                sr[(R_U + a) * GW] = us[a];
                 const T e = us[a] - ur[a];
                 su += e * (R[a] * e);
             }
 #pragma unroll
             for (int i = 0; i < NX; ++i) {
-                sr[(R_X + i) * LW] = xh[i];
-                sr[(R_XL + i) * LW] = xl[i];
+                sr[(R_X + i) * GW] = xh[i];
+                sr[(R_XL + i) * GW] = xl[i];
                 const T e = (xh[i] - xr[i]) + xl[i];
                 sx += e * (qv[i] * e);
             }
@@ -757,71 +772,7 @@ __device__ void initial_rollout(const Params<T>& P, BlockSmem<T>& S, const Lane&
             if (t < n - 1) rk4_step2(P.mdl, xh, xl, us);
         }
     }
-    S.Jc[0][L.l] = J;
-}
-
-
-// --------------------------------------------- A8 adjoint backward step ----
-// One stage of the adjoint LQR's backward sweep (Sec. IV implicit
-// differentiation, Amos et al. 2018) on the stage's frozen factorization:
-//   qh = g_t + F_t' vh_{t+1};  kh_t = -(Q_uu,ff)^-1 qh_u,f (0 on clamped rows);
-//   vh_t = qh_x + K_t' qh_u.
-// Fp, Kp, Lp point at row 0 of the stage's computed F columns, K_t and masked
-// factor in shared memory (this lane's column, rows LW apart).  Two
-// barrier-separated steps: qh (columns split like the products), then kh
-// (warp 0) and vh (rows split).
-template <typename T, int NW>
-__device__ __forceinline__ void adjoint_step(const Params<T>& P, BlockSmem<T>& S, const Lane& L, int t, bool go,
-                                             const AdjArgs<T>& A, const T* Fp, const T* Kp, const T* Lp, int mask) {
-    const int l = L.l;
-    const T hv = hv_coef(P.mdl);
-    const size_t gxo = ((size_t)L.b * P.N + t) * NX, guo = ((size_t)L.b * P.N + t) * NU;
-    if (go) {
-        T vh[NX];
-#pragma unroll
-        for (int i = 0; i < NX; ++i) vh[i] = S.vh[i][l];
-#pragma unroll
-        for (int s = 0; s < Split<NW>::NP; ++s) {
-            const int jj = Split<NW>::pcol(L.w, s);
-            if (jj < 0) continue;
-            const int j = gcol(jj);
-            T g = j < NX ? (A.gx ? A.gx[gxo + j] : T(0)) : A.gu[guo + j - NX];
-#pragma unroll
-            for (int k = 0; k < NX; ++k) g += Fp[(jj * NX + k) * LW] * vh[k];
-            S.qh[j][l] = g;
-        }
-        if (L.w == Split<NW>::CONST_W) {
-#pragma unroll
-            for (int b = 0; b < 3; ++b) {
-                const T gp = A.gx ? A.gx[gxo + b] : T(0), gv = A.gx ? A.gx[gxo + 7 + b] : T(0);
-                S.qh[b][l] = gp + vh[b];
-                S.qh[7 + b][l] = gv + (vh[7 + b] + hv * vh[b]);
-            }
-        }
-    }
-    __syncthreads();
-    if (go) {
-        T qu[NU];
-#pragma unroll
-        for (int a = 0; a < NU; ++a) qu[a] = S.qh[NX + a][l];
-        if (L.w == 0) {
-            T Lf[NL], rhs[4], y[4];
-#pragma unroll
-            for (int i = 0; i < NL; ++i) Lf[i] = Lp[i * LW];
-#pragma unroll
-            for (int a = 0; a < 4; ++a) rhs[a] = ((mask >> a) & 1) ? qu[a] : T(0);
-            chol_solve4(Lf, rhs, y);
-#pragma unroll
-            for (int a = 0; a < 4; ++a) P.kh[khrow(P, L.pos, t, a)] = ((mask >> a) & 1) ? -y[a] : T(0);
-        }
-        for (int i = L.w; i < NX; i += NW) {
-            T s = S.qh[i][l];
-#pragma unroll
-            for (int a = 0; a < NU; ++a) s += Kp[(a * NX + i) * LW] * qu[a];
-            S.vh[i][l] = s;
-        }
-    }
-    __syncthreads();
+    S.Jc[0][L.sl] = J;
 }
 
 // ---------------------------------------------- A3 Riccati with box QP ------
@@ -830,16 +781,26 @@ __device__ __forceinline__ void adjoint_step(const Params<T>& P, BlockSmem<T>& S
 //   k_t, free set <- box QP(Q_uu, q_u, u_lo - u_t, u_hi - u_t)
 //   K_t = -Q_uu,ff^-1 Q_ux,f on free rows, 0 on clamped rows
 //   V_t = Q_xx + Q_xu K_t,   v_t = q_x + Q_xu k_t
-// with the linearization of Sec. IV-1 fused in: F_{t-1} = [A B] at the
-// nominal (one forward tangent through the RK4 stages per computed column) is
-// formed while warp 0 solves stage t's box QP.  Stage t runs in three steps
-// separated by block barriers:
-//   (A) products: every warp forms its columns of W = V_{t+1} F_t and their
-//       entries of Q_t, q_t (the constant p, v columns take one warp);
-//   (B) warp 0: box QP of stage t; all warps: tangent columns of F_{t-1};
-//   (C) columns of K_t with the matching columns of V_t, v_t; gains to the
-//       scratch (for the line search); on request the tape record and the
-//       adjoint step.
+// with the linearization of Sec. IV-1 fused in (the tangent columns of F_s
+// are formed in the sweep, never stored outside shared memory).
+//
+// Pipelining.  With L_t the Cholesky factor of the free block of Q_uu,t and
+// M_t = Q_xu,t L_t^-T (zero columns for clamped controls), Q_xu K_t = -M_t M_t',
+// so V_t = Q_xx,t - M_t M_t' and
+//   Q_{t-1} = P_{t-1} - N_{t-1} N_{t-1}',  P_{t-1} = C_{t-1} + F_{t-1}' Q_xx,t F_{t-1},
+//   N_{t-1} = F_{t-1}' M_t,  q_{t-1} = c_{t-1} + F_{t-1}' v_t.
+// P_{t-1} does not depend on stage t's box QP, so it is formed while warp 0
+// solves the QPs; after them only the short steps M_t, K_t, v_t, then
+// N_{t-1}, q_{t-1} remain before stage t-1's QP can start.  Stage t runs as
+//   phase 1  warp 0: Q_uu,t = P_uu - N_u N_u', box QP (k_t, free set, factor);
+//            warps 1..NW-1: P_{t-1} (from Q_xx,t = P_xx - N_x N_x' formed on
+//            load) and the tangent columns of F_{t-2};
+//   phase 2  columns of M_t, K_t and v_t, with Q_xu,t = P_xu - N_x N_u' formed
+//            on load (gains to the scratch for the line search);
+//   phase 3  rows of N_{t-1} and q_{t-1}; on request the tape rows;
+// separated by block barriers, plus the adjoint step on request.  Quantities
+// of stages past an instance's horizon are exact zeros, so that its last
+// stage starts from V = 0, v = 0 (Q = C, q = c).
 // Options:
 //   use_lo   cost gradient at the hi + lo nominal (iterations); otherwise at
 //            x* as returned (the factorization the backward differentiates)
@@ -861,74 +822,68 @@ template <typename T> struct RicOpts {
 };
 
 // Writes the tangent columns of F_s this warp owns, or zeros when s is the
-// instance's last stage (no dynamics: with F = 0 and V_{s+1} = 0 the products
-// reduce to Q = C, q = c).
+// instance's last stage (no dynamics: with F = 0 and V_{s+1} = 0 the stage
+// reduces to Q = C, q = c).
 template <typename T, int NW>
 __device__ __forceinline__ void tangent_step(const Params<T>& P, BlockSmem<T>& S, const Lane& L, int s, int n,
                                              bool on) {
+    constexpr int A = SL<T>::A;
     if (s < 0) return;
     const bool dyn = on && s < n - 1;
     const bool last = on && s == n - 1;
-    T* Fd = &S.u.r.F[s & 1][0][L.l];
-    if (dyn) {
-        constexpr int NT = Split<NW>::NT;
-        int jj[NT], jc[NT];
-        bool any = false;
+    T* Fd = &S.u.r.F[s & 1][0][L.sl];
+    constexpr int NT = Split<NW>::NT;
+    int jj[NT], jc[NT];
+    bool any = false;
 #pragma unroll
-        for (int k = 0; k < NT; ++k) {
-            jj[k] = Split<NW>::tcol(L.w, k);
-            jc[k] = jj[k] < 0 ? -1 : gcol(jj[k]);
-            any = any || jj[k] >= 0;
-        }
-        if (!any) return;
-        const T* cs = &S.u.r.cst[s & 1][0][L.l];
+    for (int k = 0; k < NT; ++k) {
+        jj[k] = Split<NW>::tcol(L.w, k);
+        jc[k] = jj[k] < 0 ? -1 : gcol(jj[k]);
+        any = any || jj[k] >= 0;
+    }
+    if (!any) return;
+    if (dyn) {
+        const T* cs = &S.u.r.cst[s % 3][0][L.sl];
         T xs[NX], us[NU];
 #pragma unroll
-        for (int i = 0; i < NX; ++i) xs[i] = cs[(R_X + i) * LW];
+        for (int i = 0; i < NX; ++i) xs[i] = cs[(R_X + i) * A];
 #pragma unroll
-        for (int a = 0; a < NU; ++a) us[a] = cs[(R_U + a) * LW];
+        for (int a = 0; a < NU; ++a) us[a] = cs[(R_U + a) * A];
         T col[NT][NX];
         tangent_columns<T, NT>(P.mdl, xs, us, jc, col);
 #pragma unroll
         for (int k = 0; k < NT; ++k) {
             if (jj[k] < 0) continue;
 #pragma unroll
-            for (int i = 0; i < NX; ++i) Fd[(jj[k] * NX + i) * LW] = col[k][i];
+            for (int i = 0; i < NX; ++i) Fd[(jj[k] * NX + i) * A] = col[k][i];
         }
     } else if (last) {
 #pragma unroll
-        for (int k = 0; k < Split<NW>::NT; ++k) {
-            const int jj = Split<NW>::tcol(L.w, k);
-            if (jj < 0) continue;
+        for (int k = 0; k < NT; ++k) {
+            if (jj[k] < 0) continue;
 #pragma unroll
-            for (int i = 0; i < NX; ++i) Fd[(jj * NX + i) * LW] = T(0);
+            for (int i = 0; i < NX; ++i) Fd[(jj[k] * NX + i) * A] = T(0);
         }
     }
 }
 
-// Cost row j of stage t: C_jj and (C z + c)_j at the nominal.
+// Cost row j of a stage: C_jj and (C z + c)_j at the nominal.
 template <typename T>
-__device__ __forceinline__ void cost_row(const BlockSmem<T>& S, const T* cs, int l, int j, bool use_lo, T& Cd,
+__device__ __forceinline__ void cost_row(const BlockSmem<T>& S, const T* cs, int sl, int j, bool use_lo, T& Cd,
                                          T& c) {
+    constexpr int A = SL<T>::A;
     if (j < NX) {
-        const T q = cs[(R_Q + j) * LW];
-        const T e = cs[(R_X + j) * LW] - cs[(R_XR + j) * LW];
+        const T q = cs[(R_Q + j) * A];
+        const T e = cs[(R_X + j) * A] - cs[(R_XR + j) * A];
         Cd = q;
-        c = q * (use_lo ? e + cs[(R_XL + j) * LW] : e);
+        c = q * (use_lo ? e + cs[(R_XL + j) * A] : e);
     } else {
         const int a = j - NX;
-        Cd = S.R[a][l];
-        c = Cd * (cs[(R_U + a) * LW] - S.uref[a][l]);
+        Cd = S.R[a][sl];
+        c = Cd * (cs[(R_U + a) * A] - S.uref[a][sl]);
     }
 }
 
-// (A): this warp's entries of Q_t and q_t.  V_{t+1} is held in registers;
-// one loop trip per computed column j of this warp forms
-//   W[:, j] = V f_j  (the reduction index outermost: 13 accumulators side by side),
-//   q_j, the diagonal entry, the entries in the rows of the constant columns,
-//   and the entries F[:, r]' W[:, j] in the rows of the computed columns r < j,
-// two rows per trip with split accumulators.  Loops (not full unrolling) keep
-// the code of a stage small enough for the instruction cache.
 template <typename T>
 __device__ __forceinline__ T dot13(const T (&a)[NX], const T (&b)[NX]) {
     T s0 = a[0] * b[0], s1 = a[1] * b[1], s2 = a[2] * b[2];
@@ -941,109 +896,210 @@ __device__ __forceinline__ T dot13(const T (&a)[NX], const T (&b)[NX]) {
     return (s0 + s1) + s2;
 }
 
+// Phase 1, warps 1..NW-1: P_s = C_s + F_s' Q_xx,s+1 F_s (all 153 entries)
+// into Q[s & 1]; exact zeros for an instance whose stage s is past its
+// horizon.  Q_xx,s+1 = P_xx,s+1 - N_x,s+1 N_x,s+1' is formed in registers as
+// it is loaded (every warp forms its own copy; nothing waits for a shared
+// one); one loop trip per computed column j of this
+// warp forms W[:, j] = Q_xx f_j (the reduction index outermost), the diagonal
+// entry, the entries in the rows of the constant columns (p_a takes W[p_a],
+// v_a takes W[v_a] + hv W[p_a]) and F[:, r]' W[:, j] in the rows of the
+// computed columns r < j, two rows per trip.
 template <typename T, int NW>
-__device__ __forceinline__ void products(const Params<T>& P, BlockSmem<T>& S, const Lane& L, int t, bool use_lo) {
+__device__ __forceinline__ void form_p(const Params<T>& P, BlockSmem<T>& S, const Lane& L, int s, bool ons) {
+    constexpr int A = SL<T>::A;
     constexpr int NP = Split<NW>::NP;
-    const int l = L.l;
+    const int sl = L.sl;
     const T hv = hv_coef(P.mdl);
-    const T* cs = &S.u.r.cst[t & 1][0][l];
-    const T* Fb = &S.u.r.F[t & 1][0][l];
-    T* Qs = &S.u.r.Q[0][l];
-    T* qs = &S.u.r.q[0][l];
+    const T* cs = &S.u.r.cst[s % 3][0][sl];
+    const T* Fb = &S.u.r.F[s & 1][0][sl];
+    const T* Qn = &S.u.r.Q[(s + 1) & 1][0][sl];
+    const T* Nb = &S.u.r.N[0][sl];
+    T* Ps = &S.u.r.Q[s & 1][0][sl];
     const bool cw = L.w == Split<NW>::CONST_W;
     if (Split<NW>::pcol(L.w, 0) < 0 && !cw) return;
-    T V[NV], vv[NX];
+    T V[NV], nx[NX][NU];
 #pragma unroll
-    for (int e = 0; e < NV; ++e) V[e] = S.V[e][l];
+    for (int i = 0; i < NX; ++i)
 #pragma unroll
-    for (int i = 0; i < NX; ++i) vv[i] = S.v[i][l];
+        for (int a = 0; a < NU; ++a) nx[i][a] = Nb[(i * NU + a) * A];
+#pragma unroll
+    for (int i = 0; i < NX; ++i)
+#pragma unroll
+        for (int k = i; k < NX; ++k) {
+            T v = Qn[qidx(i, k) * A];
+#pragma unroll
+            for (int a = 0; a < NU; ++a) v -= nx[i][a] * nx[k][a];
+            V[vidx(i, k)] = v;
+        }
     if (cw) {
         // the block of the constant rows/columns p_a = a, v_a = 7 + a:
-        //   Q[p_a][p_b] = V[p_a][p_b] (+ C),  Q[p_a][v_b] = V[p_a][v_b] + hv V[p_a][p_b],
-        //   Q[v_a][v_b] = (V[v_a][v_b] + hv V[v_a][p_b]) + hv (V[p_a][v_b] + hv V[p_a][p_b]) (+ C),
-        //   q[p_b] = c + v[p_b],  q[v_b] = c + (v[v_b] + hv v[p_b])
+        //   P[p_a][p_b] = V[p_a][p_b] (+ C),  P[p_a][v_b] = V[p_a][v_b] + hv V[p_a][p_b],
+        //   P[v_a][v_b] = (V[v_a][v_b] + hv V[v_a][p_b]) + hv (V[p_a][v_b] + hv V[p_a][p_b]) (+ C)
 #pragma unroll
         for (int b = 0; b < 3; ++b) {
             T Cp, cp, Cv, cv;
-            cost_row(S, cs, l, b, use_lo, Cp, cp);
-            cost_row(S, cs, l, 7 + b, use_lo, Cv, cv);
-            qs[b * LW] = cp + vv[b];
-            qs[(7 + b) * LW] = cv + (vv[7 + b] + hv * vv[b]);
+            cost_row(S, cs, sl, b, false, Cp, cp);
+            cost_row(S, cs, sl, 7 + b, false, Cv, cv);
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
                 const T Vpp = V[vidx(a, b)];
                 const T Wpv = V[vidx(a, 7 + b)] + hv * Vpp;
-                Qs[qidx(a, 7 + b) * LW] = Wpv;
+                Ps[qidx(a, 7 + b) * A] = ons ? Wpv : T(0);
                 if (a <= b) {
-                    Qs[qidx(a, b) * LW] = a == b ? Cp + Vpp : Vpp;
-                    const T s = (V[vidx(7 + a, 7 + b)] + hv * V[vidx(7 + a, b)]) + hv * Wpv;
-                    Qs[qidx(7 + a, 7 + b) * LW] = a == b ? Cv + s : s;
+                    Ps[qidx(a, b) * A] = ons ? (a == b ? Cp + Vpp : Vpp) : T(0);
+                    const T v2 = (V[vidx(7 + a, 7 + b)] + hv * V[vidx(7 + a, b)]) + hv * Wpv;
+                    Ps[qidx(7 + a, 7 + b) * A] = ons ? (a == b ? Cv + v2 : v2) : T(0);
                 }
             }
         }
     }
 #pragma unroll 1
-    for (int s = 0; s < NP; ++s) {
-        const int jj = Split<NW>::pcol(L.w, s);
+    for (int k = 0; k < NP; ++k) {
+        const int jj = Split<NW>::pcol(L.w, k);
         if (jj < 0) break;
         const int j = gcol(jj);
         T f[NX], W[NX];
 #pragma unroll
-        for (int i = 0; i < NX; ++i) { f[i] = Fb[(jj * NX + i) * LW]; W[i] = T(0); }
+        for (int i = 0; i < NX; ++i) { f[i] = Fb[(jj * NX + i) * A]; W[i] = T(0); }
         T Cd, cj;
-        cost_row(S, cs, l, j, use_lo, Cd, cj);
+        cost_row(S, cs, sl, j, false, Cd, cj);
 #pragma unroll
-        for (int k = 0; k < NX; ++k)
+        for (int kk = 0; kk < NX; ++kk)
 #pragma unroll
-            for (int i = 0; i < NX; ++i) W[i] += V[vidx(i, k)] * f[k];
-        qs[j * LW] = cj + dot13(f, vv);
-        Qs[qidx(j, j) * LW] = Cd + dot13(f, W);
+            for (int i = 0; i < NX; ++i) W[i] += V[vidx(i, kk)] * f[kk];
+        Ps[qidx(j, j) * A] = ons ? Cd + dot13(f, W) : T(0);
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-            Qs[qidx(a, j) * LW] = W[a];
-            Qs[qidx(7 + a, j) * LW] = W[7 + a] + hv * W[a];
+            Ps[qidx(a, j) * A] = ons ? W[a] : T(0);
+            Ps[qidx(7 + a, j) * A] = ons ? W[7 + a] + hv * W[a] : T(0);
         }
 #pragma unroll 1
         for (int r = 0; r < jj; r += 2) {
             const int r1 = r + 1 < jj ? r + 1 : r;
             T f0[NX], f1[NX];
 #pragma unroll
-            for (int i = 0; i < NX; ++i) { f0[i] = Fb[(r * NX + i) * LW]; f1[i] = Fb[(r1 * NX + i) * LW]; }
+            for (int i = 0; i < NX; ++i) { f0[i] = Fb[(r * NX + i) * A]; f1[i] = Fb[(r1 * NX + i) * A]; }
             const T a0 = dot13(f0, W), a1 = dot13(f1, W);
-            Qs[qidx(gcol(r), j) * LW] = a0;
-            if (r1 != r) Qs[qidx(gcol(r1), j) * LW] = a1;
+            Ps[qidx(gcol(r), j) * A] = ons ? a0 : T(0);
+            if (r1 != r) Ps[qidx(gcol(r1), j) * A] = ons ? a1 : T(0);
         }
     }
 }
 
+// --------------------------------------------- A8 adjoint backward step ----
+// One stage of the adjoint LQR's backward sweep (Sec. IV implicit
+// differentiation, Amos et al. 2018) on the stage's frozen factorization:
+//   qh_t = g_t + F_t' vh_{t+1};  kh_t = -(Q_uu,ff)^-1 qh_u,f (0 on clamped rows);
+//   vh_t = qh_x + K_t' qh_u,
+// with F_t' vh_{t+1} formed one stage ahead (S.wa; zero at the last stage).
+// Kp, Lp point at row 0 of the stage's K_t and masked factor in shared
+// memory, Fp at row 0 of F_{t-1}'s computed columns (for S.wa of the next
+// stage).  Three barrier-separated steps; the copies of the caller's prefetch
+// are waited for before the last.
+template <typename T, int NW>
+__device__ __forceinline__ void adjoint_step(const Params<T>& P, BlockSmem<T>& S, const Lane& L, int t, int n,
+                                             bool go, const AdjArgs<T>& A, const T* Kp, const T* Lp, int mask,
+                                             const T* Fp) {
+    constexpr int SA = SL<T>::A;
+    const int sl = L.sl;
+    const T hv = hv_coef(P.mdl);
+    if (go) {
+        const size_t gxo = ((size_t)L.b * P.N + t) * NX, guo = ((size_t)L.b * P.N + t) * NU;
+        for (int j = L.w; j < NZ; j += NW) {
+            const T g = j < NX ? (A.gx ? A.gx[gxo + j] : T(0)) : A.gu[guo + j - NX];
+            S.qh[j][sl] = g + (t < n - 1 ? S.wa[j][sl] : T(0));
+        }
+    }
+    __syncthreads();
+    if (go) {
+        T qu[NU];
+#pragma unroll
+        for (int a = 0; a < NU; ++a) qu[a] = S.qh[NX + a][sl];
+        if (L.w == 0) {
+            T Lf[NL], rhs[4], y[4];
+#pragma unroll
+            for (int i = 0; i < NL; ++i) Lf[i] = Lp[i * SA];
+#pragma unroll
+            for (int a = 0; a < 4; ++a) rhs[a] = ((mask >> a) & 1) ? qu[a] : T(0);
+            chol_solve4(Lf, rhs, y);
+#pragma unroll
+            for (int a = 0; a < 4; ++a) P.kh[khrow(P, L.pos, t, a)] = ((mask >> a) & 1) ? -y[a] : T(0);
+        }
+        for (int i = L.w; i < NX; i += NW) {
+            T s = S.qh[i][sl];
+#pragma unroll
+            for (int a = 0; a < NU; ++a) s += Kp[(a * NX + i) * SA] * qu[a];
+            S.vh[i][sl] = s;
+        }
+    }
+    cp_async_wait_all();
+    __syncthreads();
+    // F_{t-1}' vh_t for the next stage
+    if (go && t > 0) {
+        T vh[NX];
+#pragma unroll
+        for (int i = 0; i < NX; ++i) vh[i] = S.vh[i][sl];
+        for (int j = L.w; j < NZ; j += NW) {
+            T s;
+            if (j < 3) {
+                s = vh[j];
+            } else if (j >= 7 && j < 10) {
+                s = vh[j] + hv * vh[j - 7];
+            } else {
+                const int jj = j < 7 ? j - 3 : j - 6;
+                T f[NX];
+#pragma unroll
+                for (int i = 0; i < NX; ++i) f[i] = Fp[(jj * NX + i) * SA];
+                s = dot13(f, vh);
+            }
+            S.wa[j][sl] = s;
+        }
+    }
+    __syncthreads();
+}
+
 template <typename T, int NW>
 __device__ bool riccati(const Params<T>& P, BlockSmem<T>& S, const Lane& L, int n, const RicOpts<T>& o) {
-    const int l = L.l;
+    constexpr int A = SL<T>::A;
+    const int sl = L.sl;
+    const T hv = hv_coef(P.mdl);
     const int nmax = __reduce_max_sync(FULL, n);
-    for (int e = L.w; e < NV; e += NW) S.V[e][l] = T(0);
-    for (int e = L.w; e < NX; e += NW) { S.v[e][l] = T(0); S.vh[e][l] = T(0); }
+    // The factorization the backward differentiates forms V_t = Q_xx + Q_xu K_t
+    // explicitly after the box QP and P_{t-1} = C + F' V_t F from it (N = 0),
+    // which keeps the subtraction of the controlled directions in the 13 x 13
+    // value Hessian, where FP32 resolves it best; the iterations use the
+    // pipelined form above.
+    const bool vform = !o.use_lo;
     bool alive = true;
-    // copy of stage tt's nominal and cost rows into cst[tt & 1] (rows split by warp)
+    // copies of stage tt's nominal and cost rows into cst[tt % 3], and of its
+    // tape record into rec[tt & 1] (rows split by warp)
     auto stage_copy = [&](int tt) {
         if (tt >= 0 && tt < n) {
-            T* dst = &S.u.r.cst[tt & 1][0][l];
+            T* dst = &S.u.r.cst[tt % 3][0][sl];
             const T* src = P.stg + srow(P, L.pos, tt, 0);
-            for (int e = L.w; e < CST; e += NW) cp_async(dst + e * LW, src + e * LW);
+            for (int e = L.w; e < CST; e += NW) cp_async(dst + e * A, src + e * GW);
         }
         cp_async_commit();
     };
-    // copy of stage tt's tape record into rec[tt & 1] (replay)
     auto rec_copy = [&](int tt) {
         if (tt >= 0 && tt < n) {
-            T* dst = &S.u.tp.rec[tt & 1][0][l];
+            T* dst = &S.u.tp.rec[tt & 1][0][sl];
             const T* src = P.tape + trow(P, L.b, tt, 0);
-            for (int e = L.w; e < TREC; e += NW) cp_async(dst + e * LW, src + e * LW);
+            for (int e = L.w; e < TREC; e += NW) cp_async(dst + e * A, src + e * GW);
         }
         cp_async_commit();
     };
+    // replay starts at the last stage; the recursion one stage later, at a
+    // stage past every horizon (t = nmax), where everything is zero
+    const int t0 = o.replay ? nmax - 1 : nmax;
     if (o.replay) {
         rec_copy(nmax - 1);
+        cp_async_wait_all();
+        __syncthreads();
     } else {
+        for (int e = L.w; e < NQ; e += NW) S.u.r.Q[nmax & 1][e][sl] = T(0);
+        for (int e = L.w; e < NZ * NU; e += NW) S.u.r.N[e][sl] = T(0);
         stage_copy(nmax - 1);
         stage_copy(nmax - 2);
         cp_async_wait_all();
@@ -1051,143 +1107,216 @@ __device__ bool riccati(const Params<T>& P, BlockSmem<T>& S, const Lane& L, int 
         tangent_step<T, NW>(P, S, L, nmax - 1, n, n > 0);
         __syncthreads();
     }
-    for (int t = nmax - 1; t >= 0; --t) {
+    for (int t = t0; t >= 0; --t) {
         const bool on = alive && t < n;
         // the stage's factorization for the adjoint step: replayed or just formed
-        const T *Fp, *Kp, *Lp;
+        const T *Kp, *Lp, *Fp;
         int amask;
         bool ago;
         if (o.replay) {
-            cp_async_wait_all();
-            __syncthreads();
             rec_copy(t - 1);
-            const T* R = &S.u.tp.rec[t & 1][0][l];
-            Fp = R + T_F * LW;
-            Kp = R + T_K * LW;
-            Lp = R + T_L * LW;
-            amask = on ? (int)R[T_M * LW] : 0;
+            const T* R = &S.u.tp.rec[t & 1][0][sl];
+            Kp = R + T_K * A;
+            Lp = R + T_L * A;
+            Fp = &S.u.tp.rec[(t + 1) & 1][0][sl] + T_F * A;      // the record of stage t-1
+            amask = on ? (int)R[T_M * A] : 0;
             ago = on;
         } else {
-            // (A) products
-            products<T, NW>(P, S, L, t, o.use_lo);
-            cp_async_wait_all();
-            __syncthreads();
-            // (B) box QP of stage t (warp 0); tangent columns of F_{t-1}
+            // ---- phase 1
             if (L.w == 0) {
-                const T* cs = &S.u.r.cst[t & 1][0][l];
-                T H[4][4], g[4], lo[4], hi[4], d[4], Lf[NL];
+                const T* cs = &S.u.r.cst[t % 3][0][sl];
+                const T* Pt = &S.u.r.Q[t & 1][0][sl];
+                T H[4][4], g[4], lo[4], hi[4], d[4], Lf[NL], nu[NU][NU];
                 int mask = 0;
+#pragma unroll
+                for (int a = 0; a < NU; ++a)
+#pragma unroll
+                    for (int b = 0; b < NU; ++b) nu[a][b] = S.u.r.N[(NX + a) * NU + b][sl];
 #pragma unroll
                 for (int a = 0; a < 4; ++a) {
 #pragma unroll
-                    for (int bb = 0; bb < 4; ++bb) H[a][bb] = S.u.r.Q[qidx(NX + a, NX + bb)][l];
-                    g[a] = S.u.r.q[NX + a][l];
-                    const T ub = cs[(R_U + a) * LW];
-                    lo[a] = S.ulo[a][l] - ub;
-                    hi[a] = S.uhi[a][l] - ub;
+                    for (int b = a; b < 4; ++b) {
+                        T s = Pt[qidx(NX + a, NX + b) * A];
+#pragma unroll
+                        for (int k = 0; k < NU; ++k) s -= nu[a][k] * nu[b][k];
+                        H[a][b] = s;
+                        H[b][a] = s;
+                    }
+                    g[a] = S.u.r.q[t & 1][NX + a][sl];
+                    const T ub = t < n ? cs[(R_U + a) * A] : T(0);
+                    lo[a] = S.ulo[a][sl] - ub;
+                    hi[a] = S.uhi[a][sl] - ub;
                 }
                 const bool ok = box_qp(on, H, g, lo, hi, d, Lf, mask);
                 if (on) {
 #pragma unroll
-                    for (int a = 0; a < 4; ++a) S.k[a][l] = d[a];
+                    for (int a = 0; a < 4; ++a) S.k[a][sl] = d[a];
 #pragma unroll
-                    for (int i = 0; i < NL; ++i) S.L[i][l] = Lf[i];
-                    S.mask[l] = mask;
-                    S.ok[l] = ok ? 1 : 0;
+                    for (int i = 0; i < NL; ++i) S.L[i][sl] = Lf[i];
+                    S.mask[sl] = mask;
+                    S.ok[sl] = ok ? 1 : 0;
+                }
+            } else {
+                if (t >= 1 && !vform) form_p<T, NW>(P, S, L, t - 1, alive && t - 1 < n);
+                tangent_step<T, NW>(P, S, L, t - 2, n, alive && n > 0);
+            }
+            __syncthreads();
+            if (on && !S.ok[sl]) alive = false;
+            const bool go = on && alive;
+            // ---- phase 2: columns c of M_t (forward solves), K_t (back
+            // solves) and v_t
+            stage_copy(t - 3);
+            {
+                T Lf[NL], kk[NU];
+                const int mask = go ? S.mask[sl] : 0;
+#pragma unroll
+                for (int i = 0; i < NL; ++i) Lf[i] = S.L[i][sl];
+#pragma unroll
+                for (int a = 0; a < NU; ++a) kk[a] = S.k[a][sl];
+                const T* Qt = &S.u.r.Q[t & 1][0][sl];
+                const T* Nb = &S.u.r.N[0][sl];
+                T nu[NU][NU];
+#pragma unroll
+                for (int a = 0; a < NU; ++a)
+#pragma unroll
+                    for (int b = 0; b < NU; ++b) nu[a][b] = Nb[((NX + a) * NU + b) * A];
+                T* grow = go ? P.stg + srow(P, L.pos, t, 0) : nullptr;
+#pragma unroll 1
+                for (int c = L.w; c < NX; c += NW) {
+                    T qc[NU], z[NU], y[NU], nc[NU];
+#pragma unroll
+                    for (int b = 0; b < NU; ++b) nc[b] = Nb[(c * NU + b) * A];
+#pragma unroll
+                    for (int a = 0; a < NU; ++a) {
+                        T s = Qt[qidx(c, NX + a) * A];
+#pragma unroll
+                        for (int b = 0; b < NU; ++b) s -= nc[b] * nu[a][b];
+                        qc[a] = s;
+                    }
+                    // forward solve L z = qc on the free set (masked factor: clamped rows give 0)
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        T s = ((mask >> i) & 1) ? qc[i] : T(0);
+#pragma unroll
+                        for (int k = 0; k < i; ++k) s -= Lf[lidx(i, k)] * z[k];
+                        z[i] = s * Lf[10 + i];
+                    }
+                    // back solve L' y = z
+#pragma unroll
+                    for (int i = 3; i >= 0; --i) {
+                        T s = z[i];
+#pragma unroll
+                        for (int k = i + 1; k < 4; ++k) s -= Lf[lidx(k, i)] * y[k];
+                        y[i] = s * Lf[10 + i];
+                    }
+                    T vc = S.u.r.q[t & 1][c][sl];
+#pragma unroll
+                    for (int a = 0; a < NU; ++a) {
+                        vc += qc[a] * kk[a];
+                        const T kc = ((mask >> a) & 1) ? -y[a] : T(0);
+                        S.u.r.M[c * NU + a][sl] = go ? z[a] : T(0);
+                        S.K[a * NX + c][sl] = go ? kc : T(0);
+                        if (go) grow[(R_K + a * NX + c) * GW] = kc;
+                    }
+                    S.u.r.v[c][sl] = go ? vc : T(0);
+                }
+                if (L.w == 0 && go) {
+#pragma unroll
+                    for (int a = 0; a < NU; ++a) grow[(R_KK + a) * GW] = kk[a];
                 }
             }
-            tangent_step<T, NW>(P, S, L, t - 1, n, alive && n > 0);
             __syncthreads();
-            if (on && !S.ok[l]) alive = false;
-            const bool go = on && alive;
-            // (C) K_t, V_t, v_t
-            stage_copy(t - 2);
-            if (go) {
-                // the factor, k_t and Q_xu in registers, then two of this
-                // warp's columns c per loop trip: column c of K_t by the masked
-                // solve, the upper part of column c of V_t = Q_xx + Q_xu K_t and
-                // v_t[c] = q_x[c] + Q_xu[c, :] k_t
-                constexpr int NK = Split<NW>::NK;
-                T Lf[NL], kk[NU], qxu[NX][NU];
-                const int mask = S.mask[l];
-#pragma unroll
-                for (int i = 0; i < NL; ++i) Lf[i] = S.L[i][l];
-#pragma unroll
-                for (int a = 0; a < NU; ++a) kk[a] = S.k[a][l];
-#pragma unroll
-                for (int i = 0; i < NX; ++i)
-#pragma unroll
-                    for (int a = 0; a < NU; ++a) qxu[i][a] = S.u.r.Q[qidx(i, NX + a)][l];
-                T* grow = P.stg + srow(P, L.pos, t, 0);
+            if (vform) {
+                // V_t = Q_xx,t + Q_xu,t K_t in place of Q_xx,t (columns c
+                // round-robin; in this form N_t = 0, so Q_t = P_t), then
+                // P_{t-1} = C + F' V_t F
+                T* Qt = &S.u.r.Q[t & 1][0][sl];
 #pragma unroll 1
-                for (int s0 = 0; s0 < NK; s0 += 2) {
-                    int cp[2];
-                    T kc[2][NU], qc[2][NU], qxx[2][NX], qv[2];
+                for (int c = L.w; c < NX; c += NW) {
+                    T kc[NU];
 #pragma unroll
-                    for (int h = 0; h < 2; ++h) {
-                        cp[h] = s0 + h < NK ? Split<NW>::kcol(L.w, s0 + h) : -1;
-                        const int cc = cp[h] < 0 ? 0 : cp[h];
+                    for (int a = 0; a < NU; ++a) kc[a] = S.K[a * NX + c][sl];
+#pragma unroll 1
+                    for (int i = 0; i <= c; ++i) {
+                        T s = Qt[qidx(i, c) * A];
 #pragma unroll
-                        for (int a = 0; a < NU; ++a) qc[h][a] = S.u.r.Q[qidx(cc, NX + a)][l];
-#pragma unroll
-                        for (int i = 0; i < NX; ++i) qxx[h][i] = S.u.r.Q[qidx(i, cc)][l];
-                        qv[h] = S.u.r.q[cc][l];
+                        for (int a = 0; a < NU; ++a) s += Qt[qidx(i, NX + a) * A] * kc[a];
+                        Qt[qidx(i, c) * A] = s;
                     }
-                    if (cp[0] < 0) break;
+                }
+                __syncthreads();
+                if (t >= 1 && L.w >= 1) form_p<T, NW>(P, S, L, t - 1, alive && t - 1 < n);
+            }
+            // ---- phase 3: rows j of N_{t-1} = F_{t-1}' M_t (zero in the V form) and q_{t-1} = c_{t-1} + F_{t-1}' v_t
+            if (t >= 1) {
+                const int s = t - 1;
+                const bool ons = alive && s < n;
+                const T* cs = &S.u.r.cst[s % 3][0][sl];
+                const T* Fb = &S.u.r.F[s & 1][0][sl];
+                T Mr[NX][NU], vv[NX];
 #pragma unroll
-                    for (int h = 0; h < 2; ++h) {
-                        T rhs[4], y[4];
+                for (int i = 0; i < NX; ++i) {
+                    vv[i] = S.u.r.v[i][sl];
 #pragma unroll
-                        for (int a = 0; a < 4; ++a) rhs[a] = ((mask >> a) & 1) ? qc[h][a] : T(0);
-                        chol_solve4(Lf, rhs, y);
-#pragma unroll
-                        for (int a = 0; a < 4; ++a) kc[h][a] = ((mask >> a) & 1) ? -y[a] : T(0);
-                    }
-#pragma unroll
-                    for (int h = 0; h < 2; ++h) {
-                        const int c = cp[h];
-                        if (c < 0) continue;
-                        T s3 = qv[h];
+                    for (int a = 0; a < NU; ++a) Mr[i][a] = vform ? T(0) : S.u.r.M[i * NU + a][sl];
+                }
+#pragma unroll 1
+                for (int j = L.w; j < NZ; j += NW) {
+                    T Cd, c;
+                    cost_row(S, cs, sl, j, o.use_lo, Cd, c);
+                    T nj[NU], qj;
+                    if (j < 3 || (j >= 7 && j < 10)) {
+                        const int p = j < 3 ? j : j - 7;
+                        const bool vel = j >= 7;
 #pragma unroll
                         for (int a = 0; a < NU; ++a) {
-                            s3 += qc[h][a] * kk[a];
-                            S.K[a * NX + c][l] = kc[h][a];
-                            grow[(R_K + a * NX + c) * LW] = kc[h][a];
+                            const T mj = S.u.r.M[j * NU + a][sl];
+                            const T m = vel ? mj + hv * S.u.r.M[p * NU + a][sl] : mj;
+                            nj[a] = vform ? T(0) : m;
                         }
-                        S.v[c][l] = s3;
+                        qj = c + (vel ? S.u.r.v[j][sl] + hv * S.u.r.v[p][sl] : S.u.r.v[j][sl]);
+                    } else {
+                        const int jj = j < 7 ? j - 3 : j - 6;
+                        T f[NX];
 #pragma unroll
-                        for (int i = 0; i < NX; ++i) {
-                            T s2 = qxx[h][i];
+                        for (int i = 0; i < NX; ++i) f[i] = Fb[(jj * NX + i) * A];
 #pragma unroll
-                            for (int a = 0; a < NU; ++a) s2 += qxu[i][a] * kc[h][a];
-                            if (i <= c) S.V[vidx(i, c)][l] = s2;
+                        for (int a = 0; a < NU; ++a) {
+                            T mc[NX];
+#pragma unroll
+                            for (int i = 0; i < NX; ++i) mc[i] = Mr[i][a];
+                            nj[a] = dot13(f, mc);
+                        }
+                        qj = c + dot13(f, vv);
+                        if (o.tape && ons) {
+#pragma unroll
+                            for (int i = 0; i < NX; ++i) o.tape[trow(P, L.b, s, T_F + jj * NX + i)] = f[i];
                         }
                     }
-                }
-                if (L.w == 0) {
 #pragma unroll
-                    for (int a = 0; a < NU; ++a) grow[(R_KK + a) * LW] = kk[a];
+                    for (int a = 0; a < NU; ++a) S.u.r.N[j * NU + a][sl] = ons ? nj[a] : T(0);
+                    S.u.r.q[s & 1][j][sl] = ons ? qj : T(0);
                 }
             }
-            __syncthreads();
             if (o.tape && go) {
-                const int mask = S.mask[l];
-                for (int e = L.w; e < TREC; e += NW) {
+                const int mask = S.mask[sl];
+                for (int e = T_K + L.w; e < TREC; e += NW) {
                     T val;
-                    if (e < T_K) val = S.u.r.F[t & 1][e][l];
-                    else if (e < T_L) val = S.K[e - T_K][l];
-                    else if (e < T_M) val = S.L[e - T_L][l];
+                    if (e < T_L) val = S.K[e - T_K][sl];
+                    else if (e < T_M) val = S.L[e - T_L][sl];
                     else val = T(mask);
                     o.tape[trow(P, L.b, t, e)] = val;
                 }
             }
-            Fp = &S.u.r.F[t & 1][0][l];
-            Kp = &S.K[0][l];
-            Lp = &S.L[0][l];
-            amask = S.mask[l];
+            cp_async_wait_all();
+            __syncthreads();
+            Kp = &S.K[0][sl];
+            Lp = &S.L[0][sl];
+            Fp = &S.u.r.F[(t + 1) & 1][0][sl];                       // F_{t-1}
+            amask = go ? S.mask[sl] : 0;
             ago = go;
         }
-        if (o.adj) adjoint_step<T, NW>(P, S, L, t, ago, *o.adj, Fp, Kp, Lp, amask);
+        if (o.adj) adjoint_step<T, NW>(P, S, L, t, n, ago, *o.adj, Kp, Lp, amask, Fp);
     }
     return alive;
 }
@@ -1207,15 +1336,16 @@ __device__ bool riccati(const Params<T>& P, BlockSmem<T>& S, const Lane& L, int 
 // finite cost: nominal kept).
 template <typename T, int NW>
 __device__ int line_search(const Params<T>& P, BlockSmem<T>& S, const Lane& L, int n, T& Jnom, T& du_out) {
-    const int l = L.l;
+    constexpr int A = SL<T>::A;
+    const int sl = L.sl;
     const int nmax = __reduce_max_sync(FULL, n);
     const bool cl = n > 0 && L.w < P.n_alpha;
     const T alpha = L.w == 0 ? P.alpha[0] : (L.w == 1 ? P.alpha[1] : (L.w == 2 ? P.alpha[2] : P.alpha[3]));
     auto issue = [&](int tt) {
         if (tt < n) {
-            T* dst = &S.u.s.stg[tt & 1][0][l];
+            T* dst = &S.u.s.stg[tt & 1][0][sl];
             const T* src = P.stg + srow(P, L.pos, tt, 0);
-            for (int e = L.w; e < SREC; e += NW) cp_async(dst + e * LW, src + e * LW);
+            for (int e = L.w; e < SREC; e += NW) cp_async(dst + e * A, src + e * GW);
         }
         cp_async_commit();
     };
@@ -1224,26 +1354,28 @@ __device__ int line_search(const Params<T>& P, BlockSmem<T>& S, const Lane& L, i
     __syncthreads();
     T xh[NX], xl[NX], R[NU], ur[NU], ulo[NU], uhi[NU];
 #pragma unroll
-    for (int i = 0; i < NX; ++i) { xh[i] = S.x0[i][l]; xl[i] = T(0); }
+    for (int i = 0; i < NX; ++i) { xh[i] = S.x0[i][sl]; xl[i] = T(0); }
 #pragma unroll
-    for (int a = 0; a < NU; ++a) { R[a] = S.R[a][l]; ur[a] = S.uref[a][l]; ulo[a] = S.ulo[a][l]; uhi[a] = S.uhi[a][l]; }
+    for (int a = 0; a < NU; ++a) {
+        R[a] = S.R[a][sl]; ur[a] = S.uref[a][sl]; ulo[a] = S.ulo[a][sl]; uhi[a] = S.uhi[a][sl];
+    }
     T dJ = T(0), dJl = T(0), dmx = T(0);
     const int c = L.w & 3;
     for (int t = 0; t < nmax; ++t) {
         issue(t + 1);
         if (cl && t < n) {
-            const T* sb = &S.u.s.stg[t & 1][0][l];
+            const T* sb = &S.u.s.stg[t & 1][0][sl];
             T dxv[NX], uh[NU];
 #pragma unroll
-            for (int i = 0; i < NX; ++i) dxv[i] = (xh[i] - sb[(R_X + i) * LW]) + (xl[i] - sb[(R_XL + i) * LW]);
+            for (int i = 0; i < NX; ++i) dxv[i] = (xh[i] - sb[(R_X + i) * A]) + (xl[i] - sb[(R_XL + i) * A]);
             T sx = T(0), su = T(0);
 #pragma unroll
             for (int a = 0; a < NU; ++a) {
                 T s = T(0);
 #pragma unroll
-                for (int i = 0; i < NX; ++i) s += sb[(R_K + a * NX + i) * LW] * dxv[i];
-                const T ub = sb[(R_U + a) * LW];
-                const T un = ub + alpha * sb[(R_KK + a) * LW] + s;
+                for (int i = 0; i < NX; ++i) s += sb[(R_K + a * NX + i) * A] * dxv[i];
+                const T ub = sb[(R_U + a) * A];
+                const T un = ub + alpha * sb[(R_KK + a) * A] + s;
                 uh[a] = clampT(un, ulo[a], uhi[a]);
                 const T d = uh[a] - ub;
                 su += d * (R[a] * ((ub - ur[a]) + T(0.5) * d));
@@ -1252,18 +1384,18 @@ __device__ int line_search(const Params<T>& P, BlockSmem<T>& S, const Lane& L, i
             }
 #pragma unroll
             for (int i = 0; i < NX; ++i) {
-                const T eb = (sb[(R_X + i) * LW] - sb[(R_XR + i) * LW]) + sb[(R_XL + i) * LW];
-                sx += dxv[i] * (sb[(R_Q + i) * LW] * (eb + T(0.5) * dxv[i]));
+                const T eb = (sb[(R_X + i) * A] - sb[(R_XR + i) * A]) + sb[(R_XL + i) * A];
+                sx += dxv[i] * (sb[(R_Q + i) * A] * (eb + T(0.5) * dxv[i]));
             }
             acc2(dJ, dJl, sx + su);
             T* cr = P.cand + crow(P, c, L.pos, t, 0);
 #pragma unroll
             for (int i = 0; i < NX; ++i) {
-                cr[i * LW] = xh[i];
-                cr[(NX + i) * LW] = xl[i];
+                cr[i * GW] = xh[i];
+                cr[(NX + i) * GW] = xl[i];
             }
 #pragma unroll
-            for (int a = 0; a < NU; ++a) cr[(2 * NX + a) * LW] = uh[a];
+            for (int a = 0; a < NU; ++a) cr[(2 * NX + a) * GW] = uh[a];
             if (t < n - 1) rk4_step2(P.mdl, xh, xl, uh);
         }
         cp_async_wait_all();
@@ -1271,16 +1403,16 @@ __device__ int line_search(const Params<T>& P, BlockSmem<T>& S, const Lane& L, i
     }
     if (cl) {
         dJ = dJ + dJl;
-        S.Jc[L.w][l] = finiteT(dJ) ? dJ : T(INFINITY);
-        S.dmax[L.w][l] = dmx;
+        S.Jc[L.w][sl] = finiteT(dJ) ? dJ : T(INFINITY);
+        S.dmax[L.w][sl] = dmx;
     }
     __syncthreads();
     int r = 0;
     if (n > 0) {
         int best = 0;
-        T Jb = S.Jc[0][l];
+        T Jb = S.Jc[0][sl];
         for (int k = 1; k < P.n_alpha; ++k)
-            if (S.Jc[k][l] < Jb) { Jb = S.Jc[k][l]; best = k; }
+            if (S.Jc[k][sl] < Jb) { Jb = S.Jc[k][sl]; best = k; }
         if (!finiteT(Jb)) {
             r = 1;
         } else {
@@ -1290,12 +1422,12 @@ __device__ int line_search(const Params<T>& P, BlockSmem<T>& S, const Lane& L, i
                 T* dr = P.stg + srow(P, L.pos, t, R_X);
                 T buf[CREC];
 #pragma unroll
-                for (int e = 0; e < CREC; ++e) buf[e] = cr[e * LW];
+                for (int e = 0; e < CREC; ++e) buf[e] = cr[e * GW];
 #pragma unroll
-                for (int e = 0; e < CREC; ++e) dr[e * LW] = buf[e];
+                for (int e = 0; e < CREC; ++e) dr[e * GW] = buf[e];
             }
             Jnom = Jnom + Jb;
-            du_out = S.dmax[best][l];
+            du_out = S.dmax[best][sl];
         }
     }
     __syncthreads();
@@ -1316,7 +1448,7 @@ __device__ void adjoint_forward(const Params<T>& P, const BlockSmem<T>& S, const
     const size_t b = L.b;
     T dx[NX], dq[NX];
 #pragma unroll
-    for (int i = 0; i < NX; ++i) { dx[i] = T(0); dq[i] = T(0); A.dx0[b * NX + i] = S.vh[i][L.l]; }
+    for (int i = 0; i < NX; ++i) { dx[i] = T(0); dq[i] = T(0); A.dx0[b * NX + i] = S.vh[i][L.sl]; }
     for (int t = 0; t < n; ++t) {
         // the stage's operands first
         const T* kr = A.recompute ? P.stg + srow(P, L.pos, t, R_K) : P.tape + trow(P, L.b, t, T_K);
@@ -1325,7 +1457,7 @@ __device__ void adjoint_forward(const Params<T>& P, const BlockSmem<T>& S, const
         const T* Qt = Qrow(P, L.b, t);
         T K[NU * NX], kh[NU], xv[NX], xrv[NX], qv[NX], us[NU];
 #pragma unroll
-        for (int e = 0; e < NU * NX; ++e) K[e] = kr[e * LW];
+        for (int e = 0; e < NU * NX; ++e) K[e] = kr[e * GW];
 #pragma unroll
         for (int a = 0; a < NU; ++a) {
             kh[a] = P.kh[khrow(P, L.pos, t, a)];
@@ -1388,9 +1520,9 @@ __device__ void write_solution(const Params<T>& P, const Lane& L, int n) {
         if (t < n) {
             const T* sr = P.stg + srow(P, L.pos, t, 0);
 #pragma unroll
-            for (int i = 0; i < NX; ++i) buf[i] = sr[(R_X + i) * LW];
+            for (int i = 0; i < NX; ++i) buf[i] = sr[(R_X + i) * GW];
 #pragma unroll
-            for (int a = 0; a < NU; ++a) buf[NX + a] = sr[(R_U + a) * LW];
+            for (int a = 0; a < NU; ++a) buf[NX + a] = sr[(R_U + a) * GW];
         }
 #pragma unroll
         for (int i = 0; i < NX; ++i) xo[i] = buf[i];

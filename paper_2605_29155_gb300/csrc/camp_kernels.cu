@@ -1,8 +1,8 @@
 // camp_kernels.cu -- the kernel and launch sequences of the batched MPC layer.
 //
 // One kernel template, k_mpc<T, NW>, runs every phase of the method through a
-// phase machine over a pack of up to 32 instances (one instance per lane, NW
-// warps per block splitting each instance's work).  Every phase has exactly
+// phase machine over a pack of up to 32 instances (16 in FP64; one instance
+// per lane, NW warps per block splitting each instance's work).  Every phase has exactly
 // one call site, so every launch form executes the same machine code for it
 // and gives bit-identical results.
 //
@@ -78,7 +78,8 @@ __global__ void __launch_bounds__(NW * 32, 8 / NW) k_mpc(const __grid_constant__
         }
         if (base >= P.B) break;
         L.pos = base + L.l;
-        L.valid = L.l < P.ipb && L.pos < P.B;
+        L.valid = L.l < P.ipb && L.l < SL<T>::W && L.pos < P.B;
+        L.sl = L.l < SL<T>::W ? L.l : SL<T>::W;
         L.b = L.valid ? (P.order ? P.order[L.pos] : L.pos) : 0;
         int nh = P.horizon ? P.horizon[L.b] : P.N;
         nh = nh < 1 ? 1 : (nh > P.N ? P.N : nh);
@@ -106,7 +107,7 @@ __global__ void __launch_bounds__(NW * 32, 8 / NW) k_mpc(const __grid_constant__
                 __syncthreads();
                 initial_rollout<T, NW>(P, S, L, act ? n : 0);
                 __syncthreads();
-                J = S.Jc[0][L.l];
+                J = S.Jc[0][L.sl];
                 if (act) {
                     if (!finiteT(J)) status = ST_NONFINITE;
                     else if (P.max_iter == 0) status = ST_MAX_ITER;
