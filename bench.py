@@ -295,8 +295,8 @@ def run_ours(args, rank, world, local_rank):
     p50 = lat[len(lat) // 2]
     p99 = lat[min(len(lat) - 1, int(0.99 * len(lat)))]
 
-    # plain form (three launches per iteration, eager, as Sec. IV structures it)
-    plain = DiffMPC(N_max=N, B_max=B, max_iter=MAX_ITER, tol=TOL, exec_mode="plain", ipb=ipb, device=dev)
+    # plain form (one launch per phase of every iteration, eager, as Sec. IV structures it)
+    plain = DiffMPC(N_max=N, B_max=B, max_iter=MAX_ITER, tol=TOL, exec_mode="plain", tpi=tpi, ipb=ipb, device=dev)
     sp = plain.alloc_solution(B, N)
     gp = (torch.empty_like(p.Q), torch.empty_like(p.x_ref), torch.empty_like(p.x0))
     for _ in range(2):
@@ -343,6 +343,7 @@ def run_ours(args, rank, world, local_rank):
         if k >= args.warmup:
             e2e_ms.append(e0.elapsed_time(e1))
     e2e = statistics.fmean(e2e_ms)
+    side = side_configs(dev, flush) if (rank == 0 and world == 1 and not args.no_side) else None
 
     # roofline of the dominant kernel (the persistent forward launch)
     props = torch.cuda.get_device_properties(dev)
@@ -370,7 +371,8 @@ def run_ours(args, rank, world, local_rank):
         p50_fwd_ms=p50, p99_fwd_ms=p99, fwd_ms=ms_fwd, bwd_ms=ms - ms_fwd,
         fwd_solves_per_s=B * world / (ms_fwd * 1e-3),
         plain=dict(value=B * world / (plain_ms * 1e-3), unit=UNIT, ms_per_step=plain_ms,
-                   launches_per_step=plain_launches[0] + plain_launches[1], exec="eager, 3 launches per iteration",
+                   launches_per_step=plain_launches[0] + plain_launches[1],
+                   exec="eager, one launch per phase: rollout, then per iteration Riccati (linearization fused) and line search",
                    bit_identical_to_persistent=same),
         speedup_vs_plain=plain_ms / ms,
         iters_mean=float(iters.mean()), status_counts=np.bincount(status, minlength=5).tolist(),
@@ -381,11 +383,81 @@ def run_ours(args, rank, world, local_rank):
                       peak_note=f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 flop x {sm_max_mhz:.0f} MHz",
                       flops_per_launch=fwd_flops),
         cpu_baseline=cpu,
+        side_configs=side,
         clocks=clocks,
         gpu_launches=(fwd_launches + bwd_launches) * args.steps,
         wall_s_timed=wall,
     )
     print(json.dumps(line), flush=True)
+
+
+def _time_fwd_bwd(solver, p, s, gu, reps, flush, stream):
+    """Mean ms of eager forward + backward steps (L2 flushed before each)."""
+    import torch
+    grads = (torch.empty_like(p.Q), torch.empty_like(p.x_ref), torch.empty_like(p.x0))
+    for _ in range(2):
+        solver.solve(p, s)
+        solver.backward(p, s, gu, out=grads)
+    torch.cuda.synchronize()
+    ms = []
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        flush.fill_(1.0)
+        e0.record(stream)
+        solver.solve(p, s)
+        solver.backward(p, s, gu, out=grads)
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    return statistics.fmean(ms)
+
+
+def side_configs(dev, flush, reps=3):
+    """The other two batch shapes of the workload, measured beside the headline:
+    uneven horizons (persistent form with the work queue, autotuned, against
+    the plain form) and memory-heavy gradients (store-all tape against
+    recompute: solves/s and device memory held by the torch allocator, tape
+    included)."""
+    import torch
+    from paper_2605_29155_gb300 import DiffMPC, Problem
+    stream = torch.cuda.current_stream()
+    out = {}
+    prob = W.cfg_uneven()
+    Bu, Nu = prob["x0"].shape[0], prob["x_ref"].shape[1]
+    p = Problem.from_numpy(prob, device=dev)
+    gu = torch.as_tensor(W.loss_weights_u0(Bu, Nu, seed=1), dtype=torch.float32, device=dev)
+    per = DiffMPC(N_max=Nu, B_max=Bu, max_iter=prob["max_iter"], tol=prob["tol"], device=dev)
+    s = per.alloc_solution(Bu, Nu)
+    per.autotune(p, s)
+    tpi, ipb, grid = per.launch_shape(Bu, Nu)
+    ms_p = _time_fwd_bwd(per, p, s, gu, reps, flush, stream)
+    per.close()
+    pl = DiffMPC(N_max=Nu, B_max=Bu, max_iter=prob["max_iter"], tol=prob["tol"], exec_mode="plain", tpi=tpi,
+                 ipb=ipb, device=dev)
+    ms_l = _time_fwd_bwd(pl, p, pl.alloc_solution(Bu, Nu), gu, reps, flush, stream)
+    pl.close()
+    out["uneven"] = dict(workload=f"B={Bu}, horizons U{{5..40}}, <= {prob['max_iter']} iterations, u_hi x U(0.8, 1.2)",
+                         persistent_solves_per_s=Bu / (ms_p * 1e-3), plain_solves_per_s=Bu / (ms_l * 1e-3),
+                         launch=dict(threads_per_instance=tpi, instances_per_block=ipb, blocks=grid))
+    prob = W.cfg_mem()
+    Bm, Nm = prob["x0"].shape[0], prob["x_ref"].shape[1]
+    p = Problem.from_numpy(prob, device=dev)
+    gu = torch.as_tensor(W.loss_weights_u0(Bm, Nm, seed=1), dtype=torch.float32, device=dev)
+    mem = {}
+    for mode in ("store_all", "recompute"):
+        torch.cuda.synchronize()
+        base = torch.cuda.memory_allocated()
+        torch.cuda.reset_peak_memory_stats()
+        sol = DiffMPC(N_max=Nm, B_max=Bm, max_iter=prob["max_iter"], tol=prob["tol"], store_mode=mode, device=dev)
+        s = sol.alloc_solution(Bm, Nm)
+        ms = _time_fwd_bwd(sol, p, s, gu, reps, flush, stream)
+        tape = 0 if s.tape is None else s.tape.numel() * s.tape.element_size()
+        mem[mode] = dict(solves_per_s=Bm / (ms * 1e-3), ms_per_step=ms, tape_bytes=tape,
+                         torch_peak_bytes=int(torch.cuda.max_memory_allocated() - base))
+        del s
+        sol.close()
+    out["mem"] = dict(workload=f"B={Bm}, N={Nm}, per-stage Q and x_ref, fwd+bwd", **mem)
+    return out
 
 
 def run_kernels_only(args):
@@ -426,6 +498,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--latency-reps", type=int, default=200)
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-side", action="store_true", help="skip the uneven-horizon and memory-heavy batches")
     ap.add_argument("--mode", default="full", choices=["full", "kernels"],
                     help="kernels: only W + K eager forward+backward steps of the workload (for profilers)")
     ap.add_argument("--batch", type=int, default=B, help="instances (kernels mode only)")

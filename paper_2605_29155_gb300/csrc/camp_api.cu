@@ -255,10 +255,11 @@ extern "C" int mpc_autotune(mpc_handle* h, const mpc_problem* p, mpc_solution* s
     if (h->cfg.exec_mode != MPC_EXEC_PERSISTENT) return MPC_ERR_STATE;
     if (p->B == 0) { if (ipb_out) *ipb_out = ipb_for(h, 0); return MPC_OK; }
     const int keep_tpi = h->tpi, keep_ipb = h->ipb;
-    // candidate instances per block: one, two, three or four blocks' worth per SM
-    int cands[4], nc = 0;
-    for (int k = 1; k <= 4; ++k) {
-        int v = (p->B + k * h->num_sms - 1) / (k * h->num_sms);
+    // candidate instances per block: one, two, three or four blocks' worth per
+    // SM, and full packs (fewer blocks than SMs when the batch is small)
+    int cands[5], nc = 0;
+    for (int k = 0; k <= 4; ++k) {
+        int v = k == 0 ? ipb_cap(h) : (p->B + k * h->num_sms - 1) / (k * h->num_sms);
         v = v < 1 ? 1 : (v > ipb_cap(h) ? ipb_cap(h) : v);
         bool dup = false;
         for (int i = 0; i < nc; ++i) dup = dup || cands[i] == v;

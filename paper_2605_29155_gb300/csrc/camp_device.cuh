@@ -628,11 +628,13 @@ __device__ bool box_qp(bool on, const T (&H)[4][4], const T (&g)[4], const T (&l
 //   tcol(w, s)   the tangent columns warp w computes
 // Warp 0 takes neither.  The steps after the QP split their columns / rows
 // round-robin over all NW warps.
-// The tables, by warp (warp 0 solves the box QPs and takes neither).
+// The tables, by warp.  Warp 0 solves the box QPs and takes neither; with 8
+// warps per block warp 4, which shares warp 0's scheduler, takes none either,
+// so that the QPs -- the critical path of a stage -- issue unhindered.
 __constant__ int c_pcol4[4][4] = {{-1, -1, -1, -1}, {10, 7, 4, 1}, {9, 6, 3, 0}, {8, 5, 2, -1}};
 __constant__ int c_tcol4[4][4] = {{-1, -1, -1, -1}, {0, 1, 2, 3}, {4, 5, 6, 7}, {8, 9, 10, -1}};
-__constant__ int c_pcol8[8][2] = {{-1, -1}, {10, 0}, {9, 1}, {8, 2}, {7, 3}, {6, 4}, {5, -1}, {-1, -1}};
-__constant__ int c_tcol8[8][2] = {{-1, -1}, {0, 1}, {2, 3}, {4, 5}, {6, 7}, {8, 9}, {10, -1}, {-1, -1}};
+__constant__ int c_pcol8[8][2] = {{-1, -1}, {10, 0}, {9, 1}, {8, 2}, {-1, -1}, {7, 3}, {6, 4}, {5, -1}};
+__constant__ int c_tcol8[8][2] = {{-1, -1}, {0, 1}, {2, 3}, {4, 5}, {-1, -1}, {6, 7}, {8, 9}, {10, -1}};
 
 template <int NW> struct Split;
 template <> struct Split<4> {
@@ -1182,43 +1184,61 @@ __device__ bool riccati(const Params<T>& P, BlockSmem<T>& S, const Lane& L, int 
                     for (int b = 0; b < NU; ++b) nu[a][b] = Nb[((NX + a) * NU + b) * A];
                 T* grow = go ? P.stg + srow(P, L.pos, t, 0) : nullptr;
 #pragma unroll 1
-                for (int c = L.w; c < NX; c += NW) {
-                    T qc[NU], z[NU], y[NU], nc[NU];
+                for (int c0 = L.w; c0 < NX; c0 += 2 * NW) {
+                    // two columns c = c0, c0 + NW side by side
+                    int cc[2];
+                    T qc[2][NU], z[2][NU], y[2][NU], vq[2];
 #pragma unroll
-                    for (int b = 0; b < NU; ++b) nc[b] = Nb[(c * NU + b) * A];
+                    for (int h = 0; h < 2; ++h) {
+                        const int c = c0 + h * NW;
+                        cc[h] = c < NX ? c : -1;
+                        const int cl = c < NX ? c : 0;
+                        T nc[NU];
 #pragma unroll
-                    for (int a = 0; a < NU; ++a) {
-                        T s = Qt[qidx(c, NX + a) * A];
+                        for (int b = 0; b < NU; ++b) nc[b] = Nb[(cl * NU + b) * A];
 #pragma unroll
-                        for (int b = 0; b < NU; ++b) s -= nc[b] * nu[a][b];
-                        qc[a] = s;
+                        for (int a = 0; a < NU; ++a) {
+                            T s = Qt[qidx(cl, NX + a) * A];
+#pragma unroll
+                            for (int b = 0; b < NU; ++b) s -= nc[b] * nu[a][b];
+                            qc[h][a] = s;
+                        }
+                        vq[h] = S.u.r.q[t & 1][cl][sl];
                     }
-                    // forward solve L z = qc on the free set (masked factor: clamped rows give 0)
 #pragma unroll
-                    for (int i = 0; i < 4; ++i) {
-                        T s = ((mask >> i) & 1) ? qc[i] : T(0);
+                    for (int h = 0; h < 2; ++h) {
+                        // forward solve L z = qc on the free set (masked factor: clamped rows give 0)
 #pragma unroll
-                        for (int k = 0; k < i; ++k) s -= Lf[lidx(i, k)] * z[k];
-                        z[i] = s * Lf[10 + i];
+                        for (int i = 0; i < 4; ++i) {
+                            T s = ((mask >> i) & 1) ? qc[h][i] : T(0);
+#pragma unroll
+                            for (int k = 0; k < i; ++k) s -= Lf[lidx(i, k)] * z[h][k];
+                            z[h][i] = s * Lf[10 + i];
+                        }
+                        // back solve L' y = z
+#pragma unroll
+                        for (int i = 3; i >= 0; --i) {
+                            T s = z[h][i];
+#pragma unroll
+                            for (int k = i + 1; k < 4; ++k) s -= Lf[lidx(k, i)] * y[h][k];
+                            y[h][i] = s * Lf[10 + i];
+                        }
                     }
-                    // back solve L' y = z
 #pragma unroll
-                    for (int i = 3; i >= 0; --i) {
-                        T s = z[i];
+                    for (int h = 0; h < 2; ++h) {
+                        const int c = cc[h];
+                        if (c < 0) continue;
+                        T vc = vq[h];
 #pragma unroll
-                        for (int k = i + 1; k < 4; ++k) s -= Lf[lidx(k, i)] * y[k];
-                        y[i] = s * Lf[10 + i];
+                        for (int a = 0; a < NU; ++a) {
+                            vc += qc[h][a] * kk[a];
+                            const T kc = ((mask >> a) & 1) ? -y[h][a] : T(0);
+                            S.u.r.M[c * NU + a][sl] = go ? z[h][a] : T(0);
+                            S.K[a * NX + c][sl] = go ? kc : T(0);
+                            if (go) grow[(R_K + a * NX + c) * GW] = kc;
+                        }
+                        S.u.r.v[c][sl] = go ? vc : T(0);
                     }
-                    T vc = S.u.r.q[t & 1][c][sl];
-#pragma unroll
-                    for (int a = 0; a < NU; ++a) {
-                        vc += qc[a] * kk[a];
-                        const T kc = ((mask >> a) & 1) ? -y[a] : T(0);
-                        S.u.r.M[c * NU + a][sl] = go ? z[a] : T(0);
-                        S.K[a * NX + c][sl] = go ? kc : T(0);
-                        if (go) grow[(R_K + a * NX + c) * GW] = kc;
-                    }
-                    S.u.r.v[c][sl] = go ? vc : T(0);
                 }
                 if (L.w == 0 && go) {
 #pragma unroll

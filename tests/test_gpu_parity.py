@@ -123,10 +123,13 @@ def test_recompute_backward_is_bit_identical_to_store_all(dtype):
                                             ("float64", 8, 7)])
 def test_launch_shapes_agree(dtype, tpi, ipb):
     """Every launch shape runs the same per-instance arithmetic.  Results are
-    bit-identical across instances per block, and across threads per instance
-    in FP64; in FP32 a different threads-per-instance count is a different
-    compiled kernel whose rounding can differ (fused multiply-add choices),
-    so there converged instances must agree to the parity tolerance."""
+    bit-identical across instances per block (the same compiled kernel).  A
+    different threads-per-instance count is a different compiled kernel whose
+    rounding can differ (the compiler's fused multiply-add choices), and a
+    rounding-level difference can move a solve's convergence test by one
+    iteration: there instances converged in both agree to the tolerance of a
+    converged solve (FP64: 1e-6, the last step is below tol; FP32: the parity
+    tolerance)."""
     dt = getattr(torch, dtype)
     prob = cached_problem("track", 70, 20, 4, True)
     gu, gx = _grads(70, 20, 9)
@@ -134,14 +137,14 @@ def test_launch_shapes_agree(dtype, tpi, ipb):
     ref = run_gpu(prob, dt, 8, 1e-6, gu, gx, tpi=ref_tpi, ipb=4)
     got = run_gpu(prob, dt, 8, 1e-6, gu, gx, tpi=tpi, ipb=ipb)
     assert set(ref) == set(got)
-    if dtype == "float64" or tpi == ref_tpi:
+    if tpi == ref_tpi:
         for k in ref:
             np.testing.assert_array_equal(ref[k], got[k], err_msg=k)
     else:
         conv = (ref["status"] == 0) & (got["status"] == 0)
         assert conv.sum() >= 10
         err = np.linalg.norm(got["u"][conv] - ref["u"][conv], axis=(1, 2)) / np.linalg.norm(ref["u"][conv], axis=(1, 2))
-        assert err.max() <= U_TOL32
+        assert err.max() <= (U_TOL64C if dtype == "float64" else U_TOL32)
 
 
 # ------------------------------------------------------------- edge cases --
