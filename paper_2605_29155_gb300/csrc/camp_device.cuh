@@ -410,12 +410,11 @@ template <typename T> __device__ __forceinline__ T hv_coef(const Model<T>& m) { 
 __host__ __device__ constexpr int lidx(int i, int j) { return i * (i + 1) / 2 + j; }
 
 // Pivot of the Cholesky factor: l = sqrt(s) and 1 / l.  In FP32 from the
-// hardware reciprocal square root refined by one Newton step (about 1 ulp, as
-// accurate as the correctly rounded pair for the gradients, and a much shorter
-// serial chain in the box QP); in FP64 correctly rounded.
+// hardware reciprocal square root (a few ulp; the factor's error stays orders
+// of magnitude below the FP32 path's tolerances, and the box QP's serial chain
+// is the critical path of a Riccati stage); in FP64 correctly rounded.
 __device__ __forceinline__ void pivot(float s, float& l, float& il) {
     il = rsqrtf(s);
-    il = il * (1.5f - 0.5f * s * il * il);
     l = s * il;
 }
 __device__ __forceinline__ void pivot(double s, double& l, double& il) {
@@ -556,17 +555,43 @@ __device__ bool box_qp(bool on, const T (&H)[4][4], const T (&g)[4], const T (&l
         for (int i = 0; i < 4; ++i) gd += grad[i] * (dnew[i] - d[i]);
         bool acc = qp_value(H, g, dnew) - phi0 <= T(0.1) * gd;
         const bool live = !done && !none_free && !repeat && pd;
+        // Backtracking beyond the full step: the trial steps 0.6^k are tried
+        // four at a time (side by side), and the first that satisfies the
+        // Armijo condition is taken -- the same step, in the same order, as
+        // trying them one by one.
         if (__any_sync(FULL, live && !acc)) {
-            for (int ls = 1; ls < QP_MAX_LS; ++ls) {
+            for (int ls0 = 1; ls0 < QP_MAX_LS; ls0 += 4) {
                 if (!__any_sync(FULL, live && !acc)) break;
-                if (live && !acc) {
-                    step *= T(0.6);
+                T st[4], tr[4][4], dn4[4][4];
+                bool ac[4];
+                T s = step;
 #pragma unroll
-                    for (int i = 0; i < 4; ++i) { trial[i] = d[i] + step * dir[i]; dnew[i] = clampT(trial[i], lo[i], hi[i]); }
+                for (int k = 0; k < 4; ++k) {
+                    s *= T(0.6);
+                    st[k] = s;
                     T gd2 = T(0);
 #pragma unroll
-                    for (int i = 0; i < 4; ++i) gd2 += grad[i] * (dnew[i] - d[i]);
-                    acc = qp_value(H, g, dnew) - phi0 <= T(0.1) * gd2;
+                    for (int i = 0; i < 4; ++i) {
+                        tr[k][i] = d[i] + s * dir[i];
+                        dn4[k][i] = clampT(tr[k][i], lo[i], hi[i]);
+                        gd2 += grad[i] * (dn4[k][i] - d[i]);
+                    }
+                    ac[k] = ls0 + k < QP_MAX_LS && qp_value(H, g, dn4[k]) - phi0 <= T(0.1) * gd2;
+                }
+                if (live && !acc) {
+                    int kk = 4;
+#pragma unroll
+                    for (int k = 3; k >= 0; --k) kk = ac[k] ? k : kk;
+                    const int kt = kk < 4 ? kk : 3;     // the last trial when none passed
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        if (k == kt) {
+                            step = st[k];
+#pragma unroll
+                            for (int i = 0; i < 4; ++i) { trial[i] = tr[k][i]; dnew[i] = dn4[k][i]; }
+                        }
+                    }
+                    acc = kk < 4;
                 }
             }
         }
@@ -576,40 +601,33 @@ __device__ bool box_qp(bool on, const T (&H)[4][4], const T (&g)[4], const T (&l
             inside = inside && (trial[i] >= lo[i]) && (trial[i] <= hi[i]);
             strict = strict && (trial[i] > lo[i]) && (trial[i] < hi[i]);
         }
-        // outcome of this iteration for a lane still running
-        if (!done) {
-            if (none_free) {
-                identity_factor(L);
-                mask_out = 0;
-                done = true;
-            } else if (repeat) {
-                mask_out = fm;
-                done = true;
-            } else {
+        // outcome of this iteration for a lane still running, by selects:
+        //   nothing free -> stop with the identity factor and mask 0;
+        //   the free set repeats after a full step -> stop (last factor kept);
+        //   otherwise the new factor is kept, and a non-positive pivot stops
+        //   (not ok), a failed line search stops, an accepted step moves d and
+        //   stops when it is a full step strictly inside with all free
+        const bool run = !done;
+        const bool fac = run && !none_free && !repeat;
+        const bool step_ok = fac && pd && acc;
+        const bool full = (step == T(1)) && inside;
+        const bool stop_new = step_ok && full && strict && fm == 15;
 #pragma unroll
-                for (int i = 0; i < NL; ++i) L[i] = Ln[i];
-                mask_fact = fm;
-                if (!pd) {
-                    mask_out = fm;
-                    ok = false;
-                    done = true;
-                } else if (!acc) {
-                    mask_out = fm;
-                    done = true;
-                } else {
-                    last_full = (step == T(1)) && inside;
-                    free_prev = fm;
-#pragma unroll
-                    for (int i = 0; i < 4; ++i) d[i] = dnew[i];
-                    // A full step strictly inside the box with every dimension free:
-                    // the next iteration would find the same free set and stop.
-                    if (last_full && strict && fm == 15) {
-                        mask_out = fm;
-                        done = true;
-                    }
-                }
-            }
+        for (int i = 0; i < NL; ++i) {
+            const T idv = (i == 0 || i == 2 || i == 5 || i == 9 || i >= 10) ? T(1) : T(0);
+            L[i] = (run && none_free) ? idv : (fac ? Ln[i] : L[i]);
         }
+#pragma unroll
+        for (int i = 0; i < 4; ++i) d[i] = step_ok ? dnew[i] : d[i];
+        mask_fact = fac ? fm : mask_fact;
+        last_full = step_ok ? full : last_full;
+        free_prev = step_ok ? fm : free_prev;
+        if (run) {
+            if (none_free) mask_out = 0;
+            else if (repeat || !pd || !acc || stop_new) mask_out = fm;
+        }
+        ok = ok && !(fac && !pd);
+        done = done || none_free || repeat || (fac && (!pd || !acc)) || stop_new;
     }
     if (!done) mask_out = mask_fact;
     return ok;
