@@ -457,7 +457,59 @@ def side_configs(dev, flush, reps=3):
         del s
         sol.close()
     out["mem"] = dict(workload=f"B={Bm}, N={Nm}, per-stage Q and x_ref, fwd+bwd", **mem)
+    out["hover_latency"] = hover_latency(dev, flush)
     return out
+
+
+def hover_latency(dev, flush, reps=30):
+    """Per-call latency in the setting of the paper's solver-latency comparison
+    (Sec. V, Table II): hover stabilisation at random targets, B in {1, 256},
+    horizon N in {2, 10, 50}.  Each call runs exactly 5 iterations (tol 0),
+    the upper bound of a control update.  Eager API calls (what a control loop
+    issues), L2 flushed before each; medians of `reps` calls:
+      device_ms  CUDA events around the call on its stream (host launch
+                 overhead included, since the GPU waits for it)
+      wall_ms    host clock around the call plus a synchronize."""
+    import torch
+    from paper_2605_29155_gb300 import DiffMPC, Problem
+    stream = torch.cuda.current_stream()
+    rows = []
+    for Bh in (1, 256):
+        for Nh in (2, 10, 50):
+            prob = W.hover_targets(Bh, Nh, seed=4)
+            p = Problem.from_numpy(prob, device=dev)
+            gu = torch.as_tensor(W.loss_weights_u0(Bh, Nh, seed=1), dtype=torch.float32, device=dev)
+            sol = DiffMPC(N_max=Nh, B_max=Bh, max_iter=5, tol=0.0, device=dev)
+            s = sol.alloc_solution(Bh, Nh)
+            grads = (torch.empty_like(p.Q), torch.empty_like(p.x_ref), torch.empty_like(p.x0))
+            sol.autotune(p, s)
+            for _ in range(3):
+                sol.solve(p, s)
+                sol.backward(p, s, gu, out=grads)
+            torch.cuda.synchronize()
+            t = {k: [] for k in ("fwd_dev", "bwd_dev", "fwd_wall", "bwd_wall")}
+            for _ in range(reps):
+                for part in ("fwd", "bwd"):
+                    flush.fill_(1.0)
+                    torch.cuda.synchronize()
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    w0 = time.perf_counter()
+                    e0.record(stream)
+                    if part == "fwd":
+                        sol.solve(p, s)
+                    else:
+                        sol.backward(p, s, gu, out=grads)
+                    e1.record(stream)
+                    e1.synchronize()
+                    t[part + "_wall"].append((time.perf_counter() - w0) * 1e3)
+                    t[part + "_dev"].append(e0.elapsed_time(e1))
+            med = {k: statistics.median(v) for k, v in t.items()}
+            rows.append(dict(B=Bh, N=Nh, fwd_device_ms=med["fwd_dev"], bwd_device_ms=med["bwd_dev"],
+                             fwd_wall_ms=med["fwd_wall"], bwd_wall_ms=med["bwd_wall"],
+                             iters=float(s.iters.float().mean()), launch=list(sol.launch_shape(Bh, Nh))))
+            sol.close()
+    return dict(workload="hover stabilisation at random targets, exactly 5 iterations (tol 0), fwd and bwd "
+                         "per eager API call, medians of %d" % reps, rows=rows)
 
 
 def run_kernels_only(args):

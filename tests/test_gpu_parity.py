@@ -57,6 +57,27 @@ def test_fp64_to_convergence_matches_oracle(name, B, N, horizons, mi):
     assert not fails, fails[:5]
 
 
+@pytest.mark.parametrize("B,N", [(5, 2), (6, 50)])
+def test_short_and_long_horizons_match_oracle(B, N):
+    """The horizons of the solver-latency setting (hover, N = 2 and 50, exactly
+    five iterations with tol = 0), handles sized to N: FP64 values agree with
+    the oracle to rounding, FP32 within the product tolerances."""
+    prob = cached_problem("hover", B, N, 7)
+    gu, gx = _grads(B, N, 3)
+    idx = list(range(B))
+    orc = oracle_solve(prob, idx, 5, 0.0, gu, gx)
+    gpu = run_gpu(prob, torch.float64, 5, 0.0, gu, gx)
+    report, fails = compare(gpu, orc, idx, U_TOL64, J_TOL64, G_TOL64, skip_ties=TIE64)
+    print("fp64", N, report)
+    assert report["compared"] >= B - 1
+    assert not fails, fails[:5]
+    gpu32 = run_gpu(prob, torch.float32, 5, 0.0, gu, gx)
+    assert np.all(np.isfinite(gpu32["u"])) and np.all(gpu32["iters"] == 5)
+    for i in range(B):
+        u_or = orc[i][1].U
+        assert np.linalg.norm(gpu32["u"][i] - u_or) <= 1e-3 * max(np.linalg.norm(u_or), 1e-6)
+
+
 # --------------------------------------------------- FP32: the product path --
 
 @pytest.mark.parametrize("name,B,N,horizons,mi", [("hover", 64, 20, False, 20), ("track", 64, 20, True, 20),
