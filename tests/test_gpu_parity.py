@@ -236,6 +236,45 @@ def test_hover_fixed_point_on_gpu():
     assert np.all(g64["status"] == 0) and np.all(g64["iters"] == 1)
 
 
+def test_warm_start_matches_oracle():
+    """A1 with a warm start: U^0 = clamp(u_init), some entries outside the box.
+    FP64, three iterations with tol 0: the oracle's values to rounding."""
+    B, N = 8, 10
+    prob = dict(cached_problem("hover", B, N, 11))
+    rng = np.random.default_rng(12)
+    prob["u_init"] = rng.uniform(-1.0, 9.5, size=(B, N, 4))
+    gu, gx = _grads(B, N, 4)
+    idx = list(range(B))
+    orc = oracle_solve(prob, idx, 3, 0.0, gu, gx)
+    gpu = run_gpu(prob, torch.float64, 3, 0.0, gu, gx)
+    report, fails = compare(gpu, orc, idx, U_TOL64, J_TOL64, G_TOL64, skip_ties=TIE64)
+    print(report)
+    assert report["compared"] >= B - 1
+    assert not fails, fails[:5]
+
+
+def test_receding_horizon_with_shifted_warm_start():
+    """The receding-horizon loop around the solve (Algorithm 2): apply u_0,
+    move to the predicted x_1, warm-start the next solve from the shifted
+    controls.  Four steps in FP64, GPU and oracle side by side."""
+    B, N, steps = 6, 10, 4
+    prob = dict(cached_problem("hover", B, N, 13))
+    idx = list(range(B))
+    for k in range(steps):
+        orc = oracle_solve(prob, idx, 10, 1e-6)
+        gpu = run_gpu(prob, torch.float64, 10, 1e-6)
+        for i in idx:
+            u_or = orc[i][1].U
+            assert np.linalg.norm(gpu["u"][i] - u_or) <= U_TOL64C * max(np.linalg.norm(u_or), 1e-6), (k, i)
+        if k > 0:
+            # the shifted warm start leaves little to do
+            assert np.mean(gpu["iters"]) <= first_iters
+        else:
+            first_iters = np.mean(gpu["iters"])
+        prob["x0"] = gpu["x"][:, 1].copy()
+        prob["u_init"] = np.concatenate([gpu["u"][:, 1:], gpu["u"][:, -1:]], axis=1)
+
+
 # ------------------------------------------------- API, graphs, autograd --
 
 def test_api_errors_on_gpu():
