@@ -458,6 +458,57 @@ def side_configs(dev, flush, reps=3):
         sol.close()
     out["mem"] = dict(workload=f"B={Bm}, N={Nm}, per-stage Q and x_ref, fwd+bwd", **mem)
     out["hover_latency"] = hover_latency(dev, flush)
+    out["closed_loop_track"] = closed_loop_track(dev)
+    return out
+
+
+def closed_loop_track(dev, B=4096, N=20, K=50):
+    """Receding-horizon control on the race-track batch (the loop of
+    Algorithm 2 around the solve): each of K environment steps solves the
+    forward problem, moves every instance to its predicted x_1, slides the
+    reference window by one stage and warm-starts the next solve from the
+    shifted controls.  Timed with CUDA events over all K steps (eager calls;
+    the shifts are device copies)."""
+    import torch
+    from paper_2605_29155_gb300 import DiffMPC, Problem
+    prob = W.race_track(B, N + K, seed=0)
+    full_ref = torch.as_tensor(prob["x_ref"], dtype=torch.float32, device=dev)
+    p = Problem.from_numpy(dict(prob, x_ref=np.ascontiguousarray(prob["x_ref"][:, :N])), device=dev)
+    x0_start = p.x0.clone()
+    sol = DiffMPC(N_max=N, B_max=B, max_iter=MAX_ITER, tol=TOL, device=dev)
+    s = sol.alloc_solution(B, N)
+    sol.autotune(p, s)
+    u_init = torch.empty(B, N, 4, dtype=torch.float32, device=dev)
+    iters = torch.zeros(B, dtype=torch.int64, device=dev)
+
+    def run():
+        p.x0.copy_(x0_start)
+        p.u_init = None
+        iters.zero_()
+        for k in range(K):
+            p.x_ref.copy_(full_ref[:, k:k + N])
+            sol.solve(p, s)
+            iters.add_(s.iters)
+            p.x0.copy_(s.x[:, 1])
+            u_init[:, :-1].copy_(s.u[:, 1:])
+            u_init[:, -1].copy_(s.u[:, -1])
+            p.u_init = u_init
+
+    run()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    run()
+    e1.record()
+    e1.synchronize()
+    ms = e0.elapsed_time(e1)
+    err = torch.linalg.norm(p.x0[:, 0:3] - full_ref[:, K, 0:3], dim=1)
+    out = dict(workload=f"race track B={B}, N={N}, {K} receding-horizon steps, <= {MAX_ITER} iterations each, "
+                        "warm start from the shifted solution",
+               instance_steps_per_s=B * K / (ms * 1e-3), ms_per_env_step=ms / K,
+               iters_per_solve=float(iters.float().mean()) / K,
+               final_position_error_m_median=float(err.median()))
+    sol.close()
     return out
 
 

@@ -253,23 +253,32 @@ def test_warm_start_matches_oracle():
     assert not fails, fails[:5]
 
 
-def test_receding_horizon_with_shifted_warm_start():
+@pytest.mark.parametrize("name", ["hover", "track"])
+def test_receding_horizon_with_shifted_warm_start(name):
     """The receding-horizon loop around the solve (Algorithm 2): apply u_0,
     move to the predicted x_1, warm-start the next solve from the shifted
-    controls.  Four steps in FP64, GPU and oracle side by side."""
+    controls and, on the track, slide the reference window by one stage.
+    Four steps in FP64, GPU and oracle side by side."""
     B, N, steps = 6, 10, 4
-    prob = dict(cached_problem("hover", B, N, 13))
+    if name == "hover":
+        prob = dict(cached_problem("hover", B, N, 13))
+        full_ref = np.repeat(prob["x_ref"][:, :1], N + steps, axis=1)
+    else:
+        prob = dict(W.race_track(B, N + steps, seed=13))
+        full_ref = prob["x_ref"]
     idx = list(range(B))
     for k in range(steps):
-        orc = oracle_solve(prob, idx, 10, 1e-6)
-        gpu = run_gpu(prob, torch.float64, 10, 1e-6)
+        prob["x_ref"] = full_ref[:, k:k + N].copy()
+        orc = oracle_solve(prob, idx, 40, 1e-6)
+        gpu = run_gpu(prob, torch.float64, 40, 1e-6)
+        assert np.all(gpu["status"] == 0), (k, gpu["status"])
         for i in idx:
             u_or = orc[i][1].U
             assert np.linalg.norm(gpu["u"][i] - u_or) <= U_TOL64C * max(np.linalg.norm(u_or), 1e-6), (k, i)
-        if k > 0:
+        if name == "hover" and k > 0:
             # the shifted warm start leaves little to do
             assert np.mean(gpu["iters"]) <= first_iters
-        else:
+        elif k == 0:
             first_iters = np.mean(gpu["iters"])
         prob["x0"] = gpu["x"][:, 1].copy()
         prob["u_init"] = np.concatenate([gpu["u"][:, 1:], gpu["u"][:, -1:]], axis=1)
