@@ -46,6 +46,8 @@ class Gradients:
     du_ref: np.ndarray  # [nu]
     dX: np.ndarray      # [N, nx]  d_tau (state part)
     dU: np.ndarray      # [N, nu]  d_tau (control part)
+    dC: np.ndarray | None = None   # like prob.C: dL/dC_t (summed over t when C is shared)
+    dc: np.ndarray | None = None   # like prob.c: dL/dc_t
 
 
 def _assemble(prob, sol, dX, dU, dx0):
@@ -65,7 +67,19 @@ def _assemble(prob, sol, dX, dU, dx0):
     for t in range(n):
         dR += dU[t] * (sol.U[t] - prob.u_ref)
         du_ref += -prob.R * dU[t]
-    return Gradients(dQ, dxr, dx0, dR, du_ref, dX, dU)
+    # the general form: dL/dc_t = d_tau_t, dL/dC_t = 1/2 (d_tau_t tau*_t' + tau*_t d_tau_t')
+    # (shaped like prob.C and prob.c; for the surrogate, C like Q and c per stage)
+    nz = nx + nu
+    NC = prob.C.shape[0] if prob.general else prob.Q.shape[0]
+    Nc = prob.c.shape[0] if prob.general else N
+    dC = np.zeros((NC, nz, nz))
+    dc = np.zeros((Nc, nz))
+    for t in range(n):
+        d = np.concatenate([dX[t], dU[t]])
+        z = np.concatenate([sol.X[t], sol.U[t]])
+        dC[t if NC > 1 else 0] += 0.5 * (np.outer(d, z) + np.outer(z, d))
+        dc[t if Nc > 1 else 0] += d
+    return Gradients(dQ, dxr, dx0, dR, du_ref, dX, dU, dC, dc)
 
 
 def adjoint(prob, sol, grad_x, grad_u) -> Gradients:
@@ -105,7 +119,7 @@ def _kkt_matrix(prob, sol):
     nz = nx + nu
     H = np.zeros((n * nz, n * nz))
     for t in range(n):
-        H[t * nz:(t + 1) * nz, t * nz:(t + 1) * nz] = np.diag(np.concatenate([prob.Qt(t), prob.R]))
+        H[t * nz:(t + 1) * nz, t * nz:(t + 1) * nz] = prob.Ct(t)
     rows = []
     # x_0 = x_init
     for i in range(nx):
@@ -159,7 +173,7 @@ def dense_kkt_adjoint(prob, sol, grad_x, grad_u) -> Gradients:
     return _assemble(prob, sol, dX, dU, dx0)
 
 
-def frozen_lqr_solve(prob, sol, model, Q=None, x_ref=None, x0=None, R=None, u_ref=None):
+def frozen_lqr_solve(prob, sol, model, Q=None, x_ref=None, x0=None, R=None, u_ref=None, C=None, c=None):
     """Primal solution of the frozen LQR at tau* for perturbed cost / initial
     state: dynamics x_{t+1} = F_t tau_t + f_t with f_t = f(tau*_t) - F_t tau*_t,
     clamped controls held at u*.  Returns (X, U).  Finite differences of
@@ -172,13 +186,13 @@ def frozen_lqr_solve(prob, sol, model, Q=None, x_ref=None, x0=None, R=None, u_re
     x0 = prob.x0 if x0 is None else x0
     R = prob.R if R is None else R
     u_ref = prob.u_ref if u_ref is None else u_ref
-    p2 = dataclasses.replace(prob, Q=Q, x_ref=x_ref, x0=x0, R=R, u_ref=u_ref)
+    C = prob.C if C is None else C
+    c = prob.c if c is None else c
+    p2 = dataclasses.replace(prob, Q=Q, x_ref=x_ref, x0=x0, R=R, u_ref=u_ref, C=C, c=c)
     Kkt, nv, clamped = _kkt_matrix(p2, sol)
     rhs = np.zeros(Kkt.shape[0])
     for t in range(n):
-        Qt = p2.Qt(t)
-        rhs[t * nz:t * nz + nx] = Qt * x_ref[t]
-        rhs[t * nz + nx:(t + 1) * nz] = R * u_ref
+        rhs[t * nz:(t + 1) * nz] = -p2.ct(t)
     r = nv
     rhs[r:r + nx] = x0
     r += nx

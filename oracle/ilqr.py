@@ -4,7 +4,8 @@
     s.t.        x_{t+1} = f(x_t, u_t),  x_0 = x_init,  u_lo <= u_t <= u_hi
 
 with the diagonal surrogate of Eq. (2): C_t = diag(Q_t, R) and
-c_t = [-Q_t * x_ref_t; -R * u_ref].  The iteration is Algorithm 2's inner
+c_t = [-Q_t * x_ref_t; -R * u_ref], or with general C_t (symmetric positive
+semidefinite) and c_t when the problem carries them.  The iteration is Algorithm 2's inner
 loop (Rollout -> {LQ, FBP, FFP, Converged?}) with the three stages of
 Sec. IV: 1) rollout and linearization, 2) Riccati backward pass with the box
 QP (Tassa et al. 2014), 3) forward pass with the line search over
@@ -56,9 +57,30 @@ class Problem:
     u_hi: np.ndarray        # [nu]
     n: int                  # horizon actually solved (<= N)
     u_init: np.ndarray | None = None   # [N, nu] warm start
+    # General stage cost of Eq. (2), 1/2 z' C_t z + c_t' z with z = [x; u]:
+    # when C is given it replaces the diagonal surrogate (Q, x_ref, R, u_ref)
+    # in the cost; Nc = 1 shares one (C, c) over the stages.
+    C: np.ndarray | None = None        # [Nc, nz, nz], symmetric positive semidefinite
+    c: np.ndarray | None = None        # [Nc, nz]
 
     def Qt(self, t):
         return self.Q[t] if self.Q.shape[0] > 1 else self.Q[0]
+
+    @property
+    def general(self):
+        return self.C is not None
+
+    def Ct(self, t):
+        """C_t of Eq. (2): the general matrix, or diag(Q_t, R)."""
+        if self.general:
+            return self.C[t] if self.C.shape[0] > 1 else self.C[0]
+        return np.diag(np.concatenate([self.Qt(t), self.R]))
+
+    def ct(self, t):
+        """c_t of Eq. (2): the general vector, or [-Q_t x_ref_t; -R u_ref]."""
+        if self.general:
+            return self.c[t] if self.c.shape[0] > 1 else self.c[0]
+        return np.concatenate([-self.Qt(t) * self.x_ref[t], -self.R * self.u_ref])
 
 
 def problem_from_batch(batch: dict, i: int) -> Problem:
@@ -66,16 +88,25 @@ def problem_from_batch(batch: dict, i: int) -> Problem:
     N = batch["x_ref"].shape[1]
     n = int(hz[i]) if hz is not None else N
     ui = batch.get("u_init")
+    Cb, cb = batch.get("C"), batch.get("c")
     return Problem(x0=np.asarray(batch["x0"][i], float), Q=np.asarray(batch["Q"][i], float),
                    x_ref=np.asarray(batch["x_ref"][i], float), R=np.asarray(batch["R"][i], float),
                    u_ref=np.asarray(batch["u_ref"][i], float), u_lo=np.asarray(batch["u_lo"][i], float),
                    u_hi=np.asarray(batch["u_hi"][i], float), n=n,
-                   u_init=None if ui is None else np.asarray(ui[i], float))
+                   u_init=None if ui is None else np.asarray(ui[i], float),
+                   C=None if Cb is None else np.asarray(Cb[i], float),
+                   c=None if cb is None else np.asarray(cb[i], float))
 
 
 def total_cost(prob: Problem, X, U):
-    """Centred form of Eq. (3)'s objective over stages 0..n-1 (reading R1)."""
+    """Centred form of Eq. (3)'s objective over stages 0..n-1 (reading R1);
+    with a general cost, Eq. (3)'s objective itself."""
     J = 0.0
+    if prob.general:
+        for t in range(prob.n):
+            z = np.concatenate([X[t], U[t]])
+            J += 0.5 * (z @ prob.Ct(t) @ z) + prob.ct(t) @ z
+        return J
     for t in range(prob.n):
         dx = X[t] - prob.x_ref[t]
         du = U[t] - prob.u_ref
@@ -91,6 +122,15 @@ def cost_change(prob: Problem, X, U, Xa, Ua, with_scale=False):
     rounding error of the sum is relative to."""
     dJ = 0.0
     scale = 0.0
+    if prob.general:
+        # d' (C (z + d/2) + c): the same identity for a general C
+        for t in range(prob.n):
+            z = np.concatenate([X[t], U[t]])
+            d = np.concatenate([Xa[t] - X[t], Ua[t] - U[t]])
+            tz = d * (prob.Ct(t) @ (z + 0.5 * d) + prob.ct(t))
+            dJ += tz.sum()
+            scale += np.abs(tz).sum()
+        return (dJ, scale) if with_scale else dJ
     for t in range(prob.n):
         dx = Xa[t] - X[t]
         du = Ua[t] - U[t]
@@ -126,8 +166,12 @@ def backward_pass(prob: Problem, X, U, F, free_override=None) -> BackwardResult:
     Ks, ks, frees, Ls, Quus, Quxs = [None] * n, [None] * n, [None] * n, [None] * n, [None] * n, [None] * n
     margin = np.inf
     for t in reversed(range(n)):
-        Ct = np.diag(np.concatenate([prob.Qt(t), prob.R]))
-        ct = np.concatenate([prob.Qt(t) * (X[t] - prob.x_ref[t]), prob.R * (U[t] - prob.u_ref)])
+        if prob.general:
+            Ct = prob.Ct(t)
+            ct = Ct @ np.concatenate([X[t], U[t]]) + prob.ct(t)
+        else:
+            Ct = np.diag(np.concatenate([prob.Qt(t), prob.R]))
+            ct = np.concatenate([prob.Qt(t) * (X[t] - prob.x_ref[t]), prob.R * (U[t] - prob.u_ref)])
         if t < n - 1:
             Ft = F[t]
             Qm = Ct + Ft.T @ V @ Ft
