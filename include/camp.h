@@ -88,9 +88,10 @@ typedef struct mpc_config {
     double alpha[4];        /* coefficients in (0, 1], default {1, .5, .25, .1}        */
     int    store_mode;      /* MPC_STORE_ALL or MPC_RECOMPUTE                          */
     int    exec_mode;       /* MPC_EXEC_PERSISTENT or MPC_EXEC_PLAIN                   */
-    int    tpi;             /* threads per instance: 0 (auto = 16), 8, 16 or 32        */
-    int    ipb;             /* instances per block: 0 (auto) or 1..32 (power of 2),    */
-                            /* with tpi * ipb a multiple of 32 between 32 and 256       */
+    int    tpi;             /* threads per instance = warps per block: 0 (4 until      */
+                            /* mpc_autotune picks), 4 or 8                              */
+    int    ipb;             /* instances per block (one per lane): 0 (auto) or 1..32,  */
+                            /* 1..16 in MPC_F64                                         */
 } mpc_config;
 
 typedef struct mpc_problem {
@@ -132,8 +133,10 @@ int mpc_create(const mpc_config *cfg, mpc_handle **out);
  * sure no call on it is still running on the GPU. */
 int mpc_destroy(mpc_handle *h);
 
-/* Bytes of tape mpc_solve_fwd writes for a (B, N) problem: B*N*288 elements
- * in MPC_STORE_ALL mode, 0 in MPC_RECOMPUTE mode (or for a NULL handle). */
+/* Bytes of tape mpc_solve_fwd writes for a (B, N) problem: ceil(B/32)*32*N*210
+ * elements of the handle's dtype in MPC_STORE_ALL mode (per stage and instance:
+ * the 11 computed columns of F_t, K_t, the masked factor of Q_uu,ff and the free
+ * mask), 0 in MPC_RECOMPUTE mode (or for a NULL handle). */
 size_t mpc_tape_bytes(const mpc_handle *h, int B, int N);
 
 /* Forward solve (Eq. (3) by box-constrained iLQR, Algorithm 2's inner loop):
@@ -175,7 +178,7 @@ int mpc_launch_count(const mpc_handle *h, int has_horizon, int *fwd, int *bwd);
  * control loop that must not allocate after start-up, a plug-in whose host
  * application owns every device allocation).  Same problem, outputs and
  * per-instance statuses as mpc_solve_fwd in the persistent form, without a
- * handle: the scratch is one statically allocated device array (15.5 MB,
+ * handle: the scratch is one statically allocated device array (9.7 MB,
  * held on every device the library runs on until the process exits).
  *   cfg    as for mpc_create, dtype must be MPC_F32 (exec_mode, tpi, ipb,
  *          N_max and B_max are ignored); MPC_STORE_ALL writes the tape.
