@@ -459,7 +459,53 @@ def side_configs(dev, flush, reps=3):
     out["mem"] = dict(workload=f"B={Bm}, N={Nm}, per-stage Q and x_ref, fwd+bwd", **mem)
     out["hover_latency"] = hover_latency(dev, flush)
     out["closed_loop_track"] = closed_loop_track(dev)
+    out["general_cost"] = general_cost_track(dev, flush, reps)
     return out
+
+
+def general_cost_track(dev, flush, reps, B=4096, N=20):
+    """The benchmark batch with the general stage cost of Eq. (2): a dense C
+    per instance (diag(Q, R) + 0.05 M'M / 17, M ~ N(0, 1), shared over the
+    stages) and c_t = -C z_ref,t per stage; forward + backward (dL/dC, dL/dc,
+    dL/dx0), eager, L2 flushed before each step."""
+    import torch
+    from paper_2605_29155_gb300 import DiffMPC, Problem
+    prob = W.race_track(B, N, seed=0)
+    rng = np.random.default_rng(21)
+    M = rng.normal(size=(B, 17, 17))
+    diag = np.concatenate([prob["Q"][:, 0], prob["R"]], axis=1)
+    C = np.einsum("bi,ij->bij", diag, np.eye(17)) + 0.05 * np.einsum("bki,bkj->bij", M, M) / 17
+    zr = np.concatenate([prob["x_ref"], np.repeat(prob["u_ref"][:, None], N, axis=1)], axis=2)
+    c = -np.einsum("bij,btj->bti", C, zr)
+    p = Problem.from_numpy(dict(prob, C=C[:, None], c=c), device=dev)
+    gu = torch.as_tensor(W.loss_weights_u0(B, N, seed=1), dtype=torch.float32, device=dev)
+    sol = DiffMPC(N_max=N, B_max=B, max_iter=MAX_ITER, tol=TOL, device=dev)
+    s = sol.alloc_solution(B, N)
+    sol.autotune(p, s)
+    out = (torch.empty_like(p.C), torch.empty_like(p.c), torch.empty_like(p.x0))
+    for _ in range(2):
+        sol.solve(p, s)
+        sol.backward_general(p, s, gu, out=out)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    ms, fw = [], []
+    for _ in range(max(reps, 5)):
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        flush.fill_(1.0)
+        e0.record(stream)
+        sol.solve(p, s)
+        e1.record(stream)
+        sol.backward_general(p, s, gu, out=out)
+        e2.record(stream)
+        e2.synchronize()
+        ms.append(e0.elapsed_time(e2))
+        fw.append(e0.elapsed_time(e1))
+    res = dict(workload=f"race track B={B}, N={N}, dense C (shared) and per-stage c, fwd+bwd",
+               solves_per_s=B / (statistics.fmean(ms) * 1e-3), fwd_ms=statistics.fmean(fw),
+               bwd_ms=statistics.fmean(ms) - statistics.fmean(fw), iters_mean=float(s.iters.float().mean()),
+               launch=list(sol.launch_shape(B, N)))
+    sol.close()
+    return res
 
 
 def closed_loop_track(dev, B=4096, N=20, K=50):

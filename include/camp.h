@@ -106,12 +106,22 @@ typedef struct mpc_problem {
     const void *u_lo;       /* [B, 4]   u_min                                          */
     const void *u_hi;       /* [B, 4]   u_max (>= u_lo)                                */
     const void *u_init;     /* [B, N, 4] warm start, or NULL for clamp(u_ref)          */
+    /* General stage cost of Eq. (2), 1/2 z_t' C_t z_t + c_t' z_t with z_t = [x_t; u_t],
+     * in place of the diagonal form: NULL C selects the diagonal form (Q, Nq, x_ref,
+     * R and u_ref as above).  With C given, Q, Nq and x_ref are not read (may be
+     * NULL), R is not used, u_ref only gives the start U^0, and the cost reported
+     * is Eq. (3)'s objective itself. */
+    const void *C;          /* [B, NC, 17, 17] symmetric positive semidefinite C_t     */
+    int         NC;         /* 1 (one C for every stage) or N                          */
+    const void *c;          /* [B, Nc, 17] c_t (required with C)                       */
+    int         Nc;         /* 1 or N                                                  */
 } mpc_problem;
 
 typedef struct mpc_solution {
     void   *u;              /* [B, N, 4]  u* (zero past each horizon); u*_0 is the action */
     void   *x;              /* [B, N, 13] x* (x*_0 = x_init; zero past each horizon)    */
     void   *cost;           /* [B] sum_t 1/2|x-x_ref|_Q^2 + 1/2|u-u_ref|_R^2 at (x*,u*)  */
+                            /* (general cost: sum_t 1/2 z'C z + c'z)                  */
     int    *iters;          /* [B] iterations executed                                 */
     int    *status;         /* [B] MPC_ST_*                                             */
     void   *tape;           /* MPC_STORE_ALL: >= mpc_tape_bytes(B, N) bytes, 256-aligned */
@@ -156,6 +166,16 @@ int mpc_solve_fwd(mpc_handle *h, const mpc_problem *p, mpc_solution *s, cudaStre
 int mpc_solve_bwd(mpc_handle *h, const mpc_problem *p, const mpc_solution *s,
                   const void *grad_u, const void *grad_x,
                   void *dQ, void *dx_ref, void *dx0, cudaStream_t stream);
+
+/* Backward solve for a problem with the general cost (p->C non-NULL): as
+ * mpc_solve_bwd, but writes dL/dC (dC [B, NC, 17, 17], symmetric:
+ * 1/2 (d_tau z*' + z* d_tau') per stage, summed over the stages when NC = 1),
+ * dL/dc (dc [B, Nc, 17]: d_tau per stage, summed when Nc = 1) and dL/dx_init
+ * (dx0 [B, 13]).  MPC_ERR_STATE for a problem with the diagonal form (and
+ * mpc_solve_bwd returns MPC_ERR_STATE for one with the general form). */
+int mpc_solve_bwd_general(mpc_handle *h, const mpc_problem *p, const mpc_solution *s,
+                          const void *grad_u, const void *grad_x,
+                          void *dC, void *dc, void *dx0, cudaStream_t stream);
 
 /* Time the persistent forward for each launch shape (threads per instance x
  * instances per block; a nonzero tpi or ipb in the config pins that value) on

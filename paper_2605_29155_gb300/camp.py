@@ -20,7 +20,7 @@ MPC_ST_CONVERGED, MPC_ST_STALLED, MPC_ST_MAX_ITER, MPC_ST_NONFINITE, MPC_ST_NONP
 
 EXPORTED = ("mpc_config_default", "mpc_create", "mpc_destroy", "mpc_tape_bytes", "mpc_solve_fwd",
             "mpc_solve_bwd", "mpc_autotune", "mpc_launch_shape", "mpc_launch_count", "mpc_strerror",
-            "mpc_status_str", "mpc_solve_fwd_noalloc")
+            "mpc_status_str", "mpc_solve_fwd_noalloc", "mpc_solve_bwd_general")
 MPC_NOALLOC_B_MAX, MPC_NOALLOC_N_MAX = 256, 40
 
 
@@ -35,7 +35,8 @@ class mpc_config(ctypes.Structure):
 class mpc_problem(ctypes.Structure):
     _fields_ = [("B", c_int), ("N", c_int), ("horizon", c_void_p), ("x0", c_void_p), ("Q", c_void_p),
                 ("Nq", c_int), ("x_ref", c_void_p), ("R", c_void_p), ("u_ref", c_void_p), ("u_lo", c_void_p),
-                ("u_hi", c_void_p), ("u_init", c_void_p)]
+                ("u_hi", c_void_p), ("u_init", c_void_p), ("C", c_void_p), ("NC", c_int), ("c", c_void_p),
+                ("Nc", c_int)]
 
 
 class mpc_solution(ctypes.Structure):
@@ -61,6 +62,9 @@ def _load():
     lib.mpc_solve_bwd.argtypes = [c_void_p, POINTER(mpc_problem), POINTER(mpc_solution), c_void_p, c_void_p,
                                   c_void_p, c_void_p, c_void_p, c_void_p]
     lib.mpc_solve_bwd.restype = c_int
+    lib.mpc_solve_bwd_general.argtypes = [c_void_p, POINTER(mpc_problem), POINTER(mpc_solution), c_void_p,
+                                          c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]
+    lib.mpc_solve_bwd_general.restype = c_int
     lib.mpc_autotune.argtypes = [c_void_p, POINTER(mpc_problem), POINTER(mpc_solution), c_void_p, POINTER(c_int)]
     lib.mpc_autotune.restype = c_int
     lib.mpc_launch_shape.argtypes = [c_void_p, c_int, c_int, POINTER(c_int), POINTER(c_int), POINTER(c_int)]
@@ -120,6 +124,12 @@ def mpc_solve_bwd(h, prob: mpc_problem, sol: mpc_solution, grad_u: int, grad_x: 
                   dx0: int, stream: int) -> int:
     return _lib.mpc_solve_bwd(h, byref(prob), byref(sol), c_void_p(grad_u), c_void_p(grad_x or None),
                               c_void_p(dQ), c_void_p(dx_ref), c_void_p(dx0), c_void_p(stream))
+
+
+def mpc_solve_bwd_general(h, prob: mpc_problem, sol: mpc_solution, grad_u: int, grad_x: int, dC: int, dc: int,
+                          dx0: int, stream: int) -> int:
+    return _lib.mpc_solve_bwd_general(h, byref(prob), byref(sol), c_void_p(grad_u), c_void_p(grad_x or None),
+                                      c_void_p(dC), c_void_p(dc), c_void_p(dx0), c_void_p(stream))
 
 
 def mpc_autotune(h, prob: mpc_problem, sol: mpc_solution, stream: int):

@@ -155,9 +155,16 @@ static int check_problem(const mpc_handle* h, const mpc_problem* p) {
     if (!h || !p) return MPC_ERR_ARG;
     if (p->B < 0 || p->B > h->cfg.B_max) return MPC_ERR_SHAPE;
     if (p->N < 1 || p->N > h->cfg.N_max) return MPC_ERR_SHAPE;
-    if (p->Nq != 1 && p->Nq != p->N) return MPC_ERR_SHAPE;
+    if (p->C) {
+        // general cost: C and c with their own sharing; Q and x_ref unused
+        if (!p->c) return MPC_ERR_ARG;
+        if ((p->NC != 1 && p->NC != p->N) || (p->Nc != 1 && p->Nc != p->N)) return MPC_ERR_SHAPE;
+    } else if (p->Nq != 1 && p->Nq != p->N) {
+        return MPC_ERR_SHAPE;
+    }
     if (p->B == 0) return MPC_OK;
-    if (!p->x0 || !p->Q || !p->x_ref || !p->R || !p->u_ref || !p->u_lo || !p->u_hi) return MPC_ERR_ARG;
+    if (!p->x0 || !p->R || !p->u_ref || !p->u_lo || !p->u_hi) return MPC_ERR_ARG;
+    if (!p->C && (!p->Q || !p->x_ref)) return MPC_ERR_ARG;
     return MPC_OK;
 }
 
@@ -187,6 +194,10 @@ static Params<T> make_params(const mpc_handle* h, const mpc_problem* p, const mp
     P.ulo = (const T*)p->u_lo;
     P.uhi = (const T*)p->u_hi;
     P.uinit = (const T*)p->u_init;
+    P.Cg = (const T*)p->C;
+    P.cg = (const T*)p->c;
+    P.NC = p->C ? p->NC : 1;
+    P.Nc = p->C ? p->Nc : 1;
     P.u = (T*)s->u;
     P.x = (T*)s->x;
     P.cost = (T*)s->cost;
@@ -228,6 +239,7 @@ extern "C" int mpc_solve_bwd(mpc_handle* h, const mpc_problem* p, const mpc_solu
     if (r != MPC_OK) return r;
     if (!s) return MPC_ERR_ARG;
     if (p->B == 0) return MPC_OK;
+    if (p->C) return MPC_ERR_STATE;     // a general cost has mpc_solve_bwd_general
     if (!s->u || !s->x || !s->status || !grad_u || !dQ || !dx_ref || !dx0) return MPC_ERR_ARG;
     const int recompute = h->cfg.store_mode == MPC_RECOMPUTE;
     if (!recompute && (!s->tape || s->tape_bytes < mpc_tape_bytes(h, p->B, p->N))) return MPC_ERR_ARG;
@@ -237,12 +249,40 @@ extern "C" int mpc_solve_bwd(mpc_handle* h, const mpc_problem* p, const mpc_solu
     if (h->cfg.dtype == MPC_F64) {
         const Params<double> P = make_params<double>(h, p, s, ipb);
         AdjArgs<double> A{(const double*)grad_u, (const double*)grad_x, (double*)dQ, (double*)dx_ref,
-                          (double*)dx0, recompute};
+                          (double*)dx0, nullptr, nullptr, recompute};
         e = launch_backward<double>(P, A, h->tpi, grid, h->order, stream);
     } else {
         const Params<float> P = make_params<float>(h, p, s, ipb);
         AdjArgs<float> A{(const float*)grad_u, (const float*)grad_x, (float*)dQ, (float*)dx_ref, (float*)dx0,
-                         recompute};
+                         nullptr, nullptr, recompute};
+        e = launch_backward<float>(P, A, h->tpi, grid, h->order, stream);
+    }
+    return e == cudaSuccess ? MPC_OK : MPC_ERR_CUDA;
+}
+
+extern "C" int mpc_solve_bwd_general(mpc_handle* h, const mpc_problem* p, const mpc_solution* s,
+                                     const void* grad_u, const void* grad_x, void* dC, void* dc, void* dx0,
+                                     cudaStream_t stream) {
+    int r = check_problem(h, p);
+    if (r != MPC_OK) return r;
+    if (!s) return MPC_ERR_ARG;
+    if (!p->C) return MPC_ERR_STATE;    // the diagonal form has mpc_solve_bwd
+    if (p->B == 0) return MPC_OK;
+    if (!s->u || !s->x || !s->status || !grad_u || !dC || !dc || !dx0) return MPC_ERR_ARG;
+    const int recompute = h->cfg.store_mode == MPC_RECOMPUTE;
+    if (!recompute && (!s->tape || s->tape_bytes < mpc_tape_bytes(h, p->B, p->N))) return MPC_ERR_ARG;
+    cudaError_t e;
+    const int ipb = ipb_for(h, p->B);
+    const int grid = grid_for(h, p->B, ipb);
+    if (h->cfg.dtype == MPC_F64) {
+        const Params<double> P = make_params<double>(h, p, s, ipb);
+        AdjArgs<double> A{(const double*)grad_u, (const double*)grad_x, nullptr, nullptr, (double*)dx0,
+                          (double*)dC, (double*)dc, recompute};
+        e = launch_backward<double>(P, A, h->tpi, grid, h->order, stream);
+    } else {
+        const Params<float> P = make_params<float>(h, p, s, ipb);
+        AdjArgs<float> A{(const float*)grad_u, (const float*)grad_x, nullptr, nullptr, (float*)dx0, (float*)dC,
+                         (float*)dc, recompute};
         e = launch_backward<float>(P, A, h->tpi, grid, h->order, stream);
     }
     return e == cudaSuccess ? MPC_OK : MPC_ERR_CUDA;

@@ -87,6 +87,8 @@ template <typename T> struct Params {
     const int* horizon;
     const int* order;                   // processing order of the instances (or NULL)
     const T *x0, *Q, *xref, *R, *uref, *ulo, *uhi, *uinit;
+    const T *Cg, *cg;                   // general cost of Eq. (2): C [B, NC, 17, 17], c [B, Nc, 17] (or NULL)
+    int NC, Nc;
     T *u, *x, *cost;
     int *iters, *status;
     T* tape;
@@ -97,8 +99,20 @@ template <typename T> struct Params {
 template <typename T> struct AdjArgs {
     const T *gu, *gx;
     T *dQ, *dxref, *dx0;
+    T *dC, *dc;                         // general cost: dL/dC [B, NC, 17, 17], dL/dc [B, Nc, 17]
     int recompute;
 };
+
+// The general stage cost of instance b at stage t: C_t (17 x 17, row-major,
+// symmetric) and c_t, shared over the stages when NC (Nc) is 1.
+template <typename T>
+__device__ __forceinline__ const T* Cmat(const Params<T>& P, int b, int t) {
+    return P.Cg + ((size_t)b * P.NC + (P.NC > 1 ? t : 0)) * (NZ * NZ);
+}
+template <typename T>
+__device__ __forceinline__ const T* cvec(const Params<T>& P, int b, int t) {
+    return P.cg + ((size_t)b * P.Nc + (P.Nc > 1 ? t : 0)) * NZ;
+}
 
 // Packed upper-triangular indices (row <= column) of V (13 x 13) and Q (17 x 17).
 __host__ __device__ constexpr int vidx(int i, int j) {
@@ -721,16 +735,22 @@ __device__ void load_constants(const Params<T>& P, BlockSmem<T>& S, const Lane& 
 // The cost rows Q_t, x_ref,t of every stage t < n into the scratch records
 // (stages split by warp).  With `nominal` also x*, u* from the solution
 // outputs as the nominal (x lo = 0): the backward's re-factorization point.
-template <typename T, int NW>
+template <typename T, int NW, bool GEN>
 __device__ void load_stage_rows(const Params<T>& P, const Lane& L, int n, bool nominal) {
     if (!L.valid) return;
     for (int t = L.w; t < n; t += NW) {
-        const T* q = Qrow(P, L.b, t);
-        const T* xr = P.xref + ((size_t)L.b * P.N + t) * NX;
         T* dr = P.stg + srow(P, L.pos, t, 0);
         T buf[2 * NX];
+        if constexpr (GEN) {
+            // the diagonal cost rows are not used with a general cost
 #pragma unroll
-        for (int i = 0; i < NX; ++i) { buf[i] = q[i]; buf[NX + i] = xr[i]; }
+            for (int i = 0; i < 2 * NX; ++i) buf[i] = T(0);
+        } else {
+            const T* q = Qrow(P, L.b, t);
+            const T* xr = P.xref + ((size_t)L.b * P.N + t) * NX;
+#pragma unroll
+            for (int i = 0; i < NX; ++i) { buf[i] = q[i]; buf[NX + i] = xr[i]; }
+        }
         if (nominal) {
             const T* xs = P.x + ((size_t)L.b * P.N + t) * NX;
             const T* us = P.u + ((size_t)L.b * P.N + t) * NU;
@@ -753,7 +773,7 @@ __device__ void load_stage_rows(const Params<T>& P, const Lane& L, int n, bool n
 // U^0 = clamp(u_init or u_ref), X^0 by RK4 from x_init, J^0 (warp 0; the
 // state is carried as hi + lo).  Writes the nominal records; returns J^0 in
 // S.Jc[0] for the block (after the caller's barrier).
-template <typename T, int NW>
+template <typename T, int NW, bool GEN>
 __device__ void initial_rollout(const Params<T>& P, BlockSmem<T>& S, const Lane& L, int n) {
     if (L.w != 0) return;
     T J = T(0);
@@ -788,7 +808,27 @@ __device__ void initial_rollout(const Params<T>& P, BlockSmem<T>& S, const Lane&
                 const T e = (xh[i] - xr[i]) + xl[i];
                 sx += e * (qv[i] * e);
             }
-            J += T(0.5) * sx + T(0.5) * su;
+            if constexpr (GEN) {
+                // 1/2 z' C z + c' z = sum_i z_i (1/2 (C z)_i + c_i)
+                const T* Cm = Cmat(P, L.b, t);
+                const T* cv = cvec(P, L.b, t);
+                T z[NZ];
+#pragma unroll
+                for (int i = 0; i < NX; ++i) z[i] = xh[i] + xl[i];
+#pragma unroll
+                for (int a = 0; a < NU; ++a) z[NX + a] = us[a];
+                T sz = T(0);
+#pragma unroll
+                for (int i = 0; i < NZ; ++i) {
+                    T cz = T(0);
+#pragma unroll
+                    for (int k = 0; k < NZ; ++k) cz += Cm[i * NZ + k] * z[k];
+                    sz += z[i] * (T(0.5) * cz + cv[i]);
+                }
+                J += sz;
+            } else {
+                J += T(0.5) * sx + T(0.5) * su;
+            }
             if (t < n - 1) rk4_step2(P.mdl, xh, xl, us);
         }
     }
@@ -887,11 +927,25 @@ __device__ __forceinline__ void tangent_step(const Params<T>& P, BlockSmem<T>& S
     }
 }
 
-// Cost row j of a stage: C_jj and (C z + c)_j at the nominal.
-template <typename T>
-__device__ __forceinline__ void cost_row(const BlockSmem<T>& S, const T* cs, int sl, int j, bool use_lo, T& Cd,
-                                         T& c) {
+// Cost row j of stage s: C_jj and (C z + c)_j at the nominal z (x as hi + lo
+// with use_lo).  GEN: the general C_s, c_s of Eq. (2) (read from the input).
+template <typename T, bool GEN>
+__device__ __forceinline__ void cost_row(const Params<T>& P, const BlockSmem<T>& S, const T* cs, const Lane& L,
+                                         int s, int j, bool use_lo, T& Cd, T& c) {
     constexpr int A = SL<T>::A;
+    const int sl = L.sl;
+    if constexpr (GEN) {
+        const T* Cr = Cmat(P, L.b, s) + j * NZ;
+        T acc = cvec(P, L.b, s)[j];
+#pragma unroll
+        for (int k = 0; k < NX; ++k)
+            acc += Cr[k] * (use_lo ? cs[(R_X + k) * A] + cs[(R_XL + k) * A] : cs[(R_X + k) * A]);
+#pragma unroll
+        for (int a = 0; a < NU; ++a) acc += Cr[NX + a] * cs[(R_U + a) * A];
+        Cd = Cr[j];
+        c = acc;
+        return;
+    }
     if (j < NX) {
         const T q = cs[(R_Q + j) * A];
         const T e = cs[(R_X + j) * A] - cs[(R_XR + j) * A];
@@ -925,7 +979,9 @@ __device__ __forceinline__ T dot13(const T (&a)[NX], const T (&b)[NX]) {
 // entry, the entries in the rows of the constant columns (p_a takes W[p_a],
 // v_a takes W[v_a] + hv W[p_a]) and F[:, r]' W[:, j] in the rows of the
 // computed columns r < j, two rows per trip.
-template <typename T, int NW>
+// GEN: the general C_s of Eq. (2) enters every entry of P_s, not only the
+// diagonal.
+template <typename T, int NW, bool GEN>
 __device__ __forceinline__ void form_p(const Params<T>& P, BlockSmem<T>& S, const Lane& L, int s, bool ons) {
     constexpr int A = SL<T>::A;
     constexpr int NP = Split<NW>::NP;
@@ -936,6 +992,7 @@ __device__ __forceinline__ void form_p(const Params<T>& P, BlockSmem<T>& S, cons
     const T* Qn = &S.u.r.Q[(s + 1) & 1][0][sl];
     const T* Nb = &S.u.r.N[0][sl];
     T* Ps = &S.u.r.Q[s & 1][0][sl];
+    const T* Cm = GEN ? Cmat(P, L.b, s) : nullptr;
     const bool cw = L.w == Split<NW>::CONST_W;
     if (Split<NW>::pcol(L.w, 0) < 0 && !cw) return;
     T V[NV], nx[NX][NU];
@@ -959,17 +1016,18 @@ __device__ __forceinline__ void form_p(const Params<T>& P, BlockSmem<T>& S, cons
 #pragma unroll
         for (int b = 0; b < 3; ++b) {
             T Cp, cp, Cv, cv;
-            cost_row(S, cs, sl, b, false, Cp, cp);
-            cost_row(S, cs, sl, 7 + b, false, Cv, cv);
+            cost_row<T, GEN>(P, S, cs, L, s, b, false, Cp, cp);
+            cost_row<T, GEN>(P, S, cs, L, s, 7 + b, false, Cv, cv);
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
                 const T Vpp = V[vidx(a, b)];
                 const T Wpv = V[vidx(a, 7 + b)] + hv * Vpp;
-                Ps[qidx(a, 7 + b) * A] = ons ? Wpv : T(0);
+                Ps[qidx(a, 7 + b) * A] = ons ? (GEN ? Cm[a * NZ + 7 + b] + Wpv : Wpv) : T(0);
                 if (a <= b) {
-                    Ps[qidx(a, b) * A] = ons ? (a == b ? Cp + Vpp : Vpp) : T(0);
+                    Ps[qidx(a, b) * A] = ons ? (GEN ? Cm[a * NZ + b] + Vpp : (a == b ? Cp + Vpp : Vpp)) : T(0);
                     const T v2 = (V[vidx(7 + a, 7 + b)] + hv * V[vidx(7 + a, b)]) + hv * Wpv;
-                    Ps[qidx(7 + a, 7 + b) * A] = ons ? (a == b ? Cv + v2 : v2) : T(0);
+                    Ps[qidx(7 + a, 7 + b) * A] =
+                        ons ? (GEN ? Cm[(7 + a) * NZ + 7 + b] + v2 : (a == b ? Cv + v2 : v2)) : T(0);
                 }
             }
         }
@@ -983,7 +1041,7 @@ __device__ __forceinline__ void form_p(const Params<T>& P, BlockSmem<T>& S, cons
 #pragma unroll
         for (int i = 0; i < NX; ++i) { f[i] = Fb[(jj * NX + i) * A]; W[i] = T(0); }
         T Cd, cj;
-        cost_row(S, cs, sl, j, false, Cd, cj);
+        cost_row<T, GEN>(P, S, cs, L, s, j, false, Cd, cj);
 #pragma unroll
         for (int kk = 0; kk < NX; ++kk)
 #pragma unroll
@@ -991,8 +1049,9 @@ __device__ __forceinline__ void form_p(const Params<T>& P, BlockSmem<T>& S, cons
         Ps[qidx(j, j) * A] = ons ? Cd + dot13(f, W) : T(0);
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-            Ps[qidx(a, j) * A] = ons ? W[a] : T(0);
-            Ps[qidx(7 + a, j) * A] = ons ? W[7 + a] + hv * W[a] : T(0);
+            Ps[qidx(a, j) * A] = ons ? (GEN ? Cm[a * NZ + j] + W[a] : W[a]) : T(0);
+            const T wv = W[7 + a] + hv * W[a];
+            Ps[qidx(7 + a, j) * A] = ons ? (GEN ? Cm[(7 + a) * NZ + j] + wv : wv) : T(0);
         }
 #pragma unroll 1
         for (int r = 0; r < jj; r += 2) {
@@ -1001,8 +1060,8 @@ __device__ __forceinline__ void form_p(const Params<T>& P, BlockSmem<T>& S, cons
 #pragma unroll
             for (int i = 0; i < NX; ++i) { f0[i] = Fb[(r * NX + i) * A]; f1[i] = Fb[(r1 * NX + i) * A]; }
             const T a0 = dot13(f0, W), a1 = dot13(f1, W);
-            Ps[qidx(gcol(r), j) * A] = ons ? a0 : T(0);
-            if (r1 != r) Ps[qidx(gcol(r1), j) * A] = ons ? a1 : T(0);
+            Ps[qidx(gcol(r), j) * A] = ons ? (GEN ? Cm[gcol(r) * NZ + j] + a0 : a0) : T(0);
+            if (r1 != r) Ps[qidx(gcol(r1), j) * A] = ons ? (GEN ? Cm[gcol(r1) * NZ + j] + a1 : a1) : T(0);
         }
     }
 }
@@ -1079,7 +1138,7 @@ __device__ __forceinline__ void adjoint_step(const Params<T>& P, BlockSmem<T>& S
     __syncthreads();
 }
 
-template <typename T, int NW>
+template <typename T, int NW, bool GEN>
 __device__ bool riccati(const Params<T>& P, BlockSmem<T>& S, const Lane& L, int n, const RicOpts<T>& o) {
     constexpr int A = SL<T>::A;
     const int sl = L.sl;
@@ -1177,7 +1236,7 @@ __device__ bool riccati(const Params<T>& P, BlockSmem<T>& S, const Lane& L, int 
                     S.ok[sl] = ok ? 1 : 0;
                 }
             } else {
-                if (t >= 1 && !vform) form_p<T, NW>(P, S, L, t - 1, alive && t - 1 < n);
+                if (t >= 1 && !vform) form_p<T, NW, GEN>(P, S, L, t - 1, alive && t - 1 < n);
                 tangent_step<T, NW>(P, S, L, t - 2, n, alive && n > 0);
             }
             __syncthreads();
@@ -1283,7 +1342,7 @@ __device__ bool riccati(const Params<T>& P, BlockSmem<T>& S, const Lane& L, int 
                     }
                 }
                 __syncthreads();
-                if (t >= 1 && L.w >= 1) form_p<T, NW>(P, S, L, t - 1, alive && t - 1 < n);
+                if (t >= 1 && L.w >= 1) form_p<T, NW, GEN>(P, S, L, t - 1, alive && t - 1 < n);
             }
             // ---- phase 3: rows j of N_{t-1} = F_{t-1}' M_t (zero in the V form) and q_{t-1} = c_{t-1} + F_{t-1}' v_t
             if (t >= 1) {
@@ -1301,7 +1360,7 @@ __device__ bool riccati(const Params<T>& P, BlockSmem<T>& S, const Lane& L, int 
 #pragma unroll 1
                 for (int j = L.w; j < NZ; j += NW) {
                     T Cd, c;
-                    cost_row(S, cs, sl, j, o.use_lo, Cd, c);
+                    cost_row<T, GEN>(P, S, cs, L, s, j, o.use_lo, Cd, c);
                     T nj[NU], qj;
                     if (j < 3 || (j >= 7 && j < 10)) {
                         const int p = j < 3 ? j : j - 7;
@@ -1372,7 +1431,7 @@ __device__ bool riccati(const Params<T>& P, BlockSmem<T>& S, const Lane& L, int 
 // nominal and cost rows are copied into shared memory by all warps one stage
 // ahead.  Returns 0 (step taken: du, J updated) or 1 (no candidate with a
 // finite cost: nominal kept).
-template <typename T, int NW>
+template <typename T, int NW, bool GEN>
 __device__ int line_search(const Params<T>& P, BlockSmem<T>& S, const Lane& L, int n, T& Jnom, T& du_out) {
     constexpr int A = SL<T>::A;
     const int sl = L.sl;
@@ -1425,7 +1484,34 @@ __device__ int line_search(const Params<T>& P, BlockSmem<T>& S, const Lane& L, i
                 const T eb = (sb[(R_X + i) * A] - sb[(R_XR + i) * A]) + sb[(R_XL + i) * A];
                 sx += dxv[i] * (sb[(R_Q + i) * A] * (eb + T(0.5) * dxv[i]));
             }
-            acc2(dJ, dJl, sx + su);
+            if constexpr (GEN) {
+                // d' (C (z + d/2) + c) with the general C_t, c_t
+                const T* Cm = Cmat(P, L.b, t);
+                const T* cv = cvec(P, L.b, t);
+                T zh[NZ], dz[NZ];
+#pragma unroll
+                for (int i = 0; i < NX; ++i) {
+                    dz[i] = dxv[i];
+                    zh[i] = (sb[(R_X + i) * A] + sb[(R_XL + i) * A]) + T(0.5) * dxv[i];
+                }
+#pragma unroll
+                for (int a = 0; a < NU; ++a) {
+                    const T ub = sb[(R_U + a) * A];
+                    dz[NX + a] = uh[a] - ub;
+                    zh[NX + a] = ub + T(0.5) * dz[NX + a];
+                }
+                T sg = T(0);
+#pragma unroll
+                for (int i = 0; i < NZ; ++i) {
+                    T r = cv[i];
+#pragma unroll
+                    for (int k = 0; k < NZ; ++k) r += Cm[i * NZ + k] * zh[k];
+                    sg += dz[i] * r;
+                }
+                acc2(dJ, dJl, sg);
+            } else {
+                acc2(dJ, dJl, sx + su);
+            }
             T* cr = P.cand + crow(P, c, L.pos, t, 0);
 #pragma unroll
             for (int i = 0; i < NX; ++i) {
@@ -1479,20 +1565,20 @@ __device__ int line_search(const Params<T>& P, BlockSmem<T>& S, const Lane& L, i
 //   dQ_t = dx_t * (x*_t - x_ref,t),  dx_ref,t = -Q_t * dx_t,  dx0 = vh_0.
 // Warp 0, one instance per lane.  K_t comes from the tape (store-all) or the
 // gain records the re-factorization wrote (recompute).
-template <typename T, int NW>
+template <typename T, int NW, bool GEN>
 __device__ void adjoint_forward(const Params<T>& P, const BlockSmem<T>& S, const Lane& L, int n,
                                 const AdjArgs<T>& A) {
     if (L.w != 0 || n <= 0) return;
     const size_t b = L.b;
-    T dx[NX], dq[NX];
+    T dx[NX], dq[NX], dcs[NZ];
 #pragma unroll
     for (int i = 0; i < NX; ++i) { dx[i] = T(0); dq[i] = T(0); A.dx0[b * NX + i] = S.vh[i][L.sl]; }
+#pragma unroll
+    for (int i = 0; i < NZ; ++i) dcs[i] = T(0);
     for (int t = 0; t < n; ++t) {
         // the stage's operands first
         const T* kr = A.recompute ? P.stg + srow(P, L.pos, t, R_K) : P.tape + trow(P, L.b, t, T_K);
         const T* xs = P.x + (b * P.N + t) * NX;
-        const T* xr = P.xref + (b * P.N + t) * NX;
-        const T* Qt = Qrow(P, L.b, t);
         T K[NU * NX], kh[NU], xv[NX], xrv[NX], qv[NX], us[NU];
 #pragma unroll
         for (int e = 0; e < NU * NX; ++e) K[e] = kr[e * GW];
@@ -1502,7 +1588,13 @@ __device__ void adjoint_forward(const Params<T>& P, const BlockSmem<T>& S, const
             us[a] = P.u[(b * P.N + t) * NU + a];
         }
 #pragma unroll
-        for (int i = 0; i < NX; ++i) { xv[i] = xs[i]; xrv[i] = xr[i]; qv[i] = Qt[i]; }
+        for (int i = 0; i < NX; ++i) xv[i] = xs[i];
+        if constexpr (!GEN) {
+            const T* xr = P.xref + (b * P.N + t) * NX;
+            const T* Qt = Qrow(P, L.b, t);
+#pragma unroll
+            for (int i = 0; i < NX; ++i) { xrv[i] = xr[i]; qv[i] = Qt[i]; }
+        }
         T du[NU];
 #pragma unroll
         for (int a = 0; a < NU; ++a) {
@@ -1511,12 +1603,41 @@ __device__ void adjoint_forward(const Params<T>& P, const BlockSmem<T>& S, const
             for (int i = 0; i < NX; ++i) s += K[a * NX + i] * dx[i];
             du[a] = s;
         }
+        if constexpr (GEN) {
+            // dL/dc_t = d_tau_t, dL/dC_t = 1/2 (d_tau_t z*_t' + z*_t d_tau_t')
+            T d[NZ], z[NZ];
 #pragma unroll
-        for (int i = 0; i < NX; ++i) {
-            const T e = xv[i] - xrv[i];
-            if (P.Nq > 1) A.dQ[(b * P.Nq + t) * NX + i] = dx[i] * e;
-            else dq[i] += dx[i] * e;
-            A.dxref[(b * P.N + t) * NX + i] = -qv[i] * dx[i];
+            for (int i = 0; i < NX; ++i) { d[i] = dx[i]; z[i] = xv[i]; }
+#pragma unroll
+            for (int a = 0; a < NU; ++a) { d[NX + a] = du[a]; z[NX + a] = us[a]; }
+            if (P.Nc > 1) {
+#pragma unroll
+                for (int i = 0; i < NZ; ++i) A.dc[(b * P.Nc + t) * NZ + i] = d[i];
+            } else {
+#pragma unroll
+                for (int i = 0; i < NZ; ++i) dcs[i] += d[i];
+            }
+            T* dCt = A.dC + (b * P.NC + (P.NC > 1 ? t : 0)) * (NZ * NZ);
+            const bool first = P.NC > 1 || t == 0;
+            // upper triangle formed, mirrored: dL/dC stays exactly symmetric
+            for (int i = 0; i < NZ; ++i) {
+#pragma unroll
+                for (int k = 0; k < NZ; ++k) {
+                    if (k < i) continue;
+                    const T v = T(0.5) * (d[i] * z[k] + z[i] * d[k]);
+                    const T w = first ? v : dCt[i * NZ + k] + v;
+                    dCt[i * NZ + k] = w;
+                    dCt[k * NZ + i] = w;
+                }
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < NX; ++i) {
+                const T e = xv[i] - xrv[i];
+                if (P.Nq > 1) A.dQ[(b * P.Nq + t) * NX + i] = dx[i] * e;
+                else dq[i] += dx[i] * e;
+                A.dxref[(b * P.N + t) * NX + i] = -qv[i] * dx[i];
+            }
         }
         if (t < n - 1) {
             T sp[32], nx[NX];
@@ -1526,21 +1647,37 @@ __device__ void adjoint_forward(const Params<T>& P, const BlockSmem<T>& S, const
             for (int i = 0; i < NX; ++i) dx[i] = nx[i];
         }
     }
-    for (int e = n * NX; e < P.N * NX; ++e) A.dxref[b * P.N * NX + e] = T(0);
-    if (P.Nq > 1) {
-        for (int e = n * NX; e < P.Nq * NX; ++e) A.dQ[b * P.Nq * NX + e] = T(0);
-    } else {
+    if constexpr (GEN) {
+        if (P.Nc > 1) {
+            for (int e = n * NZ; e < P.Nc * NZ; ++e) A.dc[b * P.Nc * NZ + e] = T(0);
+        } else {
 #pragma unroll
-        for (int i = 0; i < NX; ++i) A.dQ[b * NX + i] = dq[i];
+            for (int i = 0; i < NZ; ++i) A.dc[b * NZ + i] = dcs[i];
+        }
+        if (P.NC > 1)
+            for (int e = n * NZ * NZ; e < P.NC * NZ * NZ; ++e) A.dC[b * P.NC * NZ * NZ + e] = T(0);
+    } else {
+        for (int e = n * NX; e < P.N * NX; ++e) A.dxref[b * P.N * NX + e] = T(0);
+        if (P.Nq > 1) {
+            for (int e = n * NX; e < P.Nq * NX; ++e) A.dQ[b * P.Nq * NX + e] = T(0);
+        } else {
+#pragma unroll
+            for (int i = 0; i < NX; ++i) A.dQ[b * NX + i] = dq[i];
+        }
     }
 }
 
-template <typename T, int NW>
+template <typename T, int NW, bool GEN>
 __device__ void zero_grads(const Params<T>& P, const AdjArgs<T>& A, const Lane& L, bool act) {
     if (!act) return;
     const size_t b = L.b;
-    for (int e = L.w; e < P.Nq * NX; e += NW) A.dQ[b * P.Nq * NX + e] = T(0);
-    for (int e = L.w; e < P.N * NX; e += NW) A.dxref[b * P.N * NX + e] = T(0);
+    if constexpr (GEN) {
+        for (int e = L.w; e < P.NC * NZ * NZ; e += NW) A.dC[b * P.NC * NZ * NZ + e] = T(0);
+        for (int e = L.w; e < P.Nc * NZ; e += NW) A.dc[b * P.Nc * NZ + e] = T(0);
+    } else {
+        for (int e = L.w; e < P.Nq * NX; e += NW) A.dQ[b * P.Nq * NX + e] = T(0);
+        for (int e = L.w; e < P.N * NX; e += NW) A.dxref[b * P.N * NX + e] = T(0);
+    }
     for (int i = L.w; i < NX; i += NW) A.dx0[b * NX + i] = T(0);
 }
 

@@ -1,10 +1,11 @@
 // camp_kernels.cu -- the kernel and launch sequences of the batched MPC layer.
 //
-// One kernel template, k_mpc<T, NW>, runs every phase of the method through a
+// One kernel template, k_mpc<T, NW, GEN>, runs every phase of the method through a
 // phase machine over a pack of up to 32 instances (16 in FP64; one instance
 // per lane, NW warps per block splitting each instance's work).  Every phase has exactly
 // one call site, so every launch form executes the same machine code for it
-// and gives bit-identical results.
+// and gives bit-identical results.  GEN selects the stage cost: the diagonal
+// form of Eq. (2) (Q, x_ref, R, u_ref) or a general C_t, c_t.
 //
 // Forward (Sec. IV, Algorithm 2's inner loop):
 //   persistent form (one launch): each block pulls packs of instances from an
@@ -56,7 +57,7 @@ __device__ __forceinline__ bool pack_any(bool v) { return __any_sync(FULL, v) !=
 // mode >= 0: plain form, run phase `mode` once for pack blockIdx.x.
 // mode == MODE_FWD / MODE_BWD: persistent forward / backward over the work queue.
 // `last`: the plain line-search launch of the final iteration.
-template <typename T, int NW>
+template <typename T, int NW, bool GEN>
 __global__ void __launch_bounds__(NW * 32, 8 / NW) k_mpc(const __grid_constant__ Params<T> P,
                                                           const __grid_constant__ AdjArgs<T> A, int mode, int last) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -103,9 +104,9 @@ __global__ void __launch_bounds__(NW * 32, 8 / NW) k_mpc(const __grid_constant__
             int next = PH_DONE;
             if (ph == PH_INIT) {
                 const bool act = applies;
-                load_stage_rows<T, NW>(P, L, act ? n : 0, false);
+                load_stage_rows<T, NW, GEN>(P, L, act ? n : 0, false);
                 __syncthreads();
-                initial_rollout<T, NW>(P, S, L, act ? n : 0);
+                initial_rollout<T, NW, GEN>(P, S, L, act ? n : 0);
                 __syncthreads();
                 J = S.Jc[0][L.sl];
                 if (act) {
@@ -130,7 +131,7 @@ __global__ void __launch_bounds__(NW * 32, 8 / NW) k_mpc(const __grid_constant__
                     o.adj = &A;
                     o.replay = !A.recompute;
                 }
-                const bool ok = riccati<T, NW>(P, S, L, act ? n : 0, o);
+                const bool ok = riccati<T, NW, GEN>(P, S, L, act ? n : 0, o);
                 if (ph == PH_RIC) {
                     if (act && !ok) status = ST_NONPD;
                     next = pack_any(act && ok) ? PH_LS : after_fwd;
@@ -145,7 +146,7 @@ __global__ void __launch_bounds__(NW * 32, 8 / NW) k_mpc(const __grid_constant__
             } else if (ph == PH_LS) {
                 const bool act = applies && status == ST_RUNNING;
                 T du = T(0);
-                const int r = line_search<T, NW>(P, S, L, act ? n : 0, J, du);
+                const int r = line_search<T, NW, GEN>(P, S, L, act ? n : 0, J, du);
                 if (act) {
                     if (r) status = ST_STALLED;
                     else if (du < P.tol) status = ST_CONVERGED;
@@ -160,13 +161,13 @@ __global__ void __launch_bounds__(NW * 32, 8 / NW) k_mpc(const __grid_constant__
                 okb = L.valid && finished_ok(st);
                 next = PH_BFWD;
                 if (pack_any(okb)) {
-                    if (A.recompute) load_stage_rows<T, NW>(P, L, okb ? n : 0, true);
+                    if (A.recompute) load_stage_rows<T, NW, GEN>(P, L, okb ? n : 0, true);
                     next = PH_BSWEEP;
                 }
                 __syncthreads();
             } else if (ph == PH_BFWD) {
-                adjoint_forward<T, NW>(P, S, L, okb ? n : 0, A);
-                zero_grads<T, NW>(P, A, L, L.valid && !okb);
+                adjoint_forward<T, NW, GEN>(P, S, L, okb ? n : 0, A);
+                zero_grads<T, NW, GEN>(P, A, L, L.valid && !okb);
                 next = PH_DONE;
             }
             if (plain) break;
@@ -207,33 +208,47 @@ __global__ void k_lpt_order(const int* horizon, int B, int N, int* order) {
 // ------------------------------------------------------------ host side ----
 template <typename T> size_t block_smem_bytes() { return sizeof(BlockSmem<T>); }
 
-template <typename T> static const void* kernel_for(int nw) {
-    return nw == 8 ? (const void*)k_mpc<T, 8> : (const void*)k_mpc<T, 4>;
+// The kernel for nw warps per block, with the diagonal cost (gen false) or the
+// general cost of Eq. (2).
+template <typename T> static const void* kernel_for(int nw, bool gen = false) {
+    if (gen) return nw == 8 ? (const void*)k_mpc<T, 8, true> : (const void*)k_mpc<T, 4, true>;
+    return nw == 8 ? (const void*)k_mpc<T, 8, false> : (const void*)k_mpc<T, 4, false>;
 }
 
 template <typename T> cudaError_t prepare_kernels() {
     cudaError_t e;
-    for (int nw = 4; nw <= 8; nw *= 2) {
-        if ((e = cudaFuncSetAttribute(kernel_for<T>(nw), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)sizeof(BlockSmem<T>))))
-            return e;
-    }
+    for (int g = 0; g < 2; ++g)
+        for (int nw = 4; nw <= 8; nw *= 2) {
+            if ((e = cudaFuncSetAttribute(kernel_for<T>(nw, g == 1), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)sizeof(BlockSmem<T>))))
+                return e;
+        }
     return cudaSuccess;
 }
 
 template <typename T> int persistent_blocks_per_sm(int nw) {
-    int nb = 0;
-    const cudaError_t e =
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel_for<T>(nw), nw * 32, sizeof(BlockSmem<T>));
-    return e == cudaSuccess ? nb : 0;
+    int nb = 1 << 30;
+    for (int g = 0; g < 2; ++g) {
+        int k = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&k, kernel_for<T>(nw, g == 1), nw * 32,
+                                                          sizeof(BlockSmem<T>)) != cudaSuccess)
+            return 0;
+        nb = k < nb ? k : nb;
+    }
+    return nb;
 }
 
 template <typename T>
 static void launch_nw(int nw, int grid, cudaStream_t st, const Params<T>& P, const AdjArgs<T>& A, int mode,
                       int last) {
     const size_t smem = sizeof(BlockSmem<T>);
-    if (nw == 8) k_mpc<T, 8><<<grid, 256, smem, st>>>(P, A, mode, last);
-    else k_mpc<T, 4><<<grid, 128, smem, st>>>(P, A, mode, last);
+    if (P.Cg) {
+        if (nw == 8) k_mpc<T, 8, true><<<grid, 256, smem, st>>>(P, A, mode, last);
+        else k_mpc<T, 4, true><<<grid, 128, smem, st>>>(P, A, mode, last);
+    } else {
+        if (nw == 8) k_mpc<T, 8, false><<<grid, 256, smem, st>>>(P, A, mode, last);
+        else k_mpc<T, 4, false><<<grid, 128, smem, st>>>(P, A, mode, last);
+    }
 }
 
 template <typename T>

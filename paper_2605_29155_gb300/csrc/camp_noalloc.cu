@@ -98,6 +98,7 @@ extern "C" int mpc_solve_fwd_noalloc(const mpc_config* cfg, const mpc_problem* p
     int r = check_config(cfg);
     if (r != MPC_OK) return r;
     if (!p || !s) return MPC_ERR_ARG;
+    if (p->C) return MPC_ERR_ARG;       // the diagonal cost form only
     if (p->B < 0 || p->B > MPC_NOALLOC_B_MAX) return MPC_ERR_SHAPE;
     if (p->N < 1 || p->N > MPC_NOALLOC_N_MAX) return MPC_ERR_SHAPE;
     if (p->Nq != 1 && p->Nq != p->N) return MPC_ERR_SHAPE;

@@ -29,6 +29,10 @@ class Problem:
     u_hi: torch.Tensor      # [B, 4]
     horizon: torch.Tensor | None = None   # [B] int32
     u_init: torch.Tensor | None = None    # [B, N, 4]
+    # general stage cost of Eq. (2) in place of the diagonal one (Q, x_ref, R
+    # unused; u_ref still gives the start U^0)
+    C: torch.Tensor | None = None         # [B, NC, 17, 17], NC in {1, N}
+    c: torch.Tensor | None = None         # [B, Nc, 17], Nc in {1, N}
 
     @property
     def B(self):
@@ -44,10 +48,12 @@ class Problem:
             return torch.as_tensor(a, dtype=dtype, device=device).contiguous()
         hz = d.get("horizon")
         ui = d.get("u_init")
+        Cg, cg = d.get("C"), d.get("c")
         return Problem(x0=t(d["x0"]), Q=t(d["Q"]), x_ref=t(d["x_ref"]), R=t(d["R"]), u_ref=t(d["u_ref"]),
                        u_lo=t(d["u_lo"]), u_hi=t(d["u_hi"]),
                        horizon=None if hz is None else torch.as_tensor(hz, dtype=torch.int32, device=device).contiguous(),
-                       u_init=None if ui is None else t(ui))
+                       u_init=None if ui is None else t(ui), C=None if Cg is None else t(Cg),
+                       c=None if cg is None else t(cg))
 
 
 @dataclasses.dataclass
@@ -113,13 +119,18 @@ class DiffMPC:
 
     # -- marshalling ----------------------------------------------------------------
     def _cproblem(self, p: Problem):
-        for name in ("x0", "Q", "x_ref", "R", "u_ref", "u_lo", "u_hi"):
+        names = ("x0", "Q", "x_ref", "R", "u_ref", "u_lo", "u_hi") + (("C", "c") if p.C is not None else ())
+        for name in names:
             t = getattr(p, name)
-            if t.dtype != self.dtype or not t.is_contiguous() or t.device.type != "cuda":
+            if t is None or t.dtype != self.dtype or not t.is_contiguous() or t.device.type != "cuda":
                 raise ValueError(f"{name} must be a contiguous {self.dtype} CUDA tensor")
+        if p.C is not None and (p.C.dim() != 4 or p.C.shape[2:] != (17, 17) or p.c.dim() != 3 or p.c.shape[2] != 17):
+            raise ValueError("C must be [B, NC, 17, 17] and c [B, Nc, 17]")
         return camp.mpc_problem(B=p.B, N=p.N, horizon=_ptr(p.horizon), x0=_ptr(p.x0), Q=_ptr(p.Q),
                                 Nq=p.Q.shape[1], x_ref=_ptr(p.x_ref), R=_ptr(p.R), u_ref=_ptr(p.u_ref),
-                                u_lo=_ptr(p.u_lo), u_hi=_ptr(p.u_hi), u_init=_ptr(p.u_init))
+                                u_lo=_ptr(p.u_lo), u_hi=_ptr(p.u_hi), u_init=_ptr(p.u_init),
+                                C=_ptr(p.C), NC=0 if p.C is None else p.C.shape[1],
+                                c=_ptr(p.c), Nc=0 if p.c is None else p.c.shape[1])
 
     def alloc_solution(self, B, N) -> Solution:
         dev, dt = self.device, self.dtype
@@ -153,6 +164,19 @@ class DiffMPC:
         camp.check(camp.mpc_solve_bwd(self.h, self._cproblem(p), self._csolution(s), gu.data_ptr(), _ptr(gx),
                                       dQ.data_ptr(), dxr.data_ptr(), dx0.data_ptr(), stream), "mpc_solve_bwd")
         return dQ, dxr, dx0
+
+    def backward_general(self, p: Problem, s: Solution, grad_u, grad_x=None, out=None):
+        """Gradients of a general-cost problem: (dL/dC, dL/dc, dL/dx0)."""
+        if out is None:
+            out = (torch.empty_like(p.C), torch.empty_like(p.c), torch.empty_like(p.x0))
+        dC, dc, dx0 = out
+        gu = grad_u.contiguous()
+        gx = None if grad_x is None else grad_x.contiguous()
+        stream = torch.cuda.current_stream(self.device).cuda_stream
+        camp.check(camp.mpc_solve_bwd_general(self.h, self._cproblem(p), self._csolution(s), gu.data_ptr(), _ptr(gx),
+                                              dC.data_ptr(), dc.data_ptr(), dx0.data_ptr(), stream),
+                   "mpc_solve_bwd_general")
+        return dC, dc, dx0
 
     def autotune(self, p: Problem, s: Solution | None = None) -> int:
         s = s if s is not None else self.alloc_solution(p.B, p.N)

@@ -1,0 +1,166 @@
+"""Parity of the general stage cost of Eq. (2) -- dense C_t (state-control
+cross terms included) and c_t -- on the CUDA path (through the C ABI) with the
+FP64 oracle, and its gradients dL/dC_t, dL/dc_t, dL/dx0."""
+import numpy as np
+import pytest
+
+import workloads as W
+from gpu_support import G_TOL64C, J_TOL64C, QUAD, TIE64
+from oracle import adjoint, ilqr
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def general_problem(B, N, seed, NC, Nc, cfg="hover"):
+    """A seeded batch with C = diag(Q, R) + 0.05 M'M / 17 (M ~ N(0, 1), 17 x 17)
+    and c_t = -C z_ref,t, z_ref,t = [x_ref_t; u_ref]: the hover or track
+    targets with cross terms.  NC, Nc in {1, N}."""
+    b = W.hover_targets(B, N, seed=seed) if cfg == "hover" else W.race_track(B, N, seed=seed)
+    rng = np.random.default_rng(seed + 100)
+    C = np.zeros((B, NC, 17, 17))
+    c = np.zeros((B, Nc, 17))
+    for i in range(B):
+        for k in range(NC):
+            M = rng.normal(size=(17, 17))
+            C[i, k] = np.diag(np.concatenate([b["Q"][i, 0], b["R"][i]])) + 0.05 * (M.T @ M) / 17
+        for k in range(Nc):
+            Ck = C[i, k if NC > 1 else 0]
+            c[i, k] = -Ck @ np.concatenate([b["x_ref"][i, k], b["u_ref"][i]])
+    return dict(b, C=C, c=c)
+
+
+def run_general(prob, dtype, max_iter, tol, gu, gx=None, store_mode="store_all"):
+    from paper_2605_29155_gb300 import DiffMPC, Problem
+    B, N = prob["x0"].shape[0], prob["x_ref"].shape[1]
+    solver = DiffMPC(N_max=N, B_max=B, dtype=dtype, max_iter=max_iter, tol=tol, store_mode=store_mode)
+    p = Problem.from_numpy(prob, dtype=dtype)
+    s = solver.solve(p)
+    g_u = torch.as_tensor(gu, dtype=dtype, device="cuda")
+    g_x = None if gx is None else torch.as_tensor(gx, dtype=dtype, device="cuda")
+    dC, dc, dx0 = solver.backward_general(p, s, g_u, g_x)
+    torch.cuda.synchronize()
+    out = dict(u=s.u, x=s.x, cost=s.cost, iters=s.iters, status=s.status, dC=dC, dc=dc, dx0=dx0)
+    res = {k: v.detach().cpu().numpy() for k, v in out.items()}
+    solver.close()
+    return res
+
+
+def oracle_general(prob, idx, max_iter, tol, gu, gx=None):
+    out = []
+    N = prob["x_ref"].shape[1]
+    for i in idx:
+        pr = ilqr.problem_from_batch(prob, i)
+        so = ilqr.solve(QUAD, pr, max_iter, tol)
+        gr = adjoint.adjoint(pr, so, np.zeros((N, 13)) if gx is None else gx[i], gu[i])
+        out.append((pr, so, gr))
+    return out
+
+
+def rel(a, b, floor):
+    return float(np.linalg.norm(np.ravel(a) - np.ravel(b)) / max(np.linalg.norm(np.ravel(b)), floor))
+
+
+def _grads(B, N, seed):
+    rng = np.random.default_rng(seed)
+    return rng.normal(size=(B, N, 4)), rng.normal(size=(B, N, 13)) * 0.1
+
+
+@pytest.mark.parametrize("NC,Nc,cfg", [(1, 10, "hover"), (10, 1, "hover"), (10, 10, "track")])
+def test_fp64_general_cost_identical_to_oracle(NC, Nc, cfg):
+    """Same kernels in double, three iterations with tol = 0 (every decision
+    clear-cut): controls, cost and dL/dC, dL/dc, dL/dx0 agree to rounding,
+    with C shared or per stage and c shared or per stage."""
+    B, N = 8, 10
+    prob = general_problem(B, N, 3, NC, Nc, cfg)
+    gu, gx = _grads(B, N, 5)
+    g = run_general(prob, torch.float64, 3, 0.0, gu, gx)
+    orc = oracle_general(prob, range(B), 3, 0.0, gu, gx)
+    compared = 0
+    for i, (pr, so, gr) in enumerate(orc):
+        if so.ls_margin < TIE64:
+            continue
+        compared += 1
+        assert g["status"][i] == so.status and g["iters"][i] == so.iters, i
+        assert rel(g["u"][i], so.U, 1e-6) < 1e-8, i
+        assert abs(g["cost"][i] - ilqr.total_cost(pr, so.X, so.U)) <= 1e-10 * max(1.0, abs(g["cost"][i])), i
+        for name, a, b_ in (("dC", g["dC"][i], gr.dC), ("dc", g["dc"][i], gr.dc), ("dx0", g["dx0"][i], gr.dx0)):
+            assert rel(a, b_, 1e-9) < 1e-7, (i, name, rel(a, b_, 1e-9))
+    assert compared >= B - 1
+    # dL/dC is symmetric, as the oracle's
+    assert np.allclose(g["dC"], np.swapaxes(g["dC"], -1, -2), rtol=0, atol=0)
+
+
+@pytest.mark.parametrize("cfg", ["hover", "track"])
+def test_fp32_general_cost_matches_oracle(cfg):
+    """The product path: FP32 against the FP64 oracle on converged instances,
+    controls within 1e-4, each gradient block within 1e-3 (relative), and the
+    cost within 1e-5 of the size of its terms: the general cost is not centred,
+    so 1/2 z'Cz and c'z largely cancel and a rounding error of the sum is
+    relative to sum_t |1/2 z'C z| + |c'z|, not to the small total."""
+    B, N = 32, 20
+    prob = general_problem(B, N, 7, 1, N, cfg)
+    gu, _ = _grads(B, N, 8)
+    g = run_general(prob, torch.float32, 30, 1e-6, gu)
+    orc = oracle_general(prob, range(B), 30, 1e-6, gu)
+    compared, bad = 0, []
+    for i, (pr, so, gr) in enumerate(orc):
+        if so.status != ilqr.CONVERGED or g["status"][i] not in (0, 1):
+            continue
+        compared += 1
+        J = ilqr.total_cost(pr, so.X, so.U)
+        zs = [np.concatenate([so.X[t], so.U[t]]) for t in range(pr.n)]
+        scale = sum(abs(0.5 * z @ pr.Ct(t) @ z) + abs(pr.ct(t) @ z) for t, z in enumerate(zs))
+        errs = dict(u=rel(g["u"][i], so.U, 1e-6), J=abs(g["cost"][i] - J) / max(scale, 1e-12),
+                    dC=rel(g["dC"][i], gr.dC, 1e-9), dc=rel(g["dc"][i], gr.dc, 1e-9), dx0=rel(g["dx0"][i], gr.dx0, 1e-9))
+        if errs["u"] > 1e-4 or errs["J"] > 1e-5 or max(errs["dC"], errs["dc"], errs["dx0"]) > 1e-3:
+            bad.append((i, errs))
+    print(cfg, "compared", compared, "bad", bad[:3])
+    assert compared >= 0.75 * B
+    assert not bad, bad[:3]
+
+
+def test_diagonal_C_through_the_general_path_matches_the_diagonal_path():
+    """C_t = diag(Q_t, R), c_t = [-Q_t x_ref_t; -R u_ref] given explicitly: the
+    same controls as the diagonal form, a cost lower by the dropped constant,
+    and dL/dQ_i = dL/dC_ii - sum_t x_ref,t,i dL/dc_t,i.  FP64 to convergence:
+    the two forms round the cost gradient differently, so the last step (below
+    tol) may differ, as between any two converged FP64 runs."""
+    from gpu_support import run_gpu
+    B, N = 6, 10
+    b = W.hover_targets(B, N, seed=9)
+    C = np.zeros((B, 1, 17, 17))
+    c = np.zeros((B, N, 17))
+    for i in range(B):
+        C[i, 0] = np.diag(np.concatenate([b["Q"][i, 0], b["R"][i]]))
+        for t in range(N):
+            c[i, t] = np.concatenate([-b["Q"][i, 0] * b["x_ref"][i, t], -b["R"][i] * b["u_ref"][i]])
+    gu, _ = _grads(B, N, 10)
+    d = run_gpu(b, torch.float64, 10, 1e-9, gu)
+    g = run_general(dict(b, C=C, c=c), torch.float64, 10, 1e-9, gu)
+    np.testing.assert_allclose(g["u"], d["u"], rtol=0, atol=1e-8)
+    const = 0.5 * (np.einsum("bi,bti,bti->b", b["Q"][:, 0], b["x_ref"], b["x_ref"]) +
+                   N * np.einsum("bi,bi,bi->b", b["R"], b["u_ref"], b["u_ref"]))
+    np.testing.assert_allclose(g["cost"] + const, d["cost"], rtol=J_TOL64C, atol=1e-12)
+    dQ = np.diagonal(g["dC"][:, 0], axis1=-2, axis2=-1)[:, :13] - np.einsum("bti,bti->bi", b["x_ref"], g["dc"][:, :, :13])
+    for a, b_ in ((dQ, d["dQ"][:, 0]), (g["dx0"], d["dx0"])):
+        for i in range(B):
+            assert rel(a[i], b_[i], 1e-9) < G_TOL64C, i
+
+
+def test_general_recompute_backward_is_bit_identical_to_store_all():
+    B, N = 40, 12
+    prob = general_problem(B, N, 11, N, N, "track")
+    gu, gx = _grads(B, N, 12)
+    a = run_general(prob, torch.float32, 8, 1e-6, gu, gx, store_mode="store_all")
+    r = run_general(prob, torch.float32, 8, 1e-6, gu, gx, store_mode="recompute")
+    for k in ("u", "dC", "dc", "dx0"):
+        assert np.array_equal(a[k], r[k]), k
