@@ -164,3 +164,42 @@ def test_general_recompute_backward_is_bit_identical_to_store_all():
     r = run_general(prob, torch.float32, 8, 1e-6, gu, gx, store_mode="recompute")
     for k in ("u", "dC", "dc", "dx0"):
         assert np.array_equal(a[k], r[k]), k
+
+
+def test_general_cost_api_errors():
+    """Validation of the general-cost fields: c is required with C, NC and Nc
+    must be 1 or N, each backward entry point refuses the other cost form, and
+    the allocation-free forward takes only the diagonal form."""
+    from paper_2605_29155_gb300 import DiffMPC, Problem, camp
+    B, N = 4, 10
+    prob = general_problem(B, N, 13, 1, N)
+    p = Problem.from_numpy(prob)
+    s = DiffMPC(N_max=N, B_max=B)
+    sol = s.alloc_solution(B, N)
+    st = torch.cuda.current_stream().cuda_stream
+    cs = s._csolution(sol)
+    cp = s._cproblem(p)
+    cp.c = None
+    assert camp.mpc_solve_fwd(s.h, cp, cs, st) == camp.MPC_ERR_ARG
+    cp = s._cproblem(p)
+    cp.NC = 3
+    assert camp.mpc_solve_fwd(s.h, cp, cs, st) == camp.MPC_ERR_SHAPE
+    cp = s._cproblem(p)
+    cp.Nc = 0
+    assert camp.mpc_solve_fwd(s.h, cp, cs, st) == camp.MPC_ERR_SHAPE
+    # Q and x_ref are not needed with a general cost
+    cp = s._cproblem(p)
+    cp.Q = None
+    cp.x_ref = None
+    assert camp.mpc_solve_fwd(s.h, cp, cs, st) == camp.MPC_OK
+    g = torch.zeros(B, N, 4, device="cuda")
+    dC, dc, dx0 = torch.empty_like(p.C), torch.empty_like(p.c), torch.empty_like(p.x0)
+    dQ, dxr = torch.empty_like(p.Q), torch.empty_like(p.x_ref)
+    assert camp.mpc_solve_bwd(s.h, s._cproblem(p), cs, g.data_ptr(), 0, dQ.data_ptr(), dxr.data_ptr(),
+                              dx0.data_ptr(), st) == camp.MPC_ERR_STATE
+    pd = Problem.from_numpy({k: v for k, v in prob.items() if k not in ("C", "c")})
+    assert camp.mpc_solve_bwd_general(s.h, s._cproblem(pd), cs, g.data_ptr(), 0, dC.data_ptr(), dc.data_ptr(),
+                                      dx0.data_ptr(), st) == camp.MPC_ERR_STATE
+    assert camp.mpc_solve_fwd_noalloc(s.cfg, s._cproblem(p), cs, st) == camp.MPC_ERR_ARG
+    torch.cuda.synchronize()
+    s.close()
