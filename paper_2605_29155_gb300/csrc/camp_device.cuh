@@ -1617,18 +1617,12 @@ __device__ void adjoint_forward(const Params<T>& P, const BlockSmem<T>& S, const
 #pragma unroll
                 for (int i = 0; i < NZ; ++i) dcs[i] += d[i];
             }
-            T* dCt = A.dC + (b * P.NC + (P.NC > 1 ? t : 0)) * (NZ * NZ);
-            const bool first = P.NC > 1 || t == 0;
-            // upper triangle formed, mirrored: dL/dC stays exactly symmetric
-            for (int i = 0; i < NZ; ++i) {
+            // d_tau_t and z*_t into the (free) candidate scratch, by position:
+            // all warps form dL/dC from them afterwards (assemble_dC)
 #pragma unroll
-                for (int k = 0; k < NZ; ++k) {
-                    if (k < i) continue;
-                    const T v = T(0.5) * (d[i] * z[k] + z[i] * d[k]);
-                    const T w = first ? v : dCt[i * NZ + k] + v;
-                    dCt[i * NZ + k] = w;
-                    dCt[k * NZ + i] = w;
-                }
+            for (int i = 0; i < NZ; ++i) {
+                P.cand[crow(P, 0, L.pos, t, i)] = d[i];
+                P.cand[crow(P, 1, L.pos, t, i)] = z[i];
             }
         } else {
 #pragma unroll
@@ -1654,8 +1648,6 @@ __device__ void adjoint_forward(const Params<T>& P, const BlockSmem<T>& S, const
 #pragma unroll
             for (int i = 0; i < NZ; ++i) A.dc[b * NZ + i] = dcs[i];
         }
-        if (P.NC > 1)
-            for (int e = n * NZ * NZ; e < P.NC * NZ * NZ; ++e) A.dC[b * P.NC * NZ * NZ + e] = T(0);
     } else {
         for (int e = n * NX; e < P.N * NX; ++e) A.dxref[b * P.N * NX + e] = T(0);
         if (P.Nq > 1) {
@@ -1663,6 +1655,42 @@ __device__ void adjoint_forward(const Params<T>& P, const BlockSmem<T>& S, const
         } else {
 #pragma unroll
             for (int i = 0; i < NX; ++i) A.dQ[b * NX + i] = dq[i];
+        }
+    }
+}
+
+// General cost: dL/dC_t = 1/2 (d_tau_t z*_t' + z*_t d_tau_t') from the stage
+// vectors adjoint_forward left in the candidate scratch (after a block
+// barrier), summed over the stages when C is shared.  The 153 upper entries
+// are split over the NW warps and mirrored, so dL/dC is exactly symmetric;
+// stages past the horizon get zeros.
+template <typename T, int NW>
+__device__ void assemble_dC(const Params<T>& P, const AdjArgs<T>& A, const Lane& L, int n) {
+    if (!L.valid || n <= 0) return;
+    const size_t b = L.b;
+    for (int e = L.w; e < NZ * (NZ + 1) / 2; e += NW) {
+        int i = 0, r = e;
+        while (r >= NZ - i) { r -= NZ - i; ++i; }
+        const int k = i + r;
+        T acc = T(0);
+        for (int t = 0; t < P.N; ++t) {
+            T v = T(0);
+            if (t < n) {
+                const T di = P.cand[crow(P, 0, L.pos, t, i)], dk = P.cand[crow(P, 0, L.pos, t, k)];
+                const T zi = P.cand[crow(P, 1, L.pos, t, i)], zk = P.cand[crow(P, 1, L.pos, t, k)];
+                v = T(0.5) * (di * zk + zi * dk);
+            }
+            if (P.NC > 1) {
+                T* dCt = A.dC + (b * P.NC + t) * (NZ * NZ);
+                dCt[i * NZ + k] = v;
+                dCt[k * NZ + i] = v;
+            } else {
+                acc += v;
+            }
+        }
+        if (P.NC == 1) {
+            A.dC[b * NZ * NZ + i * NZ + k] = acc;
+            A.dC[b * NZ * NZ + k * NZ + i] = acc;
         }
     }
 }

@@ -167,6 +167,10 @@ __global__ void __launch_bounds__(NW * 32, 8 / NW) k_mpc(const __grid_constant__
                 __syncthreads();
             } else if (ph == PH_BFWD) {
                 adjoint_forward<T, NW, GEN>(P, S, L, okb ? n : 0, A);
+                if constexpr (GEN) {
+                    __syncthreads();
+                    assemble_dC<T, NW>(P, A, L, okb ? n : 0);
+                }
                 zero_grads<T, NW, GEN>(P, A, L, L.valid && !okb);
                 next = PH_DONE;
             }
