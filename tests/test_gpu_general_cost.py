@@ -38,10 +38,10 @@ def general_problem(B, N, seed, NC, Nc, cfg="hover"):
     return dict(b, C=C, c=c)
 
 
-def run_general(prob, dtype, max_iter, tol, gu, gx=None, store_mode="store_all"):
+def run_general(prob, dtype, max_iter, tol, gu, gx=None, store_mode="store_all", tpi=0):
     from paper_2605_29155_gb300 import DiffMPC, Problem
     B, N = prob["x0"].shape[0], prob["x_ref"].shape[1]
-    solver = DiffMPC(N_max=N, B_max=B, dtype=dtype, max_iter=max_iter, tol=tol, store_mode=store_mode)
+    solver = DiffMPC(N_max=N, B_max=B, dtype=dtype, max_iter=max_iter, tol=tol, store_mode=store_mode, tpi=tpi)
     p = Problem.from_numpy(prob, dtype=dtype)
     s = solver.solve(p)
     g_u = torch.as_tensor(gu, dtype=dtype, device="cuda")
@@ -74,15 +74,16 @@ def _grads(B, N, seed):
     return rng.normal(size=(B, N, 4)), rng.normal(size=(B, N, 13)) * 0.1
 
 
-@pytest.mark.parametrize("NC,Nc,cfg", [(1, 10, "hover"), (10, 1, "hover"), (10, 10, "track")])
-def test_fp64_general_cost_identical_to_oracle(NC, Nc, cfg):
+@pytest.mark.parametrize("NC,Nc,cfg,tpi", [(1, 10, "hover", 4), (10, 1, "hover", 4), (10, 10, "track", 4),
+                                            (1, 10, "track", 8)])
+def test_fp64_general_cost_identical_to_oracle(NC, Nc, cfg, tpi):
     """Same kernels in double, three iterations with tol = 0 (every decision
     clear-cut): controls, cost and dL/dC, dL/dc, dL/dx0 agree to rounding,
     with C shared or per stage and c shared or per stage."""
     B, N = 8, 10
     prob = general_problem(B, N, 3, NC, Nc, cfg)
     gu, gx = _grads(B, N, 5)
-    g = run_general(prob, torch.float64, 3, 0.0, gu, gx)
+    g = run_general(prob, torch.float64, 3, 0.0, gu, gx, tpi=tpi)
     orc = oracle_general(prob, range(B), 3, 0.0, gu, gx)
     compared = 0
     for i, (pr, so, gr) in enumerate(orc):
@@ -109,7 +110,7 @@ def test_fp32_general_cost_matches_oracle(cfg):
     B, N = 32, 20
     prob = general_problem(B, N, 7, 1, N, cfg)
     gu, _ = _grads(B, N, 8)
-    g = run_general(prob, torch.float32, 30, 1e-6, gu)
+    g = run_general(prob, torch.float32, 30, 1e-6, gu, tpi=8 if cfg == "track" else 4)
     orc = oracle_general(prob, range(B), 30, 1e-6, gu)
     compared, bad = 0, []
     for i, (pr, so, gr) in enumerate(orc):
