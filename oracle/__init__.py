@@ -19,10 +19,13 @@ complex-step check drives it).  Each function cites the passage it follows:
              w.r.t. (C_t, c_t) and x_init at the converged solution), as an
              adjoint LQR sweep, plus an independent dense-KKT solve used only to
              cross-check it.
+  costmap.py the actor's cost map (Sec. V-A: MLP with two 512-unit ReLU
+             layers and a sigmoid output), observation -> per-stage Q, with
+             its backward from dL/dQ.
 
 Pins (tests/test_oracle_*.py) tie every function to something other than
 itself: complex-step and finite differences, closed-form trajectories, exact
 LQR on linear-quadratic instances, brute-force active-set enumeration and
 dense KKT solves.
 """
-from . import model, boxqp, ilqr, adjoint  # noqa: F401
+from . import model, boxqp, ilqr, adjoint, costmap  # noqa: F401
