@@ -191,3 +191,24 @@ def test_general_adjoint_matches_fd_of_whole_solver_linear_dynamics(seed):
                L(dataclasses.replace(prob, C=prob.C - eps * E))) / (2 * eps)
         ana = gr.dC[t, i, j] if i == j else gr.dC[t, i, j] + gr.dC[t, j, i]
         assert abs(num - ana) <= 1e-5 * max(1.0, abs(num)), (t, i, j, num, ana)
+
+
+@pytest.mark.parametrize("general", [False, True])
+def test_stagewise_cost_change_is_the_difference_of_costs(general):
+    """Reading R4: the line search compares candidates by the stage-wise cost
+    change d'(C (z + d/2) + c); for the quadratic cost it equals
+    J(z + d) - J(z) exactly (up to rounding), for the diagonal and the
+    general form, and its scale bounds the terms."""
+    rng = np.random.default_rng(21)
+    b = W.hover_targets(2, 7, seed=22)
+    prob = ilqr.problem_from_batch(b, 1)
+    if general:
+        M = rng.normal(size=(7, 17, 17))
+        C = np.einsum("tki,tkj->tij", M, M) / 17 + np.diag(np.concatenate([prob.Q[0], prob.R]))
+        prob = dataclasses.replace(prob, C=C, c=rng.normal(size=(7, 17)))
+    X, U = rng.normal(size=(7, 13)), rng.normal(size=(7, 4)) + 2.0
+    Xa, Ua = X + 0.1 * rng.normal(size=X.shape), U + 0.1 * rng.normal(size=U.shape)
+    dJ, scale = ilqr.cost_change(prob, X, U, Xa, Ua, with_scale=True)
+    ref = ilqr.total_cost(prob, Xa, Ua) - ilqr.total_cost(prob, X, U)
+    assert abs(dJ - ref) <= 1e-12 * max(1.0, abs(ilqr.total_cost(prob, X, U)))
+    assert scale >= abs(dJ)
