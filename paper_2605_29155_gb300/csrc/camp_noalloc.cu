@@ -14,10 +14,14 @@
 // runs on, until the process exits.
 //
 // Set-up: the first call on a device looks up the array's device address
-// (cudaGetSymbolAddress) with that device current; make that first call before
-// any stream capture.  Every call shares the one array and leaves its contents
-// behind: the work-queue counter is cleared on the stream at the start of each
-// call, and every other scratch entry is written before it is read.  Calls
+// (cudaGetSymbolAddress) and raises the kernels' shared-memory limit
+// (cudaFuncSetAttribute) with that device current; make that first call before
+// any stream capture.  The address is cached per device for the life of the
+// process: after cudaDeviceReset (or any teardown of the device's primary
+// context) it is stale, and this entry point must not be called again.
+// Every call shares the one array and leaves its contents behind: the
+// work-queue counter is cleared on the stream at the start of each call, and
+// every other scratch entry is written before it is read.  Calls
 // whose GPU work overlaps (different streams, or different host threads
 // without ordering) race on the array and must not be issued.
 #include <math.h>
@@ -57,6 +61,11 @@ std::mutex g_setup_mutex;
 float* g_scratch_dev[NA_MAX_DEVICES] = {};
 int g_num_sms[NA_MAX_DEVICES] = {};
 
+// Once per device, with that device current: the array's device address, the
+// SM count, and the kernels' shared-memory limit.  The FP32 kernels need far
+// more dynamic shared memory than the default 48 KB; mpc_create raises that
+// limit too, but a caller of this entry point may never create a handle.
+// cudaFuncSetAttribute allocates nothing.
 int setup_device(int dev, float** scratch, int* sms) {
     if (dev < 0 || dev >= NA_MAX_DEVICES) return MPC_ERR_CUDA;
     std::lock_guard<std::mutex> lock(g_setup_mutex);
@@ -66,6 +75,7 @@ int setup_device(int dev, float** scratch, int* sms) {
         int n = 0;
         if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0)
             return MPC_ERR_CUDA;
+        if (prepare_kernels<float>() != cudaSuccess) return MPC_ERR_CUDA;
         g_num_sms[dev] = n;
         g_scratch_dev[dev] = (float*)p;
     }

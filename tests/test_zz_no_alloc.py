@@ -3,6 +3,10 @@ device memory while running (its scratch is a fixed device array inside the
 library).  Checked through the C ABI against mpc_solve_fwd on two calls in a
 row, the second on a different problem shape, so that state the shared array
 keeps from the first call cannot leak into the second."""
+import os
+import subprocess
+import sys
+
 import numpy as np
 import pytest
 
@@ -85,3 +89,73 @@ def test_noalloc_rejects_sizes_beyond_its_array(lib):
     assert lib.mpc_solve_fwd_noalloc(cfg, long_, lib.mpc_solution(), 0) == lib.MPC_ERR_SHAPE
     cfg.dtype = lib.MPC_F64
     assert lib.mpc_solve_fwd_noalloc(cfg, lib.mpc_problem(B=8, N=20, Nq=1), lib.mpc_solution(), 0) == lib.MPC_ERR_ARG
+
+
+_FRESH = r"""
+import sys
+import numpy as np
+import torch
+sys.path.insert(0, sys.argv[1])
+import workloads as W
+from paper_2605_29155_gb300 import camp
+prob = W.hover_targets(16, 10, seed=31)
+B, N = 16, 10
+dev = torch.device("cuda", 0)
+torch.cuda.set_device(dev)
+t = {k: torch.as_tensor(prob[k], dtype=torch.float32, device=dev).contiguous()
+     for k in ("x0", "Q", "x_ref", "R", "u_ref", "u_lo", "u_hi")}
+out = dict(u=torch.full((B, N, 4), float("nan"), device=dev), x=torch.full((B, N, 13), float("nan"), device=dev),
+           cost=torch.full((B,), float("nan"), device=dev), iters=torch.zeros(B, dtype=torch.int32, device=dev),
+           status=torch.full((B,), -7, dtype=torch.int32, device=dev),
+           tape=torch.empty((B + 31) // 32 * 32 * N * 210, device=dev))
+cfg = camp.mpc_config_default()
+cfg.max_iter, cfg.tol = 20, 1e-6
+cp = camp.mpc_problem(B=B, N=N, x0=t["x0"].data_ptr(), Q=t["Q"].data_ptr(), Nq=t["Q"].shape[1],
+                      x_ref=t["x_ref"].data_ptr(), R=t["R"].data_ptr(), u_ref=t["u_ref"].data_ptr(),
+                      u_lo=t["u_lo"].data_ptr(), u_hi=t["u_hi"].data_ptr())
+cs = camp.mpc_solution(u=out["u"].data_ptr(), x=out["x"].data_ptr(), cost=out["cost"].data_ptr(),
+                       iters=out["iters"].data_ptr(), status=out["status"].data_ptr(), tape=out["tape"].data_ptr(),
+                       tape_bytes=out["tape"].numel() * 4)
+code = camp.mpc_solve_fwd_noalloc(cfg, cp, cs, torch.cuda.current_stream().cuda_stream)
+assert code == camp.MPC_OK, camp.mpc_strerror(code)
+torch.cuda.synchronize()
+res = {k + "_na": v.cpu().numpy() for k, v in out.items() if k != "tape"}
+# a handle solve on the same inputs, only after the allocation-free call
+from paper_2605_29155_gb300 import DiffMPC, Problem
+ref = DiffMPC(N_max=N, B_max=B, max_iter=20, tol=1e-6)
+s = ref.solve(Problem.from_numpy(prob))
+torch.cuda.synchronize()
+res.update({k + "_h": getattr(s, k).cpu().numpy() for k in ("u", "x", "cost", "iters", "status")})
+ref.close()
+np.savez(sys.argv[2], **res)
+"""
+
+
+def test_noalloc_in_a_fresh_process_without_any_handle(lib, tmp_path):
+    """The entry point's own use: a process that never creates a handle (so
+    nothing but this call prepares the kernels) solves a hover batch; its
+    result is checked against the FP64 oracle and against a handle solve made
+    afterwards in the same process."""
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    out = tmp_path / "fresh.npz"
+    r = subprocess.run([sys.executable, "-c", _FRESH, root, str(out)], capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stdout[-2000:] + r.stderr[-4000:]
+    d = np.load(out)
+    np.testing.assert_array_equal(d["status_na"], d["status_h"])
+    np.testing.assert_array_equal(d["iters_na"], d["iters_h"])
+    for k in ("u", "x", "cost"):
+        a, b = d[k + "_na"], d[k + "_h"]
+        assert np.isfinite(a).all()
+        assert np.max(np.abs(a - b)) <= U_TOL32 * max(1.0, np.abs(b).max()), k
+    from gpu_support import oracle_solve
+    prob = W.hover_targets(16, 10, seed=31)
+    orc = oracle_solve(prob, range(16), 20, 1e-6)
+    compared = 0
+    for i, (_, so, _) in enumerate(orc):
+        if so.status != 0:
+            continue
+        compared += 1
+        err = np.linalg.norm(d["u_na"][i] - so.U) / max(np.linalg.norm(so.U), 1e-6)
+        assert err <= U_TOL32, (i, err)
+        assert abs(float(d["cost_na"][i]) - so.J) <= J_TOL32 * max(abs(so.J), 1e-12), i
+    assert compared >= 12
