@@ -105,8 +105,7 @@ def run_reference(args, rank, world):
         return
     cores = os.cpu_count() or 1
     per_step = max(cores, 32)
-    ctx = mp.get_context("spawn")
-    with ctx.Pool(cores, initializer=_pin_threads) as pool:
+    with _oracle_pool(cores) as pool:
         for _ in range(args.warmup):
             oracle_rate(cores, seed=99, pool=pool, cores=cores)
         rates, t_all = [], time.perf_counter()
@@ -125,9 +124,24 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
-def _pin_threads():
-    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+_BLAS_VARS = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")
+
+
+def _oracle_pool(cores):
+    """A spawned pool of `cores` oracle processes with one BLAS thread each:
+    the workers inherit the environment when they start, before they import
+    numpy."""
+    old = {v: os.environ.get(v) for v in _BLAS_VARS}
+    for v in _BLAS_VARS:
         os.environ[v] = "1"
+    try:
+        return mp.get_context("spawn").Pool(cores)
+    finally:
+        for v, val in old.items():
+            if val is None:
+                os.environ.pop(v, None)
+            else:
+                os.environ[v] = val
 
 
 # ------------------------------------------------------------------ clocks --
@@ -192,6 +206,46 @@ class ClockSampler:
 
 # ------------------------------------------------------------- GPU arm -----
 
+def fp32_fma_peak(dev, local_rank):
+    """Measured FP32 multiply-add throughput (mpc_fp32_fma_probe: 2 blocks of
+    1024 threads per SM, 8 independent FMA chains per thread): `burst` is the
+    best of 10 single launches of about 2 ms (the denominator for a kernel
+    timed alone); `sustained` is 1 s of back-to-back launches, with the SM
+    clocks sampled during it."""
+    import torch
+    from paper_2605_29155_gb300 import camp
+    sink = torch.zeros(1, device=dev)
+    stream = torch.cuda.current_stream()
+    code, fl = camp.mpc_fp32_fma_probe(64, sink.data_ptr(), stream.cuda_stream)
+    camp.check(code, "mpc_fp32_fma_probe")
+    torch.cuda.synchronize()
+    trips = 2000
+    best = 0.0
+    for _ in range(10):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        code, fl = camp.mpc_fp32_fma_probe(trips, sink.data_ptr(), stream.cuda_stream)
+        e1.record(stream)
+        e1.synchronize()
+        best = max(best, fl / (e0.elapsed_time(e1) * 1e-3) / 1e12)
+    reps = max(1, int(1.0 / max(fl / (best * 1e12), 1e-6)))
+    with ClockSampler(local_rank) as clk:
+        clk.mark()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        total = 0.0
+        for _ in range(reps):
+            code, fl = camp.mpc_fp32_fma_probe(trips, sink.data_ptr(), stream.cuda_stream)
+            total += fl
+        e1.record(stream)
+        e1.synchronize()
+        clk.mark()
+    sustained = total / (e0.elapsed_time(e1) * 1e-3) / 1e12
+    return dict(burst_tflops=best, sustained_tflops=sustained, clocks_sustained=clk.summary(),
+                how="mpc_fp32_fma_probe: 2 x 1024 threads per SM, 8 FMA chains per thread; burst = best of 10 "
+                    f"launches of {trips} x 16 FMA per chain, sustained = {reps} launches back to back")
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
 
@@ -206,16 +260,22 @@ def run_ours(args, rank, world, local_rank):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
 
-    # CPU baseline first (spawned pool, before any further GPU work), rank 0 only
+    # CPU baseline first (spawned pools, before any further GPU work), rank 0 only
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cores = os.cpu_count() or 1
         sample = max(4 * cores, 64)
-        with mp.get_context("spawn").Pool(cores, initializer=_pin_threads) as pool:
+        with _oracle_pool(cores) as pool:
             oracle_rate(cores, seed=99, pool=pool, cores=cores)
             rate = oracle_rate(sample, seed=0, pool=pool, cores=cores)
+        with _oracle_pool(1) as pool:
+            rate1 = oracle_rate(16, seed=0, pool=pool, cores=1)
         cpu = dict(value=rate, unit=UNIT, cores=cores, kind="oracle",
-                   sample=f"first {sample} instances of the race-track workload, fwd+bwd, FP64, {cores} processes")
+                   sample=f"first {sample} instances of the race-track workload, fwd+bwd, FP64, {cores} processes",
+                   one_thread=dict(value=rate1, unit=UNIT, cores=1,
+                                   sample="first 16 instances of the same workload, one process"))
+
+    fma_peak = fp32_fma_peak(dev, local_rank)
 
     prob = W.cfg_track(seed=rank)
     gu_np = W.loss_weights_u0(B, N, seed=1 + rank)
@@ -350,7 +410,8 @@ def run_ours(args, rank, world, local_rank):
     sms = props.multi_processor_count
     clocks = clk.summary()
     sm_max_mhz = (clocks or {}).get("sm_max_mhz") or 2070.0
-    peak_tflops = sms * FP32_LANES_PER_SM * 2 * sm_max_mhz * 1e6 / 1e12
+    nominal_tflops = sms * FP32_LANES_PER_SM * 2 * sm_max_mhz * 1e6 / 1e12
+    peak_tflops = fma_peak["burst_tflops"]
     hz = np.full(B, N)
     fwd_flops = float(np.sum(iters * (hz - 1)) * FLOP_STAGE_ITER + np.sum(hz - 1) * FLOP_STAGE_FINAL)
     achieved = fwd_flops / (ms_fwd * 1e-3) / 1e12
@@ -380,8 +441,10 @@ def run_ours(args, rank, world, local_rank):
                  d2h_bytes_per_step=int(d2h), api="paper_2605_29155_gb300.DiffMPC.solve/backward (ctypes C ABI), eager"),
         roofline=dict(kernel="k_mpc<float> persistent forward", bound="alu", achieved=achieved, peak=peak_tflops,
                       unit="TFLOP/s", frac=achieved / peak_tflops, traffic=_traffic(),
-                      peak_note=f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 flop x {sm_max_mhz:.0f} MHz",
-                      flops_per_launch=fwd_flops),
+                      peak_note="of measured: FP32 FMA throughput, burst (mpc_fp32_fma_probe); nominal "
+                                f"{sms} SMs x {FP32_LANES_PER_SM} lanes x 2 flop x {sm_max_mhz:.0f} MHz = "
+                                f"{nominal_tflops:.1f} TFLOP/s",
+                      fp32_peak=fma_peak, flops_per_launch=fwd_flops),
         cpu_baseline=cpu,
         side_configs=side,
         clocks=clocks,

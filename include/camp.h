@@ -57,6 +57,8 @@ extern "C" {
 /* what the forward keeps for the backward (Sec. IV: differentiate at the solution) */
 #define MPC_STORE_ALL   0      /* tape holds F_t, K_t, chol(Q_uu,ff), free set per stage */
 #define MPC_RECOMPUTE   1      /* no tape: the backward re-linearises and re-factors    */
+#define MPC_STORE_AUTO  2      /* per (B, N): store the tape when it fits the config's  */
+                               /* tape_budget, else recompute                          */
 
 /* how the forward iterations are launched */
 #define MPC_EXEC_PERSISTENT 0  /* one persistent launch, work queue over instances      */
@@ -86,12 +88,15 @@ typedef struct mpc_config {
     double tol;             /* convergence threshold on max |du| [N]                   */
     int    n_alpha;         /* number of line-search coefficients, 1..4                */
     double alpha[4];        /* coefficients in (0, 1], default {1, .5, .25, .1}        */
-    int    store_mode;      /* MPC_STORE_ALL or MPC_RECOMPUTE                          */
+    int    store_mode;      /* MPC_STORE_ALL, MPC_RECOMPUTE or MPC_STORE_AUTO          */
     int    exec_mode;       /* MPC_EXEC_PERSISTENT or MPC_EXEC_PLAIN                   */
     int    tpi;             /* threads per instance = warps per block: 0 (4 until      */
                             /* mpc_autotune picks), 4 or 8                              */
     int    ipb;             /* instances per block (one per lane): 0 (auto) or 1..32,  */
                             /* 1..16 in MPC_F64                                         */
+    size_t tape_budget;     /* MPC_STORE_AUTO: largest tape [bytes] a (B, N) shape may  */
+                            /* store; 0 = a quarter of the device memory free at       */
+                            /* mpc_create                                               */
 } mpc_config;
 
 typedef struct mpc_problem {
@@ -124,7 +129,7 @@ typedef struct mpc_solution {
                             /* (general cost: sum_t 1/2 z'C z + c'z)                  */
     int    *iters;          /* [B] iterations executed                                 */
     int    *status;         /* [B] MPC_ST_*                                             */
-    void   *tape;           /* MPC_STORE_ALL: >= mpc_tape_bytes(B, N) bytes, 256-aligned */
+    void   *tape;           /* >= mpc_tape_bytes(B, N) bytes, 256-aligned (none if 0)   */
     size_t  tape_bytes;
 } mpc_solution;
 
@@ -146,11 +151,15 @@ int mpc_destroy(mpc_handle *h);
 /* Bytes of tape mpc_solve_fwd writes for a (B, N) problem: ceil(B/32)*32*N*210
  * elements of the handle's dtype in MPC_STORE_ALL mode (per stage and instance:
  * the 11 computed columns of F_t, K_t, the masked factor of Q_uu,ff and the free
- * mask), 0 in MPC_RECOMPUTE mode (or for a NULL handle). */
+ * mask), 0 in MPC_RECOMPUTE mode (or for a NULL handle).  In MPC_STORE_AUTO mode
+ * the same size when it is at most the handle's budget (mpc_config.tape_budget,
+ * by default a quarter of the device memory free at mpc_create), else 0: solves
+ * of that shape then recompute.  This is how a caller learns which way a shape
+ * goes. */
 size_t mpc_tape_bytes(const mpc_handle *h, int B, int N);
 
 /* Forward solve (Eq. (3) by box-constrained iLQR, Algorithm 2's inner loop):
- * writes u, x, cost, iters, status and, in MPC_STORE_ALL mode, the tape with
+ * writes u, x, cost, iters, status and, when mpc_tape_bytes(B, N) > 0, the tape with
  * the linearization and factorization at the returned iterate.  Enqueued on
  * `stream`; returns before the GPU finishes.  Errors: MPC_ERR_ARG (NULL
  * pointer, bad Nq, tape too small), MPC_ERR_SHAPE (B > B_max, N outside
@@ -190,7 +199,8 @@ int mpc_autotune(mpc_handle *h, const mpc_problem *p, mpc_solution *s,
 int mpc_launch_shape(const mpc_handle *h, int B, int N, int *tpi, int *ipb, int *grid);
 
 /* Number of kernel launches one mpc_solve_fwd / mpc_solve_bwd on (B, N, with or
- * without per-instance horizons) enqueues in the handle's configuration. */
+ * without per-instance horizons) enqueues in the handle's configuration (in
+ * MPC_STORE_AUTO mode: for the (B_max, N_max) shape). */
 int mpc_launch_count(const mpc_handle *h, int has_horizon, int *fwd, int *bwd);
 
 /* Forward solve that allocates nothing.  The paper has no counterpart: this is
@@ -204,13 +214,25 @@ int mpc_launch_count(const mpc_handle *h, int has_horizon, int *fwd, int *bwd);
  *          N_max and B_max are ignored); MPC_STORE_ALL writes the tape.
  *   p, s   device pointers as for mpc_solve_fwd; B <= MPC_NOALLOC_B_MAX and
  *          N <= MPC_NOALLOC_N_MAX, else MPC_ERR_SHAPE.
- * The first call on a device looks the array up with that device current;
- * make it before any stream capture.  All calls share the array: calls whose
- * GPU work overlaps race on it and must not be issued.  Errors as for
- * mpc_solve_fwd. */
+ * The first call on a device looks the array up and sets the kernels' shared-
+ * memory limit with that device current; make it before any stream capture.
+ * No handle (mpc_create) is needed before it.  The looked-up address is cached
+ * per device for the life of the process and is invalid after cudaDeviceReset.
+ * All calls share the array: calls whose GPU work overlaps race on it and must
+ * not be issued.  Errors as for mpc_solve_fwd. */
 #define MPC_NOALLOC_B_MAX 256
 #define MPC_NOALLOC_N_MAX 40
 int mpc_solve_fwd_noalloc(const mpc_config *cfg, const mpc_problem *p, mpc_solution *s, cudaStream_t stream);
+
+/* Measurement support (the paper has no counterpart): the FP32 multiply-add
+ * throughput of this GPU, the denominator of the forward solve's roofline.
+ * Enqueues on `stream` one launch of 2 blocks of 1024 threads per SM, each
+ * thread running 8 independent chains of `trips` x 16 fused multiply-adds, and
+ * returns in *flops (may be NULL) the flops it executes (2 per multiply-add);
+ * the caller times it (CUDA events) and divides.  `sink` is a device float
+ * the kernel practically never writes.  Errors: MPC_ERR_ARG (trips < 1, NULL
+ * sink), MPC_ERR_CUDA. */
+int mpc_fp32_fma_probe(int trips, float *sink, cudaStream_t stream, double *flops);
 
 /* Static text for a return code (mpc_strerror) or an MPC_ST_* status (mpc_status_str). */
 const char *mpc_strerror(int code);

@@ -14,13 +14,14 @@ LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libcamp.so"
 
 MPC_OK, MPC_ERR_ARG, MPC_ERR_SHAPE, MPC_ERR_CUDA, MPC_ERR_TIMEOUT, MPC_ERR_STATE = 0, -1, -2, -3, -4, -5
 MPC_F32, MPC_F64 = 0, 1
-MPC_STORE_ALL, MPC_RECOMPUTE = 0, 1
+MPC_STORE_ALL, MPC_RECOMPUTE, MPC_STORE_AUTO = 0, 1, 2
 MPC_EXEC_PERSISTENT, MPC_EXEC_PLAIN = 0, 1
 MPC_ST_CONVERGED, MPC_ST_STALLED, MPC_ST_MAX_ITER, MPC_ST_NONFINITE, MPC_ST_NONPD = 0, 1, 2, 3, 4
 
 EXPORTED = ("mpc_config_default", "mpc_create", "mpc_destroy", "mpc_tape_bytes", "mpc_solve_fwd",
             "mpc_solve_bwd", "mpc_autotune", "mpc_launch_shape", "mpc_launch_count", "mpc_strerror",
-            "mpc_status_str", "mpc_solve_fwd_noalloc", "mpc_solve_bwd_general")
+            "mpc_status_str", "mpc_solve_fwd_noalloc", "mpc_solve_bwd_general", "mpc_fp32_fma_probe",
+            "mpc_costmap_workspace_bytes", "mpc_costmap_forward", "mpc_costmap_backward")
 MPC_NOALLOC_B_MAX, MPC_NOALLOC_N_MAX = 256, 40
 
 
@@ -29,7 +30,7 @@ class mpc_config(ctypes.Structure):
                 ("dt", c_double), ("mass", c_double), ("inertia", c_double * 3), ("arm", c_double),
                 ("kappa_yaw", c_double), ("gravity", c_double), ("max_iter", c_int), ("tol", c_double),
                 ("n_alpha", c_int), ("alpha", c_double * 4), ("store_mode", c_int), ("exec_mode", c_int),
-                ("tpi", c_int), ("ipb", c_int)]
+                ("tpi", c_int), ("ipb", c_int), ("tape_budget", c_size_t)]
 
 
 class mpc_problem(ctypes.Structure):
@@ -42,6 +43,12 @@ class mpc_problem(ctypes.Structure):
 class mpc_solution(ctypes.Structure):
     _fields_ = [("u", c_void_p), ("x", c_void_p), ("cost", c_void_p), ("iters", c_void_p),
                 ("status", c_void_p), ("tape", c_void_p), ("tape_bytes", c_size_t)]
+
+
+class mpc_costmap(ctypes.Structure):
+    _fields_ = [("n_in", c_int), ("hidden", c_int), ("n_out", c_int), ("W1", c_void_p), ("b1", c_void_p),
+                ("W2", c_void_p), ("b2", c_void_p), ("W3", c_void_p), ("b3", c_void_p), ("q_lo", ctypes.c_float),
+                ("q_hi", ctypes.c_float)]
 
 
 def _load():
@@ -77,6 +84,16 @@ def _load():
     lib.mpc_status_str.restype = ctypes.c_char_p
     lib.mpc_solve_fwd_noalloc.argtypes = [POINTER(mpc_config), POINTER(mpc_problem), POINTER(mpc_solution), c_void_p]
     lib.mpc_solve_fwd_noalloc.restype = c_int
+    lib.mpc_fp32_fma_probe.argtypes = [c_int, c_void_p, c_void_p, POINTER(c_double)]
+    lib.mpc_fp32_fma_probe.restype = c_int
+    lib.mpc_costmap_workspace_bytes.argtypes = [c_int, c_int, c_int]
+    lib.mpc_costmap_workspace_bytes.restype = c_size_t
+    lib.mpc_costmap_forward.argtypes = [POINTER(mpc_costmap), c_int, c_int, c_void_p, c_void_p, c_void_p, c_void_p,
+                                        c_void_p]
+    lib.mpc_costmap_forward.restype = c_int
+    lib.mpc_costmap_backward.argtypes = [POINTER(mpc_costmap), c_int, c_int, c_void_p, c_void_p, c_void_p, c_void_p,
+                                         c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]
+    lib.mpc_costmap_backward.restype = c_int
     return lib
 
 
@@ -155,6 +172,29 @@ def mpc_launch_count(h, has_horizon: bool):
 
 def mpc_solve_fwd_noalloc(cfg: mpc_config, prob: mpc_problem, sol: mpc_solution, stream: int) -> int:
     return _lib.mpc_solve_fwd_noalloc(byref(cfg), byref(prob), byref(sol), c_void_p(stream))
+
+
+def mpc_fp32_fma_probe(trips: int, sink: int, stream: int):
+    """Returns (code, flops enqueued)."""
+    fl = c_double(0.0)
+    code = _lib.mpc_fp32_fma_probe(trips, c_void_p(sink), c_void_p(stream), byref(fl))
+    return code, fl.value
+
+
+def mpc_costmap_workspace_bytes(B: int, hidden: int, n_out: int) -> int:
+    return _lib.mpc_costmap_workspace_bytes(B, hidden, n_out)
+
+
+def mpc_costmap_forward(net: mpc_costmap, B: int, N: int, x0: int, x_ref: int, Q: int, ws: int, stream: int) -> int:
+    return _lib.mpc_costmap_forward(byref(net), B, N, c_void_p(x0), c_void_p(x_ref), c_void_p(Q), c_void_p(ws),
+                                    c_void_p(stream))
+
+
+def mpc_costmap_backward(net: mpc_costmap, B: int, N: int, x0: int, x_ref: int, dQ: int, ws: int, dW1: int, db1: int,
+                         dW2: int, db2: int, dW3: int, db3: int, d_obs: int, stream: int) -> int:
+    return _lib.mpc_costmap_backward(byref(net), B, N, c_void_p(x0), c_void_p(x_ref), c_void_p(dQ), c_void_p(ws),
+                                     c_void_p(dW1), c_void_p(db1), c_void_p(dW2), c_void_p(db2), c_void_p(dW3),
+                                     c_void_p(db3), c_void_p(d_obs or None), c_void_p(stream))
 
 
 def mpc_strerror(code: int) -> str:

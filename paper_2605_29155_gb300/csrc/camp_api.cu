@@ -21,6 +21,7 @@ struct mpc_handle {
     int* order;             // [B_max] longest-horizon-first order
     int tpi;                // threads per instance (warps per block): 4 or 8
     int ipb;                // instances per block, 0 = as many as fill one block per SM
+    size_t tape_budget;     // MPC_STORE_AUTO: largest tape (bytes) a shape may store
 };
 
 static size_t elem_size(int dtype) { return dtype == MPC_F64 ? sizeof(double) : sizeof(float); }
@@ -71,7 +72,8 @@ static int validate_config(const mpc_config* c) {
     if (c->n_alpha < 1 || c->n_alpha > 4) return MPC_ERR_ARG;
     for (int i = 0; i < c->n_alpha; ++i)
         if (!(c->alpha[i] > 0.0 && c->alpha[i] <= 1.0)) return MPC_ERR_ARG;
-    if (c->store_mode != MPC_STORE_ALL && c->store_mode != MPC_RECOMPUTE) return MPC_ERR_ARG;
+    if (c->store_mode != MPC_STORE_ALL && c->store_mode != MPC_RECOMPUTE && c->store_mode != MPC_STORE_AUTO)
+        return MPC_ERR_ARG;
     if (c->exec_mode != MPC_EXEC_PERSISTENT && c->exec_mode != MPC_EXEC_PLAIN) return MPC_ERR_ARG;
     if (c->tpi != 0 && c->tpi != 4 && c->tpi != 8) return MPC_ERR_ARG;
     if (c->ipb < 0 || c->ipb > (c->dtype == MPC_F64 ? 16 : 32)) return MPC_ERR_ARG;
@@ -95,6 +97,12 @@ extern "C" int mpc_create(const mpc_config* cfg, mpc_handle** out) {
     }
     const cudaError_t pe = cfg->dtype == MPC_F64 ? prepare_kernels<double>() : prepare_kernels<float>();
     if (pe != cudaSuccess) { free(h); return MPC_ERR_CUDA; }
+    if (cfg->store_mode == MPC_STORE_AUTO) {
+        // the tape budget: the config's, or a quarter of the device memory free at creation
+        size_t free_b = 0, total_b = 0;
+        if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) { free(h); return MPC_ERR_CUDA; }
+        h->tape_budget = cfg->tape_budget ? cfg->tape_budget : free_b / 4;
+    }
     h->slots = cfg->B_max;
     const size_t es = elem_size(cfg->dtype);
     const size_t S = (size_t)h->slots;
@@ -126,8 +134,16 @@ extern "C" int mpc_destroy(mpc_handle* h) {
     return MPC_OK;
 }
 
+// Whether solves of shape (B, N) keep the tape: always in MPC_STORE_ALL, never
+// in MPC_RECOMPUTE, and in MPC_STORE_AUTO when the tape fits the budget.
+static bool stores_tape(const mpc_handle* h, int B, int N) {
+    if (h->cfg.store_mode == MPC_STORE_ALL) return true;
+    if (h->cfg.store_mode == MPC_RECOMPUTE) return false;
+    return tape_elems(B > 0 ? B : 0, N > 0 ? N : 0) * elem_size(h->cfg.dtype) <= h->tape_budget;
+}
+
 extern "C" size_t mpc_tape_bytes(const mpc_handle* h, int B, int N) {
-    if (!h || B <= 0 || N <= 0 || h->cfg.store_mode != MPC_STORE_ALL) return 0;
+    if (!h || B <= 0 || N <= 0 || !stores_tape(h, B, N)) return 0;
     return tape_elems(B, N) * elem_size(h->cfg.dtype);
 }
 
@@ -179,7 +195,7 @@ static Params<T> make_params(const mpc_handle* h, const mpc_problem* p, const mp
     P.Nq = p->Nq;
     P.max_iter = h->cfg.max_iter;
     P.n_alpha = h->cfg.n_alpha;
-    P.store_all = h->cfg.store_mode == MPC_STORE_ALL;
+    P.store_all = stores_tape(h, p->B, p->N) ? 1 : 0;
     P.N_ws = h->cfg.N_max;
     P.ipb = ipb;
     P.tol = (T)h->cfg.tol;
@@ -217,7 +233,7 @@ extern "C" int mpc_solve_fwd(mpc_handle* h, const mpc_problem* p, mpc_solution* 
     if (!s) return MPC_ERR_ARG;
     if (p->B == 0) return MPC_OK;
     if (!s->u || !s->x || !s->cost || !s->iters || !s->status) return MPC_ERR_ARG;
-    if (h->cfg.store_mode == MPC_STORE_ALL) {
+    if (stores_tape(h, p->B, p->N)) {
         if (!s->tape || s->tape_bytes < mpc_tape_bytes(h, p->B, p->N)) return MPC_ERR_ARG;
     }
     cudaError_t e;
@@ -241,7 +257,7 @@ extern "C" int mpc_solve_bwd(mpc_handle* h, const mpc_problem* p, const mpc_solu
     if (p->B == 0) return MPC_OK;
     if (p->C) return MPC_ERR_STATE;     // a general cost has mpc_solve_bwd_general
     if (!s->u || !s->x || !s->status || !grad_u || !dQ || !dx_ref || !dx0) return MPC_ERR_ARG;
-    const int recompute = h->cfg.store_mode == MPC_RECOMPUTE;
+    const int recompute = stores_tape(h, p->B, p->N) ? 0 : 1;
     if (!recompute && (!s->tape || s->tape_bytes < mpc_tape_bytes(h, p->B, p->N))) return MPC_ERR_ARG;
     cudaError_t e;
     const int ipb = ipb_for(h, p->B);
@@ -269,7 +285,7 @@ extern "C" int mpc_solve_bwd_general(mpc_handle* h, const mpc_problem* p, const 
     if (!p->C) return MPC_ERR_STATE;    // the diagonal form has mpc_solve_bwd
     if (p->B == 0) return MPC_OK;
     if (!s->u || !s->x || !s->status || !grad_u || !dC || !dc || !dx0) return MPC_ERR_ARG;
-    const int recompute = h->cfg.store_mode == MPC_RECOMPUTE;
+    const int recompute = stores_tape(h, p->B, p->N) ? 0 : 1;
     if (!recompute && (!s->tape || s->tape_bytes < mpc_tape_bytes(h, p->B, p->N))) return MPC_ERR_ARG;
     cudaError_t e;
     const int ipb = ipb_for(h, p->B);
@@ -350,7 +366,7 @@ extern "C" int mpc_launch_count(const mpc_handle* h, int has_horizon, int* fwd, 
     const int hz = has_horizon ? 1 : 0;
     if (fwd) {
         if (h->cfg.exec_mode == MPC_EXEC_PERSISTENT) *fwd = 1 + hz;
-        else *fwd = hz + 2 + 2 * h->cfg.max_iter + (h->cfg.store_mode == MPC_STORE_ALL ? 1 : 0);
+        else *fwd = hz + 2 + 2 * h->cfg.max_iter + (stores_tape(h, h->cfg.B_max, h->cfg.N_max) ? 1 : 0);
     }
     if (bwd) *bwd = 1 + hz;
     return MPC_OK;

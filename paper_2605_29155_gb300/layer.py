@@ -80,7 +80,7 @@ class DiffMPC:
 
     def __init__(self, N_max=40, B_max=8192, dtype=torch.float32, max_iter=8, tol=1e-6,
                  store_mode="store_all", exec_mode="persistent", ipb=0, model=None, alphas=None,
-                 device=None, tpi=0):
+                 device=None, tpi=0, tape_budget=0):
         if not torch.cuda.is_available():
             raise RuntimeError("DiffMPC needs a CUDA device (libcamp.so has no CPU path)")
         self.device = torch.device(device or "cuda")
@@ -88,10 +88,14 @@ class DiffMPC:
         cfg = camp.mpc_config_default()
         cfg.N_max, cfg.B_max, cfg.dtype = int(N_max), int(B_max), _DTYPES[dtype]
         cfg.max_iter, cfg.tol = int(max_iter), float(tol)
-        cfg.store_mode = camp.MPC_STORE_ALL if store_mode == "store_all" else camp.MPC_RECOMPUTE
+        modes = {"store_all": camp.MPC_STORE_ALL, "recompute": camp.MPC_RECOMPUTE, "auto": camp.MPC_STORE_AUTO}
+        if store_mode not in modes:
+            raise ValueError(f"store_mode must be one of {sorted(modes)}")
+        cfg.store_mode = modes[store_mode]
         cfg.exec_mode = camp.MPC_EXEC_PERSISTENT if exec_mode == "persistent" else camp.MPC_EXEC_PLAIN
         cfg.ipb = int(ipb)
         cfg.tpi = int(tpi)
+        cfg.tape_budget = int(tape_budget)
         if model is not None:
             cfg.dt, cfg.mass, cfg.arm, cfg.kappa_yaw, cfg.gravity = model.dt, model.mass, model.arm, model.kappa, model.gravity
             for i in range(3):
