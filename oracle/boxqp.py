@@ -14,7 +14,16 @@ and backtracked until an Armijo condition holds.
 
 Readings (the paper gives no parameters):
   start       d = clamp(0)
-  clamped     (d_i <= lo_i and grad_i > 0) or (d_i >= hi_i and grad_i < 0)
+  clamped     Bertsekas' epsilon-active set: a dimension within
+              eps_i = EPS_REL (1 + hi_i - lo_i) of a bound whose gradient points
+              out of the box, (d_i <= lo_i + eps_i and grad_i > 0) or
+              (d_i >= hi_i - eps_i and grad_i < 0); it is set onto that bound
+              and the gradient re-evaluated there.  With an exact comparison
+              instead, a control a rounding error inside its bound counts as
+              interior: the Newton step on every dimension, projected, is then
+              no descent direction, the line search fails and the QP returns
+              d = 0 with every dimension free, so the result would jump with
+              rounding-level changes of its inputs.
   stop        no free dimension, or the free set equals the one of the previous
               iteration after a full (step 1) Newton step that the projection
               did not cut (then d is the minimiser on that face and the clamped
@@ -33,6 +42,7 @@ MAX_IT = 20
 MAX_LS = 30
 ARMIJO = 0.1
 STEP_DEC = 0.6
+EPS_REL = 1e-6
 
 
 def cholesky(H):
@@ -69,9 +79,14 @@ def solve(H, g, lo, hi):
     last_full = False
     L = None
     free_fact = np.zeros(n, dtype=bool)
+    eps = EPS_REL * (1.0 + (hi - lo))
     for _ in range(MAX_IT):
         grad = g + H @ d
-        clamped = ((d <= lo) & (grad > 0)) | ((d >= hi) & (grad < 0))
+        at_lo = (d <= lo + eps) & (grad > 0)
+        at_hi = (d >= hi - eps) & (grad < 0)
+        d = np.where(at_lo, lo, np.where(at_hi, hi, d))
+        grad = g + H @ d
+        clamped = at_lo | at_hi
         free = ~clamped
         if not free.any():
             return d, free, None, True

@@ -236,6 +236,7 @@ class Solution:
     qp_margin: float     # smallest |grad| behind a clamped/free decision
     alpha_hist: list
     ls_margin_any: float = np.inf   # the same over every alpha decision, material or not
+    du_hist: list = dataclasses.field(default_factory=list)   # max_t |u^k_t - u^(k-1)_t| of every step (R5)
 
 
 def linearize(model, prob: Problem, X, U):
@@ -257,7 +258,7 @@ def solve(model, prob: Problem, max_iter=10, tol=1e-6, alphas=ALPHAS) -> Solutio
     J = total_cost(prob, X, U)
     status, iters = MAX_ITER, 0
     ls_margin, qp_margin, ls_margin_any = np.inf, np.inf, np.inf
-    hist = []
+    hist, du_hist = [], []
     if not np.isfinite(J):
         return Solution(X, U, J, 0, NONFINITE, [], None, ls_margin, qp_margin, hist, ls_margin_any)
     for it in range(max_iter):
@@ -296,6 +297,7 @@ def solve(model, prob: Problem, max_iter=10, tol=1e-6, alphas=ALPHAS) -> Solutio
             hist.append(None)
             break
         hist.append(alphas[best])
+        du_hist.append(du)
         J = J + Js[best]
         X, U = cands[best][1], cands[best][2]
         if du < tol:
@@ -303,7 +305,8 @@ def solve(model, prob: Problem, max_iter=10, tol=1e-6, alphas=ALPHAS) -> Solutio
             break
     F = linearize(model, prob, X, U)
     bp = backward_pass(prob, X, U, F)
-    return Solution(X, U, total_cost(prob, X, U), iters, status, F, bp, ls_margin, qp_margin, hist, ls_margin_any)
+    return Solution(X, U, total_cost(prob, X, U), iters, status, F, bp, ls_margin, qp_margin, hist, ls_margin_any,
+                    du_hist)
 
 
 def at_iterate(model, prob: Problem, U, free_override=None) -> Solution:

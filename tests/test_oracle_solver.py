@@ -43,7 +43,61 @@ def test_boxqp_matches_enumeration(seed):
     # every clamped dimension sits on a bound with its gradient pointing out
     grad = g + H @ d
     for i in np.flatnonzero(~free):
-        assert (d[i] <= lo[i] and grad[i] > 0) or (d[i] >= hi[i] and grad[i] < 0)
+        assert (d[i] == lo[i] and grad[i] > 0) or (d[i] == hi[i] and grad[i] < 0)
+
+
+# Stage 0 of a race-track instance's fourth iteration: two rotors at their
+# 0 N bound (u = [2.2387, 0, 0, 1.0517] N), the rotor pairs nearly collinear in H.
+NEAR_H = np.array([[8.29442083, -8.24721083, 1.51574164, -1.65046398],
+                   [-8.24721083, 8.68940243, -1.57066555, 1.50579661],
+                   [1.51574164, -1.57066555, 8.408479, -8.05725247],
+                   [-1.65046398, 1.50579661, -8.05725247, 8.1897023]])
+NEAR_G = np.array([-2.17662926, 3.60192572, 2.73650408, -1.44773018])
+NEAR_U = np.array([2.23866527, 0.0, 0.0, 1.05174372])
+
+
+@pytest.mark.parametrize("shift", [0.0, 1e-12, -1e-12, 3e-7])
+def test_boxqp_near_bound_controls_match_enumeration(shift):
+    """Controls a rounding error (or a fraction of the epsilon-active width)
+    inside their bound, with the gradient pointing out of the box: the QP
+    clamps them (Bertsekas' epsilon-active set) and returns the unique KKT
+    point, the same for every shift, instead of a result that jumps with
+    the rounding of its inputs."""
+    u = NEAR_U.copy()
+    u[1] += abs(shift)
+    u[2] += abs(shift)
+    lo, hi = -u, 8.5 - u
+    d, free, L, ok = boxqp.solve(NEAR_H, NEAR_G, lo, hi)
+    assert ok
+    sols = boxqp.enumerate_kkt(NEAR_H, NEAR_G, lo, hi)
+    assert len(sols) == 1
+    np.testing.assert_allclose(d, sols[0], atol=1e-9)
+    np.testing.assert_array_equal(free, [True, False, False, True])
+    # the clamped controls sit exactly on their bound
+    assert d[1] == lo[1] and d[2] == lo[2]
+
+
+@pytest.mark.parametrize("seed", range(20))
+def test_boxqp_epsilon_active_matches_enumeration(seed):
+    """Random strictly convex QPs whose start lies within the epsilon-active
+    width of a bound in some dimensions: the result is the enumerated KKT
+    point of the same QP to within that width."""
+    rng = np.random.default_rng(100 + seed)
+    A = rng.normal(size=(4, 4))
+    H = A @ A.T + 0.05 * np.eye(4)
+    g = rng.normal(scale=3.0, size=4)
+    lo = -rng.uniform(0.0, 1.0, 4)
+    hi = rng.uniform(0.0, 1.0, 4)
+    near = rng.integers(0, 4)
+    if seed % 2:
+        lo[near] = -0.5 * boxqp.EPS_REL * (1.0 + hi[near] - lo[near]) * rng.uniform()
+    else:
+        hi[near] = 0.5 * boxqp.EPS_REL * (1.0 + hi[near] - lo[near]) * rng.uniform()
+    d, free, L, ok = boxqp.solve(H, g, lo, hi)
+    assert ok
+    sols = boxqp.enumerate_kkt(H, g, lo, hi)
+    assert len(sols) >= 1
+    np.testing.assert_allclose(d, sols[0], atol=1e-5)
 
 
 def test_boxqp_interior_is_newton_step():
