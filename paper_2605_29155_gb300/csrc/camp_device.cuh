@@ -192,6 +192,16 @@ template <typename T> __device__ __forceinline__ void cp_async(T* dst, const T* 
         asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src) : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+
+// Drops the L2 lines of `bytes` of dead scratch at p (128-byte aligned)
+// without writing them back to HBM; their contents become undefined.  The
+// block's threads split the lines; the caller makes sure that no thread still
+// reads them and that no other block's data shares them.
+__device__ __forceinline__ void l2_discard(void* p, size_t bytes) {
+    char* c = (char*)p;
+    for (size_t o = (size_t)threadIdx.x * 128; o < bytes; o += (size_t)blockDim.x * 128)
+        asm volatile("discard.global.L2 [%0], 128;" ::"l"(c + o) : "memory");
+}
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
 // ------------------------------------------------------------------ model ----
@@ -510,8 +520,12 @@ template <typename T> __device__ __forceinline__ void identity_factor(T (&L)[NL]
 
 // Projected-Newton box QP (Tassa et al. 2014, Bertsekas 1982):
 //   min 1/2 d'Hd + g'd  s.t. lo <= d <= hi,  start d = clamp(0).
-// Clamped set: at a bound with the gradient pointing out of the box.  Newton
-// step on the free set, projected onto the box, Armijo backtracking (0.1, x0.6).
+// Clamped set: Bertsekas' epsilon-active set -- within eps_i = 1e-6 (1 + hi_i
+// - lo_i) of a bound with the gradient pointing out of the box; such a
+// dimension is set onto the bound and the gradient re-evaluated there (an
+// exact comparison would let a rounding error decide whether a control on its
+// bound is free, and with it the whole step).  Newton step on the free set,
+// projected onto the box, Armijo backtracking (0.1, x0.6).
 // Stops with no free dimension, or when the free set repeats after a full step
 // the projection did not cut, or after QP_MAX_IT iterations.  Returns false on
 // a non-positive pivot.  `L` and `mask` describe the last factored free set.
@@ -523,8 +537,12 @@ template <typename T> __device__ __forceinline__ void identity_factor(T (&L)[NL]
 template <typename T>
 __device__ bool box_qp(bool on, const T (&H)[4][4], const T (&g)[4], const T (&lo)[4], const T (&hi)[4],
                        T (&d)[4], T (&L)[NL], int& mask_out) {
+    T eps[4];
 #pragma unroll
-    for (int i = 0; i < 4; ++i) d[i] = clampT(T(0), lo[i], hi[i]);
+    for (int i = 0; i < 4; ++i) {
+        d[i] = clampT(T(0), lo[i], hi[i]);
+        eps[i] = T(1e-6) * (T(1) + (hi[i] - lo[i]));
+    }
     int free_prev = -1, mask_fact = 0;
     bool last_full = false, done = !on, ok = true;
     identity_factor(L);
@@ -540,13 +558,38 @@ __device__ bool box_qp(bool on, const T (&H)[4][4], const T (&g)[4], const T (&l
             grad[i] = s;
         }
         int fm = 0;
+        bool moved = false;
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
-            const bool cl = (d[i] <= lo[i] && grad[i] > T(0)) || (d[i] >= hi[i] && grad[i] < T(0));
-            fm |= cl ? 0 : (1 << i);
+            const bool al = d[i] <= lo[i] + eps[i] && grad[i] > T(0);
+            const bool ah = d[i] >= hi[i] - eps[i] && grad[i] < T(0);
+            const T dc = al ? lo[i] : (ah ? hi[i] : d[i]);
+            moved = moved || (!done && dc != d[i]);
+            d[i] = done ? d[i] : dc;
+            fm |= (al || ah) ? 0 : (1 << i);
+        }
+        if (__any_sync(FULL, moved)) {
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                T s = g[i];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) s += H[i][k] * d[k];
+                grad[i] = s;
+            }
         }
         const bool none_free = fm == 0;
         const bool repeat = last_full && fm == free_prev;
+        if (__all_sync(FULL, done || none_free || repeat)) {
+            // Every lane stops in this trip without a new factor (typically
+            // the trip that confirms a free set): the outcomes the full trip
+            // below would select, without its factorization and line search.
+            if (!done) {
+                if (none_free) identity_factor(L);
+                mask_out = none_free ? 0 : fm;
+            }
+            done = true;
+            break;
+        }
         T Ln[NL];
         const bool pd = chol_masked(H, fm, Ln);
         T rhs[4], dn[4], dir[4];
@@ -1555,6 +1598,14 @@ __device__ int line_search(const Params<T>& P, BlockSmem<T>& S, const Lane& L, i
         }
     }
     __syncthreads();
+    // The candidates are dead until the next line search writes them again:
+    // when the pack owns whole groups of the scratch layout, their lines leave
+    // L2 without a write-back.
+    const int base = L.pos - L.l;
+    if (P.ipb == GW && base % GW == 0) {
+        for (int c2 = 0; c2 < P.n_alpha; ++c2)
+            l2_discard(P.cand + crow(P, c2, base, 0, 0), (size_t)nmax * CREC * GW * sizeof(T));
+    }
     return r;
 }
 
@@ -1564,17 +1615,25 @@ __device__ int line_search(const Params<T>& P, BlockSmem<T>& S, const Lane& L, i
 // instead of 17 columns); with d_tau_t = [dx_t; du_t]:
 //   dQ_t = dx_t * (x*_t - x_ref,t),  dx_ref,t = -Q_t * dx_t,  dx0 = vh_0.
 // Warp 0, one instance per lane.  K_t comes from the tape (store-all) or the
-// gain records the re-factorization wrote (recompute).
+// gain records the re-factorization wrote (recompute).  x*_t - x_ref,t is
+// formed from the state as the forward carried it, hi + lo, re-rolled here
+// from x_init and u* (the returned x* is its rounding): a tracking error much
+// smaller than the state keeps its digits.
 template <typename T, int NW, bool GEN>
 __device__ void adjoint_forward(const Params<T>& P, const BlockSmem<T>& S, const Lane& L, int n,
                                 const AdjArgs<T>& A) {
     if (L.w != 0 || n <= 0) return;
     const size_t b = L.b;
-    T dx[NX], dq[NX], dcs[NZ];
+    // the sums over the stages of a shared Q (c) are carried as hi + lo
+    // (acc2): their terms can cancel to a sum far smaller than themselves
+    T dx[NX], dq[NX], dql[NX], dcs[NZ], dcl[NZ], xh[NX], xl[NX];
 #pragma unroll
-    for (int i = 0; i < NX; ++i) { dx[i] = T(0); dq[i] = T(0); A.dx0[b * NX + i] = S.vh[i][L.sl]; }
+    for (int i = 0; i < NX; ++i) {
+        dx[i] = T(0); dq[i] = T(0); dql[i] = T(0); A.dx0[b * NX + i] = S.vh[i][L.sl];
+        xh[i] = S.x0[i][L.sl]; xl[i] = T(0);
+    }
 #pragma unroll
-    for (int i = 0; i < NZ; ++i) dcs[i] = T(0);
+    for (int i = 0; i < NZ; ++i) { dcs[i] = T(0); dcl[i] = T(0); }
     for (int t = 0; t < n; ++t) {
         // the stage's operands first
         const T* kr = A.recompute ? P.stg + srow(P, L.pos, t, R_K) : P.tape + trow(P, L.b, t, T_K);
@@ -1615,7 +1674,7 @@ __device__ void adjoint_forward(const Params<T>& P, const BlockSmem<T>& S, const
                 for (int i = 0; i < NZ; ++i) A.dc[(b * P.Nc + t) * NZ + i] = d[i];
             } else {
 #pragma unroll
-                for (int i = 0; i < NZ; ++i) dcs[i] += d[i];
+                for (int i = 0; i < NZ; ++i) acc2(dcs[i], dcl[i], d[i]);
             }
             // d_tau_t and z*_t into the (free) candidate scratch, by position:
             // all warps form dL/dC from them afterwards (assemble_dC)
@@ -1627,9 +1686,9 @@ __device__ void adjoint_forward(const Params<T>& P, const BlockSmem<T>& S, const
         } else {
 #pragma unroll
             for (int i = 0; i < NX; ++i) {
-                const T e = xv[i] - xrv[i];
+                const T e = (xh[i] - xrv[i]) + xl[i];
                 if (P.Nq > 1) A.dQ[(b * P.Nq + t) * NX + i] = dx[i] * e;
-                else dq[i] += dx[i] * e;
+                else acc2(dq[i], dql[i], dx[i] * e);
                 A.dxref[(b * P.N + t) * NX + i] = -qv[i] * dx[i];
             }
         }
@@ -1639,6 +1698,7 @@ __device__ void adjoint_forward(const Params<T>& P, const BlockSmem<T>& S, const
             rk4_tangent(P.mdl, sp, dx, du, nx);
 #pragma unroll
             for (int i = 0; i < NX; ++i) dx[i] = nx[i];
+            if constexpr (!GEN) rk4_step2(P.mdl, xh, xl, us);
         }
     }
     if constexpr (GEN) {
@@ -1646,7 +1706,7 @@ __device__ void adjoint_forward(const Params<T>& P, const BlockSmem<T>& S, const
             for (int e = n * NZ; e < P.Nc * NZ; ++e) A.dc[b * P.Nc * NZ + e] = T(0);
         } else {
 #pragma unroll
-            for (int i = 0; i < NZ; ++i) A.dc[b * NZ + i] = dcs[i];
+            for (int i = 0; i < NZ; ++i) A.dc[b * NZ + i] = dcs[i] + dcl[i];
         }
     } else {
         for (int e = n * NX; e < P.N * NX; ++e) A.dxref[b * P.N * NX + e] = T(0);
@@ -1654,7 +1714,7 @@ __device__ void adjoint_forward(const Params<T>& P, const BlockSmem<T>& S, const
             for (int e = n * NX; e < P.Nq * NX; ++e) A.dQ[b * P.Nq * NX + e] = T(0);
         } else {
 #pragma unroll
-            for (int i = 0; i < NX; ++i) A.dQ[b * NX + i] = dq[i];
+            for (int i = 0; i < NX; ++i) A.dQ[b * NX + i] = dq[i] + dql[i];
         }
     }
 }
@@ -1672,7 +1732,7 @@ __device__ void assemble_dC(const Params<T>& P, const AdjArgs<T>& A, const Lane&
         int i = 0, r = e;
         while (r >= NZ - i) { r -= NZ - i; ++i; }
         const int k = i + r;
-        T acc = T(0);
+        T acc = T(0), accl = T(0);     // hi + lo sum over the stages of a shared C
         for (int t = 0; t < P.N; ++t) {
             T v = T(0);
             if (t < n) {
@@ -1685,12 +1745,13 @@ __device__ void assemble_dC(const Params<T>& P, const AdjArgs<T>& A, const Lane&
                 dCt[i * NZ + k] = v;
                 dCt[k * NZ + i] = v;
             } else {
-                acc += v;
+                acc2(acc, accl, v);
             }
         }
         if (P.NC == 1) {
-            A.dC[b * NZ * NZ + i * NZ + k] = acc;
-            A.dC[b * NZ * NZ + k * NZ + i] = acc;
+            const T tot = acc + accl;
+            A.dC[b * NZ * NZ + i * NZ + k] = tot;
+            A.dC[b * NZ * NZ + k * NZ + i] = tot;
         }
     }
 }
@@ -1707,6 +1768,32 @@ __device__ void zero_grads(const Params<T>& P, const AdjArgs<T>& A, const Lane& 
         for (int e = L.w; e < P.N * NX; e += NW) A.dxref[b * P.N * NX + e] = T(0);
     }
     for (int i = L.w; i < NX; i += NW) A.dx0[b * NX + i] = T(0);
+}
+
+// A7: the cost of the diagonal form (reading R1's centred sum, all terms
+// non-negative) at the returned iterate, evaluated afresh from the nominal
+// records with the state as hi + lo.  The running J^0 + sum of accepted cost
+// changes carries rounding relative to J^0, which a solve can lower by orders
+// of magnitude; this sum's rounding is relative to the returned cost.  Warp 0.
+template <typename T>
+__device__ T final_cost(const Params<T>& P, const BlockSmem<T>& S, const Lane& L, int n) {
+    T J = T(0);
+    for (int t = 0; t < n; ++t) {
+        const T* sr = P.stg + srow(P, L.pos, t, 0);
+        T sx = T(0), su = T(0);
+#pragma unroll
+        for (int i = 0; i < NX; ++i) {
+            const T e = (sr[(R_X + i) * GW] - sr[(R_XR + i) * GW]) + sr[(R_XL + i) * GW];
+            sx += e * (sr[(R_Q + i) * GW] * e);
+        }
+#pragma unroll
+        for (int a = 0; a < NU; ++a) {
+            const T e = sr[(R_U + a) * GW] - S.uref[a][L.sl];
+            su += e * (S.R[a][L.sl] * e);
+        }
+        J += T(0.5) * sx + T(0.5) * su;
+    }
+    return J;
 }
 
 // A7: the nominal trajectory into the caller's u*, x* (zero past the horizon).

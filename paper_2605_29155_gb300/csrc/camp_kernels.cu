@@ -154,6 +154,9 @@ __global__ void __launch_bounds__(NW * 32, 8 / NW) k_mpc(const __grid_constant__
                 }
                 next = pack_any(act && status == ST_RUNNING) ? PH_RIC : after_fwd;
             } else if (ph == PH_END) {
+                if constexpr (!GEN) {
+                    if (L.w == 0 && applies && finiteT(J)) J = final_cost<T>(P, S, L, n);
+                }
                 write_solution<T, NW>(P, L, applies ? n : 0);
                 next = PH_DONE;
             } else if (ph == PH_BPREP) {
@@ -183,6 +186,13 @@ __global__ void __launch_bounds__(NW * 32, 8 / NW) k_mpc(const __grid_constant__
             P.status[L.b] = status;
         }
         __syncthreads();
+        // After A7 the pack's stage records are dead (the backward writes its
+        // own): when the pack owns whole groups, their lines leave L2 without
+        // a write-back.
+        if ((mode == MODE_FWD || mode == PH_END) && P.ipb == GW && base % GW == 0) {
+            const int nmax = __reduce_max_sync(FULL, n);
+            l2_discard(P.stg + srow(P, base, 0, 0), (size_t)nmax * SREC * GW * sizeof(T));
+        }
     }
 }
 
