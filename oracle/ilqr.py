@@ -151,20 +151,25 @@ class BackwardResult:
     Quu: list
     Qux: list
     margin: float  # smallest |grad_i| over bound-decided dimensions (degeneracy)
+    band: float = np.inf   # smallest distance of a control to the edge of the QP's epsilon band
 
 
-def backward_pass(prob: Problem, X, U, F, free_override=None) -> BackwardResult:
+def backward_pass(prob: Problem, X, U, F, free_override=None, qp_perturb=None) -> BackwardResult:
     """Sec. IV-2: Riccati recursion with the per-stage box QP, t = n-1 .. 0.
 
     Q_t = C_t + F_t' V_{t+1} F_t,  q_t = (C_t z_t + c_t) + F_t' v_{t+1}
     (V_n = 0, v_n = 0; stage n-1 has no dynamics term).  ``free_override``
     (a free mask per stage) replaces the box QP's free sets in K_t, the
-    factor and the value update: the LQR of a given active set."""
+    factor and the value update: the LQR of a given active set.
+    ``qp_perturb`` (test instrument, None in the method) maps each stage's
+    (Q_uu, q_u) to the pair the box QP gets, to measure how sensitive a step
+    is to errors of its inputs (reading R11)."""
     n, nx, nu = prob.n, X.shape[1], U.shape[1]
     V = np.zeros((nx, nx))
     v = np.zeros(nx)
     Ks, ks, frees, Ls, Quus, Quxs = [None] * n, [None] * n, [None] * n, [None] * n, [None] * n, [None] * n
     margin = np.inf
+    band = np.inf
     for t in reversed(range(n)):
         if prob.general:
             Ct = prob.Ct(t)
@@ -184,9 +189,14 @@ def backward_pass(prob: Problem, X, U, F, free_override=None) -> BackwardResult:
         qx, qu = qv[:nx], qv[nx:]
         lo = prob.u_lo - U[t]
         hi = prob.u_hi - U[t]
-        k, free, L, ok = boxqp.solve(Quu, qu, lo, hi)
+        qs = {}
+        if qp_perturb is not None:
+            Quu, qu = qp_perturb(Quu, qu)
+        k, free, L, ok = boxqp.solve(Quu, qu, lo, hi, stats=qs)
+        margin = min(margin, qs.get("grad", np.inf))
+        band = min(band, qs.get("band", np.inf))
         if not ok:
-            return BackwardResult(False, Ks, ks, frees, Ls, Quus, Quxs, margin)
+            return BackwardResult(False, Ks, ks, frees, Ls, Quus, Quxs, margin, band)
         if free_override is not None:
             free = np.asarray(free_override[t], dtype=bool)
             fi0 = np.flatnonzero(free)
@@ -205,7 +215,7 @@ def backward_pass(prob: Problem, X, U, F, free_override=None) -> BackwardResult:
         V = 0.5 * (V + V.T)
         v = qx + K.T @ Quu @ k + K.T @ qu + Qux.T @ k
         Ks[t], ks[t], frees[t], Ls[t], Quus[t], Quxs[t] = K, k, free, L, Quu, Qux
-    return BackwardResult(True, Ks, ks, frees, Ls, Quus, Quxs, margin)
+    return BackwardResult(True, Ks, ks, frees, Ls, Quus, Quxs, margin, band)
 
 
 def forward_pass(model, prob: Problem, X, U, bp: BackwardResult, alpha):
@@ -237,6 +247,7 @@ class Solution:
     alpha_hist: list
     ls_margin_any: float = np.inf   # the same over every alpha decision, material or not
     du_hist: list = dataclasses.field(default_factory=list)   # max_t |u^k_t - u^(k-1)_t| of every step (R5)
+    qp_band: float = np.inf   # smallest distance of a control to the edge of a QP's epsilon band
 
 
 def linearize(model, prob: Problem, X, U):
@@ -244,9 +255,10 @@ def linearize(model, prob: Problem, X, U):
     return [model.jacobian(X[t], U[t]) for t in range(prob.n - 1)]
 
 
-def solve(model, prob: Problem, max_iter=10, tol=1e-6, alphas=ALPHAS) -> Solution:
+def solve(model, prob: Problem, max_iter=10, tol=1e-6, alphas=ALPHAS, qp_perturb=None) -> Solution:
     """Algorithm 2's inner loop for one instance, then the factorization at the
-    returned iterate that the backward pass differentiates (Sec. IV)."""
+    returned iterate that the backward pass differentiates (Sec. IV).
+    ``qp_perturb``: see backward_pass (test instrument)."""
     n = prob.n
     N = prob.x_ref.shape[0]
     nx, nu = prob.x0.shape[0], prob.u_ref.shape[0]
@@ -257,18 +269,19 @@ def solve(model, prob: Problem, max_iter=10, tol=1e-6, alphas=ALPHAS) -> Solutio
     X[:n] = model.rollout(prob.x0, U[:n])
     J = total_cost(prob, X, U)
     status, iters = MAX_ITER, 0
-    ls_margin, qp_margin, ls_margin_any = np.inf, np.inf, np.inf
+    ls_margin, qp_margin, ls_margin_any, qp_band = np.inf, np.inf, np.inf, np.inf
     hist, du_hist = [], []
     if not np.isfinite(J):
         return Solution(X, U, J, 0, NONFINITE, [], None, ls_margin, qp_margin, hist, ls_margin_any)
     for it in range(max_iter):
         iters = it + 1
         F = linearize(model, prob, X, U)
-        bp = backward_pass(prob, X, U, F)
+        bp = backward_pass(prob, X, U, F, qp_perturb=qp_perturb)
         if not bp.ok:
             status = NONPD
             break
         qp_margin = min(qp_margin, bp.margin)
+        qp_band = min(qp_band, bp.band)
         cands = []
         scale = 1e-300
         for a in alphas:
@@ -306,7 +319,7 @@ def solve(model, prob: Problem, max_iter=10, tol=1e-6, alphas=ALPHAS) -> Solutio
     F = linearize(model, prob, X, U)
     bp = backward_pass(prob, X, U, F)
     return Solution(X, U, total_cost(prob, X, U), iters, status, F, bp, ls_margin, qp_margin, hist, ls_margin_any,
-                    du_hist)
+                    du_hist, qp_band)
 
 
 def at_iterate(model, prob: Problem, U, free_override=None) -> Solution:

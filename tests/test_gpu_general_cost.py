@@ -38,10 +38,12 @@ def general_problem(B, N, seed, NC, Nc, cfg="hover"):
     return dict(b, C=C, c=c)
 
 
-def run_general(prob, dtype, max_iter, tol, gu, gx=None, store_mode="store_all", tpi=0):
+def run_general(prob, dtype, max_iter, tol, gu, gx=None, store_mode="store_all", tpi=0, exec_mode="persistent",
+                ipb=0):
     from paper_2605_29155_gb300 import DiffMPC, Problem
     B, N = prob["x0"].shape[0], prob["x_ref"].shape[1]
-    solver = DiffMPC(N_max=N, B_max=B, dtype=dtype, max_iter=max_iter, tol=tol, store_mode=store_mode, tpi=tpi)
+    solver = DiffMPC(N_max=N, B_max=B, dtype=dtype, max_iter=max_iter, tol=tol, store_mode=store_mode, tpi=tpi,
+                     exec_mode=exec_mode, ipb=ipb)
     p = Problem.from_numpy(prob, dtype=dtype)
     s = solver.solve(p)
     g_u = torch.as_tensor(gu, dtype=dtype, device="cuda")
@@ -103,16 +105,19 @@ def test_fp64_general_cost_identical_to_oracle(NC, Nc, cfg, tpi):
 @pytest.mark.parametrize("cfg", ["hover", "track"])
 def test_fp32_general_cost_matches_oracle(cfg):
     """The product path: FP32 against the FP64 oracle on converged instances,
-    controls within 1e-4, each gradient block within 1e-3 (relative), and the
-    cost within 1e-5 of the size of its terms: the general cost is not centred,
-    so 1/2 z'Cz and c'z largely cancel and a rounding error of the sum is
-    relative to sum_t |1/2 z'C z| + |c'z|, not to the small total."""
+    controls within 1e-4 and each gradient block within 1e-3 (relative), and
+    the cost within 1e-5 of the size of its terms, sum_t |1/2 z'C z| + |c'z|.
+    The general cost is not centred: with c_t = -C z_ref it equals
+    1/2 (z - z_ref)' C (z - z_ref) - 1/2 z_ref' C z_ref, and on hover
+    instances the two parts nearly cancel (J = 0.010 against terms of 5.0 on
+    instance 25), so an FP32 sum can resolve J only relative to its terms
+    (measured: <= 1e-7 of them).  The plain relative error is reported."""
     B, N = 32, 20
     prob = general_problem(B, N, 7, 1, N, cfg)
     gu, _ = _grads(B, N, 8)
     g = run_general(prob, torch.float32, 30, 1e-6, gu, tpi=8 if cfg == "track" else 4)
     orc = oracle_general(prob, range(B), 30, 1e-6, gu)
-    compared, bad = 0, []
+    compared, bad, worst = 0, [], {}
     for i, (pr, so, gr) in enumerate(orc):
         if so.status != ilqr.CONVERGED or g["status"][i] not in (0, 1):
             continue
@@ -120,11 +125,14 @@ def test_fp32_general_cost_matches_oracle(cfg):
         J = ilqr.total_cost(pr, so.X, so.U)
         zs = [np.concatenate([so.X[t], so.U[t]]) for t in range(pr.n)]
         scale = sum(abs(0.5 * z @ pr.Ct(t) @ z) + abs(pr.ct(t) @ z) for t, z in enumerate(zs))
-        errs = dict(u=rel(g["u"][i], so.U, 1e-6), J=abs(g["cost"][i] - J) / max(scale, 1e-12),
+        errs = dict(u=rel(g["u"][i], so.U, 1e-6), J=abs(g["cost"][i] - J) / max(abs(J), 1e-12),
+                    J_terms=abs(g["cost"][i] - J) / max(scale, 1e-12),
                     dC=rel(g["dC"][i], gr.dC, 1e-9), dc=rel(g["dc"][i], gr.dc, 1e-9), dx0=rel(g["dx0"][i], gr.dx0, 1e-9))
-        if errs["u"] > 1e-4 or errs["J"] > 1e-5 or max(errs["dC"], errs["dc"], errs["dx0"]) > 1e-3:
+        for k_, v in errs.items():
+            worst[k_] = max(worst.get(k_, 0.0), v)
+        if errs["u"] > 1e-4 or errs["J_terms"] > 1e-5 or max(errs["dC"], errs["dc"], errs["dx0"]) > 1e-3:
             bad.append((i, errs))
-    print(cfg, "compared", compared, "bad", bad[:3])
+    print(cfg, "compared", compared, "worst", worst, "bad", bad[:3])
     assert compared >= 0.75 * B
     assert not bad, bad[:3]
 
@@ -155,6 +163,56 @@ def test_diagonal_C_through_the_general_path_matches_the_diagonal_path():
     for a, b_ in ((dQ, d["dQ"][:, 0]), (g["dx0"], d["dx0"])):
         for i in range(B):
             assert rel(a[i], b_[i], 1e-9) < G_TOL64C, i
+
+
+@pytest.mark.parametrize("NC,Nc", [(1, 1), (1, "N"), ("N", 1), ("N", "N")])
+@pytest.mark.parametrize("exec_mode", ["persistent", "plain"])
+def test_general_cost_uneven_horizons_both_launch_forms(NC, Nc, exec_mode):
+    """Per-instance horizons with the general cost, C and c each shared or per
+    stage, in the persistent form (longest-horizon-first work queue) and the
+    plain form: FP64, three iterations with tol = 0, against the oracle to
+    rounding -- controls, cost, dL/dC, dL/dc, dL/dx0 -- and exact zeros in
+    every output and per-stage gradient past each instance's horizon."""
+    B, N = 12, 10
+    NC = N if NC == "N" else NC
+    Nc = N if Nc == "N" else Nc
+    prob = general_problem(B, N, 17, NC, Nc, "track")
+    prob["horizon"] = W.uneven_horizons(B, 1, N, 18)
+    gu, gx = _grads(B, N, 19)
+    g = run_general(prob, torch.float64, 3, 0.0, gu, gx, exec_mode=exec_mode, tpi=4, ipb=5)
+    orc = oracle_general(prob, range(B), 3, 0.0, gu, gx)
+    compared = 0
+    for i, (pr, so, gr) in enumerate(orc):
+        n = pr.n
+        assert not g["u"][i, n:].any() and not g["x"][i, n:].any(), i
+        if NC > 1:
+            assert not g["dC"][i, n:].any(), i
+        if Nc > 1:
+            assert not g["dc"][i, n:].any(), i
+        if so.ls_margin < TIE64:
+            continue
+        compared += 1
+        assert g["status"][i] == so.status and g["iters"][i] == so.iters, i
+        # same decisions; FP64 rounding in another arithmetic order, amplified by the
+        # conditioning of short-horizon instances with cross terms, reaches ~2e-8 here
+        assert rel(g["u"][i], so.U, 1e-6) < 1e-7, (i, rel(g["u"][i], so.U, 1e-6))
+        assert abs(g["cost"][i] - ilqr.total_cost(pr, so.X, so.U)) <= 1e-10 * max(1.0, abs(g["cost"][i])), i
+        for name, a, b_ in (("dC", g["dC"][i], gr.dC), ("dc", g["dc"][i], gr.dc), ("dx0", g["dx0"][i], gr.dx0)):
+            assert rel(a, b_, 1e-9) < 1e-6, (i, name, rel(a, b_, 1e-9))
+    assert compared >= B - 1
+
+
+def test_general_plain_form_is_bit_identical_to_persistent():
+    """FP32, uneven horizons, per-stage C and c: the plain form (one launch
+    per phase) gives the persistent form's bits."""
+    B, N = 40, 12
+    prob = general_problem(B, N, 23, N, N, "track")
+    prob["horizon"] = W.uneven_horizons(B, 1, N, 24)
+    gu, gx = _grads(B, N, 25)
+    a = run_general(prob, torch.float32, 8, 1e-6, gu, gx, exec_mode="persistent", tpi=4, ipb=8)
+    b = run_general(prob, torch.float32, 8, 1e-6, gu, gx, exec_mode="plain", tpi=4, ipb=5)
+    for k in a:
+        np.testing.assert_array_equal(a[k], b[k], err_msg=k)
 
 
 def test_general_recompute_backward_is_bit_identical_to_store_all():
