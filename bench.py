@@ -523,7 +523,81 @@ def side_configs(dev, flush, reps=3):
     out["hover_latency"] = hover_latency(dev, flush)
     out["closed_loop_track"] = closed_loop_track(dev)
     out["general_cost"] = general_cost_track(dev, flush, reps)
+    out["costmap_fused"] = costmap_fused_track(dev, flush)
     return out
+
+
+def costmap_fused_track(dev, flush, B=4096, N=20, reps=20):
+    """The actor's cost map fused with the solve (Sec. V-A, Algorithm 2's
+    (C, c) <- pi(x)): observation -> 2 x 512 ReLU -> sigmoid-scaled Q_t written
+    straight into the solve's Q buffer -> MPC forward -> adjoint dL/dQ ->
+    cost-map backward to the weights, all four in one CUDA graph; the MLP's
+    layers run on the tensor cores (tcgen05, 3xTF32).  Random-init weights of
+    that architecture; L2 flushed between replays.  Also the MLP's forward
+    and backward alone, each its own graph."""
+    import torch
+    from paper_2605_29155_gb300 import CostMap, DiffMPC, Problem
+    prob = W.race_track(B, N, seed=0)
+    params = W.costmap_weights(26, N * 13, seed=0)
+    p = Problem.from_numpy(dict(prob, Q=np.ones((B, N, 13))), device=dev)
+    gu = torch.as_tensor(W.loss_weights_u0(B, N, seed=1), dtype=torch.float32, device=dev)
+    cm = CostMap(params, N, B, device=dev)
+    sol = DiffMPC(N_max=N, B_max=B, max_iter=MAX_ITER, tol=TOL, device=dev)
+    s = sol.alloc_solution(B, N)
+    cm.forward(p.x0, p.x_ref, Q=p.Q)
+    sol.autotune(p, s)
+    grads = (torch.empty_like(p.Q), torch.empty_like(p.x_ref), torch.empty_like(p.x0))
+    wg = [torch.empty_like(t) for t in (cm.W1, cm.b1, cm.W2, cm.b2, cm.W3, cm.b3)]
+
+    def whole():
+        cm.forward(p.x0, p.x_ref, Q=p.Q)
+        sol.solve(p, s)
+        sol.backward(p, s, gu, out=grads)
+        cm.backward(p.x0, p.x_ref, grads[0], out=wg)
+
+    def mlp_fwd():
+        cm.forward(p.x0, p.x_ref, Q=p.Q)
+
+    def mlp_bwd():
+        cm.backward(p.x0, p.x_ref, grads[0], out=wg)
+
+    graphs = {}
+    side = torch.cuda.Stream(device=dev)
+    for name, fn in (("fused", whole), ("mlp_fwd", mlp_fwd), ("mlp_bwd", mlp_bwd)):
+        for _ in range(2):
+            fn()
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):
+            with torch.cuda.graph(g):
+                fn()
+        torch.cuda.current_stream().wait_stream(side)
+        graphs[name] = g
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    ms = {}
+    for name, g in graphs.items():
+        t = []
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            flush.fill_(1.0)
+            e0.record(stream)
+            g.replay()
+            e1.record(stream)
+            e1.synchronize()
+            t.append(e0.elapsed_time(e1))
+        ms[name] = statistics.median(t)
+    flops_fwd = 2.0 * B * (26 * 512 + 512 * 512 + 512 * N * 13)
+    flag = cm.wait_flag()
+    res = dict(workload=f"race track B={B}, N={N}: cost map (26 -> 512 -> 512 -> {N * 13}, random init) -> "
+                        "MPC fwd+bwd -> cost-map bwd, one CUDA graph",
+               solves_per_s=B / (ms["fused"] * 1e-3), ms_fused=ms["fused"], ms_mlp_fwd=ms["mlp_fwd"],
+               ms_mlp_bwd=ms["mlp_bwd"], mlp_share=(ms["mlp_fwd"] + ms["mlp_bwd"]) / ms["fused"],
+               mlp_fwd_tflops_3xtf32=3 * flops_fwd / (ms["mlp_fwd"] * 1e-3) / 1e12,
+               mlp_fwd_flops=flops_fwd, device_wait_flag=flag, iters_mean=float(s.iters.float().mean()))
+    sol.close()
+    return res
 
 
 def general_cost_track(dev, flush, reps, B=4096, N=20):

@@ -1,0 +1,441 @@
+// camp_costmap.cu -- the actor's cost map (Sec. V-A, Sec. III-C) on the
+// tensor cores: an MLP with two hidden layers of 512 ReLU units and a sigmoid
+// output scaled to the cost weights' bounds, observation -> per-stage Q_t, and
+// its backward from dL/dQ (the MPC adjoint's gradient) to the weights.
+//
+// Every layer is one dense contraction, run by one kernel: C = A B' on 5th
+// generation tensor cores (tcgen05.mma, kind::tf32, one 128 x 128 FP32
+// accumulator tile in tensor memory per CTA), with the layer's bias and
+// activation fused into the epilogue that reads the accumulator back
+// (tcgen05.ld).  FP32 accuracy comes from the 3xTF32 split (Ootomo & Yokota,
+// "Recovering single precision accuracy from Tensor Cores while surpassing the
+// FP32 theoretical peak performance", 2022): each operand x is split into
+// x_hi = tf32(x) and x_lo = tf32(x - x_hi), and A B' = A_hi B_hi' + A_hi B_lo'
+// + A_lo B_hi' to within FP32 rounding.
+//
+// Operands are staged in shared memory by the CTA's threads in the canonical
+// K-major layout without swizzle (8-row x 16-byte core matrices), through
+// accessors that also assemble the observation [x_init; x_ref,0], append the
+// row of ones whose product gives a bias gradient, and form dL/da3 =
+// dL/dQ (q_hi - q_lo) s (1 - s) on the fly.  Two stages of K = 16 alternate:
+// while the tensor core works on one, the threads fill the other; an mbarrier
+// signalled by tcgen05.commit tells when a stage is free again.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "camp.h"
+#include "camp_costmap.h"
+
+namespace cmap {
+
+constexpr int TM = 128;             // rows of an accumulator tile (M of one MMA)
+constexpr int TN = 128;             // columns (N of one MMA), = TMEM columns
+constexpr int TK = 16;              // K of one pipeline stage: two MMA k-steps of 8
+constexpr int THREADS = 128;        // 4 warps: warp w reads TMEM lanes 32w .. 32w+31
+constexpr int TILE_FLOATS = TM * TK;                // one operand tile (TM == TN)
+constexpr int STAGE_FLOATS = 4 * TILE_FLOATS;       // A_hi, A_lo, B_hi, B_lo
+constexpr int SMEM_BYTES = 2 * STAGE_FLOATS * 4 + 64;
+constexpr long long WAIT_LIMIT = 1ll << 24;         // bounded mbarrier waits
+
+// Operand kinds: how element (r, k) of A (r = m) or B (r = n) is read.
+enum Kind {
+    K_PLAIN = 0,      // p[r s0 + k s1], r < rows, k < K
+    K_ONES_ROW = 1,   // as K_PLAIN for r < rows; r == rows gives 1 (bias-gradient row)
+    K_OBS = 2,        // the observation: o(b, j) = j < 13 ? x0[b, j] : x_ref[b, 0, j - 13], with
+                      // (b, j) = (r, k) (s0 = 0) or (k, r) (s0 = 1); r == rows gives 1 when ones
+    K_DA3 = 3         // dL/da3 = dQ (q_hi - q_lo) s (1 - s), dQ = p, s = p2, at p[r s0 + k s1]
+};
+
+struct Operand {
+    const float* p;
+    const float* p2;
+    long long s0, s1;
+    int rows;         // valid rows (r >= rows reads 0, except a ones row)
+    int kind;
+    int ones;         // K_OBS: add the ones row at r == rows
+    int ld2;          // K_OBS: x_ref row stride (N * 13)
+};
+
+enum Epi {
+    E_STORE = 0,      // C[m, n] = acc
+    E_BIAS_RELU = 1,  // C[m, n] = max(acc + bias[n], 0)
+    E_SIGQ = 2,       // s = sigmoid(acc + bias[n]); C2[m, n] = s; C[m, n] = q_lo + (q_hi - q_lo) s
+    E_MASK = 3,       // C[m, n] = acc * (H[m, n] > 0), H = C2
+    E_SPLIT = 4       // m < M - 1: C[m, n] = acc; m == M - 1: C2[n] = acc (weight and bias gradients)
+};
+
+struct Gemm {
+    Operand A, B;
+    int M, N, K;
+    int epi;
+    const float* bias;
+    float* C;
+    long long ldc;
+    float* C2;
+    long long ldc2;
+    float q_lo, q_hi;
+    int* err;
+};
+
+__device__ __forceinline__ float load_op(const Operand& o, int r, int k, int K, float q_span) {
+    if (k >= K) return 0.f;
+    if (o.kind == K_OBS) {
+        int b = o.s0 ? k : r, j = o.s0 ? r : k;
+        if (r == o.rows) return o.ones ? 1.f : 0.f;
+        if (r > o.rows) return 0.f;
+        return j < 13 ? o.p[(long long)b * 13 + j] : o.p2[(long long)b * o.ld2 + (j - 13)];
+    }
+    if (r >= o.rows) return (o.kind == K_ONES_ROW && r == o.rows) ? 1.f : 0.f;
+    const long long i = (long long)r * o.s0 + (long long)k * o.s1;
+    if (o.kind == K_DA3) {
+        const float s = o.p2[i];
+        return o.p[i] * q_span * s * (1.f - s);
+    }
+    return o.p[i];
+}
+
+__device__ __forceinline__ uint32_t to_tf32(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return r;
+}
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// Float offset of element (r, k) of a [128 x TK] tile in the canonical K-major
+// layout without swizzle: core matrices of 8 rows x 4 floats (128 contiguous
+// bytes), the TK / 4 cores of an 8-row group side by side.
+__device__ __forceinline__ int core_off(int r, int k) { return ((r >> 3) * (TK / 4) + (k >> 2)) * 32 + (r & 7) * 4 + (k & 3); }
+
+// Shared-memory matrix descriptor of tcgen05: start address, leading-dimension
+// byte offset (between the core matrices adjacent in K), stride-dimension byte
+// offset (between the 8-row groups), descriptor version 1, no swizzle.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+    return (uint64_t)((addr >> 4) & 0x3FFF) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | ((uint64_t)1 << 46);
+}
+
+// Instruction descriptor of tcgen05.mma kind::tf32: FP32 accumulator, TF32
+// A and B, both K-major, N >> 3 at bit 17, M >> 4 at bit 24.
+constexpr uint32_t IDESC = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(TN >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
+
+__device__ __forceinline__ void mma_tf32(uint32_t d, uint64_t a, uint64_t b, uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d),
+        "l"(a), "l"(b), "r"(IDESC), "r"(acc));
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t mbar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
+    for (long long i = 0; i < WAIT_LIMIT; ++i) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.b32 %0, 1, 0, p;\n\t}\n"
+            : "=r"(done)
+            : "r"(mbar), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// One K = TK stage of A (rows m0..m0+127) and B (rows n0..n0+127) into shared
+// memory as hi / lo TF32 tiles.  Threads walk k fastest when the operand is
+// contiguous in k, else r fastest, so that global reads coalesce either way.
+__device__ __forceinline__ void fill_tile(const Operand& o, int r0, int k0, int K, float q_span, float* hi, float* lo) {
+    const bool kfast = o.kind == K_OBS ? o.s0 == 0 : o.s1 == 1;
+#pragma unroll 4
+    for (int e = threadIdx.x; e < TM * TK; e += THREADS) {
+        const int r = kfast ? e / TK : e % TM;
+        const int k = kfast ? e % TK : e / TM;
+        const float x = load_op(o, r0 + r, k0 + k, K, q_span);
+        const uint32_t h = to_tf32(x);
+        const uint32_t l = to_tf32(x - __uint_as_float(h));
+        const int off = core_off(r, k);
+        hi[off] = __uint_as_float(h);
+        lo[off] = __uint_as_float(l);
+    }
+}
+
+__global__ void __launch_bounds__(THREADS, 1) k_gemm_3xtf32(const __grid_constant__ Gemm g) {
+    extern __shared__ __align__(1024) float sm[];
+    __shared__ __align__(8) uint64_t mbar[2];
+    __shared__ uint32_t tmem_slot;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int m0 = blockIdx.y * TM, n0 = blockIdx.x * TN;
+    const float q_span = g.q_hi - g.q_lo;
+
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[0])) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[1])) : "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                     "r"(TN)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_slot;
+
+    const int nk = (g.K + TK - 1) / TK;
+    auto stage = [&](int s) { return sm + s * STAGE_FLOATS; };
+    auto fill = [&](int c) {
+        float* st = stage(c & 1);
+        fill_tile(g.A, m0, c * TK, g.K, q_span, st, st + TILE_FLOATS);
+        fill_tile(g.B, n0, c * TK, g.K, q_span, st + 2 * TILE_FLOATS, st + 3 * TILE_FLOATS);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    };
+    fill(0);
+    __syncthreads();
+    bool ok = true;
+    int issued = -1;                    // the last chunk whose MMAs were committed
+    for (int c = 0; c < nk; ++c) {
+        issued = c;
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            float* st = stage(c & 1);
+            const uint32_t a_hi = smem_u32(st), a_lo = smem_u32(st + TILE_FLOATS);
+            const uint32_t b_hi = smem_u32(st + 2 * TILE_FLOATS), b_lo = smem_u32(st + 3 * TILE_FLOATS);
+#pragma unroll
+            for (int j = 0; j < TK / 8; ++j) {
+                const uint32_t off = j * 256;            // two 16-byte K cores per k-step of 8
+                const uint32_t lbo = 128, sbo = (TK / 4) * 128;
+                const uint32_t first = (c == 0 && j == 0) ? 0u : 1u;
+                mma_tf32(tmem, smem_desc(a_lo + off, lbo, sbo), smem_desc(b_hi + off, lbo, sbo), first);
+                mma_tf32(tmem, smem_desc(a_hi + off, lbo, sbo), smem_desc(b_lo + off, lbo, sbo), 1u);
+                mma_tf32(tmem, smem_desc(a_hi + off, lbo, sbo), smem_desc(b_hi + off, lbo, sbo), 1u);
+            }
+            mma_commit(smem_u32(&mbar[c & 1]));
+        }
+        if (c + 1 < nk) {
+            // stage (c + 1) & 1 was last read by the MMAs of chunk c - 1
+            if (c >= 1 && !mbar_wait(smem_u32(&mbar[(c - 1) & 1]), ((c - 1) >> 1) & 1)) ok = false;
+            if (!__syncthreads_and(ok)) { ok = false; break; }
+            fill(c + 1);
+            __syncthreads();
+        }
+    }
+    // the last issued chunk's commit covers every MMA issued before it; this
+    // (bounded) wait also runs after a failure, before the memory is freed
+    if (issued >= 0 && !mbar_wait(smem_u32(&mbar[issued & 1]), (issued >> 1) & 1)) ok = false;
+    if (!__syncthreads_and(ok)) ok = false;
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (ok) {
+        const int m = m0 + warp * 32 + (tid & 31);
+#pragma unroll 1
+        for (int cb = 0; cb < TN; cb += 16) {
+            float v[16];
+            tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)cb, v);
+            if (m >= g.M) continue;
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                const int n = n0 + cb + i;
+                if (n >= g.N) continue;
+                const float a = v[i];
+                const long long ci = (long long)m * g.ldc + n;
+                switch (g.epi) {
+                    case E_BIAS_RELU: g.C[ci] = fmaxf(a + g.bias[n], 0.f); break;
+                    case E_SIGQ: {
+                        const float s = 1.f / (1.f + expf(-(a + g.bias[n])));
+                        g.C2[(long long)m * g.ldc2 + n] = s;
+                        g.C[ci] = g.q_lo + (g.q_hi - g.q_lo) * s;
+                        break;
+                    }
+                    case E_MASK: g.C[ci] = g.C2[(long long)m * g.ldc2 + n] > 0.f ? a : 0.f; break;
+                    case E_SPLIT:
+                        if (m < g.M - 1) g.C[ci] = a;
+                        else g.C2[n] = a;
+                        break;
+                    default: g.C[ci] = a; break;
+                }
+            }
+        }
+    } else if (tid == 0) {
+        atomicExch(g.err, 1);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TN) : "memory");
+    }
+}
+
+cudaError_t launch(const Gemm& g, cudaStream_t st) {
+    static int prepared[64] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev >= 0 && dev < 64 && !prepared[dev]) {
+        e = cudaFuncSetAttribute(k_gemm_3xtf32, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+        if (e != cudaSuccess) return e;
+        prepared[dev] = 1;
+    }
+    const dim3 grid((g.N + TN - 1) / TN, (g.M + TM - 1) / TM);
+    k_gemm_3xtf32<<<grid, THREADS, SMEM_BYTES, st>>>(g);
+    return cudaGetLastError();
+}
+
+Operand plain(const float* p, long long s0, long long s1, int rows, int kind = K_PLAIN) {
+    Operand o{};
+    o.p = p;
+    o.s0 = s0;
+    o.s1 = s1;
+    o.rows = rows;
+    o.kind = kind;
+    return o;
+}
+
+// Workspace layout: the error flag (an int in the first 256 bytes), then the
+// floats h1 [B, H], h2 [B, H], s [B, n_out], da2 [B, H], da1 [B, H].
+struct Ws {
+    float *h1, *h2, *s, *da2, *da1;
+    int* err;
+};
+Ws carve(void* ws, int B, int H, int n_out) {
+    float* f = (float*)((char*)ws + 256);
+    const size_t bh = ((size_t)B * H + 63) & ~(size_t)63, bo = ((size_t)B * n_out + 63) & ~(size_t)63;
+    Ws w;
+    w.err = (int*)ws;
+    w.h1 = f;
+    w.h2 = w.h1 + bh;
+    w.s = w.h2 + bh;
+    w.da2 = w.s + bo;
+    w.da1 = w.da2 + bh;
+    return w;
+}
+
+int check_net(const mpc_costmap* net, int B, int N) {
+    if (!net || !net->W1 || !net->b1 || !net->W2 || !net->b2 || !net->W3 || !net->b3) return MPC_ERR_ARG;
+    if (net->n_in != 26 || net->hidden < 1 || net->n_out != N * 13) return MPC_ERR_SHAPE;
+    if (B < 0 || N < 1) return MPC_ERR_SHAPE;
+    if (!(net->q_hi > net->q_lo)) return MPC_ERR_ARG;
+    return MPC_OK;
+}
+
+}  // namespace cmap
+
+using namespace cmap;
+
+extern "C" size_t mpc_costmap_workspace_bytes(int B, int hidden, int n_out) {
+    if (B < 0 || hidden < 1 || n_out < 1) return 0;
+    const size_t bh = ((size_t)B * hidden + 63) & ~(size_t)63, bo = ((size_t)B * n_out + 63) & ~(size_t)63;
+    return (4 * bh + bo) * sizeof(float) + 256;
+}
+
+extern "C" int mpc_costmap_forward(const mpc_costmap* net, int B, int N, const float* x0, const float* x_ref,
+                                   float* Q, void* ws, cudaStream_t stream) {
+    int r = check_net(net, B, N);
+    if (r != MPC_OK) return r;
+    if (B == 0) return MPC_OK;
+    if (!x0 || !x_ref || !Q || !ws) return MPC_ERR_ARG;
+    const int H = net->hidden, n_out = net->n_out;
+    Ws w = carve(ws, B, H, n_out);
+    if (cudaMemsetAsync(w.err, 0, sizeof(int), stream) != cudaSuccess) return MPC_ERR_CUDA;
+    Gemm g{};
+    g.err = w.err;
+    g.q_lo = net->q_lo;
+    g.q_hi = net->q_hi;
+    // h1 = relu(o W1 + b1): A(m, k) = o(m, k), B(n, k) = W1[k, n]
+    g.A = Operand{x0, x_ref, 0, 0, B, K_OBS, 0, N * 13};
+    g.B = plain(net->W1, 1, H, H);
+    g.M = B; g.N = H; g.K = 26;
+    g.epi = E_BIAS_RELU; g.bias = net->b1; g.C = w.h1; g.ldc = H;
+    if (launch(g, stream) != cudaSuccess) return MPC_ERR_CUDA;
+    // h2 = relu(h1 W2 + b2)
+    g.A = plain(w.h1, H, 1, B);
+    g.B = plain(net->W2, 1, H, H);
+    g.K = H; g.bias = net->b2; g.C = w.h2;
+    if (launch(g, stream) != cudaSuccess) return MPC_ERR_CUDA;
+    // Q = q_lo + (q_hi - q_lo) sigmoid(h2 W3 + b3), written as [B, N, 13]; s kept for the backward
+    g.A = plain(w.h2, H, 1, B);
+    g.B = plain(net->W3, 1, n_out, n_out);
+    g.N = n_out; g.epi = E_SIGQ; g.bias = net->b3; g.C = Q; g.ldc = n_out; g.C2 = w.s; g.ldc2 = n_out;
+    if (launch(g, stream) != cudaSuccess) return MPC_ERR_CUDA;
+    return MPC_OK;
+}
+
+extern "C" int mpc_costmap_backward(const mpc_costmap* net, int B, int N, const float* x0, const float* x_ref,
+                                    const float* dQ, void* ws, float* dW1, float* db1, float* dW2, float* db2,
+                                    float* dW3, float* db3, float* d_obs, cudaStream_t stream) {
+    int r = check_net(net, B, N);
+    if (r != MPC_OK) return r;
+    if (!dW1 || !db1 || !dW2 || !db2 || !dW3 || !db3) return MPC_ERR_ARG;
+    const int H = net->hidden, n_out = net->n_out;
+    if (B == 0) {
+        // no samples: every gradient is zero
+        const size_t z[6] = {(size_t)26 * H, (size_t)H, (size_t)H * H, (size_t)H, (size_t)H * n_out, (size_t)n_out};
+        float* p[6] = {dW1, db1, dW2, db2, dW3, db3};
+        for (int i = 0; i < 6; ++i)
+            if (cudaMemsetAsync(p[i], 0, z[i] * sizeof(float), stream) != cudaSuccess) return MPC_ERR_CUDA;
+        return MPC_OK;
+    }
+    if (!x0 || !x_ref || !dQ || !ws) return MPC_ERR_ARG;
+    Ws w = carve(ws, B, H, n_out);
+    Gemm g{};
+    g.err = w.err;
+    g.q_lo = net->q_lo;
+    g.q_hi = net->q_hi;
+    // [dW3; db3] = [h2 | 1]' da3, da3 = dQ (q_hi - q_lo) s (1 - s): A(m, k) = h2[k, m], B(n, k) = da3[k, n]
+    g.A = plain(w.h2, 1, H, H, K_ONES_ROW);
+    g.B = Operand{dQ, w.s, 1, n_out, n_out, K_DA3, 0, 0};
+    g.M = H + 1; g.N = n_out; g.K = B;
+    g.epi = E_SPLIT; g.C = dW3; g.ldc = n_out; g.C2 = db3;
+    if (launch(g, stream) != cudaSuccess) return MPC_ERR_CUDA;
+    // da2 = (da3 W3') * (h2 > 0): A(m, k) = da3[m, k], B(n, k) = W3[n, k]
+    g.A = Operand{dQ, w.s, n_out, 1, B, K_DA3, 0, 0};
+    g.B = plain(net->W3, n_out, 1, H);
+    g.M = B; g.N = H; g.K = n_out;
+    g.epi = E_MASK; g.C = w.da2; g.ldc = H; g.C2 = w.h2; g.ldc2 = H;
+    if (launch(g, stream) != cudaSuccess) return MPC_ERR_CUDA;
+    // [dW2; db2] = [h1 | 1]' da2
+    g.A = plain(w.h1, 1, H, H, K_ONES_ROW);
+    g.B = plain(w.da2, 1, H, H);
+    g.M = H + 1; g.N = H; g.K = B;
+    g.epi = E_SPLIT; g.C = dW2; g.ldc = H; g.C2 = db2;
+    if (launch(g, stream) != cudaSuccess) return MPC_ERR_CUDA;
+    // da1 = (da2 W2') * (h1 > 0)
+    g.A = plain(w.da2, H, 1, B);
+    g.B = plain(net->W2, H, 1, H);
+    g.M = B; g.N = H; g.K = H;
+    g.epi = E_MASK; g.C = w.da1; g.ldc = H; g.C2 = w.h1; g.ldc2 = H;
+    if (launch(g, stream) != cudaSuccess) return MPC_ERR_CUDA;
+    // [dW1; db1] = [o | 1]' da1: A(m, k) = o(k, m)
+    g.A = Operand{x0, x_ref, 1, 0, 26, K_OBS, 1, N * 13};
+    g.B = plain(w.da1, 1, H, H);
+    g.M = 27; g.N = H; g.K = B;
+    g.epi = E_SPLIT; g.C = dW1; g.ldc = H; g.C2 = db1;
+    if (launch(g, stream) != cudaSuccess) return MPC_ERR_CUDA;
+    if (d_obs) {
+        // dL/do = da1 W1': A(m, k) = da1[m, k], B(n, k) = W1[n, k]
+        g.A = plain(w.da1, H, 1, B);
+        g.B = plain(net->W1, H, 1, 26);
+        g.M = B; g.N = 26; g.K = H;
+        g.epi = E_STORE; g.C = d_obs; g.ldc = 26;
+        if (launch(g, stream) != cudaSuccess) return MPC_ERR_CUDA;
+    }
+    return MPC_OK;
+}

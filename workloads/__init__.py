@@ -222,3 +222,17 @@ def subset(prob: dict, idx) -> dict:
         else:
             out[k] = v
     return out
+
+
+def costmap_weights(n_in: int, n_out: int, seed: int = 0, hidden: int = 512):
+    """Random-init weights (W1, b1, W2, b2, W3, b3) of the actor's cost map,
+    n_in -> hidden -> hidden -> n_out, W_l of shape [n_in_l, n_out_l], every
+    entry uniform in +-1/sqrt(n_in_l) (seeded): the stand-in for trained
+    weights of that architecture."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for a, b in ((n_in, hidden), (hidden, hidden), (hidden, n_out)):
+        lim = 1.0 / np.sqrt(a)
+        out.append(rng.uniform(-lim, lim, size=(a, b)))
+        out.append(rng.uniform(-lim, lim, size=b))
+    return out
