@@ -71,8 +71,14 @@ def chol_solve(L, b):
     return y
 
 
-def solve(H, g, lo, hi):
-    """Projected-Newton box QP.  Returns (d, free[bool], L, ok)."""
+def solve(H, g, lo, hi, stats=None):
+    """Projected-Newton box QP.  Returns (d, free[bool], L, ok).
+
+    ``stats`` (a dict, optional) receives the margins behind the clamped /
+    free decisions of every iteration (degeneracy bookkeeping, reading R11):
+    'grad', the smallest |grad_i| / (1 + max|g|) of a dimension inside the
+    epsilon band of a bound (its sign decides), and 'band', the smallest
+    distance of a dimension to the edge of that band, / (1 + hi_i - lo_i)."""
     n = g.shape[0]
     d = np.clip(np.zeros(n), lo, hi)
     free_prev = None
@@ -80,8 +86,15 @@ def solve(H, g, lo, hi):
     L = None
     free_fact = np.zeros(n, dtype=bool)
     eps = EPS_REL * (1.0 + (hi - lo))
+    gscale = 1.0 + np.max(np.abs(g))
     for _ in range(MAX_IT):
         grad = g + H @ d
+        if stats is not None:
+            near = (d <= lo + eps) | (d >= hi - eps)
+            if near.any():
+                stats["grad"] = min(stats.get("grad", np.inf), float(np.min(np.abs(grad[near]))) / gscale)
+            edge = np.minimum(np.abs(d - (lo + eps)), np.abs((hi - eps) - d)) / (1.0 + (hi - lo))
+            stats["band"] = min(stats.get("band", np.inf), float(np.min(edge)))
         at_lo = (d <= lo + eps) & (grad > 0)
         at_hi = (d >= hi - eps) & (grad < 0)
         d = np.where(at_lo, lo, np.where(at_hi, hi, d))
