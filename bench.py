@@ -52,10 +52,14 @@ FP32_LANES_PER_SM = 128
 L2_FLUSH_BYTES = 256 << 20
 
 
+# the sources the MPC kernel (k_mpc) is compiled from
+KERNEL_SOURCES = ("camp_device.cuh", "camp_internal.h", "camp_kernels.cu")
+
+
 def _kernel_hash():
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_2605_29155_gb300", "csrc")
-    for f in sorted(os.listdir(d)):
+    for f in KERNEL_SOURCES:
         h.update(open(os.path.join(d, f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -776,6 +780,34 @@ def run_kernels_only(args):
     solver.close()
 
 
+def run_costmap_only(args):
+    """W + K eager cost-map forward + backward passes (B instances, N = 20,
+    random-init weights), nothing else: the command the committed ncu summary
+    of the tensor-core kernel was taken with."""
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2605_29155_gb300 import CostMap
+    Bk = args.batch
+    prob = W.race_track(Bk, N, seed=0)
+    cm = CostMap(W.costmap_weights(26, N * 13, seed=0), N, Bk)
+    x0 = torch.as_tensor(prob["x0"], dtype=torch.float32, device="cuda")
+    xr = torch.as_tensor(prob["x_ref"], dtype=torch.float32, device="cuda")
+    dQ = torch.as_tensor(np.random.default_rng(1).normal(size=(Bk, N, 13)), dtype=torch.float32, device="cuda")
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for k in range(args.warmup + args.steps):
+        if k == args.warmup:
+            torch.cuda.synchronize()
+            e0.record()
+        cm.forward(x0, xr)
+        cm.backward(x0, xr, dQ)
+    e1.record()
+    torch.cuda.synchronize()
+    print(json.dumps(dict(mode="costmap", B=Bk, N=N, steps=args.steps, ms_per_step=e0.elapsed_time(e1) / args.steps,
+                          wait_flag=cm.wait_flag())))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -785,14 +817,18 @@ def main():
     ap.add_argument("--latency-reps", type=int, default=200)
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-side", action="store_true", help="skip the uneven-horizon and memory-heavy batches")
-    ap.add_argument("--mode", default="full", choices=["full", "kernels"],
-                    help="kernels: only W + K eager forward+backward steps of the workload (for profilers)")
+    ap.add_argument("--mode", default="full", choices=["full", "kernels", "costmap"],
+                    help="kernels: only W + K eager forward+backward steps of the workload (for profilers); "
+                         "costmap: only W + K cost-map forward+backward passes")
     ap.add_argument("--batch", type=int, default=B, help="instances (kernels mode only)")
     ap.add_argument("--tpi", type=int, default=0, help="threads per instance, 0 = default (kernels mode only)")
     ap.add_argument("--ipb", type=int, default=0, help="instances per block, 0 = default (kernels mode only)")
     args = ap.parse_args()
     if args.mode == "kernels":
         run_kernels_only(args)
+        return
+    if args.mode == "costmap":
+        run_costmap_only(args)
         return
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", args.gpus if args.gpus == 1 else 1))

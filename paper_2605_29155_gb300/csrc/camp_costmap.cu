@@ -32,11 +32,14 @@ namespace cmap {
 constexpr int TM = 128;             // rows of an accumulator tile (M of one MMA)
 constexpr int TN = 128;             // columns (N of one MMA), = TMEM columns
 constexpr int TK = 16;              // K of one pipeline stage: two MMA k-steps of 8
-constexpr int THREADS = 128;        // 4 warps: warp w reads TMEM lanes 32w .. 32w+31
+constexpr int THREADS = 256;        // 8 warps: warp w reads TMEM lanes 32 (w % 4) .., columns 64 (w / 4) ..
 constexpr int TILE_FLOATS = TM * TK;                // one operand tile (TM == TN)
 constexpr int STAGE_FLOATS = 4 * TILE_FLOATS;       // A_hi, A_lo, B_hi, B_lo
 constexpr int SMEM_BYTES = 2 * STAGE_FLOATS * 4 + 64;
 constexpr long long WAIT_LIMIT = 1ll << 24;         // bounded mbarrier waits
+constexpr int SPLIT_MIN_K = 1024;                   // contractions this long are split over K ...
+constexpr int SPLIT_MAX = 32;                       // ... into at most this many parts
+constexpr int SPLIT_CHUNK = 128;                    // of at least this K each
 
 // Operand kinds: how element (r, k) of A (r = m) or B (r = n) is read.
 enum Kind {
@@ -76,6 +79,8 @@ struct Gemm {
     long long ldc2;
     float q_lo, q_hi;
     int* err;
+    int kper;           // split-K: K per part (a multiple of TK); 0 = no split
+    float* part;        // split-K: [parts, M, N] partial accumulators
 };
 
 __device__ __forceinline__ float load_op(const Operand& o, int r, int k, int K, float q_span) {
@@ -159,21 +164,53 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-// One K = TK stage of A (rows m0..m0+127) and B (rows n0..n0+127) into shared
-// memory as hi / lo TF32 tiles.  Threads walk k fastest when the operand is
-// contiguous in k, else r fastest, so that global reads coalesce either way.
+__device__ __forceinline__ void put_split(float* hi, float* lo, int off, float x) {
+    const uint32_t h = to_tf32(x);
+    hi[off] = __uint_as_float(h);
+    lo[off] = __uint_as_float(to_tf32(x - __uint_as_float(h)));
+}
+
+// One K = TK stage of A (rows r0..r0+127) or B into shared memory as hi / lo
+// TF32 tiles.  Threads take four consecutive elements along the dimension the
+// operand is contiguous in (k, or r), so that global reads coalesce and, where
+// the four are 16-byte aligned and in bounds, are one vector load; the
+// observation and ragged or misaligned edges take the scalar path.
 __device__ __forceinline__ void fill_tile(const Operand& o, int r0, int k0, int K, float q_span, float* hi, float* lo) {
     const bool kfast = o.kind == K_OBS ? o.s0 == 0 : o.s1 == 1;
-#pragma unroll 4
-    for (int e = threadIdx.x; e < TM * TK; e += THREADS) {
+    const bool vec_kind = o.kind != K_OBS;
+#pragma unroll 2
+    for (int e = threadIdx.x * 4; e < TM * TK; e += THREADS * 4) {
         const int r = kfast ? e / TK : e % TM;
         const int k = kfast ? e % TK : e / TM;
-        const float x = load_op(o, r0 + r, k0 + k, K, q_span);
-        const uint32_t h = to_tf32(x);
-        const uint32_t l = to_tf32(x - __uint_as_float(h));
-        const int off = core_off(r, k);
-        hi[off] = __uint_as_float(h);
-        lo[off] = __uint_as_float(l);
+        const int rr = r0 + r, kk = k0 + k;
+        // the four elements (r, k..k+3) or (r..r+3, k)
+        bool vec = vec_kind;
+        long long i0 = 0;
+        if (vec) {
+            const bool inb = kfast ? (kk + 3 < K && rr < o.rows) : (rr + 3 < o.rows && kk < K);
+            i0 = (long long)rr * o.s0 + (long long)kk * o.s1;
+            vec = inb && ((((size_t)(o.p + i0)) & 15) == 0) &&
+                  (o.kind != K_DA3 || ((((size_t)(o.p2 + i0)) & 15) == 0));
+        }
+        if (vec) {
+            float4 v = *reinterpret_cast<const float4*>(o.p + i0);
+            if (o.kind == K_DA3) {
+                const float4 sv = *reinterpret_cast<const float4*>(o.p2 + i0);
+                v.x *= q_span * sv.x * (1.f - sv.x);
+                v.y *= q_span * sv.y * (1.f - sv.y);
+                v.z *= q_span * sv.z * (1.f - sv.z);
+                v.w *= q_span * sv.w * (1.f - sv.w);
+            }
+            const float x4[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+            for (int j = 0; j < 4; ++j) put_split(hi, lo, kfast ? core_off(r, k + j) : core_off(r + j, k), x4[j]);
+        } else {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int rj = kfast ? r : r + j, kj = kfast ? k + j : k;
+                put_split(hi, lo, core_off(rj, kj), load_op(o, r0 + rj, k0 + kj, K, q_span));
+            }
+        }
     }
 }
 
@@ -184,6 +221,9 @@ __global__ void __launch_bounds__(THREADS, 1) k_gemm_3xtf32(const __grid_constan
     const int tid = threadIdx.x, warp = tid >> 5;
     const int m0 = blockIdx.y * TM, n0 = blockIdx.x * TN;
     const float q_span = g.q_hi - g.q_lo;
+    // this CTA's range of K: all of it, or part blockIdx.z of a split
+    const int kbeg = g.kper ? blockIdx.z * g.kper : 0;
+    const int kend = g.kper ? min(g.K, kbeg + g.kper) : g.K;
 
     if (tid == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[0])) : "memory");
@@ -200,12 +240,12 @@ __global__ void __launch_bounds__(THREADS, 1) k_gemm_3xtf32(const __grid_constan
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = tmem_slot;
 
-    const int nk = (g.K + TK - 1) / TK;
+    const int nk = (kend - kbeg + TK - 1) / TK;
     auto stage = [&](int s) { return sm + s * STAGE_FLOATS; };
     auto fill = [&](int c) {
         float* st = stage(c & 1);
-        fill_tile(g.A, m0, c * TK, g.K, q_span, st, st + TILE_FLOATS);
-        fill_tile(g.B, n0, c * TK, g.K, q_span, st + 2 * TILE_FLOATS, st + 3 * TILE_FLOATS);
+        fill_tile(g.A, m0, kbeg + c * TK, kend, q_span, st, st + TILE_FLOATS);
+        fill_tile(g.B, n0, kbeg + c * TK, kend, q_span, st + 2 * TILE_FLOATS, st + 3 * TILE_FLOATS);
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     };
     fill(0);
@@ -244,17 +284,25 @@ __global__ void __launch_bounds__(THREADS, 1) k_gemm_3xtf32(const __grid_constan
     if (!__syncthreads_and(ok)) ok = false;
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     if (ok) {
-        const int m = m0 + warp * 32 + (tid & 31);
+        // warp w reads the accumulator rows of its TMEM lane quarter, in the
+        // columns of its half
+        const int quarter = warp & 3, half = warp >> 2;
+        const int m = m0 + quarter * 32 + (tid & 31);
 #pragma unroll 1
-        for (int cb = 0; cb < TN; cb += 16) {
+        for (int cb = half * (TN / 2); cb < (half + 1) * (TN / 2); cb += 16) {
             float v[16];
-            tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)cb, v);
+            tmem_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)cb, v);
             if (m >= g.M) continue;
 #pragma unroll
             for (int i = 0; i < 16; ++i) {
                 const int n = n0 + cb + i;
                 if (n >= g.N) continue;
                 const float a = v[i];
+                if (g.kper) {
+                    // a part of a split contraction: the raw partial sum
+                    g.part[((long long)blockIdx.z * g.M + m) * g.N + n] = a;
+                    continue;
+                }
                 const long long ci = (long long)m * g.ldc + n;
                 switch (g.epi) {
                     case E_BIAS_RELU: g.C[ci] = fmaxf(a + g.bias[n], 0.f); break;
@@ -284,7 +332,29 @@ __global__ void __launch_bounds__(THREADS, 1) k_gemm_3xtf32(const __grid_constan
     }
 }
 
-cudaError_t launch(const Gemm& g, cudaStream_t st) {
+// The parts of a split contraction summed in a fixed order (deterministic),
+// then the store of E_STORE / E_SPLIT.
+__global__ void k_splitk_reduce(const __grid_constant__ Gemm g, int parts) {
+    const long long total = (long long)g.M * g.N;
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const int m = (int)(idx / g.N), n = (int)(idx % g.N);
+        float a = 0.f;
+        for (int z = 0; z < parts; ++z) a += g.part[((long long)z * g.M + m) * g.N + n];
+        if (g.epi == E_SPLIT && m == g.M - 1) g.C2[n] = a;
+        else g.C[(long long)m * g.ldc + n] = a;
+    }
+}
+
+// Parts of a split over K for a contraction of length K (1 = no split).
+int split_parts(int K) {
+    if (K < SPLIT_MIN_K) return 1;
+    int p = (K + SPLIT_CHUNK - 1) / SPLIT_CHUNK;
+    return p < SPLIT_MAX ? p : SPLIT_MAX;
+}
+
+cudaError_t launch(const Gemm& gin, cudaStream_t st) {
+    Gemm g = gin;
     static int prepared[64] = {};
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -294,8 +364,20 @@ cudaError_t launch(const Gemm& g, cudaStream_t st) {
         if (e != cudaSuccess) return e;
         prepared[dev] = 1;
     }
-    const dim3 grid((g.N + TN - 1) / TN, (g.M + TM - 1) / TM);
+    const int parts = g.part && (g.epi == E_STORE || g.epi == E_SPLIT) ? split_parts(g.K) : 1;
+    g.kper = 0;
+    if (parts > 1) {
+        const int per = (g.K + parts - 1) / parts;
+        g.kper = (per + TK - 1) / TK * TK;
+    }
+    const int nz = g.kper ? (g.K + g.kper - 1) / g.kper : 1;
+    const dim3 grid((g.N + TN - 1) / TN, (g.M + TM - 1) / TM, nz);
     k_gemm_3xtf32<<<grid, THREADS, SMEM_BYTES, st>>>(g);
+    if (nz > 1) {
+        const long long total = (long long)g.M * g.N;
+        const int blocks = (int)((total + 255) / 256 < 1024 ? (total + 255) / 256 : 1024);
+        k_splitk_reduce<<<blocks, 256, 0, st>>>(g, nz);
+    }
     return cudaGetLastError();
 }
 
@@ -310,11 +392,14 @@ Operand plain(const float* p, long long s0, long long s1, int rows, int kind = K
 }
 
 // Workspace layout: the error flag (an int in the first 256 bytes), then the
-// floats h1 [B, H], h2 [B, H], s [B, n_out], da2 [B, H], da1 [B, H].
+// floats h1 [B, H], h2 [B, H], s [B, n_out], da2 [B, H], da1 [B, H], and the
+// partial sums of the split weight-gradient contractions [SPLIT_MAX, H + 1,
+// max(H, n_out)].
 struct Ws {
-    float *h1, *h2, *s, *da2, *da1;
+    float *h1, *h2, *s, *da2, *da1, *part;
     int* err;
 };
+size_t part_floats(int H, int n_out) { return (size_t)SPLIT_MAX * (H + 1) * (H > n_out ? H : n_out); }
 Ws carve(void* ws, int B, int H, int n_out) {
     float* f = (float*)((char*)ws + 256);
     const size_t bh = ((size_t)B * H + 63) & ~(size_t)63, bo = ((size_t)B * n_out + 63) & ~(size_t)63;
@@ -325,6 +410,7 @@ Ws carve(void* ws, int B, int H, int n_out) {
     w.s = w.h2 + bh;
     w.da2 = w.s + bo;
     w.da1 = w.da2 + bh;
+    w.part = w.da1 + bh;
     return w;
 }
 
@@ -343,7 +429,7 @@ using namespace cmap;
 extern "C" size_t mpc_costmap_workspace_bytes(int B, int hidden, int n_out) {
     if (B < 0 || hidden < 1 || n_out < 1) return 0;
     const size_t bh = ((size_t)B * hidden + 63) & ~(size_t)63, bo = ((size_t)B * n_out + 63) & ~(size_t)63;
-    return (4 * bh + bo) * sizeof(float) + 256;
+    return (4 * bh + bo + part_floats(hidden, n_out)) * sizeof(float) + 256;
 }
 
 extern "C" int mpc_costmap_forward(const mpc_costmap* net, int B, int N, const float* x0, const float* x_ref,
@@ -403,38 +489,38 @@ extern "C" int mpc_costmap_backward(const mpc_costmap* net, int B, int N, const 
     g.A = plain(w.h2, 1, H, H, K_ONES_ROW);
     g.B = Operand{dQ, w.s, 1, n_out, n_out, K_DA3, 0, 0};
     g.M = H + 1; g.N = n_out; g.K = B;
-    g.epi = E_SPLIT; g.C = dW3; g.ldc = n_out; g.C2 = db3;
+    g.epi = E_SPLIT; g.C = dW3; g.ldc = n_out; g.C2 = db3; g.part = w.part;
     if (launch(g, stream) != cudaSuccess) return MPC_ERR_CUDA;
     // da2 = (da3 W3') * (h2 > 0): A(m, k) = da3[m, k], B(n, k) = W3[n, k]
     g.A = Operand{dQ, w.s, n_out, 1, B, K_DA3, 0, 0};
     g.B = plain(net->W3, n_out, 1, H);
     g.M = B; g.N = H; g.K = n_out;
-    g.epi = E_MASK; g.C = w.da2; g.ldc = H; g.C2 = w.h2; g.ldc2 = H;
+    g.epi = E_MASK; g.C = w.da2; g.ldc = H; g.C2 = w.h2; g.ldc2 = H; g.part = nullptr;
     if (launch(g, stream) != cudaSuccess) return MPC_ERR_CUDA;
     // [dW2; db2] = [h1 | 1]' da2
     g.A = plain(w.h1, 1, H, H, K_ONES_ROW);
     g.B = plain(w.da2, 1, H, H);
     g.M = H + 1; g.N = H; g.K = B;
-    g.epi = E_SPLIT; g.C = dW2; g.ldc = H; g.C2 = db2;
+    g.epi = E_SPLIT; g.C = dW2; g.ldc = H; g.C2 = db2; g.part = w.part;
     if (launch(g, stream) != cudaSuccess) return MPC_ERR_CUDA;
     // da1 = (da2 W2') * (h1 > 0)
     g.A = plain(w.da2, H, 1, B);
     g.B = plain(net->W2, H, 1, H);
     g.M = B; g.N = H; g.K = H;
-    g.epi = E_MASK; g.C = w.da1; g.ldc = H; g.C2 = w.h1; g.ldc2 = H;
+    g.epi = E_MASK; g.C = w.da1; g.ldc = H; g.C2 = w.h1; g.ldc2 = H; g.part = nullptr;
     if (launch(g, stream) != cudaSuccess) return MPC_ERR_CUDA;
     // [dW1; db1] = [o | 1]' da1: A(m, k) = o(k, m)
     g.A = Operand{x0, x_ref, 1, 0, 26, K_OBS, 1, N * 13};
     g.B = plain(w.da1, 1, H, H);
     g.M = 27; g.N = H; g.K = B;
-    g.epi = E_SPLIT; g.C = dW1; g.ldc = H; g.C2 = db1;
+    g.epi = E_SPLIT; g.C = dW1; g.ldc = H; g.C2 = db1; g.part = w.part;
     if (launch(g, stream) != cudaSuccess) return MPC_ERR_CUDA;
     if (d_obs) {
         // dL/do = da1 W1': A(m, k) = da1[m, k], B(n, k) = W1[n, k]
         g.A = plain(w.da1, H, 1, B);
         g.B = plain(net->W1, H, 1, 26);
         g.M = B; g.N = 26; g.K = H;
-        g.epi = E_STORE; g.C = d_obs; g.ldc = 26;
+        g.epi = E_STORE; g.C = d_obs; g.ldc = 26; g.part = nullptr;
         if (launch(g, stream) != cudaSuccess) return MPC_ERR_CUDA;
     }
     return MPC_OK;
