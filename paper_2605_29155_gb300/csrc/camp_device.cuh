@@ -176,6 +176,24 @@ template <typename T> struct alignas(16) BlockSmem {
     } u;
 };
 
+// General cost with one C shared over the stages (NC = 1): the pack's C is
+// staged once into shared memory right after BlockSmem, as [entry][lane] rows
+// like the other per-instance matrices (kernels of the general cost are
+// launched with this region added to their dynamic shared memory).
+template <typename T> constexpr size_t gen_smem_bytes() { return sizeof(T) * (NZ * NZ) * SL<T>::A; }
+template <typename T>
+__device__ __forceinline__ T* cshared(const BlockSmem<T>& S) {
+    return reinterpret_cast<T*>(reinterpret_cast<char*>(const_cast<BlockSmem<T>*>(&S)) + sizeof(BlockSmem<T>));
+}
+
+// Entry e = i * 17 + k of an instance's C_t: from the shared-memory copy when
+// C is shared over the stages, else from the caller's array (through L1).
+template <typename T> struct CView {
+    const T* p;
+    int stride;
+    __device__ __forceinline__ T operator()(int e) const { return p[(size_t)e * stride]; }
+};
+
 template <typename T> __device__ __forceinline__ T clampT(T v, T lo, T hi) {
     return v < lo ? lo : (v > hi ? hi : v);
 }
@@ -733,6 +751,12 @@ struct Lane {
     bool valid;
 };
 
+template <typename T>
+__device__ __forceinline__ CView<T> cview(const Params<T>& P, const BlockSmem<T>& S, const Lane& L, int t) {
+    if (P.NC == 1) return CView<T>{cshared(S) + L.sl, SL<T>::A};
+    return CView<T>{Cmat(P, L.b, t), 1};
+}
+
 // Scratch row e of stage t for position pos ([group][stage][row][GW]).
 template <typename T>
 __device__ __forceinline__ size_t srow(const Params<T>& P, int pos, int t, int e) {
@@ -758,9 +782,17 @@ __device__ __forceinline__ const T* Qrow(const Params<T>& P, int b, int t) {
     return P.Q + ((size_t)b * P.Nq + (P.Nq > 1 ? t : 0)) * NX;
 }
 
-// The pack's per-instance constants into shared memory (rows split by warp).
-template <typename T, int NW>
+// The pack's per-instance constants into shared memory (rows split by warp);
+// with a general cost shared over the stages, also C.
+template <typename T, int NW, bool GEN>
 __device__ void load_constants(const Params<T>& P, BlockSmem<T>& S, const Lane& L) {
+    if constexpr (GEN) {
+        if (L.valid && P.NC == 1) {
+            T* Cs = cshared(S);
+            const T* Cg = P.Cg + (size_t)L.b * (NZ * NZ);
+            for (int e = L.w; e < NZ * NZ; e += NW) Cs[e * SL<T>::A + L.sl] = Cg[e];
+        }
+    }
     if (L.valid) {
         for (int e = L.w; e < NX + 4 * NU; e += NW) {
             if (e < NX) {
@@ -785,9 +817,11 @@ __device__ void load_stage_rows(const Params<T>& P, const Lane& L, int n, bool n
         T* dr = P.stg + srow(P, L.pos, t, 0);
         T buf[2 * NX];
         if constexpr (GEN) {
-            // the diagonal cost rows are not used with a general cost
+            // the diagonal cost rows are not used with a general cost: they
+            // hold c_t instead (rows R_Q .. R_Q + 16), the rest zeros
+            const T* cv = cvec(P, L.b, t);
 #pragma unroll
-            for (int i = 0; i < 2 * NX; ++i) buf[i] = T(0);
+            for (int i = 0; i < 2 * NX; ++i) buf[i] = i < NZ ? cv[i] : T(0);
         } else {
             const T* q = Qrow(P, L.b, t);
             const T* xr = P.xref + ((size_t)L.b * P.N + t) * NX;
@@ -853,8 +887,10 @@ __device__ void initial_rollout(const Params<T>& P, BlockSmem<T>& S, const Lane&
             }
             if constexpr (GEN) {
                 // 1/2 z' C z + c' z = sum_i z_i (1/2 (C z)_i + c_i)
-                const T* Cm = Cmat(P, L.b, t);
-                const T* cv = cvec(P, L.b, t);
+                const CView<T> Cm = cview(P, S, L, t);
+                T cv[NZ];
+#pragma unroll
+                for (int i = 0; i < NZ; ++i) cv[i] = sr[(R_Q + i) * GW];
                 T z[NZ];
 #pragma unroll
                 for (int i = 0; i < NX; ++i) z[i] = xh[i] + xl[i];
@@ -865,7 +901,7 @@ __device__ void initial_rollout(const Params<T>& P, BlockSmem<T>& S, const Lane&
                 for (int i = 0; i < NZ; ++i) {
                     T cz = T(0);
 #pragma unroll
-                    for (int k = 0; k < NZ; ++k) cz += Cm[i * NZ + k] * z[k];
+                    for (int k = 0; k < NZ; ++k) cz += Cm(i * NZ + k) * z[k];
                     sz += z[i] * (T(0.5) * cz + cv[i]);
                 }
                 J += sz;
@@ -978,14 +1014,14 @@ __device__ __forceinline__ void cost_row(const Params<T>& P, const BlockSmem<T>&
     constexpr int A = SL<T>::A;
     const int sl = L.sl;
     if constexpr (GEN) {
-        const T* Cr = Cmat(P, L.b, s) + j * NZ;
-        T acc = cvec(P, L.b, s)[j];
+        const CView<T> Cm = cview(P, S, L, s);
+        T acc = cs[(R_Q + j) * A];
 #pragma unroll
         for (int k = 0; k < NX; ++k)
-            acc += Cr[k] * (use_lo ? cs[(R_X + k) * A] + cs[(R_XL + k) * A] : cs[(R_X + k) * A]);
+            acc += Cm(j * NZ + k) * (use_lo ? cs[(R_X + k) * A] + cs[(R_XL + k) * A] : cs[(R_X + k) * A]);
 #pragma unroll
-        for (int a = 0; a < NU; ++a) acc += Cr[NX + a] * cs[(R_U + a) * A];
-        Cd = Cr[j];
+        for (int a = 0; a < NU; ++a) acc += Cm(j * NZ + NX + a) * cs[(R_U + a) * A];
+        Cd = Cm(j * NZ + j);
         c = acc;
         return;
     }
@@ -1035,7 +1071,8 @@ __device__ __forceinline__ void form_p(const Params<T>& P, BlockSmem<T>& S, cons
     const T* Qn = &S.u.r.Q[(s + 1) & 1][0][sl];
     const T* Nb = &S.u.r.N[0][sl];
     T* Ps = &S.u.r.Q[s & 1][0][sl];
-    const T* Cm = GEN ? Cmat(P, L.b, s) : nullptr;
+    CView<T> Cm{nullptr, 0};
+    if constexpr (GEN) Cm = cview(P, S, L, s);
     const bool cw = L.w == Split<NW>::CONST_W;
     if (Split<NW>::pcol(L.w, 0) < 0 && !cw) return;
     T V[NV], nx[NX][NU];
@@ -1065,12 +1102,12 @@ __device__ __forceinline__ void form_p(const Params<T>& P, BlockSmem<T>& S, cons
             for (int a = 0; a < 3; ++a) {
                 const T Vpp = V[vidx(a, b)];
                 const T Wpv = V[vidx(a, 7 + b)] + hv * Vpp;
-                Ps[qidx(a, 7 + b) * A] = ons ? (GEN ? Cm[a * NZ + 7 + b] + Wpv : Wpv) : T(0);
+                Ps[qidx(a, 7 + b) * A] = ons ? (GEN ? Cm(a * NZ + 7 + b) + Wpv : Wpv) : T(0);
                 if (a <= b) {
-                    Ps[qidx(a, b) * A] = ons ? (GEN ? Cm[a * NZ + b] + Vpp : (a == b ? Cp + Vpp : Vpp)) : T(0);
+                    Ps[qidx(a, b) * A] = ons ? (GEN ? Cm(a * NZ + b) + Vpp : (a == b ? Cp + Vpp : Vpp)) : T(0);
                     const T v2 = (V[vidx(7 + a, 7 + b)] + hv * V[vidx(7 + a, b)]) + hv * Wpv;
                     Ps[qidx(7 + a, 7 + b) * A] =
-                        ons ? (GEN ? Cm[(7 + a) * NZ + 7 + b] + v2 : (a == b ? Cv + v2 : v2)) : T(0);
+                        ons ? (GEN ? Cm((7 + a) * NZ + 7 + b) + v2 : (a == b ? Cv + v2 : v2)) : T(0);
                 }
             }
         }
@@ -1092,9 +1129,9 @@ __device__ __forceinline__ void form_p(const Params<T>& P, BlockSmem<T>& S, cons
         Ps[qidx(j, j) * A] = ons ? Cd + dot13(f, W) : T(0);
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-            Ps[qidx(a, j) * A] = ons ? (GEN ? Cm[a * NZ + j] + W[a] : W[a]) : T(0);
+            Ps[qidx(a, j) * A] = ons ? (GEN ? Cm(a * NZ + j) + W[a] : W[a]) : T(0);
             const T wv = W[7 + a] + hv * W[a];
-            Ps[qidx(7 + a, j) * A] = ons ? (GEN ? Cm[(7 + a) * NZ + j] + wv : wv) : T(0);
+            Ps[qidx(7 + a, j) * A] = ons ? (GEN ? Cm((7 + a) * NZ + j) + wv : wv) : T(0);
         }
 #pragma unroll 1
         for (int r = 0; r < jj; r += 2) {
@@ -1103,8 +1140,8 @@ __device__ __forceinline__ void form_p(const Params<T>& P, BlockSmem<T>& S, cons
 #pragma unroll
             for (int i = 0; i < NX; ++i) { f0[i] = Fb[(r * NX + i) * A]; f1[i] = Fb[(r1 * NX + i) * A]; }
             const T a0 = dot13(f0, W), a1 = dot13(f1, W);
-            Ps[qidx(gcol(r), j) * A] = ons ? (GEN ? Cm[gcol(r) * NZ + j] + a0 : a0) : T(0);
-            if (r1 != r) Ps[qidx(gcol(r1), j) * A] = ons ? (GEN ? Cm[gcol(r1) * NZ + j] + a1 : a1) : T(0);
+            Ps[qidx(gcol(r), j) * A] = ons ? (GEN ? Cm(gcol(r) * NZ + j) + a0 : a0) : T(0);
+            if (r1 != r) Ps[qidx(gcol(r1), j) * A] = ons ? (GEN ? Cm(gcol(r1) * NZ + j) + a1 : a1) : T(0);
         }
     }
 }
@@ -1529,8 +1566,7 @@ __device__ int line_search(const Params<T>& P, BlockSmem<T>& S, const Lane& L, i
             }
             if constexpr (GEN) {
                 // d' (C (z + d/2) + c) with the general C_t, c_t
-                const T* Cm = Cmat(P, L.b, t);
-                const T* cv = cvec(P, L.b, t);
+                const CView<T> Cm = cview(P, S, L, t);
                 T zh[NZ], dz[NZ];
 #pragma unroll
                 for (int i = 0; i < NX; ++i) {
@@ -1546,9 +1582,9 @@ __device__ int line_search(const Params<T>& P, BlockSmem<T>& S, const Lane& L, i
                 T sg = T(0);
 #pragma unroll
                 for (int i = 0; i < NZ; ++i) {
-                    T r = cv[i];
+                    T r = sb[(R_Q + i) * A];
 #pragma unroll
-                    for (int k = 0; k < NZ; ++k) r += Cm[i * NZ + k] * zh[k];
+                    for (int k = 0; k < NZ; ++k) r += Cm(i * NZ + k) * zh[k];
                     sg += dz[i] * r;
                 }
                 acc2(dJ, dJl, sg);

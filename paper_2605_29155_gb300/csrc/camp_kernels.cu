@@ -85,7 +85,7 @@ __global__ void __launch_bounds__(NW * 32, 8 / NW) k_mpc(const __grid_constant__
         int nh = P.horizon ? P.horizon[L.b] : P.N;
         nh = nh < 1 ? 1 : (nh > P.N ? P.N : nh);
         const int n = L.valid ? nh : 0;
-        load_constants<T, NW>(P, S, L);
+        load_constants<T, NW, GEN>(P, S, L);
 
         // per-instance state, the same in every warp
         int status = ST_RUNNING, iters = 0;
@@ -222,6 +222,12 @@ __global__ void k_lpt_order(const int* horizon, int B, int N, int* order) {
 // ------------------------------------------------------------ host side ----
 template <typename T> size_t block_smem_bytes() { return sizeof(BlockSmem<T>); }
 
+// Dynamic shared memory of a block: BlockSmem, plus the shared C of the
+// general cost behind it for those kernels.
+template <typename T> static size_t smem_for(bool gen) {
+    return sizeof(BlockSmem<T>) + (gen ? gen_smem_bytes<T>() : 0);
+}
+
 // The kernel for nw warps per block, with the diagonal cost (gen false) or the
 // general cost of Eq. (2).
 template <typename T> static const void* kernel_for(int nw, bool gen = false) {
@@ -234,7 +240,7 @@ template <typename T> cudaError_t prepare_kernels() {
     for (int g = 0; g < 2; ++g)
         for (int nw = 4; nw <= 8; nw *= 2) {
             if ((e = cudaFuncSetAttribute(kernel_for<T>(nw, g == 1), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)sizeof(BlockSmem<T>))))
+                                          (int)smem_for<T>(g == 1))))
                 return e;
         }
     return cudaSuccess;
@@ -245,7 +251,7 @@ template <typename T> int persistent_blocks_per_sm(int nw) {
     for (int g = 0; g < 2; ++g) {
         int k = 0;
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&k, kernel_for<T>(nw, g == 1), nw * 32,
-                                                          sizeof(BlockSmem<T>)) != cudaSuccess)
+                                                          smem_for<T>(g == 1)) != cudaSuccess)
             return 0;
         nb = k < nb ? k : nb;
     }
@@ -255,7 +261,7 @@ template <typename T> int persistent_blocks_per_sm(int nw) {
 template <typename T>
 static void launch_nw(int nw, int grid, cudaStream_t st, const Params<T>& P, const AdjArgs<T>& A, int mode,
                       int last) {
-    const size_t smem = sizeof(BlockSmem<T>);
+    const size_t smem = smem_for<T>(P.Cg != nullptr);
     if (P.Cg) {
         if (nw == 8) k_mpc<T, 8, true><<<grid, 256, smem, st>>>(P, A, mode, last);
         else k_mpc<T, 4, true><<<grid, 128, smem, st>>>(P, A, mode, last);
