@@ -742,12 +742,39 @@ def hover_latency(dev, flush, reps=30):
                     t[part + "_wall"].append((time.perf_counter() - w0) * 1e3)
                     t[part + "_dev"].append(e0.elapsed_time(e1))
             med = {k: statistics.median(v) for k, v in t.items()}
-            rows.append(dict(B=Bh, N=Nh, fwd_device_ms=med["fwd_dev"], bwd_device_ms=med["bwd_dev"],
-                             fwd_wall_ms=med["fwd_wall"], bwd_wall_ms=med["bwd_wall"],
-                             iters=float(s.iters.float().mean()), launch=list(sol.launch_shape(Bh, Nh))))
+            row = dict(B=Bh, N=Nh, fwd_device_ms=med["fwd_dev"], bwd_device_ms=med["bwd_dev"],
+                       fwd_wall_ms=med["fwd_wall"], bwd_wall_ms=med["bwd_wall"],
+                       iters=float(s.iters.float().mean()), launch=list(sol.launch_shape(Bh, Nh)))
             sol.close()
+            # the stage-parallel Riccati form (one instance per block; the
+            # backward re-factors, so the forward keeps no tape)
+            sc = DiffMPC(N_max=Nh, B_max=Bh, max_iter=5, tol=0.0, device=dev, exec_mode="scan",
+                         store_mode="recompute")
+            ss = sc.alloc_solution(Bh, Nh)
+            for _ in range(3):
+                sc.solve(p, ss)
+                sc.backward(p, ss, gu, out=grads)
+            torch.cuda.synchronize()
+            tf, tb = [], []
+            for _ in range(reps):
+                for part, acc in (("fwd", tf), ("bwd", tb)):
+                    flush.fill_(1.0)
+                    torch.cuda.synchronize()
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    if part == "fwd":
+                        sc.solve(p, ss)
+                    else:
+                        sc.backward(p, ss, gu, out=grads)
+                    e1.record(stream)
+                    e1.synchronize()
+                    acc.append(e0.elapsed_time(e1))
+            row.update(scan_fwd_device_ms=statistics.median(tf), scan_bwd_device_ms=statistics.median(tb))
+            sc.close()
+            rows.append(row)
     return dict(workload="hover stabilisation at random targets, exactly 5 iterations (tol 0), fwd and bwd "
-                         "per eager API call, medians of %d" % reps, rows=rows)
+                         "per eager API call, medians of %d; scan_*: exec_mode scan (stage-parallel Riccati), "
+                         "recompute" % reps, rows=rows)
 
 
 def run_kernels_only(args):

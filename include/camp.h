@@ -63,6 +63,16 @@ extern "C" {
 /* how the forward iterations are launched */
 #define MPC_EXEC_PERSISTENT 0  /* one persistent launch, work queue over instances      */
 #define MPC_EXEC_PLAIN      1  /* three launches per iteration (Sec. IV's structure)     */
+#define MPC_EXEC_SCAN       2  /* the plain form with one instance per block and the     */
+                               /* Riccati recursion of Sec. IV-2 in parallel over the   */
+                               /* stages: the associative-scan LQR of the related work  */
+                               /* in Sec. II, run to a fixed point of the box QPs' free  */
+                               /* sets (same K_t, k_t as the sequential recursion up to */
+                               /* rounding).  For small batches and long horizons.      */
+                               /* The general cost keeps the sequential Riccati phase.  */
+                               /* Needs R > 0 (the elements use R^-1).  mpc_create      */
+                               /* allocates about (N_max * 1.6k + 9k) * sizeof(dtype)   */
+                               /* bytes more per instance of B_max.                      */
 
 /* per-instance status written by mpc_solve_fwd */
 #define MPC_ST_CONVERGED  0    /* max_t |u^k_t - u^(k-1)_t|_inf < tol after a step      */
@@ -89,7 +99,7 @@ typedef struct mpc_config {
     int    n_alpha;         /* number of line-search coefficients, 1..4                */
     double alpha[4];        /* coefficients in (0, 1], default {1, .5, .25, .1}        */
     int    store_mode;      /* MPC_STORE_ALL, MPC_RECOMPUTE or MPC_STORE_AUTO          */
-    int    exec_mode;       /* MPC_EXEC_PERSISTENT or MPC_EXEC_PLAIN                   */
+    int    exec_mode;       /* MPC_EXEC_PERSISTENT, MPC_EXEC_PLAIN or MPC_EXEC_SCAN    */
     int    tpi;             /* threads per instance = warps per block: 0 (4 until      */
                             /* mpc_autotune picks), 4 or 8                              */
     int    ipb;             /* instances per block (one per lane): 0 (auto) or 1..32,  */

@@ -15,7 +15,7 @@ LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libcamp.so"
 MPC_OK, MPC_ERR_ARG, MPC_ERR_SHAPE, MPC_ERR_CUDA, MPC_ERR_TIMEOUT, MPC_ERR_STATE = 0, -1, -2, -3, -4, -5
 MPC_F32, MPC_F64 = 0, 1
 MPC_STORE_ALL, MPC_RECOMPUTE, MPC_STORE_AUTO = 0, 1, 2
-MPC_EXEC_PERSISTENT, MPC_EXEC_PLAIN = 0, 1
+MPC_EXEC_PERSISTENT, MPC_EXEC_PLAIN, MPC_EXEC_SCAN = 0, 1, 2
 MPC_ST_CONVERGED, MPC_ST_STALLED, MPC_ST_MAX_ITER, MPC_ST_NONFINITE, MPC_ST_NONPD = 0, 1, 2, 3, 4
 
 EXPORTED = ("mpc_config_default", "mpc_create", "mpc_destroy", "mpc_tape_bytes", "mpc_solve_fwd",

@@ -17,6 +17,7 @@ struct mpc_handle {
     void* ws;               // one allocation holding every scratch region
     size_t ws_bytes;
     void *stg, *cand, *kh;  // per-stage records, line-search candidates, adjoint k-hat
+    void* scan;             // stage-parallel Riccati workspace (MPC_EXEC_SCAN only)
     int* queue;             // [2] work-queue tickets (forward, backward)
     int* order;             // [B_max] longest-horizon-first order
     int tpi;                // threads per instance (warps per block): 4 or 8
@@ -74,7 +75,8 @@ static int validate_config(const mpc_config* c) {
         if (!(c->alpha[i] > 0.0 && c->alpha[i] <= 1.0)) return MPC_ERR_ARG;
     if (c->store_mode != MPC_STORE_ALL && c->store_mode != MPC_RECOMPUTE && c->store_mode != MPC_STORE_AUTO)
         return MPC_ERR_ARG;
-    if (c->exec_mode != MPC_EXEC_PERSISTENT && c->exec_mode != MPC_EXEC_PLAIN) return MPC_ERR_ARG;
+    if (c->exec_mode != MPC_EXEC_PERSISTENT && c->exec_mode != MPC_EXEC_PLAIN && c->exec_mode != MPC_EXEC_SCAN)
+        return MPC_ERR_ARG;
     if (c->tpi != 0 && c->tpi != 4 && c->tpi != 8) return MPC_ERR_ARG;
     if (c->ipb < 0 || c->ipb > (c->dtype == MPC_F64 ? 16 : 32)) return MPC_ERR_ARG;
     return MPC_OK;
@@ -95,7 +97,9 @@ extern "C" int mpc_create(const mpc_config* cfg, mpc_handle** out) {
         free(h);
         return MPC_ERR_CUDA;
     }
-    const cudaError_t pe = cfg->dtype == MPC_F64 ? prepare_kernels<double>() : prepare_kernels<float>();
+    cudaError_t pe = cfg->dtype == MPC_F64 ? prepare_kernels<double>() : prepare_kernels<float>();
+    if (pe == cudaSuccess && cfg->exec_mode == MPC_EXEC_SCAN)
+        pe = cfg->dtype == MPC_F64 ? prepare_scan<double>() : prepare_scan<float>();
     if (pe != cudaSuccess) { free(h); return MPC_ERR_CUDA; }
     if (cfg->store_mode == MPC_STORE_AUTO) {
         // the tape budget: the config's, or a quarter of the device memory free at creation
@@ -112,7 +116,8 @@ extern "C" int mpc_create(const mpc_config* cfg, mpc_handle** out) {
     const size_t bH = align256(kh_elems(S, Nw) * es);
     const size_t bQ = align256(2 * sizeof(int));
     const size_t bO = align256((size_t)cfg->B_max * sizeof(int));
-    h->ws_bytes = bS + bC + bH + bQ + bO;
+    const size_t bP = cfg->exec_mode == MPC_EXEC_SCAN ? align256(scan_ws_elems(S, Nw) * es) : 0;
+    h->ws_bytes = bS + bC + bH + bQ + bO + bP;
     if (cudaMalloc(&h->ws, h->ws_bytes) != cudaSuccess) { free(h); return MPC_ERR_CUDA; }
     // All-ones bytes are NaN in float and double: a read of scratch that no
     // phase wrote surfaces as a NaN result instead of stale data.
@@ -122,7 +127,8 @@ extern "C" int mpc_create(const mpc_config* cfg, mpc_handle** out) {
     h->cand = p; p += bC;
     h->kh = p; p += bH;
     h->queue = (int*)p; p += bQ;
-    h->order = (int*)p;
+    h->order = (int*)p; p += bO;
+    h->scan = bP ? p : nullptr;
     *out = h;
     return MPC_OK;
 }
@@ -223,6 +229,7 @@ static Params<T> make_params(const mpc_handle* h, const mpc_problem* p, const mp
     P.stg = (T*)h->stg;
     P.cand = (T*)h->cand;
     P.kh = (T*)h->kh;
+    P.scan = (T*)h->scan;
     P.queue = h->queue;
     return P;
 }

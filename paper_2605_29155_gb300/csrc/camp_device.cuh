@@ -93,6 +93,7 @@ template <typename T> struct Params {
     int *iters, *status;
     T* tape;
     T *stg, *cand, *kh;                 // global scratch, by position in the processing order
+    T* scan;                            // workspace of the stage-parallel Riccati (or NULL)
     int* queue;
 };
 

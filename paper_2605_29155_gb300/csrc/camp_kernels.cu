@@ -286,10 +286,18 @@ cudaError_t launch_forward(const Params<T>& Pin, int exec_mode, int nw, int grid
         launch_nw<T>(nw, grid, st, P, A, MODE_FWD, 0);
         return cudaGetLastError();
     }
+    // exec_mode 2: the plain form with one instance per block and, for the
+    // diagonal cost, the stage-parallel Riccati phase (camp_scan.cu)
+    const bool scan = exec_mode == 2;
+    if (scan) P.ipb = 1;
     const int blocks = (P.B + P.ipb - 1) / P.ipb;
     launch_nw<T>(nw, blocks, st, P, A, PH_INIT, 0);
     for (int it = 0; it < P.max_iter; ++it) {
-        launch_nw<T>(nw, blocks, st, P, A, PH_RIC, 0);
+        if (scan && !P.Cg) {
+            if ((e = launch_scan_ric<T>(P, st))) return e;
+        } else {
+            launch_nw<T>(nw, blocks, st, P, A, PH_RIC, 0);
+        }
         launch_nw<T>(nw, blocks, st, P, A, PH_LS, it == P.max_iter - 1);
     }
     if (P.store_all) launch_nw<T>(nw, blocks, st, P, A, PH_FRIC, 0);

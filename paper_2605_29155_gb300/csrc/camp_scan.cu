@@ -1,0 +1,1009 @@
+// camp_scan.cu -- the Riccati recursion of Sec. IV-2 in parallel over the
+// stages: the associative-scan LQR of the related work cited in Sec. II, made
+// to carry the per-stage box QP.  One block serves one instance; the other
+// phases of the plain launch form (rollout, line search, output) are the
+// k_mpc phases run with one instance per block.
+//
+// The scan.  With each stage's free set f_t and clamped offsets d_c fixed,
+// stage t of the LQR in the deviations (dx, du) -- cost 1/2 dx'Q_t dx + q_t'dx
+// + 1/2 du'R du + r_t'du, dynamics dx' = A_t dx + B_t du -- is the element
+//   A_e = A_t,  b_e = B_c d_c - B_f R_f^-1 r_f,  C_e = B_f R_f^-1 B_f',
+//   eta_e = -q_t,  J_e = Q_t
+// (Saerkkae and Garcia-Fernandez's conditional value-function elements, in the
+// convention V(x) = 1/2 x'Jx - eta'x; the last stage has A = B = 0).  Elements
+// combine associatively, an earlier stage i before a later suffix j, as
+//   M  = (I + C_i J_j)^-1
+//   A  = A_j M A_i,            b   = A_j M (b_i + C_i eta_j) + b_j,
+//   C  = A_j (M C_i) A_j' + C_j,   eta = A_i' M' (eta_j - J_j b_i) + eta_i,
+//   J  = A_i' (J_j M) A_i + J_i,
+// and the suffix S_t = e_t (x) ... (x) e_{n-1} holds the value function of
+// stage t: V_t = J(S_t), v_t = -eta(S_t).  M C_i and J_j M are symmetric
+// ((C_i^-1 + J_j)^-1 and (J_j^-1 + C_i)^-1) and are symmetrized, as are C and
+// J: in FP32 that keeps the scan's error near the sequential recursion's.
+//
+// The free sets.  The box QP makes the recursion depend on free-set decisions.
+// The scan therefore takes every stage's free set and clamped offsets as a
+// guess (the previous iteration's, all free at the first), scans, and solves
+// every stage's box QP from the scanned V_{t+1}, v_{t+1} in parallel.  Let c be
+// the latest stage whose free set or clamped offsets differ from the guess.
+// Stages after c saw exact values, so their results are final, and stage c's
+// QP saw an exact V_{c+1}, so its result is final too.  The stages c-1 .. 0
+// then run the sequential recursion on one warp: each box QP from the exact
+// V_{t+1}, then S_t = e_t (x) S_{t+1} for J and eta.  When the guess was right
+// (c < 0) the whole recursion took one scan; at worst it took a scan plus the
+// sequential recursion.  Either way every stage's QP is the one the
+// sequential recursion solves (same V_{t+1} up to rounding), so k_t, K_t and
+// the free sets are the sequential method's.  A non-positive pivot at a final
+// stage ends the solve as in the sequential recursion (status NONPD).
+//
+// The scan on SW warps: chunk w holds ch = ceil(n / SW) consecutive stages;
+// each warp folds its chunk from the back, the chunks' totals are scanned in
+// log2(SW) levels, and each stage's partial is combined with the suffix of the
+// chunks after it (only J and eta are needed there).
+#include "camp_device.cuh"
+#include "camp_internal.h"
+
+namespace camp {
+
+constexpr int SW = 8;                  // warps per block
+constexpr int M13 = NX * NX;
+// element layout: A (13 x 13), b, C (13 x 13), eta, J (13 x 13)
+constexpr int E_A = 0, E_B = M13, E_C = M13 + NX, E_N = 2 * M13 + NX, E_J = 2 * M13 + 2 * NX,
+              ELEM = 3 * M13 + 2 * NX;
+constexpr int SV = M13 + NX;           // J and eta of a stage's suffix
+// Per-stage record of the scan: QP data and results.
+//   H (4 x 4), g, q (13), r (4), k, masked factor (NL), free mask, ok,
+//   the guessed clamped offsets and free mask, the clamped sides (bit a: at the
+//   upper bound) of the last result (the next iteration's guess), diag(Q_t)
+constexpr int G_H = 0, G_G = 16, G_Q = 20, G_R = 33, G_K = 37, G_L = 41, G_M = 55, G_OK = 56, G_DC = 57,
+              G_AM = 61, G_SIDE = 62, G_QD = 64, GREC = 80;
+constexpr int FREC = NX * NZ;          // F_t = [A_t B_t], row-major 13 x 17
+// A stage's factors for the single-stage steps: A_t, G = B_f R_f^-1/2 (13 x 4),
+// b_t, eta_t = -q_t, diag Q_t
+constexpr int SF_A = 0, SF_G = M13, SF_B = M13 + 52, SF_E = M13 + 52 + NX, SF_Q = M13 + 52 + 2 * NX,
+              SF_SIZE = M13 + 52 + 3 * NX;
+
+// Elements of one position's workspace for horizons up to N.
+__host__ __device__ constexpr size_t scan_pos_elems(int N) {
+    return (size_t)N * (FREC + SV + GREC + SF_SIZE) + (size_t)2 * SW * ELEM;
+}
+size_t scan_ws_elems(size_t slots, int N) { return slots * scan_pos_elems(N); }
+
+template <typename T> struct ScanWs {
+    T *F, *Sv, *G, *SF, *Uc;
+};
+template <typename T> __device__ __forceinline__ ScanWs<T> scan_ws(T* base, int pos, int N) {
+    T* p = base + (size_t)pos * scan_pos_elems(N);
+    ScanWs<T> w;
+    w.F = p; p += (size_t)N * FREC;
+    w.Sv = p; p += (size_t)N * SV;
+    w.G = p; p += (size_t)N * GREC;
+    w.SF = p; p += (size_t)N * SF_SIZE;
+    w.Uc = p;
+    return w;
+}
+
+// ------------------------------------------------ warp-level 13 x 13 algebra
+// O = X Y (+ Ad), X or Y transposed as TX / TY, row strides ldx, ldy, ldo.
+// Lane l computes the entries l + 32 k (k < 6) side by side, so their
+// 13-term sums interleave.  O may not alias X or Y.  The caller syncs the warp.
+template <bool TX, bool TY, typename T>
+__device__ __forceinline__ void wmm(const T* X, int ldx, const T* Y, int ldy, T* O, int ldo, const T* Ad, int lane) {
+    constexpr int SL = (M13 + 31) / 32;
+    int r[SL], c[SL];
+    T s[SL];
+#pragma unroll
+    for (int k = 0; k < SL; ++k) {
+        const int e0 = lane + 32 * k, e = e0 < M13 ? e0 : M13 - 1;
+        r[k] = e / NX;
+        c[k] = e - NX * r[k];
+        s[k] = Ad ? Ad[r[k] * NX + c[k]] : T(0);
+    }
+#pragma unroll
+    for (int kk = 0; kk < NX; ++kk)
+#pragma unroll
+        for (int k = 0; k < SL; ++k)
+            s[k] += (TX ? X[kk * ldx + r[k]] : X[r[k] * ldx + kk]) * (TY ? Y[c[k] * ldy + kk] : Y[kk * ldy + c[k]]);
+#pragma unroll
+    for (int k = 0; k < SL; ++k)
+        if (lane + 32 * k < M13) O[r[k] * ldo + c[k]] = s[k];
+}
+
+// O <- (O + O') / 2 (row stride NX).
+template <typename T> __device__ __forceinline__ void wsym(T* O, int lane) {
+    for (int e = lane; e < M13; e += 32) {
+        const int r = e / NX, c = e - NX * r;
+        if (r < c) {
+            const T m = T(0.5) * (O[r * NX + c] + O[c * NX + r]);
+            O[r * NX + c] = m;
+            O[c * NX + r] = m;
+        }
+    }
+}
+
+// Gauss-Jordan with partial pivoting on G = [Z | I] (13 x 26, row stride 26):
+// leaves Z^-1 in the right half.  Returns false on a zero pivot.  `col` is 13
+// entries of scratch.  Lane l owns the entries l + 32 k (k < 11) throughout.
+template <typename T> __device__ bool wgj(T* G, T* col, int lane) {
+    constexpr int LD = 2 * NX, NE = NX * LD, SL = (NE + 31) / 32;
+    int ii[SL], cc[SL];
+#pragma unroll
+    for (int k = 0; k < SL; ++k) {
+        const int e0 = lane + 32 * k, e = e0 < NE ? e0 : NE - 1;
+        ii[k] = e / LD;
+        cc[k] = e - LD * ii[k];
+    }
+    bool ok = true;
+    for (int p = 0; p < NX; ++p) {
+        T v = (lane >= p && lane < NX) ? fabs(G[lane * LD + p]) : T(-1);
+        int idx = lane;
+#pragma unroll
+        for (int o = 16; o; o >>= 1) {
+            const T v2 = __shfl_xor_sync(FULL, v, o);
+            const int i2 = __shfl_xor_sync(FULL, idx, o);
+            if (v2 > v || (v2 == v && i2 < idx)) { v = v2; idx = i2; }
+        }
+        ok = ok && v > T(0);
+        if (idx != p && lane < LD) {
+            const T a = G[p * LD + lane];
+            G[p * LD + lane] = G[idx * LD + lane];
+            G[idx * LD + lane] = a;
+        }
+        __syncwarp();
+        if (lane < NX) col[lane] = G[lane * LD + p];
+        __syncwarp();
+        const T ip = T(1) / col[p];
+        T gp[SL], fi[SL], gv[SL];
+#pragma unroll
+        for (int k = 0; k < SL; ++k) {
+            gp[k] = G[p * LD + cc[k]] * ip;
+            fi[k] = col[ii[k]];
+            gv[k] = G[ii[k] * LD + cc[k]];
+        }
+        __syncwarp();
+#pragma unroll
+        for (int k = 0; k < SL; ++k)
+            if (lane + 32 * k < NE) G[ii[k] * LD + cc[k]] = ii[k] == p ? gp[k] : gv[k] - fi[k] * gp[k];
+        __syncwarp();
+    }
+    return ok;
+}
+
+// Work area of one warp (entries): two operand elements, the result, the
+// Gauss-Jordan block and four 13 x 13 temporaries, 13 of pivot scratch.
+constexpr int WA_I = 0, WA_J = ELEM, WA_O = 2 * ELEM, WA_G = 3 * ELEM, WA_T = 3 * ELEM + 2 * M13,
+              WA_COL = WA_T + 4 * M13, WA_SIZE = WA_COL + 16;
+// Work area of a sequential stage (inside the warp's area): S_{t+1}'s J and
+// eta on entry, S_t's on exit (the place the scan's Riccati steps use too);
+// F_t; temporaries.
+constexpr int SQ_J = WA_J + E_J, SQ_N = WA_J + E_N, SQ_F = WA_I, SQ_P = WA_T, SQ_X = WA_T + M13,
+              SQ_U = WA_T + 2 * M13, SQ_K = SQ_U + 64, SQ_H = SQ_U + 128, SQ_V = WA_O;
+
+// out = ei (x) ej (the earlier element first).  full: every part of the
+// result; else only J and eta (into out + E_J, out + E_N).  All in this warp's
+// shared memory; out may not alias the operands.  Returns false when
+// I + C_i J_j is singular.
+template <typename T>
+__device__ bool wcombine(const T* ei, const T* ej, T* out, T* wa, bool full, int lane) {
+    constexpr int LD = 2 * NX;
+    T* G = wa + WA_G;
+    T* T0 = wa + WA_T;
+    T* T1 = T0 + M13;
+    T* T2 = T1 + M13;
+    T* T3 = T2 + M13;
+    // G = [I + C_i J_j | I]
+    wmm<false, false>(ei + E_C, NX, ej + E_J, NX, G, LD, (const T*)nullptr, lane);
+    __syncwarp();
+    for (int e = lane; e < M13; e += 32) {
+        const int r = e / NX, c = e - NX * r;
+        if (r == c) G[r * LD + c] += T(1);
+        G[r * LD + NX + c] = r == c ? T(1) : T(0);
+    }
+    __syncwarp();
+    const bool ok = wgj(G, wa + WA_COL, lane);
+    const T* Mi = G + NX;                                   // M = (I + C_i J_j)^-1, row stride LD
+    // T0 = sym(J_j M)
+    wmm<false, false>(ej + E_J, NX, Mi, LD, T0, NX, (const T*)nullptr, lane);
+    __syncwarp();
+    wsym(T0, lane);
+    // eta: y = eta_j - J_j b_i (T3[0..12]), then z = M' y (T3[16..28])
+    if (lane < NX) {
+        T s = ej[E_N + lane];
+#pragma unroll
+        for (int k = 0; k < NX; ++k) s -= ej[E_J + lane * NX + k] * ei[E_B + k];
+        T3[lane] = s;
+    }
+    __syncwarp();
+    // T1 = A_i' T0
+    wmm<true, false>(ei + E_A, NX, T0, NX, T1, NX, (const T*)nullptr, lane);
+    if (lane < NX) {
+        T s = T(0);
+#pragma unroll
+        for (int k = 0; k < NX; ++k) s += Mi[k * LD + lane] * T3[k];
+        T3[16 + lane] = s;
+    }
+    __syncwarp();
+    // J = sym(T1 A_i) + J_i;  eta = A_i' z + eta_i
+    wmm<false, false>(T1, NX, ei + E_A, NX, out + E_J, NX, ei + E_J, lane);
+    if (lane < NX) {
+        T s = ei[E_N + lane];
+#pragma unroll
+        for (int k = 0; k < NX; ++k) s += ei[E_A + k * NX + lane] * T3[16 + k];
+        out[E_N + lane] = s;
+    }
+    __syncwarp();
+    wsym(out + E_J, lane);
+    if (!full) {
+        __syncwarp();
+        return ok;
+    }
+    // T0 = A_j M,  T1 = sym(M C_i)
+    wmm<false, false>(ej + E_A, NX, Mi, LD, T0, NX, (const T*)nullptr, lane);
+    wmm<false, false>(Mi, LD, ei + E_C, NX, T1, NX, (const T*)nullptr, lane);
+    // y = b_i + C_i eta_j (T3[0..12])
+    if (lane < NX) {
+        T s = ei[E_B + lane];
+#pragma unroll
+        for (int k = 0; k < NX; ++k) s += ei[E_C + lane * NX + k] * ej[E_N + k];
+        T3[lane] = s;
+    }
+    __syncwarp();
+    wsym(T1, lane);
+    // A = T0 A_i;  b = T0 y + b_j
+    wmm<false, false>(T0, NX, ei + E_A, NX, out + E_A, NX, (const T*)nullptr, lane);
+    if (lane < NX) {
+        T s = ej[E_B + lane];
+#pragma unroll
+        for (int k = 0; k < NX; ++k) s += T0[lane * NX + k] * T3[k];
+        out[E_B + lane] = s;
+    }
+    __syncwarp();
+    // C = sym(A_j T1 A_j') + C_j
+    wmm<false, false>(ej + E_A, NX, T1, NX, T2, NX, (const T*)nullptr, lane);
+    __syncwarp();
+    wmm<false, true>(T2, NX, ej + E_A, NX, out + E_C, NX, ej + E_C, lane);
+    __syncwarp();
+    wsym(out + E_C, lane);
+    __syncwarp();
+    return ok;
+}
+
+// Copies of ELEM entries (or a part) between global and shared memory by a warp.
+template <typename T> __device__ __forceinline__ void wcopy(T* dst, const T* src, int n, int lane) {
+    for (int e = lane; e < n; e += 32) dst[e] = src[e];
+}
+
+// ------------------------------------------------------------ the passes ---
+// Shared state of a block.
+template <typename T> struct ScanShared {
+    T R[NU], uref[NU], ulo[NU], uhi[NU];
+    int cw[2];          // per QP warp: the latest changed stage
+    int fail;
+};
+
+// ------------------------------------------- single-stage (rank-4) steps --
+// A single stage's element has C_t = G G' with G = B_f R_f^-1/2 (13 x 4, zero
+// columns for clamped controls), so combining it in front of a suffix needs
+// only the 4 x 4 matrix S = I + G'J G (Woodbury):
+//   M = (I + G G'J)^-1 = I - G S^-1 G'J,   J M = J - (J G) S^-1 (J G)',
+//   M C_t = G S^-1 G',   M' y = y - J G S^-1 G'y.
+// Stage t's factors in a warp's shared memory:
+// temporaries of a step
+constexpr int ST_JG = 0, ST_S = 52, ST_Y = 68, ST_Z = 84, ST_W4 = 136, ST_ZV = 144, ST_W = 160, ST_T1 = ST_W + M13,
+              ST_AG = ST_T1 + M13, ST_X = ST_AG + 52, ST_AM = ST_X + 52, ST_BN = ST_AM + M13, ST_SIZE = ST_BN + 16;
+
+// Every stage's factors for the guessed free sets and clamped offsets into
+// SF (one job per stage and row).
+template <typename T> __device__ void stage_factors_all(const ScanWs<T>& W, const ScanShared<T>& sh, int n) {
+    for (int job = threadIdx.x; job < n * NX; job += blockDim.x) {
+        const int t = job / NX, i = job - NX * t;
+        const T* F = W.F + (size_t)t * FREC;
+        const T* G = W.G + (size_t)t * GREC;
+        T* sf = W.SF + (size_t)t * SF_SIZE;
+        const int fm = (int)G[G_AM];
+#pragma unroll
+        for (int k = 0; k < NX; ++k) sf[SF_A + i * NX + k] = F[i * NZ + k];
+        T bi = T(0);
+#pragma unroll
+        for (int a = 0; a < NU; ++a) {
+            const T Bia = F[i * NZ + NX + a];
+            const bool fr = (fm >> a) & 1;
+            sf[SF_G + i * NU + a] = fr ? Bia / sqrt(sh.R[a]) : T(0);
+            bi += fr ? -(Bia / sh.R[a]) * G[G_R + a] : Bia * G[G_DC + a];
+        }
+        sf[SF_B + i] = bi;
+        sf[SF_E + i] = -G[G_Q + i];
+        sf[SF_Q + i] = G[G_QD + i];
+    }
+}
+
+// Asynchronous copy of n entries by a warp (cp.async; committed as one group).
+template <typename T> __device__ __forceinline__ void wprefetch(T* dst, const T* src, int n, int lane) {
+    for (int e = lane; e < n; e += 32) cp_async(dst + e, src + e);
+    cp_async_commit();
+}
+__device__ __forceinline__ void wwait() {
+    cp_async_wait_all();
+    __syncwarp();
+}
+
+// The common part of a step in front of the suffix (J, eta): J G, S = I + G'J G
+// (factored in every lane), y = eta - J b, Z = S^-1 (J G)', w = S^-1 G'y,
+// W = J - (J G) Z, z = y - (J G) w.
+template <typename T>
+__device__ void lr_common(const T* J, const T* eta, const T* sf, T* tp, int lane, T (&Ls)[NL]) {
+    for (int e = lane; e < NX * NU; e += 32) {
+        const int i = e / NU, a = e - NU * i;
+        T s = T(0);
+#pragma unroll
+        for (int k = 0; k < NX; ++k) s += J[i * NX + k] * sf[SF_G + k * NU + a];
+        tp[ST_JG + e] = s;
+    }
+    __syncwarp();
+    if (lane < 16) {
+        const int a = lane >> 2, c = lane & 3;
+        T s = a == c ? T(1) : T(0);
+#pragma unroll
+        for (int i = 0; i < NX; ++i) s += sf[SF_G + i * NU + a] * tp[ST_JG + i * NU + c];
+        tp[ST_S + lane] = s;
+    } else if (lane < 16 + NX) {
+        const int i = lane - 16;
+        T s = eta[i];
+#pragma unroll
+        for (int k = 0; k < NX; ++k) s -= J[i * NX + k] * sf[SF_B + k];
+        tp[ST_Y + i] = s;
+    }
+    __syncwarp();
+    T S[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) S[a][c] = tp[ST_S + a * 4 + c];
+    chol_masked(S, 15, Ls);                             // S = I + G'JG is positive definite
+    if (lane < NX) {
+        T rhs[4], y[4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) rhs[a] = tp[ST_JG + lane * NU + a];
+        chol_solve4(Ls, rhs, y);
+#pragma unroll
+        for (int a = 0; a < 4; ++a) tp[ST_Z + a * NX + lane] = y[a];
+    } else if (lane == NX) {
+        T rhs[4], y[4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+            T s = T(0);
+#pragma unroll
+            for (int i = 0; i < NX; ++i) s += sf[SF_G + i * NU + a] * tp[ST_Y + i];
+            rhs[a] = s;
+        }
+        chol_solve4(Ls, rhs, y);
+#pragma unroll
+        for (int a = 0; a < 4; ++a) tp[ST_W4 + a] = y[a];
+    }
+    __syncwarp();
+    for (int e = lane; e < M13; e += 32) {
+        const int i = e / NX, k = e - NX * i;
+        T s = J[e];
+#pragma unroll
+        for (int a = 0; a < NU; ++a) s -= tp[ST_JG + i * NU + a] * tp[ST_Z + a * NX + k];
+        tp[ST_W + e] = s;
+    }
+    if (lane < NX) {
+        T s = tp[ST_Y + lane];
+#pragma unroll
+        for (int a = 0; a < NU; ++a) s -= tp[ST_JG + lane * NU + a] * tp[ST_W4 + a];
+        tp[ST_ZV + lane] = s;
+    }
+    __syncwarp();
+}
+
+// J = A'W A + Q_t (symmetrized), eta = A'z + eta_t from lr_common's W, z.
+template <typename T> __device__ void lr_half_tail(T* J, T* eta, const T* sf, T* tp, int lane) {
+    wmm<false, false>(tp + ST_W, NX, sf + SF_A, NX, tp + ST_T1, NX, (const T*)nullptr, lane);
+    __syncwarp();
+    wmm<true, false>(sf + SF_A, NX, tp + ST_T1, NX, J, NX, (const T*)nullptr, lane);
+    if (lane < NX) {
+        T s = sf[SF_E + lane];
+#pragma unroll
+        for (int k = 0; k < NX; ++k) s += sf[SF_A + k * NX + lane] * tp[ST_ZV + k];
+        eta[lane] = s;
+    }
+    __syncwarp();
+    if (lane < NX) J[lane * NX + lane] += sf[SF_Q + lane];
+    __syncwarp();
+    wsym(J, lane);
+    __syncwarp();
+}
+
+// (J, eta) <- e_t (x) (J, eta): the Riccati step of stage t for its free set.
+template <typename T> __device__ void lr_half(T* J, T* eta, const T* sf, T* tp, int lane) {
+    T Ls[NL];
+    lr_common(J, eta, sf, tp, lane, Ls);
+    lr_half_tail(J, eta, sf, tp, lane);
+}
+
+// R <- e_t (x) R for a whole element R (A, b, C, eta, J) in shared memory:
+//   A_R M = A_R - (A_R G) Z,  A = (A_R M) A_t,  b = (A_R M)(b_t + G G'eta_R) + b_R,
+//   C = (A_R G) S^-1 (A_R G)' + C_R,  J, eta as in lr_half.
+template <typename T> __device__ void lr_full(T* Rl, const T* sf, T* tp, int lane) {
+    T* RA = Rl + E_A;
+    T* Rb = Rl + E_B;
+    T* RC = Rl + E_C;
+    T Ls[NL];
+    lr_common(Rl + E_J, Rl + E_N, sf, tp, lane, Ls);
+    // A_R G (13 x 4)
+    for (int e = lane; e < NX * NU; e += 32) {
+        const int i = e / NU, a = e - NU * i;
+        T s = T(0);
+#pragma unroll
+        for (int k = 0; k < NX; ++k) s += RA[i * NX + k] * sf[SF_G + k * NU + a];
+        tp[ST_AG + e] = s;
+    }
+    // G'eta_R (4) into BN[12..15]
+    if (lane >= 16 && lane < 20) {
+        const int a = lane - 16;
+        T s = T(0);
+#pragma unroll
+        for (int i = 0; i < NX; ++i) s += sf[SF_G + i * NU + a] * Rl[E_N + i];
+        tp[ST_BN + 12 + a] = s;
+    }
+    __syncwarp();
+    // X = S^-1 (A_R G)' (4 x 13);  A_R M
+    if (lane < NX) {
+        T rhs[4], y[4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) rhs[a] = tp[ST_AG + lane * NU + a];
+        chol_solve4(Ls, rhs, y);
+#pragma unroll
+        for (int a = 0; a < 4; ++a) tp[ST_X + a * NX + lane] = y[a];
+    }
+    for (int e = lane; e < M13; e += 32) {
+        const int i = e / NX, k = e - NX * i;
+        T s = RA[e];
+#pragma unroll
+        for (int a = 0; a < NU; ++a) s -= tp[ST_AG + i * NU + a] * tp[ST_Z + a * NX + k];
+        tp[ST_AM + e] = s;
+    }
+    __syncwarp();
+    // b_t + G G'eta_R into Y (y is no longer needed)
+    if (lane < NX) {
+        T s = sf[SF_B + lane];
+#pragma unroll
+        for (int a = 0; a < NU; ++a) s += sf[SF_G + lane * NU + a] * tp[ST_BN + 12 + a];
+        tp[ST_Y + lane] = s;
+    }
+    __syncwarp();
+    if (lane < NX) {
+        T s = Rb[lane];
+#pragma unroll
+        for (int k = 0; k < NX; ++k) s += tp[ST_AM + lane * NX + k] * tp[ST_Y + k];
+        tp[ST_BN + lane] = s;
+    }
+    // C = C_R + (A_R G) X
+    for (int e = lane; e < M13; e += 32) {
+        const int i = e / NX, k = e - NX * i;
+        T s = RC[e];
+#pragma unroll
+        for (int a = 0; a < NU; ++a) s += tp[ST_AG + i * NU + a] * tp[ST_X + a * NX + k];
+        RC[e] = s;
+    }
+    __syncwarp();
+    wsym(RC, lane);
+    wmm<false, false>(tp + ST_AM, NX, sf + SF_A, NX, RA, NX, (const T*)nullptr, lane);
+    if (lane < NX) Rb[lane] = tp[ST_BN + lane];
+    __syncwarp();
+    lr_half_tail(Rl + E_J, Rl + E_N, sf, tp, lane);
+}
+
+// The suffixes S_t of every stage t < n (J and eta into Sv) for the guessed
+// free sets.  Barriers inside: every thread of the block calls it.  Sets *bad
+// when some I + C J of the chunk-level combines was singular.
+template <typename T>
+__device__ void scan_suffixes(const ScanWs<T>& W, const ScanShared<T>& sh, T* wa, int n, int* bad) {
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int ch = (n + SW - 1) / SW;
+    const int last = (n - 1) / ch;
+    const int t0 = w * ch, t1 = min(n, t0 + ch) - 1;
+    T* tp = wa + WA_O;
+    bool ok = true;
+    // A: each chunk's total e_t0 (x) ... (x) e_t1, folded from the back with
+    // the single-stage steps
+    if (w <= last) {
+        T* Rl = wa + WA_J;
+        T* sb[2] = {wa + WA_I, wa + WA_I + 264};     // double-buffered stage factors
+        wprefetch(sb[0], W.SF + (size_t)t1 * SF_SIZE, SF_SIZE, lane);
+        wwait();
+        if (t1 - 1 >= t0) wprefetch(sb[1], W.SF + (size_t)(t1 - 1) * SF_SIZE, SF_SIZE, lane);
+        const T* sf = sb[0];
+        for (int e = lane; e < M13; e += 32) {
+            const int i = e / NX, k = e - NX * i;
+            T c = T(0);
+#pragma unroll
+            for (int a = 0; a < NU; ++a) c += sf[SF_G + i * NU + a] * sf[SF_G + k * NU + a];
+            Rl[E_A + e] = sf[SF_A + e];
+            Rl[E_C + e] = c;
+            Rl[E_J + e] = i == k ? sf[SF_Q + i] : T(0);
+        }
+        if (lane < NX) {
+            Rl[E_B + lane] = sf[SF_B + lane];
+            Rl[E_N + lane] = sf[SF_E + lane];
+        }
+        __syncwarp();
+        for (int t = t1 - 1, k = 1; t >= t0; --t, k ^= 1) {
+            wwait();
+            if (t - 1 >= t0) wprefetch(sb[k ^ 1], W.SF + (size_t)(t - 1) * SF_SIZE, SF_SIZE, lane);
+            lr_full(Rl, sb[k], tp, lane);
+        }
+        wcopy(W.Uc + (size_t)w * ELEM, Rl, ELEM, lane);
+    }
+    __syncthreads();
+    // B: suffix scan of the chunk totals over the chunks (log2 levels)
+    int cur = 0;
+    for (int d = 1; d <= last; d <<= 1) {
+        if (w <= last) {
+            T* dst = W.Uc + ((size_t)(cur ^ 1) * SW + w) * ELEM;
+            const T* src = W.Uc + ((size_t)cur * SW + w) * ELEM;
+            if (w + d <= last) {
+                wcopy(wa + WA_I, src, ELEM, lane);
+                wcopy(wa + WA_J, W.Uc + ((size_t)cur * SW + w + d) * ELEM, ELEM, lane);
+                __syncwarp();
+                ok = wcombine(wa + WA_I, wa + WA_J, wa + WA_O, wa, true, lane) && ok;
+                wcopy(dst, wa + WA_O, ELEM, lane);
+            } else {
+                wcopy(dst, src, ELEM, lane);
+            }
+        }
+        __syncthreads();
+        cur ^= 1;
+    }
+    // C: the Riccati steps through each chunk from the suffix of the chunks
+    // after it (zero after the last)
+    if (w <= last) {
+        T* J = wa + SQ_J;
+        T* eta = wa + SQ_N;
+        const T* U = W.Uc + ((size_t)cur * SW + w + 1) * ELEM;
+        for (int e = lane; e < SV; e += 32) {
+            const bool e_j = e < M13;
+            const T v = w < last ? (e_j ? U[E_J + e] : U[E_N + e - M13]) : T(0);
+            if (e_j) J[e] = v;
+            else eta[e - M13] = v;
+        }
+        __syncwarp();
+        T* sb[2] = {wa + WA_I, wa + WA_I + 264};
+        wprefetch(sb[0], W.SF + (size_t)t1 * SF_SIZE, SF_SIZE, lane);
+        for (int t = t1, k = 0; t >= t0; --t, k ^= 1) {
+            wwait();
+            if (t - 1 >= t0) wprefetch(sb[k ^ 1], W.SF + (size_t)(t - 1) * SF_SIZE, SF_SIZE, lane);
+            lr_half(J, eta, sb[k], tp, lane);
+            T* sv = W.Sv + (size_t)t * SV;
+            wcopy(sv, J, M13, lane);
+            wcopy(sv + M13, eta, NX, lane);
+        }
+    }
+    if (!ok && lane == 0) atomicOr(bad, 1);
+    __syncthreads();
+}
+
+// Column a of stage t's QP data: H[a'][a] = R_a d_a'a + B_a'' V_{t+1} B_a for
+// a' <= a, and g_a = r_a + B_a' v_{t+1} (V_n = 0, v_n = 0).
+template <typename T>
+__device__ __forceinline__ void qp_column(const ScanWs<T>& W, const ScanShared<T>& sh, int t, int a, int n) {
+    const T* F = W.F + (size_t)t * FREC;
+    T* G = W.G + (size_t)t * GREC;
+    T vb[NX];
+    T ga = G[G_R + a];
+    if (t + 1 < n) {
+        const T* V = W.Sv + (size_t)(t + 1) * SV;
+#pragma unroll
+        for (int i = 0; i < NX; ++i) {
+            T s = T(0);
+#pragma unroll
+            for (int k = 0; k < NX; ++k) s += V[i * NX + k] * F[k * NZ + NX + a];
+            vb[i] = s;
+        }
+#pragma unroll
+        for (int i = 0; i < NX; ++i) ga -= F[i * NZ + NX + a] * V[M13 + i];     // v = -eta
+    } else {
+#pragma unroll
+        for (int i = 0; i < NX; ++i) vb[i] = T(0);
+    }
+    for (int a2 = 0; a2 <= a; ++a2) {
+        T s = a2 == a ? sh.R[a] : T(0);
+#pragma unroll
+        for (int i = 0; i < NX; ++i) s += F[i * NZ + NX + a2] * vb[i];
+        G[G_H + a2 * NU + a] = s;
+    }
+    G[G_G + a] = ga;
+}
+
+// The QP data of every stage t < n (one job per stage and control column).
+template <typename T> __device__ void qp_inputs(const ScanWs<T>& W, const ScanShared<T>& sh, int n) {
+    for (int job = threadIdx.x; job < n * NU; job += blockDim.x) qp_column(W, sh, job / NU, job % NU, n);
+}
+
+// The box QP of stage t for the lanes with `on` (warp-collective): solves from
+// H (upper triangle, Hs[a * 4 + c] for a <= c), g and the bounds, writes k,
+// the factor, the free mask, ok, the clamped sides and the new guess to the
+// stage's record, returns them in d, Lf, mask, and returns whether the free
+// set or the clamped offsets differ from the old guess.
+template <typename T>
+__device__ bool qp_stage(const Params<T>& P, const ScanWs<T>& W, const ScanShared<T>& sh, int pos, int t, bool on,
+                         const T* Hs, const T* gs, T (&d)[4], T (&Lf)[NL], int& mask, bool& ok) {
+    const int tt = on ? t : 0;
+    T* G = W.G + (size_t)tt * GREC;
+    const T* sr = P.stg + srow(P, pos, tt, 0);
+    T H[4][4], g[4], lo[4], hi[4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+#pragma unroll
+        for (int c = 0; c < 4; ++c) H[a][c] = on ? (a <= c ? Hs[a * NU + c] : Hs[c * NU + a]) : T(a == c);
+        g[a] = on ? gs[a] : T(0);
+        const T ub = on ? sr[(R_U + a) * GW] : T(0);
+        lo[a] = sh.ulo[a] - ub;
+        hi[a] = sh.uhi[a] - ub;
+    }
+    mask = 0;
+    ok = box_qp(on, H, g, lo, hi, d, Lf, mask);
+    if (!on) return false;
+    const int am = (int)G[G_AM];
+    bool changed = mask != am;
+    int side = 0;
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+        const bool cl = !((mask >> a) & 1);
+        changed = changed || (cl && d[a] != G[G_DC + a]);
+        side |= (cl && d[a] == hi[a]) ? (1 << a) : 0;
+    }
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+        G[G_K + a] = d[a];
+        G[G_DC + a] = ((mask >> a) & 1) ? T(0) : d[a];
+    }
+#pragma unroll
+    for (int i = 0; i < NL; ++i) G[G_L + i] = Lf[i];
+    G[G_M] = (T)mask;
+    G[G_AM] = (T)mask;
+    G[G_SIDE] = (T)side;
+    G[G_OK] = ok ? T(1) : T(0);
+    return changed;
+}
+
+// The box QPs of every stage t < n on warps 0 and 1 (lane = stage) against
+// the guesses; records in sh.cw the latest stage whose result changed.
+template <typename T>
+__device__ void stage_qps(const Params<T>& P, const ScanWs<T>& W, ScanShared<T>& sh, int pos, int n) {
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (w >= 2) return;
+    int latest = -1;
+    if (w * 32 < n) {
+        const int t = w * 32 + lane;
+        const T* G = W.G + (size_t)(t < n ? t : 0) * GREC;
+        T d[4], Lf[NL];
+        int mask;
+        bool ok;
+        latest = qp_stage(P, W, sh, pos, t, t < n, G + G_H, G + G_G, d, Lf, mask, ok) ? t : -1;
+    }
+    latest = __reduce_max_sync(FULL, latest + 1) - 1;
+    if (lane == 0) sh.cw[w] = latest;
+}
+
+
+// One stage of the sequential recursion (Tassa's value update, as the oracle
+// and the sequential phase take it), on one warp:
+//   Q_xx = Q_t + A'V A,  Q_ux = B'V A,  Q_uu = R + B'V B,  q = q_t + A'v,
+//   q_u = r_t + B'v  (V, v of stage t+1, in shared memory),
+//   the box QP (unless `have_qp`: the stored result is final),
+//   K = -Q_uu,ff^-1 Q_ux,f (zero rows for clamped controls),
+//   V_t = Q_xx + Q_ux'K (symmetrized),  v_t = q + K'(Q_uu k + q_u) + Q_ux'k,
+// V_t and eta_t = -v_t into shared memory and Sv[t].  Returns false on a
+// non-positive pivot.
+template <typename T>
+__device__ bool seq_stage(const Params<T>& P, const ScanWs<T>& W, const ScanShared<T>& sh, T* wa, int pos, int t,
+                          int n, bool have_qp, int lane) {
+    T* Js = wa + SQ_J;
+    T* es = wa + SQ_N;
+    T* Fs = wa + SQ_F;
+    T* P1 = wa + SQ_P;
+    T* Qx = wa + SQ_X;
+    T* Qu = wa + SQ_U;
+    T* Kt = wa + SQ_K;
+    T* Hg = wa + SQ_H;                  // H (16, upper used), g (4)
+    T* Vn = wa + SQ_V;
+    const T* G = W.G + (size_t)t * GREC;
+    wcopy(Fs, W.F + (size_t)t * FREC, FREC, lane);
+    __syncwarp();
+    T d[4], Lf[NL];
+    int mask;
+    bool ok;
+    if (have_qp) {
+        if (lane < 16) Hg[lane] = G[G_H + lane];
+        else if (lane < 20) Hg[lane] = G[G_G + lane - 16];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) d[a] = G[G_K + a];
+#pragma unroll
+        for (int i = 0; i < NL; ++i) Lf[i] = G[G_L + i];
+        mask = (int)G[G_M];
+        ok = G[G_OK] != T(0);
+        __syncwarp();
+    } else {
+        // V B into P1 (13 x 4), then H and g
+        for (int e = lane; e < NX * NU; e += 32) {
+            const int i = e / NU, a = e - NU * i;
+            T s = T(0);
+#pragma unroll
+            for (int k = 0; k < NX; ++k) s += Js[i * NX + k] * Fs[k * NZ + NX + a];
+            P1[e] = s;
+        }
+        __syncwarp();
+        if (lane < 16) {
+            const int a2 = lane >> 2, a = lane & 3;
+            T s = a2 == a ? sh.R[a] : T(0);
+#pragma unroll
+            for (int i = 0; i < NX; ++i) s += Fs[i * NZ + NX + a2] * P1[i * NU + a];
+            Hg[lane] = s;
+        } else if (lane < 20) {
+            const int a = lane - 16;
+            T s = G[G_R + a];
+#pragma unroll
+            for (int i = 0; i < NX; ++i) s -= Fs[i * NZ + NX + a] * es[i];
+            Hg[lane] = s;
+        }
+        __syncwarp();
+        qp_stage(P, W, sh, pos, t, lane == 0, Hg, Hg + 16, d, Lf, mask, ok);
+        mask = __shfl_sync(FULL, mask, 0);
+        ok = __shfl_sync(FULL, ok ? 1 : 0, 0) != 0;
+#pragma unroll
+        for (int a = 0; a < 4; ++a) d[a] = __shfl_sync(FULL, d[a], 0);
+#pragma unroll
+        for (int i = 0; i < NL; ++i) Lf[i] = __shfl_sync(FULL, Lf[i], 0);
+    }
+    // P1 = V A;  Qx = A' P1 + Q_t;  Qu = B' P1 (4 x 13)
+    wmm<false, false>(Js, NX, Fs, NZ, P1, NX, (const T*)nullptr, lane);
+    __syncwarp();
+    wmm<true, false>(Fs, NZ, P1, NX, Qx, NX, (const T*)nullptr, lane);
+    for (int e = lane; e < NU * NX; e += 32) {
+        const int a = e / NX, c = e - NX * a;
+        T s = T(0);
+#pragma unroll
+        for (int i = 0; i < NX; ++i) s += Fs[i * NZ + NX + a] * P1[i * NX + c];
+        Qu[e] = s;
+    }
+    __syncwarp();
+    if (lane < NX) {
+        Qx[lane * NX + lane] += G[G_QD + lane];
+        T rhs[4], y[4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) rhs[a] = ((mask >> a) & 1) ? Qu[a * NX + lane] : T(0);
+        chol_solve4(Lf, rhs, y);
+#pragma unroll
+        for (int a = 0; a < 4; ++a) Kt[a * NX + lane] = ((mask >> a) & 1) ? -y[a] : T(0);
+    }
+    __syncwarp();
+    // V_t = Qx + Qu' K
+    for (int e = lane; e < M13; e += 32) {
+        const int r = e / NX, c = e - NX * r;
+        T s = Qx[e];
+#pragma unroll
+        for (int a = 0; a < NU; ++a) s += Qu[a * NX + r] * Kt[a * NX + c];
+        Vn[e] = s;
+    }
+    // v_t = q_t + A'v + K'(H k + g) + Qu' k  (v = -eta)
+    T vt = T(0);
+    if (lane < NX) {
+        T w[4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+            T s = Hg[16 + a];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) s += (a <= c ? Hg[a * NU + c] : Hg[c * NU + a]) * d[c];
+            w[a] = s;
+        }
+        T s = G[G_Q + lane];
+#pragma unroll
+        for (int k = 0; k < NX; ++k) s -= Fs[k * NZ + lane] * es[k];
+#pragma unroll
+        for (int a = 0; a < NU; ++a) s += Kt[a * NX + lane] * w[a] + Qu[a * NX + lane] * d[a];
+        vt = s;
+    }
+    __syncwarp();
+    wsym(Vn, lane);
+    __syncwarp();
+    T* so = W.Sv + (size_t)t * SV;
+    for (int e = lane; e < M13; e += 32) {
+        Js[e] = Vn[e];
+        so[e] = Vn[e];
+    }
+    if (lane < NX) {
+        es[lane] = -vt;
+        so[M13 + lane] = -vt;
+    }
+    __syncwarp();
+    return ok;
+}
+
+// K_t = -Q_uu,ff^-1 Q_ux,f (zero rows for clamped controls), Q_ux = B_t'
+// V_{t+1} A_t, and k_t into the stage records (one job per stage and state
+// column).
+template <typename T>
+__device__ void write_gains(const Params<T>& P, const ScanWs<T>& W, int pos, int n) {
+    for (int job = threadIdx.x; job < n * NX; job += blockDim.x) {
+        const int t = job / NX, c = job - NX * t;
+        const T* F = W.F + (size_t)t * FREC;
+        const T* G = W.G + (size_t)t * GREC;
+        T* grow = P.stg + srow(P, pos, t, 0);
+        T qc[NU] = {T(0), T(0), T(0), T(0)};
+        if (t + 1 < n) {
+            const T* V = W.Sv + (size_t)(t + 1) * SV;
+            T va[NX];
+#pragma unroll
+            for (int i = 0; i < NX; ++i) {
+                T s = T(0);
+#pragma unroll
+                for (int k = 0; k < NX; ++k) s += V[i * NX + k] * F[k * NZ + c];
+                va[i] = s;
+            }
+#pragma unroll
+            for (int a = 0; a < NU; ++a) {
+                T s = T(0);
+#pragma unroll
+                for (int i = 0; i < NX; ++i) s += F[i * NZ + NX + a] * va[i];
+                qc[a] = s;
+            }
+        }
+        const int mask = (int)G[G_M];
+        T Lf[NL], rhs[4], y[4];
+#pragma unroll
+        for (int i = 0; i < NL; ++i) Lf[i] = G[G_L + i];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) rhs[a] = ((mask >> a) & 1) ? qc[a] : T(0);
+        chol_solve4(Lf, rhs, y);
+#pragma unroll
+        for (int a = 0; a < NU; ++a) grow[(R_K + a * NX + c) * GW] = ((mask >> a) & 1) ? -y[a] : T(0);
+        if (c == 0) {
+#pragma unroll
+            for (int a = 0; a < NU; ++a) grow[(R_KK + a) * GW] = G[G_K + a];
+        }
+    }
+}
+
+// ---------------------------------------------------------------- kernel --
+// The Riccati phase of one iteration (A2 + A3) for the instance at position
+// blockIdx.x, in the plain launch form with one instance per block: reads the
+// nominal and cost rows from the stage records, writes K_t, k_t there, counts
+// the iteration and sets NONPD on a non-positive pivot -- what k_mpc's Riccati
+// phase does for an instance, with the stages in parallel.
+template <typename T>
+__global__ void __launch_bounds__(SW * 32, 1) k_scan_ric(const __grid_constant__ Params<T> P) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* wa = reinterpret_cast<T*>(smem_raw) + (size_t)(threadIdx.x >> 5) * WA_SIZE;
+    __shared__ ScanShared<T> sh;
+    __shared__ int s_bad;
+    const int pos = blockIdx.x;
+    if (pos >= P.B) return;
+    const int b = P.order ? P.order[pos] : pos;
+    int n = P.horizon ? P.horizon[b] : P.N;
+    n = n < 1 ? 1 : (n > P.N ? P.N : n);
+    if (P.status[b] != ST_RUNNING) return;                 // the same in every thread
+    const int iters = P.iters[b] + 1;
+    const ScanWs<T> W = scan_ws(P.scan, pos, P.N_ws);
+    const int tid = threadIdx.x;
+    if (tid < 4 * NU) {
+        const int q = tid >> 2, a = tid & 3;
+        const T* src = q == 0 ? P.R : (q == 1 ? P.uref : (q == 2 ? P.ulo : P.uhi));
+        T* dst = q == 0 ? sh.R : (q == 1 ? sh.uref : (q == 2 ? sh.ulo : sh.uhi));
+        dst[a] = src[(size_t)b * NU + a];
+    }
+    if (tid == 0) { s_bad = 0; sh.fail = 0; }
+    __syncthreads();
+    // the cost expansion at the nominal (x as hi + lo) and the first guesses
+    for (int t = tid; t < n; t += blockDim.x) {
+        const T* sr = P.stg + srow(P, pos, t, 0);
+        T* G = W.G + (size_t)t * GREC;
+#pragma unroll
+        for (int i = 0; i < NX; ++i) {
+            const T q = sr[(R_Q + i) * GW];
+            G[G_QD + i] = q;
+            G[G_Q + i] = q * ((sr[(R_X + i) * GW] - sr[(R_XR + i) * GW]) + sr[(R_XL + i) * GW]);
+        }
+        const int pm = iters > 1 ? (int)G[G_M] : 15;
+        const int ps = iters > 1 ? (int)G[G_SIDE] : 0;
+#pragma unroll
+        for (int a = 0; a < NU; ++a) {
+            const T u = sr[(R_U + a) * GW];
+            G[G_R + a] = sh.R[a] * (u - sh.uref[a]);
+            const bool cl = !((pm >> a) & 1);
+            G[G_DC + a] = cl ? (((ps >> a) & 1) ? sh.uhi[a] - u : sh.ulo[a] - u) : T(0);
+        }
+        G[G_AM] = (T)pm;
+        if (t == n - 1) {
+            for (int e = 0; e < FREC; ++e) W.F[(size_t)t * FREC + e] = T(0);
+        }
+    }
+    // A2: F_t = [A_t B_t] at the nominal x (hi part), t < n - 1: the computed
+    // columns by forward tangents, the constant ones (position, velocity) exact
+    const T hv = hv_coef(P.mdl);
+    for (int job = tid; job < (n - 1) * (NGC + 1); job += blockDim.x) {
+        const int t = job / (NGC + 1), jj = job - (NGC + 1) * t;
+        T* F = W.F + (size_t)t * FREC;
+        if (jj == NGC) {
+#pragma unroll
+            for (int i = 0; i < NX; ++i)
+#pragma unroll
+                for (int j = 0; j < 3; ++j) {
+                    F[i * NZ + j] = i == j ? T(1) : T(0);
+                    F[i * NZ + 7 + j] = (i == 7 + j) ? T(1) : (i == j ? hv : T(0));
+                }
+            continue;
+        }
+        const T* sr = P.stg + srow(P, pos, t, 0);
+        T x[NX], u[NU], col[1][NX];
+#pragma unroll
+        for (int i = 0; i < NX; ++i) x[i] = sr[(R_X + i) * GW];
+#pragma unroll
+        for (int a = 0; a < NU; ++a) u[a] = sr[(R_U + a) * GW];
+        const int jc[1] = {gcol(jj)};
+        tangent_columns<T, 1>(P.mdl, x, u, jc, col);
+#pragma unroll
+        for (int i = 0; i < NX; ++i) F[i * NZ + jc[0]] = col[0][i];
+    }
+    __syncthreads();
+    // A3: one scan pass with the guessed free sets, then the stages the guess
+    // got wrong by the sequential recursion
+    stage_factors_all(W, sh, n);
+    __syncthreads();
+    scan_suffixes(W, sh, wa, n, &s_bad);
+    qp_inputs(W, sh, n);
+    __syncthreads();
+    stage_qps(P, W, sh, pos, n);
+    __syncthreads();
+    const int c = max(sh.cw[0], sh.cw[1]);
+    // stages after c saw exact values and stage c an exact V_{c+1}: their QPs
+    // are final, and a failed one at them ends the solve
+    if (tid < n && tid >= c && W.G[(size_t)tid * GREC + G_OK] == T(0)) atomicOr(&sh.fail, 1);
+    __syncthreads();
+    // (I + C J is singular only for non-finite data: C and J are positive
+    // semidefinite, so its eigenvalues are at least 1)
+    bool fail = sh.fail != 0 || s_bad != 0;
+    if (!fail && c >= 0) {
+        if ((tid >> 5) == 0) {
+            const int lane = tid & 31;
+            // S_{c+1}'s J and eta (zero past the last stage) into the work area
+            for (int e = lane; e < SV; e += 32) {
+                const T v = c + 1 < n ? W.Sv[(size_t)(c + 1) * SV + e] : T(0);
+                wa[e < M13 ? SQ_J + e : SQ_N + e - M13] = v;
+            }
+            __syncwarp();
+            bool ok = true;
+            for (int t = c; t >= 0 && ok; --t) ok = seq_stage(P, W, sh, wa, pos, t, n, t == c, lane);
+            if (!ok && tid == 0) sh.fail = 1;
+        }
+        __syncthreads();
+        fail = sh.fail != 0;
+    }
+    if (!fail) write_gains(P, W, pos, n);
+    if (tid == 0) {
+        P.iters[b] = iters;
+        if (fail) P.status[b] = ST_NONPD;
+    }
+}
+
+size_t scan_smem_bytes(int dtype_f64) {
+    return (size_t)SW * WA_SIZE * (dtype_f64 ? sizeof(double) : sizeof(float));
+}
+
+template <typename T> cudaError_t prepare_scan() {
+    return cudaFuncSetAttribute(k_scan_ric<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)((size_t)SW * WA_SIZE * sizeof(T)));
+}
+
+template <typename T> cudaError_t launch_scan_ric(const Params<T>& P, cudaStream_t st) {
+    k_scan_ric<T><<<P.B, SW * 32, (size_t)SW * WA_SIZE * sizeof(T), st>>>(P);
+    return cudaGetLastError();
+}
+
+template cudaError_t prepare_scan<float>();
+template cudaError_t prepare_scan<double>();
+template cudaError_t launch_scan_ric<float>(const Params<float>&, cudaStream_t);
+template cudaError_t launch_scan_ric<double>(const Params<double>&, cudaStream_t);
+
+}  // namespace camp

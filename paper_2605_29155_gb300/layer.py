@@ -92,7 +92,10 @@ class DiffMPC:
         if store_mode not in modes:
             raise ValueError(f"store_mode must be one of {sorted(modes)}")
         cfg.store_mode = modes[store_mode]
-        cfg.exec_mode = camp.MPC_EXEC_PERSISTENT if exec_mode == "persistent" else camp.MPC_EXEC_PLAIN
+        modes = {"persistent": camp.MPC_EXEC_PERSISTENT, "plain": camp.MPC_EXEC_PLAIN, "scan": camp.MPC_EXEC_SCAN}
+        if exec_mode not in modes:
+            raise ValueError(f"exec_mode must be one of {sorted(modes)}")
+        cfg.exec_mode = modes[exec_mode]
         cfg.ipb = int(ipb)
         cfg.tpi = int(tpi)
         cfg.tape_budget = int(tape_budget)

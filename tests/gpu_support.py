@@ -63,6 +63,14 @@ EXCUSED_MAX_FRAC = 0.01
 CONV_BAND32 = 1e-5
 # alpha decisions FP64 cannot resolve (any size of step)
 TIE64 = 1e-9
+# the stage-parallel Riccati form in FP32 (exec_mode "scan"): folding a chunk of
+# stages into one element forms closed-loop products A_R (I + G G'J)^-1 whose
+# FP32 rounding cancels, and the costate v carries about 1e-4 of its size
+# (measured on hover N = 50 and track N = 20, against 2e-6 for the sequential
+# recursion in FP32).  A converged solve's controls are the zero of that
+# gradient, so they move by up to 2e-4 (measured): gated at U_TOL32_SCAN.  The
+# FP64 scan form keeps the sequential form's FP64 gates.
+U_TOL32_SCAN = 5e-4
 
 
 # Tape layout (opaque to callers, read here only to compare free sets): per
@@ -262,7 +270,7 @@ def stop_agrees(gs, gi, so):
     return k >= 1 and all(v < CONV_BAND32 for v in so.du_hist[k - 1:])
 
 
-def compare_iterates32(gpu, orc, idx, grad_u, grad_x=None, max_iter=None):
+def compare_iterates32(gpu, orc, idx, grad_u, grad_x=None, max_iter=None, u_tol=U_TOL32):
     """FP32 gate against the oracle's own returned iterate.  Every sampled
     instance -- converged or stopped at max_iter -- is compared: it must end
     in the oracle's state (CONVERGED and STALLED count as one normal end;
@@ -298,7 +306,7 @@ def compare_iterates32(gpu, orc, idx, grad_u, grad_x=None, max_iter=None):
             e["u"] = rel(gpu["u"][i], so.U, 1e-6)
             e["x"] = rel(gpu["x"][i], so.X, 1e-6)
             e["J"] = abs(float(gpu["cost"][i]) - so.J) / max(abs(so.J), 1e-12)
-            utol = U_TOL32 if conv else U_TOL32_ITER
+            utol = u_tol if conv else U_TOL32_ITER
             if e["u"] > utol or e["x"] > utol:
                 mine.append((int(i), "u/x", e["u"], e["x"]))
             if e["J"] > (J_TOL32 if conv else J_TOL32_ITER):

@@ -1,0 +1,143 @@
+"""Parity of the stage-parallel Riccati phase (exec_mode "scan": the
+associative-scan LQR of the related work in Sec. II with the box QPs' free
+sets guessed, then the stages the guess got wrong by the sequential
+recursion) with the FP64 oracle's sequential recursion of Sec. IV-2, and
+with the library's own sequential phase.
+
+Every stage's box QP is the one the sequential recursion solves, from the same
+V_{t+1}, v_{t+1} up to rounding, so the iterates are the oracle's: in FP64 to
+rounding while every decision is clear-cut (the same gates as the sequential
+path's FP64 tests); in FP32 the converged controls within U_TOL32_SCAN (the
+scan's FP32 costate carries more rounding than the sequential recursion's;
+the reason and the measurement are at its definition), everything else within
+the product path's gates.  The forward's final factorization and the backward
+are the library's sequential phases, so the gradients are checked as for
+those."""
+import numpy as np
+import pytest
+
+from gpu_support import (EXCUSED_MAX_FRAC, G_TOL64, G_TOL64C, J_TOL64, J_TOL64C, TIE64, U_TOL32_SCAN, U_TOL64,
+                         U_TOL64C, cached_problem, compare, compare_iterates32, oracle_solve, oracle_solve_pool, rel,
+                         run_gpu)
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def _grads(B, N, seed):
+    rng = np.random.default_rng(seed)
+    return rng.normal(size=(B, N, 4)), rng.normal(size=(B, N, 13)) * 0.1
+
+
+@pytest.mark.parametrize("name,B,N,horizons", [("hover", 8, 10, False), ("track", 37, 20, True),
+                                               ("uneven", 33, 40, False), ("mem", 9, 30, False)])
+def test_scan_fp64_early_iterations_identical_to_oracle(name, B, N, horizons):
+    """Three iterations with tol = 0 in double: values agree with the oracle's
+    to rounding (ragged horizons, shared and per-stage Q, guesses that miss
+    where saturations move)."""
+    prob = cached_problem(name, B, N, 0, horizons)
+    gu, gx = _grads(B, N, 1)
+    gpu = run_gpu(prob, torch.float64, 3, 0.0, gu, gx, N_max=40, exec_mode="scan")
+    idx = list(range(B))
+    orc = oracle_solve(prob, idx, 3, 0.0, gu, gx)
+    report, fails = compare(gpu, orc, idx, U_TOL64, J_TOL64, G_TOL64, skip_ties=TIE64)
+    print(name, report)
+    assert report["compared"] >= 0.8 * B
+    assert not fails, (fails[:5], report)
+
+
+@pytest.mark.parametrize("name,B,N,horizons,mi", [("hover", 8, 10, False, 10), ("track", 37, 20, True, 8),
+                                                  ("uneven", 33, 40, False, 12)])
+def test_scan_fp64_to_convergence_matches_oracle(name, B, N, horizons, mi):
+    prob = cached_problem(name, B, N, 0, horizons)
+    gu, gx = _grads(B, N, 1)
+    gpu = run_gpu(prob, torch.float64, mi, 1e-6, gu, gx, N_max=40, exec_mode="scan")
+    idx = list(range(B))
+    orc = oracle_solve(prob, idx, mi, 1e-6, gu, gx)
+    report, fails = compare(gpu, orc, idx, U_TOL64C, J_TOL64C, G_TOL64C, counts="final")
+    print(name, report)
+    assert not fails, (fails[:5], report)
+
+
+@pytest.mark.parametrize("B,N", [(1, 50), (5, 2), (6, 50), (3, 64)])
+def test_scan_latency_horizons_match_oracle(B, N):
+    """The horizons of the solver-latency setting (hover, exactly five
+    iterations with tol = 0), handles sized to N, and the longest horizon the
+    library takes: FP64 to rounding; FP32 within 1e-3 of the oracle's
+    controls (the sequential path's bound for this setting)."""
+    prob = cached_problem("hover", B, N, 7)
+    gu, gx = _grads(B, N, 3)
+    idx = list(range(B))
+    orc = oracle_solve(prob, idx, 5, 0.0, gu, gx)
+    gpu = run_gpu(prob, torch.float64, 5, 0.0, gu, gx, exec_mode="scan")
+    report, fails = compare(gpu, orc, idx, U_TOL64, J_TOL64, G_TOL64, skip_ties=TIE64)
+    print("fp64", B, N, report)
+    assert report["compared"] >= B - 1
+    assert not fails, (fails[:5], report)
+    gpu32 = run_gpu(prob, torch.float32, 5, 0.0, gu, gx, exec_mode="scan")
+    assert np.all(np.isfinite(gpu32["u"])) and np.all(gpu32["iters"] == 5)
+    for i in range(B):
+        u_or = orc[i][1].U
+        e = np.linalg.norm(gpu32["u"][i] - u_or) / max(np.linalg.norm(u_or), 1e-6)
+        print("fp32", i, e)
+        assert e <= 1e-3
+
+
+@pytest.mark.parametrize("name,B,N,horizons,mi", [("hover", 64, 20, False, 20), ("track", 64, 20, True, 20),
+                                                  ("hover", 24, 50, False, 20)])
+def test_scan_fp32_matches_oracle(name, B, N, horizons, mi):
+    """FP32: every instance against the oracle's own returned iterate with the
+    product path's gate, converged controls within U_TOL32_SCAN (only
+    recorded-degenerate decisions of solves stopped at max_iter excused)."""
+    prob = cached_problem(name, B, N, 0, horizons)
+    gu, gx = _grads(B, N, 2)
+    gpu = run_gpu(prob, torch.float32, mi, 1e-6, gu, gx, N_max=max(N, 40), exec_mode="scan")
+    idx = list(range(B))
+    orc = oracle_solve_pool(prob, idx, mi, 1e-6, gu, gx)
+    report, fails = compare_iterates32(gpu, orc, idx, gu, gx, u_tol=U_TOL32_SCAN)
+    print(name, N, report, fails[:5])
+    assert report["excused"] <= max(1, EXCUSED_MAX_FRAC * B)
+    assert not fails, (fails[:5], report)
+
+
+@pytest.mark.parametrize("dtype", ["float32", "float64"])
+def test_scan_agrees_with_the_sequential_phase(dtype):
+    """The same solves through the sequential plain form and the scan form:
+    same statuses and iteration counts, controls of the solves that both
+    converged within rounding of each other (FP64 the identical-decision gate
+    U_TOL64; FP32 U_TOL32_SCAN)."""
+    dt = getattr(torch, dtype)
+    prob = cached_problem("track", 48, 20, 4, True)
+    a = run_gpu(prob, dt, 20, 1e-6, exec_mode="plain", ipb=1)
+    b = run_gpu(prob, dt, 20, 1e-6, exec_mode="scan")
+    conv = (a["status"] == 0) & (b["status"] == 0)
+    assert conv.sum() >= 0.5 * len(conv)
+    if dtype == "float64":
+        assert np.array_equal(a["status"], b["status"]) and np.array_equal(a["iters"], b["iters"])
+    err = max(rel(a["u"][i], b["u"][i], 1e-6) for i in np.flatnonzero(conv))
+    print(dtype, err)
+    assert err <= (U_TOL64 if dtype == "float64" else U_TOL32_SCAN)
+
+
+def test_scan_general_cost_keeps_the_sequential_phase():
+    """A general cost in the scan form runs the sequential Riccati phase:
+    the result equals the plain form's."""
+    import workloads as W
+    B, N = 16, 10
+    prob = W.hover_targets(B, N, seed=3)
+    diag = np.concatenate([prob["Q"][:, 0], prob["R"]], axis=1)
+    C = np.einsum("bi,ij->bij", diag, np.eye(17))[:, None]
+    zr = np.concatenate([prob["x_ref"], np.repeat(prob["u_ref"][:, None], N, axis=1)], axis=2)
+    c = -np.einsum("bkij,btj->bti", C, zr)
+    gp = dict(prob, C=C, c=c)
+    a = run_gpu(gp, torch.float64, 8, 1e-6, exec_mode="plain", ipb=1)
+    b = run_gpu(gp, torch.float64, 8, 1e-6, exec_mode="scan")
+    assert np.array_equal(a["u"], b["u"]) and np.array_equal(a["iters"], b["iters"])
