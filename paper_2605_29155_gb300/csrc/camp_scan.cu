@@ -537,9 +537,11 @@ __device__ void scan_suffixes(const ScanWs<T>& W, const ScanShared<T>& sh, T* wa
         wcopy(W.Uc + (size_t)w * ELEM, Rl, ELEM, lane);
     }
     __syncthreads();
-    // B: suffix scan of the chunk totals over the chunks (log2 levels)
+    // B: suffix scan of the chunk totals over the chunks (log2 levels; the
+    // last level's results are used only for J and eta)
     int cur = 0;
     for (int d = 1; d <= last; d <<= 1) {
+        const bool full = 2 * d <= last;
         if (w <= last) {
             T* dst = W.Uc + ((size_t)(cur ^ 1) * SW + w) * ELEM;
             const T* src = W.Uc + ((size_t)cur * SW + w) * ELEM;
@@ -547,7 +549,7 @@ __device__ void scan_suffixes(const ScanWs<T>& W, const ScanShared<T>& sh, T* wa
                 wcopy(wa + WA_I, src, ELEM, lane);
                 wcopy(wa + WA_J, W.Uc + ((size_t)cur * SW + w + d) * ELEM, ELEM, lane);
                 __syncwarp();
-                ok = wcombine(wa + WA_I, wa + WA_J, wa + WA_O, wa, true, lane) && ok;
+                ok = wcombine(wa + WA_I, wa + WA_J, wa + WA_O, wa, full, lane) && ok;
                 wcopy(dst, wa + WA_O, ELEM, lane);
             } else {
                 wcopy(dst, src, ELEM, lane);
