@@ -175,7 +175,7 @@ constexpr int WA_I = 0, WA_J = ELEM, WA_O = 2 * ELEM, WA_G = 3 * ELEM, WA_T = 3 
               WA_COL = WA_T + 4 * M13, WA_SIZE = WA_COL + 16;
 // Work area of a sequential stage (inside the warp's area): S_{t+1}'s J and
 // eta on entry, S_t's on exit (the place the scan's Riccati steps use too);
-// F_t; temporaries.
+// F_t (two buffers of 224); temporaries.
 constexpr int SQ_J = WA_J + E_J, SQ_N = WA_J + E_N, SQ_F = WA_I, SQ_P = WA_T, SQ_X = WA_T + M13,
               SQ_U = WA_T + 2 * M13, SQ_K = SQ_U + 64, SQ_H = SQ_U + 128, SQ_V = WA_O;
 
@@ -297,23 +297,30 @@ constexpr int ST_JG = 0, ST_S = 52, ST_Y = 68, ST_Z = 84, ST_W4 = 136, ST_ZV = 1
 template <typename T> __device__ void stage_factors_all(const ScanWs<T>& W, const ScanShared<T>& sh, int n) {
     for (int job = threadIdx.x; job < n * NX; job += blockDim.x) {
         const int t = job / NX, i = job - NX * t;
-        const T* F = W.F + (size_t)t * FREC;
+        const T* F = W.F + (size_t)t * FREC + i * NZ;
         const T* G = W.G + (size_t)t * GREC;
         T* sf = W.SF + (size_t)t * SF_SIZE;
-        const int fm = (int)G[G_AM];
+        // every load first (one round trip), then the arithmetic
+        T f[NZ], r[NU], dc[NU];
 #pragma unroll
-        for (int k = 0; k < NX; ++k) sf[SF_A + i * NX + k] = F[i * NZ + k];
+        for (int k = 0; k < NZ; ++k) f[k] = F[k];
+#pragma unroll
+        for (int a = 0; a < NU; ++a) { r[a] = G[G_R + a]; dc[a] = G[G_DC + a]; }
+        const int fm = (int)G[G_AM];
+        const T q = G[G_Q + i], qd = G[G_QD + i];
+#pragma unroll
+        for (int k = 0; k < NX; ++k) sf[SF_A + i * NX + k] = f[k];
         T bi = T(0);
 #pragma unroll
         for (int a = 0; a < NU; ++a) {
-            const T Bia = F[i * NZ + NX + a];
+            const T Bia = f[NX + a];
             const bool fr = (fm >> a) & 1;
             sf[SF_G + i * NU + a] = fr ? Bia / sqrt(sh.R[a]) : T(0);
-            bi += fr ? -(Bia / sh.R[a]) * G[G_R + a] : Bia * G[G_DC + a];
+            bi += fr ? -(Bia / sh.R[a]) * r[a] : Bia * dc[a];
         }
         sf[SF_B + i] = bi;
-        sf[SF_E + i] = -G[G_Q + i];
-        sf[SF_Q + i] = G[G_QD + i];
+        sf[SF_E + i] = -q;
+        sf[SF_Q + i] = qd;
     }
 }
 
@@ -701,10 +708,9 @@ __device__ void stage_qps(const Params<T>& P, const ScanWs<T>& W, ScanShared<T>&
 // non-positive pivot.
 template <typename T>
 __device__ bool seq_stage(const Params<T>& P, const ScanWs<T>& W, const ScanShared<T>& sh, T* wa, int pos, int t,
-                          int n, bool have_qp, int lane) {
+                          int n, bool have_qp, int lane, T* Fs) {
     T* Js = wa + SQ_J;
     T* es = wa + SQ_N;
-    T* Fs = wa + SQ_F;
     T* P1 = wa + SQ_P;
     T* Qx = wa + SQ_X;
     T* Qu = wa + SQ_U;
@@ -712,8 +718,6 @@ __device__ bool seq_stage(const Params<T>& P, const ScanWs<T>& W, const ScanShar
     T* Hg = wa + SQ_H;                  // H (16, upper used), g (4)
     T* Vn = wa + SQ_V;
     const T* G = W.G + (size_t)t * GREC;
-    wcopy(Fs, W.F + (size_t)t * FREC, FREC, lane);
-    __syncwarp();
     T d[4], Lf[NL];
     int mask;
     bool ok;
@@ -975,8 +979,16 @@ __global__ void __launch_bounds__(SW * 32, 1) k_scan_ric(const __grid_constant__
                 wa[e < M13 ? SQ_J + e : SQ_N + e - M13] = v;
             }
             __syncwarp();
+            // F_t double-buffered: the next stage's copy runs during this one
+            T* fb[2] = {wa + SQ_F, wa + SQ_F + 224};
+            wprefetch(fb[0], W.F + (size_t)c * FREC, FREC, lane);
             bool ok = true;
-            for (int t = c; t >= 0 && ok; --t) ok = seq_stage(P, W, sh, wa, pos, t, n, t == c, lane);
+            for (int t = c, k = 0; t >= 0 && ok; --t, k ^= 1) {
+                wwait();
+                if (t > 0) wprefetch(fb[k ^ 1], W.F + (size_t)(t - 1) * FREC, FREC, lane);
+                ok = seq_stage(P, W, sh, wa, pos, t, n, t == c, lane, fb[k]);
+            }
+            cp_async_wait_all();
             if (!ok && tid == 0) sh.fail = 1;
         }
         __syncthreads();
