@@ -835,6 +835,32 @@ def run_costmap_only(args):
                           wait_flag=cm.wait_flag())))
 
 
+def run_scan_only(args):
+    """W + K eager forward solves in the stage-parallel Riccati form (hover
+    stabilisation, B instances, N = 50, exactly 5 iterations), nothing else:
+    the command the committed ncu summary of k_scan_ric was taken with."""
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2605_29155_gb300 import DiffMPC, Problem
+    Bk, Nh = args.batch, 50
+    p = Problem.from_numpy(W.hover_targets(Bk, Nh, seed=4))
+    solver = DiffMPC(N_max=Nh, B_max=Bk, max_iter=5, tol=0.0, exec_mode="scan", store_mode="recompute")
+    s = solver.alloc_solution(Bk, Nh)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for k in range(args.warmup + args.steps):
+        if k == args.warmup:
+            torch.cuda.synchronize()
+            e0.record()
+        solver.solve(p, s)
+    e1.record()
+    torch.cuda.synchronize()
+    print(json.dumps(dict(mode="scan", B=Bk, N=Nh, steps=args.steps, ms_per_step=e0.elapsed_time(e1) / args.steps,
+                          iters_mean=float(s.iters.float().mean()))))
+    solver.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -844,10 +870,11 @@ def main():
     ap.add_argument("--latency-reps", type=int, default=200)
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-side", action="store_true", help="skip the uneven-horizon and memory-heavy batches")
-    ap.add_argument("--mode", default="full", choices=["full", "kernels", "costmap"],
+    ap.add_argument("--mode", default="full", choices=["full", "kernels", "costmap", "scan"],
                     help="kernels: only W + K eager forward+backward steps of the workload (for profilers); "
-                         "costmap: only W + K cost-map forward+backward passes")
-    ap.add_argument("--batch", type=int, default=B, help="instances (kernels mode only)")
+                         "costmap: only W + K cost-map forward+backward passes; "
+                         "scan: only W + K stage-parallel forward solves (hover, N = 50)")
+    ap.add_argument("--batch", type=int, default=B, help="instances (kernels, costmap and scan modes)")
     ap.add_argument("--tpi", type=int, default=0, help="threads per instance, 0 = default (kernels mode only)")
     ap.add_argument("--ipb", type=int, default=0, help="instances per block, 0 = default (kernels mode only)")
     args = ap.parse_args()
@@ -856,6 +883,9 @@ def main():
         return
     if args.mode == "costmap":
         run_costmap_only(args)
+        return
+    if args.mode == "scan":
+        run_scan_only(args)
         return
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", args.gpus if args.gpus == 1 else 1))
