@@ -18,8 +18,10 @@
 // accessors that also assemble the observation [x_init; x_ref,0], append the
 // row of ones whose product gives a bias gradient, and form dL/da3 =
 // dL/dQ (q_hi - q_lo) s (1 - s) on the fly.  Two stages of K = 16 alternate:
-// while the tensor core works on one, the threads fill the other; an mbarrier
-// signalled by tcgen05.commit tells when a stage is free again.
+// while the tensor core works on one, the threads split the next stage's
+// elements (read into registers a trip earlier) into the other, once an
+// mbarrier signalled by tcgen05.commit tells that it is free, and send out the
+// reads of the stage after.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -170,47 +172,103 @@ __device__ __forceinline__ void put_split(float* hi, float* lo, int off, float x
     lo[off] = __uint_as_float(to_tf32(x - __uint_as_float(h)));
 }
 
-// One K = TK stage of A (rows r0..r0+127) or B into shared memory as hi / lo
-// TF32 tiles.  Threads take four consecutive elements along the dimension the
-// operand is contiguous in (k, or r), so that global reads coalesce and, where
-// the four are 16-byte aligned and in bounds, are one vector load; the
-// observation and ragged or misaligned edges take the scalar path.
-__device__ __forceinline__ void fill_tile(const Operand& o, int r0, int k0, int K, float q_span, float* hi, float* lo) {
-    const bool kfast = o.kind == K_OBS ? o.s0 == 0 : o.s1 == 1;
-    const bool vec_kind = o.kind != K_OBS;
-#pragma unroll 2
-    for (int e = threadIdx.x * 4; e < TM * TK; e += THREADS * 4) {
-        const int r = kfast ? e / TK : e % TM;
-        const int k = kfast ? e % TK : e / TM;
-        const int rr = r0 + r, kk = k0 + k;
-        // the four elements (r, k..k+3) or (r..r+3, k)
-        bool vec = vec_kind;
-        long long i0 = 0;
-        if (vec) {
-            const bool inb = kfast ? (kk + 3 < K && rr < o.rows) : (rr + 3 < o.rows && kk < K);
-            i0 = (long long)rr * o.s0 + (long long)kk * o.s1;
-            vec = inb && ((((size_t)(o.p + i0)) & 15) == 0) &&
-                  (o.kind != K_DA3 || ((((size_t)(o.p2 + i0)) & 15) == 0));
+// One K = TK stage of A (rows r0..r0+127) or B, in two steps so that the
+// global reads of the next stage overlap the tensor core's work on this one:
+// gather_tile reads the thread's EPT elements into registers, scatter_tile
+// splits them into hi / lo TF32 tiles in shared memory.  The thread-to-element
+// map depends on which dimension the operand is contiguous in:
+//   k (k-fast): four consecutive k of one row per group, one vector load where
+//     16-byte aligned and in bounds, and one 16-byte store per tile (the four
+//     are adjacent in a core matrix; a quarter-warp fills one core matrix);
+//   r (r-fast): each warp store covers one whole 8 x 4 core matrix (lane l at
+//     row l % 8, k l / 8), so the 32 stores hit 32 banks; its reads are 32-byte
+//     runs of 8 rows at four k.
+// The observation and ragged or misaligned edges take the scalar path.
+constexpr int EPT = TM * TK / THREADS;              // elements per thread and tile
+constexpr int GROUPS = EPT / 4;                     // k-fast: groups of four
+
+__device__ __forceinline__ bool k_fast(const Operand& o) { return o.kind == K_OBS ? o.s0 == 0 : o.s1 == 1; }
+
+// k-fast group g: (r, k .. k + 3), a row of one core matrix.  Each
+// quarter-warp writes one whole core matrix (rows 8 rb .. 8 rb + 7 at k-block
+// lane / 8: 128 contiguous bytes), and a warp reads 8 rows x 16 k.
+__device__ __forceinline__ void kf_pos(int g, int& r, int& k) {
+    const int lane = threadIdx.x & 31, rb = (threadIdx.x >> 5) * GROUPS + g;
+    r = rb * 8 + (lane & 7);
+    k = (lane >> 3) * 4;
+}
+// r-fast element q: core matrix cm = (threadIdx.x / 32) * EPT + q, at row
+// 8 (cm / (TK / 4)) + lane % 8 and k 4 (cm % (TK / 4)) + lane / 8
+__device__ __forceinline__ void rf_pos(int q, int& r, int& k) {
+    const int lane = threadIdx.x & 31, cm = (threadIdx.x >> 5) * EPT + q;
+    r = (cm / (TK / 4)) * 8 + (lane & 7);
+    k = (cm % (TK / 4)) * 4 + (lane >> 3);
+}
+
+__device__ __forceinline__ void gather_tile(const Operand& o, int r0, int k0, int K, float q_span, float (&v)[EPT]) {
+    if (!k_fast(o)) {
+#pragma unroll
+        for (int q = 0; q < EPT; ++q) {
+            int r, k;
+            rf_pos(q, r, k);
+            v[q] = load_op(o, r0 + r, k0 + k, K, q_span);
         }
+        return;
+    }
+#pragma unroll
+    for (int g = 0; g < GROUPS; ++g) {
+        int r, k;
+        kf_pos(g, r, k);
+        const int rr = r0 + r, kk = k0 + k;
+        bool vec = o.kind != K_OBS && kk + 3 < K && rr < o.rows;
+        const long long i0 = (long long)rr * o.s0 + (long long)kk * o.s1;
+        vec = vec && ((((size_t)(o.p + i0)) & 15) == 0) && (o.kind != K_DA3 || ((((size_t)(o.p2 + i0)) & 15) == 0));
         if (vec) {
-            float4 v = *reinterpret_cast<const float4*>(o.p + i0);
+            float4 x = *reinterpret_cast<const float4*>(o.p + i0);
             if (o.kind == K_DA3) {
                 const float4 sv = *reinterpret_cast<const float4*>(o.p2 + i0);
-                v.x *= q_span * sv.x * (1.f - sv.x);
-                v.y *= q_span * sv.y * (1.f - sv.y);
-                v.z *= q_span * sv.z * (1.f - sv.z);
-                v.w *= q_span * sv.w * (1.f - sv.w);
+                x.x *= q_span * sv.x * (1.f - sv.x);
+                x.y *= q_span * sv.y * (1.f - sv.y);
+                x.z *= q_span * sv.z * (1.f - sv.z);
+                x.w *= q_span * sv.w * (1.f - sv.w);
             }
-            const float x4[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-            for (int j = 0; j < 4; ++j) put_split(hi, lo, kfast ? core_off(r, k + j) : core_off(r + j, k), x4[j]);
+            v[4 * g + 0] = x.x;
+            v[4 * g + 1] = x.y;
+            v[4 * g + 2] = x.z;
+            v[4 * g + 3] = x.w;
         } else {
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const int rj = kfast ? r : r + j, kj = kfast ? k + j : k;
-                put_split(hi, lo, core_off(rj, kj), load_op(o, r0 + rj, k0 + kj, K, q_span));
-            }
+            for (int j = 0; j < 4; ++j) v[4 * g + j] = load_op(o, rr, kk + j, K, q_span);
         }
+    }
+}
+
+__device__ __forceinline__ void scatter_tile(const Operand& o, const float (&v)[EPT], float* hi, float* lo) {
+    if (!k_fast(o)) {
+#pragma unroll
+        for (int q = 0; q < EPT; ++q) {
+            int r, k;
+            rf_pos(q, r, k);
+            put_split(hi, lo, core_off(r, k), v[q]);
+        }
+        return;
+    }
+#pragma unroll
+    for (int g = 0; g < GROUPS; ++g) {
+        int r, k;
+        kf_pos(g, r, k);
+        float4 h, l;
+        float* hp = &h.x;
+        float* lp = &l.x;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const uint32_t t = to_tf32(v[4 * g + j]);
+            hp[j] = __uint_as_float(t);
+            lp[j] = __uint_as_float(to_tf32(v[4 * g + j] - __uint_as_float(t)));
+        }
+        const int off = core_off(r, k);                 // k % 4 == 0: 16-byte aligned
+        *reinterpret_cast<float4*>(hi + off) = h;
+        *reinterpret_cast<float4*>(lo + off) = l;
     }
 }
 
@@ -242,13 +300,20 @@ __global__ void __launch_bounds__(THREADS, 1) k_gemm_3xtf32(const __grid_constan
 
     const int nk = (kend - kbeg + TK - 1) / TK;
     auto stage = [&](int s) { return sm + s * STAGE_FLOATS; };
-    auto fill = [&](int c) {
+    float va[EPT], vb[EPT];                         // the next stage's elements, read ahead
+    auto gather = [&](int c) {
+        gather_tile(g.A, m0, kbeg + c * TK, kend, q_span, va);
+        gather_tile(g.B, n0, kbeg + c * TK, kend, q_span, vb);
+    };
+    auto scatter = [&](int c) {
         float* st = stage(c & 1);
-        fill_tile(g.A, m0, kbeg + c * TK, kend, q_span, st, st + TILE_FLOATS);
-        fill_tile(g.B, n0, kbeg + c * TK, kend, q_span, st + 2 * TILE_FLOATS, st + 3 * TILE_FLOATS);
+        scatter_tile(g.A, va, st, st + TILE_FLOATS);
+        scatter_tile(g.B, vb, st + 2 * TILE_FLOATS, st + 3 * TILE_FLOATS);
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     };
-    fill(0);
+    gather(0);
+    scatter(0);
+    if (nk > 1) gather(1);
     __syncthreads();
     bool ok = true;
     int issued = -1;                    // the last chunk whose MMAs were committed
@@ -271,10 +336,13 @@ __global__ void __launch_bounds__(THREADS, 1) k_gemm_3xtf32(const __grid_constan
             mma_commit(smem_u32(&mbar[c & 1]));
         }
         if (c + 1 < nk) {
-            // stage (c + 1) & 1 was last read by the MMAs of chunk c - 1
+            // chunk c + 1's elements were read during the previous trip; its
+            // stage (c + 1) & 1 was last read by the MMAs of chunk c - 1.  The
+            // reads of chunk c + 2 then go out for the next trip.
             if (c >= 1 && !mbar_wait(smem_u32(&mbar[(c - 1) & 1]), ((c - 1) >> 1) & 1)) ok = false;
             if (!__syncthreads_and(ok)) { ok = false; break; }
-            fill(c + 1);
+            scatter(c + 1);
+            if (c + 2 < nk) gather(c + 2);
             __syncthreads();
         }
     }
