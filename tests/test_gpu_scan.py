@@ -141,3 +141,41 @@ def test_scan_general_cost_keeps_the_sequential_phase():
     a = run_gpu(gp, torch.float64, 8, 1e-6, exec_mode="plain", ipb=1)
     b = run_gpu(gp, torch.float64, 8, 1e-6, exec_mode="scan")
     assert np.array_equal(a["u"], b["u"]) and np.array_equal(a["iters"], b["iters"])
+
+
+def test_scan_edge_cases():
+    """Horizon one (no dynamics: u* = clamp(u_ref)), every control pinned
+    (u_lo = u_hi: no free control, no gains), a non-finite input flagged and
+    isolated, and an empty batch, in the scan form."""
+    rng = np.random.default_rng(9)
+    gu = rng.normal(size=(16, 10, 4))
+    prob = dict(cached_problem("hover", 16, 10, 5))
+    prob["horizon"] = np.ones(16, dtype=np.int32)
+    prob["u_ref"] = prob["u_ref"] + np.linspace(-3, 8, 16)[:, None]
+    g = run_gpu(prob, torch.float64, 8, 1e-6, gu, exec_mode="scan")
+    np.testing.assert_allclose(g["u"][:, 0], np.clip(prob["u_ref"], 0, 8.5), atol=1e-12)
+    assert np.all(g["u"][:, 1:] == 0) and np.all(g["x"][:, 1:] == 0)
+    prob2 = dict(cached_problem("hover", 16, 10, 6))
+    prob2["u_lo"] = prob2["u_hi"] = np.full((16, 4), 3.0)
+    g2 = run_gpu(prob2, torch.float32, 8, 1e-6, gu, exec_mode="scan")
+    assert np.all(g2["u"] == 3.0) and np.all(np.isin(g2["status"], [0, 1]))
+    ref = run_gpu(prob2, torch.float32, 8, 1e-6, gu, exec_mode="plain", ipb=1)
+    assert np.array_equal(g2["status"], ref["status"]) and np.array_equal(g2["iters"], ref["iters"])
+    prob3 = dict(cached_problem("hover", 12, 10, 7))
+    prob3["x0"] = prob3["x0"].copy()
+    prob3["x0"][3, 0] = np.nan
+    prob3["Q"] = prob3["Q"].copy()
+    prob3["Q"][5, 0, 2] = np.inf
+    g3 = run_gpu(prob3, torch.float32, 8, 1e-6, gu[:12], exec_mode="scan")
+    assert g3["status"][3] == 3 and g3["status"][5] == 3
+    ok = [i for i in range(12) if i not in (3, 5)]
+    assert np.isfinite(g3["u"][ok]).all() and np.all(np.isin(g3["status"][ok], [0, 1, 2]))
+    from paper_2605_29155_gb300 import DiffMPC, Problem, camp
+    solver = DiffMPC(N_max=10, B_max=4, exec_mode="scan")
+    p = Problem.from_numpy({k: (v[:0] if isinstance(v, np.ndarray) else v)
+                            for k, v in cached_problem("hover", 4, 10, 1).items()})
+    out = solver.alloc_solution(0, 10)
+    code = camp.mpc_solve_fwd(solver.h, solver._cproblem(p), solver._csolution(out),
+                              torch.cuda.current_stream().cuda_stream)
+    assert code == camp.MPC_OK
+    solver.close()
