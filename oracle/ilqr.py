@@ -11,7 +11,7 @@ Sec. IV: 1) rollout and linearization, 2) Riccati backward pass with the box
 QP (Tassa et al. 2014), 3) forward pass with the line search over
 alpha in {1, 0.5, 0.25, 0.1}.
 
-Readings where the paper is silent (each listed in the design notes):
+Readings where the paper is silent, by number (R1, R4-R6; the others are stated where they apply):
   R1 cost   stage costs on (x_t, u_t) for t = 0..N-1, no terminal cost; the
             rollout produces x_1..x_{N-1}.  The value reported and compared
             is the centred form sum 1/2 (x-x_ref)'Q(x-x_ref) + 1/2 (u-u_ref)'R(u-u_ref),
