@@ -46,6 +46,8 @@
 namespace camp {
 
 constexpr int SW = 8;                  // warps per block
+// the stages' box QPs run with one lane per stage on warps 0 and 1
+static_assert(MAX_N <= 64, "the stage-parallel Riccati phase takes at most 64 stages");
 constexpr int M13 = NX * NX;
 // element layout: A (13 x 13), b, C (13 x 13), eta, J (13 x 13)
 constexpr int E_A = 0, E_B = M13, E_C = M13 + NX, E_N = 2 * M13 + NX, E_J = 2 * M13 + 2 * NX,
