@@ -19,7 +19,8 @@
 // and the suffix S_t = e_t (x) ... (x) e_{n-1} holds the value function of
 // stage t: V_t = J(S_t), v_t = -eta(S_t).  M C_i and J_j M are symmetric
 // ((C_i^-1 + J_j)^-1 and (J_j^-1 + C_i)^-1) and are symmetrized, as are C and
-// J: in FP32 that keeps the scan's error near the sequential recursion's.
+// J.  In FP32, composing the elements' transition parts (A, b, C) still costs
+// the costate about two digits against the sequential recursion.
 //
 // The free sets.  The box QP makes the recursion depend on free-set decisions.
 // The scan therefore takes every stage's free set and clamped offsets as a
@@ -36,10 +37,12 @@
 // the free sets are the sequential method's.  A non-positive pivot at a final
 // stage ends the solve as in the sequential recursion (status NONPD).
 //
-// The scan on SW warps: chunk w holds ch = ceil(n / SW) consecutive stages;
-// each warp folds its chunk from the back, the chunks' totals are scanned in
-// log2(SW) levels, and each stage's partial is combined with the suffix of the
-// chunks after it (only J and eta are needed there).
+// The scan on SW warps: chunk w holds ch = ceil(n / SW) consecutive stages.
+// (A) Each warp folds its chunk into one element from the back, (B) the
+// chunks' totals are suffix-scanned in log2(SW) levels of general combines,
+// and (C) each warp sweeps J and eta back through its chunk from the suffix of
+// the chunks after it.  A single stage's C = G G' has rank <= 4, so (A) and
+// (C) use the Woodbury form with a 4 x 4 factor instead of a 13 x 13 inverse.
 #include "camp_device.cuh"
 #include "camp_internal.h"
 
@@ -275,7 +278,7 @@ template <typename T> __device__ __forceinline__ void wcopy(T* dst, const T* src
     for (int e = lane; e < n; e += 32) dst[e] = src[e];
 }
 
-// ------------------------------------------------------------ the passes ---
+// -------------------------------------------------- scan, QPs and gains ---
 // Shared state of a block.
 template <typename T> struct ScanShared {
     T R[NU], uref[NU], ulo[NU], uhi[NU];
@@ -289,10 +292,15 @@ template <typename T> struct ScanShared {
 // only the 4 x 4 matrix S = I + G'J G (Woodbury):
 //   M = (I + G G'J)^-1 = I - G S^-1 G'J,   J M = J - (J G) S^-1 (J G)',
 //   M C_t = G S^-1 G',   M' y = y - J G S^-1 G'y.
-// Stage t's factors in a warp's shared memory:
-// temporaries of a step
+// A step reads stage t's factors (the SF_* layout) from a warp's shared memory
+// and keeps these temporaries there (ST_SIZE entries):
 constexpr int ST_JG = 0, ST_S = 52, ST_Y = 68, ST_Z = 84, ST_W4 = 136, ST_ZV = 144, ST_W = 160, ST_T1 = ST_W + M13,
               ST_AG = ST_T1 + M13, ST_X = ST_AG + 52, ST_AM = ST_X + 52, ST_BN = ST_AM + M13, ST_SIZE = ST_BN + 16;
+// the regions of a warp's area the steps use stay inside it
+static_assert(WA_O + ST_SIZE <= WA_SIZE, "step temporaries");
+static_assert(264 + SF_SIZE <= ELEM, "double-buffered stage factors");
+static_assert(224 + FREC <= ELEM, "double-buffered F_t of the sequential tail");
+static_assert(SQ_H + 20 <= WA_COL, "sequential-stage temporaries");
 
 // Every stage's factors for the guessed free sets and clamped offsets into
 // SF (one job per stage and row).
@@ -1001,10 +1009,6 @@ __global__ void __launch_bounds__(SW * 32, 1) k_scan_ric(const __grid_constant__
         P.iters[b] = iters;
         if (fail) P.status[b] = ST_NONPD;
     }
-}
-
-size_t scan_smem_bytes(int dtype_f64) {
-    return (size_t)SW * WA_SIZE * (dtype_f64 ? sizeof(double) : sizeof(float));
 }
 
 template <typename T> cudaError_t prepare_scan() {
