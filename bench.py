@@ -525,6 +525,7 @@ def side_configs(dev, flush, reps=3):
         sol.close()
     out["mem"] = dict(workload=f"B={Bm}, N={Nm}, per-stage Q and x_ref, fwd+bwd", **mem)
     out["hover_latency"] = hover_latency(dev, flush)
+    out["policy_latency"] = policy_latency(dev, flush)
     out["closed_loop_track"] = closed_loop_track(dev)
     out["general_cost"] = general_cost_track(dev, flush, reps)
     out["costmap_fused"] = costmap_fused_track(dev, flush)
@@ -647,6 +648,46 @@ def general_cost_track(dev, flush, reps, B=4096, N=20):
                launch=list(sol.launch_shape(B, N)))
     sol.close()
     return res
+
+
+def policy_latency(dev, flush, reps=30):
+    """Per-call latency of a policy inference in the setting of the paper's
+    Table IV: one observation -> cost map (26 -> 512 -> 512 -> T * 13, random
+    init) writing Q_t -> MPC forward with exactly K iterations (tol 0), for T
+    in {2, 5, 10} and K in {1, 5, 10}, one race-track instance.  Eager calls,
+    CUDA events around the cost map and the solve on their stream, L2 flushed
+    before each; medians of `reps` calls."""
+    import torch
+    from paper_2605_29155_gb300 import CostMap, DiffMPC, Problem
+    stream = torch.cuda.current_stream()
+    rows = []
+    for Th in (2, 5, 10):
+        prob = W.race_track(1, Th, seed=5)
+        p = Problem.from_numpy(dict(prob, Q=np.ones((1, Th, 13))), device=dev)
+        cm = CostMap(W.costmap_weights(26, Th * 13, seed=6), Th, 1)
+        for Kh in (1, 5, 10):
+            sol = DiffMPC(N_max=Th, B_max=1, max_iter=Kh, tol=0.0, device=dev)
+            s = sol.alloc_solution(1, Th)
+            for _ in range(3):
+                cm.forward(p.x0, p.x_ref, Q=p.Q)
+                sol.solve(p, s)
+            torch.cuda.synchronize()
+            ts = []
+            for _ in range(reps):
+                flush.fill_(1.0)
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                cm.forward(p.x0, p.x_ref, Q=p.Q)
+                sol.solve(p, s)
+                e1.record(stream)
+                e1.synchronize()
+                ts.append(e0.elapsed_time(e1))
+            rows.append(dict(T=Th, K=Kh, device_ms=statistics.median(ts), iters=int(s.iters[0]),
+                             wait_flag=cm.wait_flag()))
+            sol.close()
+    return dict(workload="one race-track observation -> cost map -> MPC forward with exactly K iterations, "
+                         "eager calls, medians of %d" % reps, rows=rows)
 
 
 def closed_loop_track(dev, B=4096, N=20, K=50):
