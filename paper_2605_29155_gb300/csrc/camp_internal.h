@@ -21,7 +21,7 @@ cudaError_t launch_forward(const Params<T>& P, int exec_mode, int nw, int grid, 
 // launch over P.B instances (one per block), workspace size and dynamic shared
 // memory.
 template <typename T> cudaError_t prepare_scan();
-template <typename T> cudaError_t launch_scan_ric(const Params<T>& P, cudaStream_t st);
+template <typename T> cudaError_t launch_scan_ric(const Params<T>& P, cudaStream_t st, int final_fac);
 size_t scan_ws_elems(size_t slots, int N);
 template <typename T>
 cudaError_t launch_backward(const Params<T>& P, const AdjArgs<T>& A, int nw, int grid, int* order_ws,

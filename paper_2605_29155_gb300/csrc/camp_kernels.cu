@@ -294,13 +294,19 @@ cudaError_t launch_forward(const Params<T>& Pin, int exec_mode, int nw, int grid
     launch_nw<T>(nw, blocks, st, P, A, PH_INIT, 0);
     for (int it = 0; it < P.max_iter; ++it) {
         if (scan && !P.Cg) {
-            if ((e = launch_scan_ric<T>(P, st))) return e;
+            if ((e = launch_scan_ric<T>(P, st, 0))) return e;
         } else {
             launch_nw<T>(nw, blocks, st, P, A, PH_RIC, 0);
         }
         launch_nw<T>(nw, blocks, st, P, A, PH_LS, it == P.max_iter - 1);
     }
-    if (P.store_all) launch_nw<T>(nw, blocks, st, P, A, PH_FRIC, 0);
+    if (P.store_all) {
+        if (scan && !P.Cg) {
+            if ((e = launch_scan_ric<T>(P, st, 1))) return e;
+        } else {
+            launch_nw<T>(nw, blocks, st, P, A, PH_FRIC, 0);
+        }
+    }
     launch_nw<T>(nw, blocks, st, P, A, PH_END, 0);
     return cudaGetLastError();
 }

@@ -841,7 +841,7 @@ __device__ bool seq_stage(const Params<T>& P, const ScanWs<T>& W, const ScanShar
 // V_{t+1} A_t, and k_t into the stage records (one job per stage and state
 // column).
 template <typename T>
-__device__ void write_gains(const Params<T>& P, const ScanWs<T>& W, int pos, int n) {
+__device__ void write_gains(const Params<T>& P, const ScanWs<T>& W, int pos, int n, int b, bool tape) {
     for (int job = threadIdx.x; job < n * NX; job += blockDim.x) {
         const int t = job / NX, c = job - NX * t;
         const T* F = W.F + (size_t)t * FREC;
@@ -873,6 +873,22 @@ __device__ void write_gains(const Params<T>& P, const ScanWs<T>& W, int pos, int
 #pragma unroll
         for (int a = 0; a < 4; ++a) rhs[a] = ((mask >> a) & 1) ? qc[a] : T(0);
         chol_solve4(Lf, rhs, y);
+        if (tape) {
+            // the tape record of stage t: computed column c of F_t (c < 11),
+            // column c of K_t, and with c == 0 the masked factor and the mask
+#pragma unroll
+            for (int a = 0; a < NU; ++a) P.tape[trow(P, b, t, T_K + a * NX + c)] = ((mask >> a) & 1) ? -y[a] : T(0);
+            if (c < NGC) {
+#pragma unroll
+                for (int i = 0; i < NX; ++i) P.tape[trow(P, b, t, T_F + c * NX + i)] = F[i * NZ + gcol(c)];
+            }
+            if (c == 0) {
+#pragma unroll
+                for (int i = 0; i < NL; ++i) P.tape[trow(P, b, t, T_L + i)] = Lf[i];
+                P.tape[trow(P, b, t, T_M)] = (T)mask;
+            }
+            continue;
+        }
 #pragma unroll
         for (int a = 0; a < NU; ++a) grow[(R_K + a * NX + c) * GW] = ((mask >> a) & 1) ? -y[a] : T(0);
         if (c == 0) {
@@ -889,7 +905,7 @@ __device__ void write_gains(const Params<T>& P, const ScanWs<T>& W, int pos, int
 // the iteration and sets NONPD on a non-positive pivot -- what k_mpc's Riccati
 // phase does for an instance, with the stages in parallel.
 template <typename T>
-__global__ void __launch_bounds__(SW * 32, 1) k_scan_ric(const __grid_constant__ Params<T> P) {
+__global__ void __launch_bounds__(SW * 32, 1) k_scan_ric(const __grid_constant__ Params<T> P, int final_fac) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* wa = reinterpret_cast<T*>(smem_raw) + (size_t)(threadIdx.x >> 5) * WA_SIZE;
     __shared__ ScanShared<T> sh;
@@ -899,8 +915,13 @@ __global__ void __launch_bounds__(SW * 32, 1) k_scan_ric(const __grid_constant__
     const int b = P.order ? P.order[pos] : pos;
     int n = P.horizon ? P.horizon[b] : P.N;
     n = n < 1 ? 1 : (n > P.N ? P.N : n);
-    if (P.status[b] != ST_RUNNING) return;                 // the same in every thread
-    const int iters = P.iters[b] + 1;
+    // an iteration's Riccati phase runs for a running instance and counts the
+    // iteration; the final factorization (into the tape) runs for a finished
+    // one, after the iterations
+    const int st0 = P.status[b];                            // the same in every thread
+    if (final_fac ? !(st0 == ST_CONVERGED || st0 == ST_STALLED || st0 == ST_MAX_ITER) : st0 != ST_RUNNING) return;
+    const int done = P.iters[b];                            // iterations before this phase
+    const int iters = final_fac ? done : done + 1;
     const ScanWs<T> W = scan_ws(P.scan, pos, P.N_ws);
     const int tid = threadIdx.x;
     if (tid < 4 * NU) {
@@ -921,8 +942,8 @@ __global__ void __launch_bounds__(SW * 32, 1) k_scan_ric(const __grid_constant__
             G[G_QD + i] = q;
             G[G_Q + i] = q * ((sr[(R_X + i) * GW] - sr[(R_XR + i) * GW]) + sr[(R_XL + i) * GW]);
         }
-        const int pm = iters > 1 ? (int)G[G_M] : 15;
-        const int ps = iters > 1 ? (int)G[G_SIDE] : 0;
+        const int pm = done >= 1 ? (int)G[G_M] : 15;
+        const int ps = done >= 1 ? (int)G[G_SIDE] : 0;
 #pragma unroll
         for (int a = 0; a < NU; ++a) {
             const T u = sr[(R_U + a) * GW];
@@ -1004,7 +1025,7 @@ __global__ void __launch_bounds__(SW * 32, 1) k_scan_ric(const __grid_constant__
         __syncthreads();
         fail = sh.fail != 0;
     }
-    if (!fail) write_gains(P, W, pos, n);
+    if (!fail) write_gains(P, W, pos, n, b, final_fac != 0);
     if (tid == 0) {
         P.iters[b] = iters;
         if (fail) P.status[b] = ST_NONPD;
@@ -1016,14 +1037,14 @@ template <typename T> cudaError_t prepare_scan() {
                                 (int)((size_t)SW * WA_SIZE * sizeof(T)));
 }
 
-template <typename T> cudaError_t launch_scan_ric(const Params<T>& P, cudaStream_t st) {
-    k_scan_ric<T><<<P.B, SW * 32, (size_t)SW * WA_SIZE * sizeof(T), st>>>(P);
+template <typename T> cudaError_t launch_scan_ric(const Params<T>& P, cudaStream_t st, int final_fac) {
+    k_scan_ric<T><<<P.B, SW * 32, (size_t)SW * WA_SIZE * sizeof(T), st>>>(P, final_fac);
     return cudaGetLastError();
 }
 
 template cudaError_t prepare_scan<float>();
 template cudaError_t prepare_scan<double>();
-template cudaError_t launch_scan_ric<float>(const Params<float>&, cudaStream_t);
-template cudaError_t launch_scan_ric<double>(const Params<double>&, cudaStream_t);
+template cudaError_t launch_scan_ric<float>(const Params<float>&, cudaStream_t, int);
+template cudaError_t launch_scan_ric<double>(const Params<double>&, cudaStream_t, int);
 
 }  // namespace camp
