@@ -787,10 +787,9 @@ def hover_latency(dev, flush, reps=30):
                        fwd_wall_ms=med["fwd_wall"], bwd_wall_ms=med["bwd_wall"],
                        iters=float(s.iters.float().mean()), launch=list(sol.launch_shape(Bh, Nh)))
             sol.close()
-            # the stage-parallel Riccati form (one instance per block; the
-            # backward re-factors, so the forward keeps no tape)
-            sc = DiffMPC(N_max=Nh, B_max=Bh, max_iter=5, tol=0.0, device=dev, exec_mode="scan",
-                         store_mode="recompute")
+            # the stage-parallel Riccati form (one instance per block; its
+            # final factorization writes the tape the backward replays)
+            sc = DiffMPC(N_max=Nh, B_max=Bh, max_iter=5, tol=0.0, device=dev, exec_mode="scan")
             ss = sc.alloc_solution(Bh, Nh)
             for _ in range(3):
                 sc.solve(p, ss)
@@ -814,8 +813,8 @@ def hover_latency(dev, flush, reps=30):
             sc.close()
             rows.append(row)
     return dict(workload="hover stabilisation at random targets, exactly 5 iterations (tol 0), fwd and bwd "
-                         "per eager API call, medians of %d; scan_*: exec_mode scan (stage-parallel Riccati), "
-                         "recompute" % reps, rows=rows)
+                         "per eager API call, medians of %d; scan_*: exec_mode scan (stage-parallel Riccati)" % reps,
+                rows=rows)
 
 
 def run_kernels_only(args):
