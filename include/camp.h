@@ -66,13 +66,21 @@ extern "C" {
 #define MPC_EXEC_SCAN       2  /* the plain form with one instance per block and the     */
                                /* Riccati recursion of Sec. IV-2 in parallel over the   */
                                /* stages: the associative-scan LQR of the related work  */
-                               /* in Sec. II, run to a fixed point of the box QPs' free  */
-                               /* sets (same K_t, k_t as the sequential recursion up to */
-                               /* rounding).  For small batches and long horizons.      */
-                               /* The general cost keeps the sequential Riccati phase.  */
-                               /* Needs R > 0 (the elements use R^-1).  mpc_create      */
-                               /* allocates about (N_max * 1.6k + 9k) * sizeof(dtype)   */
-                               /* bytes more per instance of B_max.                      */
+                               /* in Sec. II on the box QPs' free sets of the previous  */
+                               /* iteration, then the stages whose QP disagrees solved  */
+                               /* sequentially (same K_t, k_t as the sequential         */
+                               /* recursion up to rounding).  For small batches and     */
+                               /* long horizons.  The general cost keeps the sequential */
+                               /* Riccati phase.  Needs R > 0 (the elements use R^-1).  */
+                               /* mpc_create allocates about                            */
+                               /* (N_max * 0.75k + 8.5k) * sizeof(dtype) bytes more per */
+                               /* instance of B_max.                                    */
+#define MPC_EXEC_AUTO       3  /* persistent or scan, whichever mpc_autotune measures     */
+                               /* faster on the caller's problem (persistent until it   */
+                               /* has run; mpc_exec_form tells which).  Which one wins  */
+                               /* depends on the problem, not only its shape: a few     */
+                               /* instances whose saturations settle early favour the   */
+                               /* scan.  Allocates the scan workspace.                  */
 
 /* per-instance status written by mpc_solve_fwd */
 #define MPC_ST_CONVERGED  0    /* max_t |u^k_t - u^(k-1)_t|_inf < tol after a step      */
@@ -99,7 +107,7 @@ typedef struct mpc_config {
     int    n_alpha;         /* number of line-search coefficients, 1..4                */
     double alpha[4];        /* coefficients in (0, 1], default {1, .5, .25, .1}        */
     int    store_mode;      /* MPC_STORE_ALL, MPC_RECOMPUTE or MPC_STORE_AUTO          */
-    int    exec_mode;       /* MPC_EXEC_PERSISTENT, MPC_EXEC_PLAIN or MPC_EXEC_SCAN    */
+    int    exec_mode;       /* MPC_EXEC_PERSISTENT, _PLAIN, _SCAN or _AUTO             */
     int    tpi;             /* threads per instance = warps per block: 0 (4 until      */
                             /* mpc_autotune picks), 4 or 8                              */
     int    ipb;             /* instances per block (one per lane): 0 (auto) or 1..32,  */
@@ -200,9 +208,16 @@ int mpc_solve_bwd_general(mpc_handle *h, const mpc_problem *p, const mpc_solutio
  * instances per block; a nonzero tpi or ipb in the config pins that value) on
  * this problem (overwriting *s), keep the fastest in the handle and report its
  * ipb in *ipb_out (may be NULL; mpc_launch_shape gives the whole shape).
- * Synchronises `stream`; not capturable. */
+ * Under MPC_EXEC_AUTO it then times the stage-parallel form (MPC_EXEC_SCAN) at
+ * the best warp count and keeps whichever form was faster.  MPC_ERR_STATE for
+ * the plain and scan forms.  Synchronises `stream`; not capturable. */
 int mpc_autotune(mpc_handle *h, const mpc_problem *p, mpc_solution *s,
                  cudaStream_t stream, int *ipb_out);
+
+/* The launch form the handle's solves use (MPC_EXEC_PERSISTENT, _PLAIN or
+ * _SCAN): the config's, or under MPC_EXEC_AUTO the one mpc_autotune chose
+ * (persistent before it has run).  MPC_ERR_ARG for NULL arguments. */
+int mpc_exec_form(const mpc_handle *h, int *exec);
 
 /* Launch shape the next persistent forward on (B, N) will use: threads per
  * instance, instances per block, blocks.  Any out pointer may be NULL. */

@@ -15,11 +15,11 @@ LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libcamp.so"
 MPC_OK, MPC_ERR_ARG, MPC_ERR_SHAPE, MPC_ERR_CUDA, MPC_ERR_TIMEOUT, MPC_ERR_STATE = 0, -1, -2, -3, -4, -5
 MPC_F32, MPC_F64 = 0, 1
 MPC_STORE_ALL, MPC_RECOMPUTE, MPC_STORE_AUTO = 0, 1, 2
-MPC_EXEC_PERSISTENT, MPC_EXEC_PLAIN, MPC_EXEC_SCAN = 0, 1, 2
+MPC_EXEC_PERSISTENT, MPC_EXEC_PLAIN, MPC_EXEC_SCAN, MPC_EXEC_AUTO = 0, 1, 2, 3
 MPC_ST_CONVERGED, MPC_ST_STALLED, MPC_ST_MAX_ITER, MPC_ST_NONFINITE, MPC_ST_NONPD = 0, 1, 2, 3, 4
 
 EXPORTED = ("mpc_config_default", "mpc_create", "mpc_destroy", "mpc_tape_bytes", "mpc_solve_fwd",
-            "mpc_solve_bwd", "mpc_autotune", "mpc_launch_shape", "mpc_launch_count", "mpc_strerror",
+            "mpc_solve_bwd", "mpc_autotune", "mpc_exec_form", "mpc_launch_shape", "mpc_launch_count", "mpc_strerror",
             "mpc_status_str", "mpc_solve_fwd_noalloc", "mpc_solve_bwd_general", "mpc_fp32_fma_probe",
             "mpc_costmap_workspace_bytes", "mpc_costmap_forward", "mpc_costmap_backward")
 MPC_NOALLOC_B_MAX, MPC_NOALLOC_N_MAX = 256, 40
@@ -74,6 +74,8 @@ def _load():
     lib.mpc_solve_bwd_general.restype = c_int
     lib.mpc_autotune.argtypes = [c_void_p, POINTER(mpc_problem), POINTER(mpc_solution), c_void_p, POINTER(c_int)]
     lib.mpc_autotune.restype = c_int
+    lib.mpc_exec_form.argtypes = [c_void_p, POINTER(c_int)]
+    lib.mpc_exec_form.restype = c_int
     lib.mpc_launch_shape.argtypes = [c_void_p, c_int, c_int, POINTER(c_int), POINTER(c_int), POINTER(c_int)]
     lib.mpc_launch_shape.restype = c_int
     lib.mpc_launch_count.argtypes = [c_void_p, c_int, POINTER(c_int), POINTER(c_int)]
@@ -154,6 +156,13 @@ def mpc_autotune(h, prob: mpc_problem, sol: mpc_solution, stream: int):
     ipb = c_int(0)
     code = _lib.mpc_autotune(h, byref(prob), byref(sol), c_void_p(stream), byref(ipb))
     return code, ipb.value
+
+
+def mpc_exec_form(h):
+    """Returns (code, exec form)."""
+    e = c_int(0)
+    code = _lib.mpc_exec_form(h, byref(e))
+    return code, e.value
 
 
 def mpc_launch_shape(h, B: int, N: int):

@@ -17,7 +17,9 @@ struct mpc_handle {
     void* ws;               // one allocation holding every scratch region
     size_t ws_bytes;
     void *stg, *cand, *kh;  // per-stage records, line-search candidates, adjoint k-hat
-    void* scan;             // stage-parallel Riccati workspace (MPC_EXEC_SCAN only)
+    void* scan;             // stage-parallel Riccati workspace (MPC_EXEC_SCAN and MPC_EXEC_AUTO)
+    int exec;               // the launch form solves use: the config's, or under MPC_EXEC_AUTO
+                            // the one mpc_autotune measured faster (persistent until then)
     int* queue;             // [2] work-queue tickets (forward, backward)
     int* order;             // [B_max] longest-horizon-first order
     int tpi;                // threads per instance (warps per block): 4 or 8
@@ -75,7 +77,8 @@ static int validate_config(const mpc_config* c) {
         if (!(c->alpha[i] > 0.0 && c->alpha[i] <= 1.0)) return MPC_ERR_ARG;
     if (c->store_mode != MPC_STORE_ALL && c->store_mode != MPC_RECOMPUTE && c->store_mode != MPC_STORE_AUTO)
         return MPC_ERR_ARG;
-    if (c->exec_mode != MPC_EXEC_PERSISTENT && c->exec_mode != MPC_EXEC_PLAIN && c->exec_mode != MPC_EXEC_SCAN)
+    if (c->exec_mode != MPC_EXEC_PERSISTENT && c->exec_mode != MPC_EXEC_PLAIN && c->exec_mode != MPC_EXEC_SCAN &&
+        c->exec_mode != MPC_EXEC_AUTO)
         return MPC_ERR_ARG;
     if (c->tpi != 0 && c->tpi != 4 && c->tpi != 8) return MPC_ERR_ARG;
     if (c->ipb < 0 || c->ipb > (c->dtype == MPC_F64 ? 16 : 32)) return MPC_ERR_ARG;
@@ -98,7 +101,9 @@ extern "C" int mpc_create(const mpc_config* cfg, mpc_handle** out) {
         return MPC_ERR_CUDA;
     }
     cudaError_t pe = cfg->dtype == MPC_F64 ? prepare_kernels<double>() : prepare_kernels<float>();
-    if (pe == cudaSuccess && cfg->exec_mode == MPC_EXEC_SCAN)
+    const bool with_scan = cfg->exec_mode == MPC_EXEC_SCAN || cfg->exec_mode == MPC_EXEC_AUTO;
+    h->exec = cfg->exec_mode == MPC_EXEC_AUTO ? MPC_EXEC_PERSISTENT : cfg->exec_mode;
+    if (pe == cudaSuccess && with_scan)
         pe = cfg->dtype == MPC_F64 ? prepare_scan<double>() : prepare_scan<float>();
     if (pe != cudaSuccess) { free(h); return MPC_ERR_CUDA; }
     if (cfg->store_mode == MPC_STORE_AUTO) {
@@ -116,7 +121,7 @@ extern "C" int mpc_create(const mpc_config* cfg, mpc_handle** out) {
     const size_t bH = align256(kh_elems(S, Nw) * es);
     const size_t bQ = align256(2 * sizeof(int));
     const size_t bO = align256((size_t)cfg->B_max * sizeof(int));
-    const size_t bP = cfg->exec_mode == MPC_EXEC_SCAN ? align256(scan_ws_elems(S, Nw) * es) : 0;
+    const size_t bP = with_scan ? align256(scan_ws_elems(S, Nw) * es) : 0;
     h->ws_bytes = bS + bC + bH + bQ + bO + bP;
     if (cudaMalloc(&h->ws, h->ws_bytes) != cudaSuccess) { free(h); return MPC_ERR_CUDA; }
     // All-ones bytes are NaN in float and double: a read of scratch that no
@@ -248,10 +253,10 @@ extern "C" int mpc_solve_fwd(mpc_handle* h, const mpc_problem* p, mpc_solution* 
     const int grid = grid_for(h, p->B, ipb);
     if (h->cfg.dtype == MPC_F64) {
         const Params<double> P = make_params<double>(h, p, s, ipb);
-        e = launch_forward<double>(P, h->cfg.exec_mode, h->tpi, grid, h->order, stream);
+        e = launch_forward<double>(P, h->exec, h->tpi, grid, h->order, stream);
     } else {
         const Params<float> P = make_params<float>(h, p, s, ipb);
-        e = launch_forward<float>(P, h->cfg.exec_mode, h->tpi, grid, h->order, stream);
+        e = launch_forward<float>(P, h->exec, h->tpi, grid, h->order, stream);
     }
     return e == cudaSuccess ? MPC_OK : MPC_ERR_CUDA;
 }
@@ -315,9 +320,11 @@ extern "C" int mpc_autotune(mpc_handle* h, const mpc_problem* p, mpc_solution* s
                             int* ipb_out) {
     int r = check_problem(h, p);
     if (r != MPC_OK) return r;
-    if (h->cfg.exec_mode != MPC_EXEC_PERSISTENT) return MPC_ERR_STATE;
+    const bool auto_form = h->cfg.exec_mode == MPC_EXEC_AUTO;
+    if (h->cfg.exec_mode != MPC_EXEC_PERSISTENT && !auto_form) return MPC_ERR_STATE;
     if (p->B == 0) { if (ipb_out) *ipb_out = ipb_for(h, 0); return MPC_OK; }
-    const int keep_tpi = h->tpi, keep_ipb = h->ipb;
+    const int keep_tpi = h->tpi, keep_ipb = h->ipb, keep_exec = h->exec;
+    h->exec = MPC_EXEC_PERSISTENT;
     // candidate instances per block: one, two, three or four blocks' worth per
     // SM, and full packs (fewer blocks than SMs when the batch is small)
     int cands[5], nc = 0;
@@ -351,12 +358,38 @@ extern "C" int mpc_autotune(mpc_handle* h, const mpc_problem* p, mpc_solution* s
             if (ms < best_ms) { best_ms = ms; best_tpi = tpis[ti]; best_ipb = ipb; }
         }
     }
+    // MPC_EXEC_AUTO: the stage-parallel form at the best warp count, against
+    // the best persistent shape
+    int best_exec = MPC_EXEC_PERSISTENT;
+    if (auto_form && r == MPC_OK) {
+        h->tpi = best_tpi;
+        h->exec = MPC_EXEC_SCAN;
+        if ((r = mpc_solve_fwd(h, p, s, stream)) == MPC_OK) {
+            cudaEventRecord(e0, stream);
+            for (int rep = 0; rep < 3 && r == MPC_OK; ++rep) r = mpc_solve_fwd(h, p, s, stream);
+            cudaEventRecord(e1, stream);
+            if (r != MPC_OK || cudaEventSynchronize(e1) != cudaSuccess) {
+                r = MPC_ERR_CUDA;
+            } else {
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (ms < best_ms) best_exec = MPC_EXEC_SCAN;
+            }
+        }
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     h->tpi = r == MPC_OK ? best_tpi : keep_tpi;
     h->ipb = r == MPC_OK ? best_ipb : keep_ipb;
+    h->exec = r == MPC_OK ? best_exec : keep_exec;
     if (ipb_out) *ipb_out = ipb_for(h, p->B);
     return r;
+}
+
+extern "C" int mpc_exec_form(const mpc_handle* h, int* exec) {
+    if (!h || !exec) return MPC_ERR_ARG;
+    *exec = h->exec;
+    return MPC_OK;
 }
 
 extern "C" int mpc_launch_shape(const mpc_handle* h, int B, int N, int* tpi, int* ipb, int* grid) {
@@ -372,7 +405,7 @@ extern "C" int mpc_launch_count(const mpc_handle* h, int has_horizon, int* fwd, 
     if (!h) return MPC_ERR_ARG;
     const int hz = has_horizon ? 1 : 0;
     if (fwd) {
-        if (h->cfg.exec_mode == MPC_EXEC_PERSISTENT) *fwd = 1 + hz;
+        if (h->exec == MPC_EXEC_PERSISTENT) *fwd = 1 + hz;
         else *fwd = hz + 2 + 2 * h->cfg.max_iter + (stores_tape(h, h->cfg.B_max, h->cfg.N_max) ? 1 : 0);
     }
     if (bwd) *bwd = 1 + hz;

@@ -92,7 +92,8 @@ class DiffMPC:
         if store_mode not in modes:
             raise ValueError(f"store_mode must be one of {sorted(modes)}")
         cfg.store_mode = modes[store_mode]
-        modes = {"persistent": camp.MPC_EXEC_PERSISTENT, "plain": camp.MPC_EXEC_PLAIN, "scan": camp.MPC_EXEC_SCAN}
+        modes = {"persistent": camp.MPC_EXEC_PERSISTENT, "plain": camp.MPC_EXEC_PLAIN, "scan": camp.MPC_EXEC_SCAN,
+                 "auto": camp.MPC_EXEC_AUTO}
         if exec_mode not in modes:
             raise ValueError(f"exec_mode must be one of {sorted(modes)}")
         cfg.exec_mode = modes[exec_mode]
@@ -191,6 +192,14 @@ class DiffMPC:
         code, ipb = camp.mpc_autotune(self.h, self._cproblem(p), self._csolution(s), stream)
         camp.check(code, "mpc_autotune")
         return ipb
+
+    @property
+    def exec_form(self) -> str:
+        """The launch form solves use: "persistent", "plain" or "scan" (under
+        exec_mode "auto", the one autotune measured faster)."""
+        code, e = camp.mpc_exec_form(self.h)
+        camp.check(code, "mpc_exec_form")
+        return {camp.MPC_EXEC_PERSISTENT: "persistent", camp.MPC_EXEC_PLAIN: "plain", camp.MPC_EXEC_SCAN: "scan"}[e]
 
     def launch_shape(self, B, N):
         code, tpi, ipb, grid = camp.mpc_launch_shape(self.h, B, N)

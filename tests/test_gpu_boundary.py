@@ -1,5 +1,6 @@
-"""The boundary's configuration on the GPU: the launch-shape autotuner and
-the automatic choice between storing the tape and recomputing it."""
+"""The boundary's configuration on the GPU: the launch-shape autotuner, the
+automatic choice of launch form, and the automatic choice between storing
+the tape and recomputing it."""
 import numpy as np
 import pytest
 
@@ -44,6 +45,34 @@ def test_autotune_picks_a_valid_shape_and_solves_as_the_pinned_shape():
     assert pinned.launch_shape(B, N) == (tpi, ipb, grid)
     b = _solve(pinned, prob)
     pinned.close()
+    for k in a:
+        np.testing.assert_array_equal(a[k], b[k], err_msg=k)
+
+
+@pytest.mark.parametrize("name,B,N", [("hover", 2, 40), ("track", 8, 20)])
+def test_auto_form_keeps_the_faster_form_and_solves_as_it(name, B, N):
+    """exec_mode "auto": persistent until autotune has run; autotune times the
+    persistent shapes and the stage-parallel form on the problem and keeps the
+    faster; a solve then equals one on a handle fixed to that form (and, for
+    the persistent form, that shape) bit for bit."""
+    from paper_2605_29155_gb300 import DiffMPC, Problem
+    prob = cached_problem(name, B, N, 4)
+    p = Problem.from_numpy(prob)
+    auto = DiffMPC(N_max=N, B_max=B, max_iter=8, tol=1e-6, exec_mode="auto")
+    assert auto.exec_form == "persistent"
+    auto.autotune(p)
+    form = auto.exec_form
+    tpi, ipb, _ = auto.launch_shape(B, N)
+    print(name, B, N, "auto keeps", form, "tpi", tpi, "ipb", ipb)
+    assert form in ("persistent", "scan")
+    a = _solve(auto, prob)
+    auto.close()
+    if form == "scan":
+        fixed = DiffMPC(N_max=N, B_max=B, max_iter=8, tol=1e-6, exec_mode="scan", tpi=tpi)
+    else:
+        fixed = DiffMPC(N_max=N, B_max=B, max_iter=8, tol=1e-6, tpi=tpi, ipb=ipb)
+    b = _solve(fixed, prob)
+    fixed.close()
     for k in a:
         np.testing.assert_array_equal(a[k], b[k], err_msg=k)
 
