@@ -73,7 +73,7 @@ extern "C" {
                                /* long horizons.  The general cost keeps the sequential */
                                /* Riccati phase.  Needs R > 0 (the elements use R^-1).  */
                                /* mpc_create allocates about                            */
-                               /* (N_max * 0.75k + 8.5k) * sizeof(dtype) bytes more per */
+                               /* (N_max * 0.8k + 8.5k) * sizeof(dtype) bytes more per  */
                                /* instance of B_max.                                    */
 #define MPC_EXEC_AUTO       3  /* persistent or scan, whichever mpc_autotune measures     */
                                /* faster on the caller's problem (persistent until it   */

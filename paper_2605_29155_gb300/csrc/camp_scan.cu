@@ -20,7 +20,10 @@
 // stage t: V_t = J(S_t), v_t = -eta(S_t).  M C_i and J_j M are symmetric
 // ((C_i^-1 + J_j)^-1 and (J_j^-1 + C_i)^-1) and are symmetrized, as are C and
 // J.  In FP32, composing the elements' transition parts (A, b, C) still costs
-// the costate about two digits against the sequential recursion.
+// the costate about two digits against the sequential recursion; a costate
+// pass (refine_costate) then reruns the recursion's vector part sequentially,
+// so that k_t, the step the line search takes, carries the sequential form's
+// rounding.
 //
 // The free sets.  The box QP makes the recursion depend on free-set decisions.
 // The scan therefore takes every stage's free set and clamped offsets as a
@@ -35,7 +38,10 @@
 // sequential recursion.  Either way every stage's QP is the one the
 // sequential recursion solves (same V_{t+1} up to rounding), so k_t, K_t and
 // the free sets are the sequential method's.  A non-positive pivot at a final
-// stage ends the solve as in the sequential recursion (status NONPD).
+// stage ends the solve as in the sequential recursion (status NONPD).  The
+// final factorization at the returned iterate (the tape the backward replays)
+// runs the sequential recursion for every stage: the gradients then carry the
+// sequential form's FP32 rounding.
 //
 // The scan on SW warps: chunk w holds ch = ceil(n / SW) consecutive stages.
 // (A) Each warp folds its chunk into one element from the back, (B) the
@@ -59,10 +65,12 @@ constexpr int SV = M13 + NX;           // J and eta of a stage's suffix
 // Per-stage record of the scan: QP data and results.
 //   H (4 x 4), g, q (13), r (4), k, masked factor (NL), free mask, ok,
 //   the guessed clamped offsets and free mask, the clamped sides (bit a: at the
-//   upper bound) of the last result (the next iteration's guess), diag(Q_t)
+//   upper bound) of the last result (the next iteration's guess), diag(Q_t),
+//   Q_ux (4 x 13, row-major)
 constexpr int G_H = 0, G_G = 16, G_Q = 20, G_R = 33, G_K = 37, G_L = 41, G_M = 55, G_OK = 56, G_DC = 57,
-              G_AM = 61, G_SIDE = 62, G_QD = 64, GREC = 80;
+              G_AM = 61, G_SIDE = 62, G_QD = 64, G_QU = 80, GREC = 136;
 constexpr int FREC = NX * NZ;          // F_t = [A_t B_t], row-major 13 x 17
+constexpr int FSTR = 224;              // F_t's stride: 16-byte aligned records
 // A stage's factors for the single-stage steps: A_t, G = B_f R_f^-1/2 (13 x 4),
 // b_t, eta_t = -q_t, diag Q_t
 constexpr int SF_A = 0, SF_G = M13, SF_B = M13 + 52, SF_E = M13 + 52 + NX, SF_Q = M13 + 52 + 2 * NX,
@@ -70,7 +78,8 @@ constexpr int SF_A = 0, SF_G = M13, SF_B = M13 + 52, SF_E = M13 + 52 + NX, SF_Q 
 
 // Elements of one position's workspace for horizons up to N.
 __host__ __device__ constexpr size_t scan_pos_elems(int N) {
-    return (size_t)N * (FREC + SV + GREC + SF_SIZE) + (size_t)2 * SW * ELEM;
+    // F and G first, their records 16-byte aligned; the total a multiple of 4
+    return ((size_t)N * (FSTR + GREC + SV + SF_SIZE) + (size_t)2 * SW * ELEM + 3) / 4 * 4;
 }
 size_t scan_ws_elems(size_t slots, int N) { return slots * scan_pos_elems(N); }
 
@@ -80,9 +89,9 @@ template <typename T> struct ScanWs {
 template <typename T> __device__ __forceinline__ ScanWs<T> scan_ws(T* base, int pos, int N) {
     T* p = base + (size_t)pos * scan_pos_elems(N);
     ScanWs<T> w;
-    w.F = p; p += (size_t)N * FREC;
-    w.Sv = p; p += (size_t)N * SV;
+    w.F = p; p += (size_t)N * FSTR;
     w.G = p; p += (size_t)N * GREC;
+    w.Sv = p; p += (size_t)N * SV;
     w.SF = p; p += (size_t)N * SF_SIZE;
     w.Uc = p;
     return w;
@@ -300,6 +309,7 @@ constexpr int ST_JG = 0, ST_S = 52, ST_Y = 68, ST_Z = 84, ST_W4 = 136, ST_ZV = 1
 static_assert(WA_O + ST_SIZE <= WA_SIZE, "step temporaries");
 static_assert(264 + SF_SIZE <= ELEM, "double-buffered stage factors");
 static_assert(224 + FREC <= ELEM, "double-buffered F_t of the sequential tail");
+static_assert(FSTR >= FREC && FSTR % 4 == 0 && GREC % 4 == 0, "F and G records start on 16 bytes");
 static_assert(SQ_H + 20 <= WA_COL, "sequential-stage temporaries");
 
 // Every stage's factors for the guessed free sets and clamped offsets into
@@ -307,7 +317,7 @@ static_assert(SQ_H + 20 <= WA_COL, "sequential-stage temporaries");
 template <typename T> __device__ void stage_factors_all(const ScanWs<T>& W, const ScanShared<T>& sh, int n) {
     for (int job = threadIdx.x; job < n * NX; job += blockDim.x) {
         const int t = job / NX, i = job - NX * t;
-        const T* F = W.F + (size_t)t * FREC + i * NZ;
+        const T* F = W.F + (size_t)t * FSTR + i * NZ;
         const T* G = W.G + (size_t)t * GREC;
         T* sf = W.SF + (size_t)t * SF_SIZE;
         // every load first (one round trip), then the arithmetic
@@ -607,7 +617,7 @@ __device__ void scan_suffixes(const ScanWs<T>& W, const ScanShared<T>& sh, T* wa
 // a' <= a, and g_a = r_a + B_a' v_{t+1} (V_n = 0, v_n = 0).
 template <typename T>
 __device__ __forceinline__ void qp_column(const ScanWs<T>& W, const ScanShared<T>& sh, int t, int a, int n) {
-    const T* F = W.F + (size_t)t * FREC;
+    const T* F = W.F + (size_t)t * FSTR;
     T* G = W.G + (size_t)t * GREC;
     T vb[NX];
     T ga = G[G_R + a];
@@ -727,7 +737,7 @@ __device__ bool seq_stage(const Params<T>& P, const ScanWs<T>& W, const ScanShar
     T* Kt = wa + SQ_K;
     T* Hg = wa + SQ_H;                  // H (16, upper used), g (4)
     T* Vn = wa + SQ_V;
-    const T* G = W.G + (size_t)t * GREC;
+    T* G = W.G + (size_t)t * GREC;
     T d[4], Lf[NL];
     int mask;
     bool ok;
@@ -766,6 +776,7 @@ __device__ bool seq_stage(const Params<T>& P, const ScanWs<T>& W, const ScanShar
         }
         __syncwarp();
         qp_stage(P, W, sh, pos, t, lane == 0, Hg, Hg + 16, d, Lf, mask, ok);
+        if (lane < 20) G[lane < 16 ? G_H + lane : G_G + lane - 16] = Hg[lane];     // for the costate pass
         mask = __shfl_sync(FULL, mask, 0);
         ok = __shfl_sync(FULL, ok ? 1 : 0, 0) != 0;
 #pragma unroll
@@ -844,7 +855,7 @@ template <typename T>
 __device__ void write_gains(const Params<T>& P, const ScanWs<T>& W, int pos, int n, int b, bool tape) {
     for (int job = threadIdx.x; job < n * NX; job += blockDim.x) {
         const int t = job / NX, c = job - NX * t;
-        const T* F = W.F + (size_t)t * FREC;
+        const T* F = W.F + (size_t)t * FSTR;
         const T* G = W.G + (size_t)t * GREC;
         T* grow = P.stg + srow(P, pos, t, 0);
         T qc[NU] = {T(0), T(0), T(0), T(0)};
@@ -865,6 +876,10 @@ __device__ void write_gains(const Params<T>& P, const ScanWs<T>& W, int pos, int
                 for (int i = 0; i < NX; ++i) s += F[i * NZ + NX + a] * va[i];
                 qc[a] = s;
             }
+        }
+        if (!tape) {
+#pragma unroll
+            for (int a = 0; a < NU; ++a) W.G[(size_t)t * GREC + G_QU + a * NX + c] = qc[a];
         }
         const int mask = (int)G[G_M];
         T Lf[NL], rhs[4], y[4];
@@ -896,6 +911,133 @@ __device__ void write_gains(const Params<T>& P, const ScanWs<T>& W, int pos, int
             for (int a = 0; a < NU; ++a) grow[(R_KK + a) * GW] = G[G_K + a];
         }
     }
+}
+
+// The costate in the sequential recursion's precision.  The scan's v_t comes
+// out of composed transition parts (A, b, C), whose FP32 rounding reaches the
+// costate, and a converged solve's controls are the zero of that gradient.
+// With every stage's free set, factor, Q_uu and Q_ux as the phase found them,
+// the vector part of the recursion runs again on one warp, from the last stage
+// back:
+//   g = r_t + B_t' v_{t+1},   k_f = -Q_uu,ff^-1 (g_f + Q_uu,fc k_c)  (k_c: the
+//   clamped offsets),   v_t = q_t + A_t' v_{t+1} + Q_ux' k,
+// and k_t is rewritten in the stage records.  (The value update's K_t'(Q_uu k
+// + g) vanishes: Q_uu k + g is zero on the free set and K_t on the clamped
+// one.)  Q_uu and Q_ux come from the scan's V, but they multiply k, which is
+// small near convergence, so their rounding barely reaches v_t.  Matrix-vector
+// work only: v_{t+1} stays in lanes 0..12 and is broadcast by shuffles; each
+// stage's F_t and record are copied into a ring in shared memory (the whole
+// block's area, free by now) RC_RING - 1 stages ahead.
+constexpr int RC_F = 0, RC_G = FSTR, RC_SIZE = RC_G + GREC, RC_RING = 8;
+static_assert(RC_SIZE % 4 == 0, "ring slots start on 16 bytes");
+
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
+}
+static_assert(RC_RING * RC_SIZE <= SW * WA_SIZE, "the costate pass's ring fits the block's shared memory");
+
+// One stage's data of the costate pass, in the registers of each lane.
+template <typename T> struct RcStage {
+    T fc[NX];          // the lane's column of F_t
+    T base;            // q_t (lanes 0..12) or r_t (lanes 16..19) of that column
+    T qr[NU];          // Q_ux's column `lane`
+    T dc[NU];          // the clamped offsets
+    T H[NU][NU];       // Q_uu
+    T Lf[NL];          // its factor on the free set
+    int mask;          // the free set
+};
+
+template <typename T>
+__device__ __forceinline__ void rc_load(const T* S, int col, int cc, int li, RcStage<T>& d) {
+    const T* G = S + RC_G;
+#pragma unroll
+    for (int i = 0; i < NX; ++i) d.fc[i] = S[RC_F + i * NZ + cc];
+    d.base = col < 0 ? T(0) : (col < NX ? G[G_Q + col] : G[G_R + col - NX]);
+#pragma unroll
+    for (int a = 0; a < NU; ++a) {
+        d.qr[a] = G[G_QU + a * NX + li];
+        d.dc[a] = G[G_DC + a];
+#pragma unroll
+        for (int c = a; c < NU; ++c) d.H[a][c] = d.H[c][a] = G[G_H + a * NU + c];
+    }
+#pragma unroll
+    for (int i = 0; i < NL; ++i) d.Lf[i] = G[G_L + i];
+    d.mask = (int)G[G_M];
+}
+
+template <typename T>
+__device__ void refine_costate(const Params<T>& P, const ScanWs<T>& W, T* ring, int pos, int n, int lane) {
+    // 16-byte copies: the records and the ring's slots start on 16 bytes
+    constexpr int V = 16 / sizeof(T);
+    auto fetch = [&](int t, T* d) {
+        for (int e = lane * V; e < FSTR; e += 32 * V) cp_async16(d + RC_F + e, W.F + (size_t)t * FSTR + e);
+        for (int e = lane * V; e < GREC; e += 32 * V) cp_async16(d + RC_G + e, W.G + (size_t)t * GREC + e);
+        cp_async_commit();
+    };
+    // one commit group per stage (empty ones past stage 0): stage n-1-x in
+    // group x and slot x % RC_RING
+    for (int x = 0; x < RC_RING - 1; ++x) {
+        if (n - 1 - x >= 0) fetch(n - 1 - x, ring + x * RC_SIZE);
+        else cp_async_commit();
+    }
+    // the column of F_t this lane takes: A_t's column `lane` (lanes 0..12, for
+    // A_t' v) or B_t's column lane - 16 (lanes 16..19, for g)
+    const int col = lane < NX ? lane : (lane >= 16 && lane < 16 + NU ? NX + lane - 16 : -1);
+    const int cc = col < 0 ? 0 : col;
+    const int li = lane < NX ? lane : 0;
+    // k_t's entry `lane` in the stage records, stage n-1 first
+    T* kst = P.stg + srow(P, pos, n - 1, 0) + (size_t)(R_KK + (lane < NU ? lane : 0)) * GW;
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(RC_RING - 2) : "memory");
+    __syncwarp();
+    RcStage<T> cur, nxt;
+    rc_load(ring, col, cc, li, cur);
+    T vr = T(0);                                        // v_{t+1}, component `lane`
+    for (int t = n - 1, x = 0; t >= 0; --t, ++x) {
+        __syncwarp();                                   // the slot refilled below is read
+        const int ahead = t - (RC_RING - 1);
+        if (ahead >= 0) fetch(ahead, ring + ((x + RC_RING - 1) % RC_RING) * RC_SIZE);
+        else cp_async_commit();
+        // stage t-1's data into registers while stage t runs
+        asm volatile("cp.async.wait_group %0;\n" ::"n"(RC_RING - 2) : "memory");
+        __syncwarp();
+        if (t > 0) rc_load(ring + ((x + 1) % RC_RING) * RC_SIZE, col, cc, li, nxt);
+        // q_t + A_t' v (lanes 0..12) and g = r_t + B_t' v (lanes 16..19)
+        T s0 = cur.base, s1 = T(0);
+#pragma unroll
+        for (int i = 0; i < NX; ++i) {
+            const T vi = __shfl_sync(FULL, vr, i);
+            if (i & 1) s1 += cur.fc[i] * vi;
+            else s0 += cur.fc[i] * vi;
+        }
+        const T sf = s0 + s1;
+        T g[NU];
+#pragma unroll
+        for (int a = 0; a < NU; ++a) g[a] = __shfl_sync(FULL, sf, 16 + a);
+        // k on the free set (every lane, the same values)
+        const int mask = cur.mask;
+        T kk[NU], rhs[NU], y[NU];
+#pragma unroll
+        for (int a = 0; a < NU; ++a) kk[a] = ((mask >> a) & 1) ? T(0) : cur.dc[a];
+#pragma unroll
+        for (int a = 0; a < NU; ++a) {
+            T r = T(0);
+#pragma unroll
+            for (int c = 0; c < NU; ++c) r += ((mask >> c) & 1) ? T(0) : cur.H[a][c] * kk[c];
+            rhs[a] = ((mask >> a) & 1) ? r + g[a] : T(0);
+        }
+        chol_solve4(cur.Lf, rhs, y);
+#pragma unroll
+        for (int a = 0; a < NU; ++a) kk[a] = ((mask >> a) & 1) ? -y[a] : kk[a];
+        T v = sf;
+#pragma unroll
+        for (int a = 0; a < NU; ++a) v += cur.qr[a] * kk[a];
+        vr = lane < NX ? v : T(0);
+        if (lane < NU) *kst = lane == 0 ? kk[0] : (lane == 1 ? kk[1] : (lane == 2 ? kk[2] : kk[3]));
+        kst -= (size_t)SREC * GW;
+        if (t > 0) cur = nxt;
+    }
+    cp_async_wait_all();
 }
 
 // ---------------------------------------------------------------- kernel --
@@ -953,7 +1095,7 @@ __global__ void __launch_bounds__(SW * 32, 1) k_scan_ric(const __grid_constant__
         }
         G[G_AM] = (T)pm;
         if (t == n - 1) {
-            for (int e = 0; e < FREC; ++e) W.F[(size_t)t * FREC + e] = T(0);
+            for (int e = 0; e < FREC; ++e) W.F[(size_t)t * FSTR + e] = T(0);
         }
     }
     // A2: F_t = [A_t B_t] at the nominal x (hi part), t < n - 1: the computed
@@ -961,7 +1103,7 @@ __global__ void __launch_bounds__(SW * 32, 1) k_scan_ric(const __grid_constant__
     const T hv = hv_coef(P.mdl);
     for (int job = tid; job < (n - 1) * (NGC + 1); job += blockDim.x) {
         const int t = job / (NGC + 1), jj = job - (NGC + 1) * t;
-        T* F = W.F + (size_t)t * FREC;
+        T* F = W.F + (size_t)t * FSTR;
         if (jj == NGC) {
 #pragma unroll
             for (int i = 0; i < NX; ++i)
@@ -984,20 +1126,26 @@ __global__ void __launch_bounds__(SW * 32, 1) k_scan_ric(const __grid_constant__
         for (int i = 0; i < NX; ++i) F[i * NZ + jc[0]] = col[0][i];
     }
     __syncthreads();
-    // A3: one scan pass with the guessed free sets, then the stages the guess
-    // got wrong by the sequential recursion
-    stage_factors_all(W, sh, n);
-    __syncthreads();
-    scan_suffixes(W, sh, wa, n, &s_bad);
-    qp_inputs(W, sh, n);
-    __syncthreads();
-    stage_qps(P, W, sh, pos, n);
-    __syncthreads();
-    const int c = max(sh.cw[0], sh.cw[1]);
-    // stages after c saw exact values and stage c an exact V_{c+1}: their QPs
-    // are final, and a failed one at them ends the solve
-    if (tid < n && tid >= c && W.G[(size_t)tid * GREC + G_OK] == T(0)) atomicOr(&sh.fail, 1);
-    __syncthreads();
+    // A3 of an iteration: one scan pass with the guessed free sets, then the
+    // stages the guess got wrong by the sequential recursion.  The final
+    // factorization takes the sequential recursion for every stage: the tape's
+    // V_t and K_t then carry the sequential form's rounding, not that of the
+    // composed transition parts
+    int c = n - 1;
+    if (!final_fac) {
+        stage_factors_all(W, sh, n);
+        __syncthreads();
+        scan_suffixes(W, sh, wa, n, &s_bad);
+        qp_inputs(W, sh, n);
+        __syncthreads();
+        stage_qps(P, W, sh, pos, n);
+        __syncthreads();
+        c = max(sh.cw[0], sh.cw[1]);
+        // stages after c saw exact values and stage c an exact V_{c+1}: their
+        // QPs are final, and a failed one at them ends the solve
+        if (tid < n && tid >= c && W.G[(size_t)tid * GREC + G_OK] == T(0)) atomicOr(&sh.fail, 1);
+        __syncthreads();
+    }
     // (I + C J is singular only for non-finite data: C and J are positive
     // semidefinite, so its eigenvalues are at least 1)
     bool fail = sh.fail != 0 || s_bad != 0;
@@ -1012,12 +1160,12 @@ __global__ void __launch_bounds__(SW * 32, 1) k_scan_ric(const __grid_constant__
             __syncwarp();
             // F_t double-buffered: the next stage's copy runs during this one
             T* fb[2] = {wa + SQ_F, wa + SQ_F + 224};
-            wprefetch(fb[0], W.F + (size_t)c * FREC, FREC, lane);
+            wprefetch(fb[0], W.F + (size_t)c * FSTR, FREC, lane);
             bool ok = true;
             for (int t = c, k = 0; t >= 0 && ok; --t, k ^= 1) {
                 wwait();
-                if (t > 0) wprefetch(fb[k ^ 1], W.F + (size_t)(t - 1) * FREC, FREC, lane);
-                ok = seq_stage(P, W, sh, wa, pos, t, n, t == c, lane, fb[k]);
+                if (t > 0) wprefetch(fb[k ^ 1], W.F + (size_t)(t - 1) * FSTR, FREC, lane);
+                ok = seq_stage(P, W, sh, wa, pos, t, n, t == c && !final_fac, lane, fb[k]);
             }
             cp_async_wait_all();
             if (!ok && tid == 0) sh.fail = 1;
@@ -1026,6 +1174,10 @@ __global__ void __launch_bounds__(SW * 32, 1) k_scan_ric(const __grid_constant__
         fail = sh.fail != 0;
     }
     if (!fail) write_gains(P, W, pos, n, b, final_fac != 0);
+    if (!fail && !final_fac) {
+        __syncthreads();
+        if ((tid >> 5) == 0) refine_costate(P, W, reinterpret_cast<T*>(smem_raw), pos, n, tid & 31);
+    }
     if (tid == 0) {
         P.iters[b] = iters;
         if (fail) P.status[b] = ST_NONPD;

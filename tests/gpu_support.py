@@ -63,14 +63,6 @@ EXCUSED_MAX_FRAC = 0.01
 CONV_BAND32 = 1e-5
 # alpha decisions FP64 cannot resolve (any size of step)
 TIE64 = 1e-9
-# the stage-parallel Riccati form in FP32 (exec_mode "scan"): folding a chunk of
-# stages into one element forms closed-loop products A_R (I + G G'J)^-1 whose
-# FP32 rounding cancels, and the costate v carries about 1e-4 of its size
-# (measured on hover N = 50 and track N = 20, against 2e-6 for the sequential
-# recursion in FP32).  A converged solve's controls are the zero of that
-# gradient, so they move by up to 2e-4 (measured): gated at U_TOL32_SCAN.  The
-# FP64 scan form keeps the sequential form's FP64 gates.
-U_TOL32_SCAN = 5e-4
 
 
 # Tape layout (opaque to callers, read here only to compare free sets): per
