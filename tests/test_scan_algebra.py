@@ -155,3 +155,78 @@ def test_single_stage_step_in_woodbury_form():
         en = A.T @ z + eta_t
         assert np.max(np.abs(Jn - ref[4])) <= 1e-10 * np.max(np.abs(ref[4]))
         assert np.max(np.abs(en - ref[3])) <= 1e-10 * (1 + np.max(np.abs(ref[3])))
+
+
+def costate_pass(F, pr, X, U, free, k_clamped, Quu, Qux):
+    """The scan kernel's costate pass in FP64: with each stage's free set,
+    clamped offsets, Q_uu and Q_ux given, the vector part of the sequential
+    recursion from the last stage back,
+        g = r_t + B_t' v_{t+1},  k_f = -Q_uu,ff^-1 (g_f + Q_uu,fc k_c),
+        v_t = q_t + A_t' v_{t+1} + Q_ux' k
+    (the value update's K_t'(Q_uu k + g) is zero: Q_uu k + g vanishes on the
+    free set, K_t on the clamped one).  Returns every stage's k."""
+    n = pr.n
+    v = np.zeros(NX)
+    ks = [None] * n
+    for t in range(n - 1, -1, -1):
+        A = F[t][:, :NX] if t < n - 1 else np.zeros((NX, NX))
+        B = F[t][:, NX:] if t < n - 1 else np.zeros((NX, NU))
+        q = pr.Qt(t) * (X[t] - pr.x_ref[t])
+        g = pr.R * (U[t] - pr.u_ref) + B.T @ v
+        f = np.asarray(free[t], bool)
+        k = np.where(f, 0.0, k_clamped[t])
+        if f.any():
+            k[f] = -np.linalg.solve(Quu[t][np.ix_(f, f)], g[f] + Quu[t][np.ix_(f, ~f)] @ k[~f])
+        v = q + A.T @ v + Qux[t].T @ k
+        ks[t] = k
+    return ks
+
+
+@pytest.mark.parametrize("name,N,iters", [("hover", 50, 2), ("track", 20, 3)])
+def test_costate_pass_reproduces_the_sequential_feedforward(name, N, iters):
+    """Given the oracle's free sets, clamped offsets, Q_uu and Q_ux, the
+    costate pass gives the oracle's k_t at every stage (FP64, 1e-9)."""
+    batch = W.hover_targets(4, N, seed=5) if name == "hover" else W.race_track(4, N, seed=5)
+    clamped = 0
+    for i in range(4):
+        pr = ilqr.problem_from_batch(batch, i)
+        so = ilqr.solve(QUAD, pr, iters, 0.0)
+        F = ilqr.linearize(QUAD, pr, so.X, so.U)
+        bp = ilqr.backward_pass(pr, so.X, so.U, F)
+        assert bp.ok
+        ks = costate_pass(F, pr, so.X, so.U, bp.free, bp.k, bp.Quu, bp.Qux)
+        scale = 1.0 + max(np.max(np.abs(k)) for k in bp.k)
+        for t in range(pr.n):
+            assert np.max(np.abs(ks[t] - bp.k[t])) <= 1e-9 * scale, (i, t)
+            clamped += int((~np.asarray(bp.free[t], bool)).sum())
+    assert clamped > 0 or name == "hover"
+
+
+def test_costate_pass_is_insensitive_to_the_scan_matrices_at_convergence():
+    """Q_uu and Q_ux come from the scan's V and carry its rounding.  At a
+    converged iterate they multiply a vanishing k, so relative noise of 1e-5
+    on them moves the costate pass's k by at most 1e-8 of the controls' scale,
+    and by at least 100 times less than the same noise on the transitions
+    A_t, B_t, which carry the costate (the pass keeps the sequential
+    recursion's precision where the controls are decided)."""
+    batch = W.hover_targets(4, 50, seed=6)
+    rng = np.random.default_rng(7)
+    for i in range(4):
+        pr = ilqr.problem_from_batch(batch, i)
+        so = ilqr.solve(QUAD, pr, 20, 1e-9)
+        F = ilqr.linearize(QUAD, pr, so.X, so.U)
+        bp = ilqr.backward_pass(pr, so.X, so.U, F)
+        noisy = lambda M: [m * (1 + 1e-5 * rng.standard_normal(m.shape)) for m in M]
+        k0 = costate_pass(F, pr, so.X, so.U, bp.free, bp.k, bp.Quu, bp.Qux)
+        k1 = costate_pass(F, pr, so.X, so.U, bp.free, bp.k, noisy(bp.Quu), noisy(bp.Qux))
+        # the controls' scale: a 1e-5 error of the costate would move k by
+        # about 1e-5 of |Q_uu^-1 B'v|, which is of the order of the controls
+        scale = 1.0 + np.max(np.abs(so.U))
+        d = max(np.max(np.abs(a - b)) for a, b in zip(k0, k1))
+        # the same noise on the transitions, which carry the costate
+        Fn = [f * (1 + 1e-5 * rng.standard_normal(f.shape)) for f in F]
+        k2 = costate_pass(Fn, pr, so.X, so.U, bp.free, bp.k, bp.Quu, bp.Qux)
+        dv = max(np.max(np.abs(a - b)) for a, b in zip(k0, k2))
+        print(i, so.status, so.iters, d / scale, dv / scale)
+        assert d <= 1e-8 * scale, (i, d)
+        assert dv >= 100 * d, (i, d, dv)
