@@ -32,8 +32,8 @@
 // the latest stage whose free set or clamped offsets differ from the guess.
 // Stages after c saw exact values, so their results are final, and stage c's
 // QP saw an exact V_{c+1}, so its result is final too.  The stages c-1 .. 0
-// then run the sequential recursion on one warp: each box QP from the exact
-// V_{t+1}, then S_t = e_t (x) S_{t+1} for J and eta.  When the guess was right
+// then run the sequential recursion on the whole block: each box QP from the
+// exact V_{t+1} (on one lane, while the other warps form V A), then V_t, v_t.  When the guess was right
 // (c < 0) the whole recursion took one scan; at worst it took a scan plus the
 // sequential recursion.  Either way every stage's QP is the one the
 // sequential recursion solves (same V_{t+1} up to rounding), so k_t, K_t and
@@ -308,7 +308,7 @@ constexpr int ST_JG = 0, ST_S = 52, ST_Y = 68, ST_Z = 84, ST_W4 = 136, ST_ZV = 1
 // the regions of a warp's area the steps use stay inside it
 static_assert(WA_O + ST_SIZE <= WA_SIZE, "step temporaries");
 static_assert(264 + SF_SIZE <= ELEM, "double-buffered stage factors");
-static_assert(224 + FREC <= ELEM, "double-buffered F_t of the sequential tail");
+static_assert(FSTR + FREC <= ELEM, "double-buffered F_t of the sequential tail");
 static_assert(FSTR >= FREC && FSTR % 4 == 0 && GREC % 4 == 0, "F and G records start on 16 bytes");
 static_assert(SQ_H + 20 <= WA_COL, "sequential-stage temporaries");
 
@@ -718,17 +718,20 @@ __device__ void stage_qps(const Params<T>& P, const ScanWs<T>& W, ScanShared<T>&
 
 
 // One stage of the sequential recursion (Tassa's value update, as the oracle
-// and the sequential phase take it), on one warp:
+// and the sequential phase take it), on the whole block (every thread calls
+// it; it returns the same value in all):
 //   Q_xx = Q_t + A'V A,  Q_ux = B'V A,  Q_uu = R + B'V B,  q = q_t + A'v,
 //   q_u = r_t + B'v  (V, v of stage t+1, in shared memory),
 //   the box QP (unless `have_qp`: the stored result is final),
 //   K = -Q_uu,ff^-1 Q_ux,f (zero rows for clamped controls),
 //   V_t = Q_xx + Q_ux'K (symmetrized),  v_t = q + K'(Q_uu k + q_u) + Q_ux'k,
-// V_t and eta_t = -v_t into shared memory and Sv[t].  Returns false on a
-// non-positive pivot.
+// V_t and eta_t = -v_t into shared memory and Sv[t].  The box QP runs on one
+// lane of warp 0 while the other warps form V A; the products are spread over
+// the block's threads, one output each, in the order of the warp-level
+// products (the same rounding).  Returns false on a non-positive pivot.
 template <typename T>
 __device__ bool seq_stage(const Params<T>& P, const ScanWs<T>& W, const ScanShared<T>& sh, T* wa, int pos, int t,
-                          int n, bool have_qp, int lane, T* Fs) {
+                          int n, bool have_qp, int tid, T* Fs, int* s_ok) {
     T* Js = wa + SQ_J;
     T* es = wa + SQ_N;
     T* P1 = wa + SQ_P;
@@ -736,87 +739,97 @@ __device__ bool seq_stage(const Params<T>& P, const ScanWs<T>& W, const ScanShar
     T* Qu = wa + SQ_U;
     T* Kt = wa + SQ_K;
     T* Hg = wa + SQ_H;                  // H (16, upper used), g (4)
-    T* Vn = wa + SQ_V;
     T* G = W.G + (size_t)t * GREC;
-    T d[4], Lf[NL];
-    int mask;
-    bool ok;
-    if (have_qp) {
-        if (lane < 16) Hg[lane] = G[G_H + lane];
-        else if (lane < 20) Hg[lane] = G[G_G + lane - 16];
-#pragma unroll
-        for (int a = 0; a < 4; ++a) d[a] = G[G_K + a];
-#pragma unroll
-        for (int i = 0; i < NL; ++i) Lf[i] = G[G_L + i];
-        mask = (int)G[G_M];
-        ok = G[G_OK] != T(0);
-        __syncwarp();
-    } else {
+    const int warp = tid >> 5, lane = tid & 31;
+    if (!have_qp) {
         // V B into P1 (13 x 4), then H and g
-        for (int e = lane; e < NX * NU; e += 32) {
-            const int i = e / NU, a = e - NU * i;
+        if (tid < NX * NU) {
+            const int i = tid / NU, a = tid - NU * i;
             T s = T(0);
 #pragma unroll
             for (int k = 0; k < NX; ++k) s += Js[i * NX + k] * Fs[k * NZ + NX + a];
-            P1[e] = s;
+            P1[tid] = s;
         }
-        __syncwarp();
-        if (lane < 16) {
-            const int a2 = lane >> 2, a = lane & 3;
+        __syncthreads();
+        if (tid < 16) {
+            const int a2 = tid >> 2, a = tid & 3;
             T s = a2 == a ? sh.R[a] : T(0);
 #pragma unroll
             for (int i = 0; i < NX; ++i) s += Fs[i * NZ + NX + a2] * P1[i * NU + a];
-            Hg[lane] = s;
-        } else if (lane < 20) {
-            const int a = lane - 16;
+            Hg[tid] = s;
+        } else if (tid < 20) {
+            const int a = tid - 16;
             T s = G[G_R + a];
 #pragma unroll
             for (int i = 0; i < NX; ++i) s -= Fs[i * NZ + NX + a] * es[i];
-            Hg[lane] = s;
+            Hg[tid] = s;
         }
-        __syncwarp();
-        qp_stage(P, W, sh, pos, t, lane == 0, Hg, Hg + 16, d, Lf, mask, ok);
-        if (lane < 20) G[lane < 16 ? G_H + lane : G_G + lane - 16] = Hg[lane];     // for the costate pass
-        mask = __shfl_sync(FULL, mask, 0);
-        ok = __shfl_sync(FULL, ok ? 1 : 0, 0) != 0;
-#pragma unroll
-        for (int a = 0; a < 4; ++a) d[a] = __shfl_sync(FULL, d[a], 0);
-#pragma unroll
-        for (int i = 0; i < NL; ++i) Lf[i] = __shfl_sync(FULL, Lf[i], 0);
+        __syncthreads();
     }
-    // P1 = V A;  Qx = A' P1 + Q_t;  Qu = B' P1 (4 x 13)
-    wmm<false, false>(Js, NX, Fs, NZ, P1, NX, (const T*)nullptr, lane);
-    __syncwarp();
-    wmm<true, false>(Fs, NZ, P1, NX, Qx, NX, (const T*)nullptr, lane);
-    for (int e = lane; e < NU * NX; e += 32) {
-        const int a = e / NX, c = e - NX * a;
+    // warp 0: the box QP (or its stored result); lanes 0..12 keep d and the
+    // factor for K_t and v_t
+    T d[4], Lf[NL];
+    int mask = 0;
+    if (warp == 0) {
+        bool ok;
+        if (have_qp) {
+            if (lane < 16) Hg[lane] = G[G_H + lane];
+            else if (lane < 20) Hg[lane] = G[G_G + lane - 16];
+#pragma unroll
+            for (int a = 0; a < 4; ++a) d[a] = G[G_K + a];
+#pragma unroll
+            for (int i = 0; i < NL; ++i) Lf[i] = G[G_L + i];
+            mask = (int)G[G_M];
+            ok = G[G_OK] != T(0);
+        } else {
+            qp_stage(P, W, sh, pos, t, lane == 0, Hg, Hg + 16, d, Lf, mask, ok);
+            if (lane < 20) G[lane < 16 ? G_H + lane : G_G + lane - 16] = Hg[lane];     // for the costate pass
+            mask = __shfl_sync(FULL, mask, 0);
+            ok = __shfl_sync(FULL, ok ? 1 : 0, 0) != 0;
+#pragma unroll
+            for (int a = 0; a < 4; ++a) d[a] = __shfl_sync(FULL, d[a], 0);
+#pragma unroll
+            for (int i = 0; i < NL; ++i) Lf[i] = __shfl_sync(FULL, Lf[i], 0);
+        }
+        if (lane == 0) *s_ok = ok ? 1 : 0;
+    } else if (tid - 32 < M13) {
+        // P1 = V A
+        const int e = tid - 32, r = e / NX, c = e - NX * r;
+        T s = T(0);
+#pragma unroll
+        for (int kk = 0; kk < NX; ++kk) s += Js[r * NX + kk] * Fs[kk * NZ + c];
+        P1[e] = s;
+    }
+    __syncthreads();
+    // Qx = A' P1 (13 x 13), Qu = B' P1 (4 x 13)
+    if (tid < M13) {
+        const int r = tid / NX, c = tid - NX * r;
+        T s = T(0);
+#pragma unroll
+        for (int kk = 0; kk < NX; ++kk) s += Fs[kk * NZ + r] * P1[kk * NX + c];
+        Qx[tid] = s;
+    } else if (tid < M13 + NU * NX) {
+        const int e = tid - M13, a = e / NX, c = e - NX * a;
         T s = T(0);
 #pragma unroll
         for (int i = 0; i < NX; ++i) s += Fs[i * NZ + NX + a] * P1[i * NX + c];
         Qu[e] = s;
     }
-    __syncwarp();
-    if (lane < NX) {
-        Qx[lane * NX + lane] += G[G_QD + lane];
+    __syncthreads();
+    // column `tid` of K_t, and v_t's entry `tid` (lanes 0..12 of warp 0)
+    T vt = T(0);
+    if (tid < NX) {
+        Qx[tid * NX + tid] += G[G_QD + tid];
         T rhs[4], y[4];
 #pragma unroll
-        for (int a = 0; a < 4; ++a) rhs[a] = ((mask >> a) & 1) ? Qu[a * NX + lane] : T(0);
+        for (int a = 0; a < 4; ++a) rhs[a] = ((mask >> a) & 1) ? Qu[a * NX + tid] : T(0);
         chol_solve4(Lf, rhs, y);
+        T kc[4];
 #pragma unroll
-        for (int a = 0; a < 4; ++a) Kt[a * NX + lane] = ((mask >> a) & 1) ? -y[a] : T(0);
-    }
-    __syncwarp();
-    // V_t = Qx + Qu' K
-    for (int e = lane; e < M13; e += 32) {
-        const int r = e / NX, c = e - NX * r;
-        T s = Qx[e];
-#pragma unroll
-        for (int a = 0; a < NU; ++a) s += Qu[a * NX + r] * Kt[a * NX + c];
-        Vn[e] = s;
-    }
-    // v_t = q_t + A'v + K'(H k + g) + Qu' k  (v = -eta)
-    T vt = T(0);
-    if (lane < NX) {
+        for (int a = 0; a < 4; ++a) {
+            kc[a] = ((mask >> a) & 1) ? -y[a] : T(0);
+            Kt[a * NX + tid] = kc[a];
+        }
         T w[4];
 #pragma unroll
         for (int a = 0; a < 4; ++a) {
@@ -825,27 +838,39 @@ __device__ bool seq_stage(const Params<T>& P, const ScanWs<T>& W, const ScanShar
             for (int c = 0; c < 4; ++c) s += (a <= c ? Hg[a * NU + c] : Hg[c * NU + a]) * d[c];
             w[a] = s;
         }
-        T s = G[G_Q + lane];
+        T s = G[G_Q + tid];
 #pragma unroll
-        for (int k = 0; k < NX; ++k) s -= Fs[k * NZ + lane] * es[k];
+        for (int k = 0; k < NX; ++k) s -= Fs[k * NZ + tid] * es[k];
 #pragma unroll
-        for (int a = 0; a < NU; ++a) s += Kt[a * NX + lane] * w[a] + Qu[a * NX + lane] * d[a];
+        for (int a = 0; a < NU; ++a) s += kc[a] * w[a] + Qu[a * NX + tid] * d[a];
         vt = s;
     }
-    __syncwarp();
-    wsym(Vn, lane);
-    __syncwarp();
+    __syncthreads();
+    // V_t = Qx + Qu'K, symmetrized (the mean of the two computed entries), in
+    // place of V_{t+1} and into Sv[t]; eta_t = -v_t
     T* so = W.Sv + (size_t)t * SV;
-    for (int e = lane; e < M13; e += 32) {
-        Js[e] = Vn[e];
-        so[e] = Vn[e];
+    if (tid < M13) {
+        const int r = tid / NX, c = tid - NX * r;
+        if (r <= c) {
+            T s1 = Qx[tid], s2 = Qx[c * NX + r];
+#pragma unroll
+            for (int a = 0; a < NU; ++a) {
+                s1 += Qu[a * NX + r] * Kt[a * NX + c];
+                s2 += Qu[a * NX + c] * Kt[a * NX + r];
+            }
+            const T m = r == c ? s1 : T(0.5) * (s1 + s2);
+            Js[r * NX + c] = m;
+            Js[c * NX + r] = m;
+            so[r * NX + c] = m;
+            so[c * NX + r] = m;
+        }
     }
-    if (lane < NX) {
-        es[lane] = -vt;
-        so[M13 + lane] = -vt;
+    if (tid < NX) {
+        es[tid] = -vt;
+        so[M13 + tid] = -vt;
     }
-    __syncwarp();
-    return ok;
+    __syncthreads();
+    return *s_ok != 0;
 }
 
 // K_t = -Q_uu,ff^-1 Q_ux,f (zero rows for clamped controls), Q_ux = B_t'
@@ -1051,7 +1076,7 @@ __global__ void __launch_bounds__(SW * 32, 1) k_scan_ric(const __grid_constant__
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* wa = reinterpret_cast<T*>(smem_raw) + (size_t)(threadIdx.x >> 5) * WA_SIZE;
     __shared__ ScanShared<T> sh;
-    __shared__ int s_bad;
+    __shared__ int s_bad, s_ok;
     const int pos = blockIdx.x;
     if (pos >= P.B) return;
     const int b = P.order ? P.order[pos] : pos;
@@ -1150,26 +1175,25 @@ __global__ void __launch_bounds__(SW * 32, 1) k_scan_ric(const __grid_constant__
     // semidefinite, so its eigenvalues are at least 1)
     bool fail = sh.fail != 0 || s_bad != 0;
     if (!fail && c >= 0) {
-        if ((tid >> 5) == 0) {
-            const int lane = tid & 31;
-            // S_{c+1}'s J and eta (zero past the last stage) into the work area
-            for (int e = lane; e < SV; e += 32) {
-                const T v = c + 1 < n ? W.Sv[(size_t)(c + 1) * SV + e] : T(0);
-                wa[e < M13 ? SQ_J + e : SQ_N + e - M13] = v;
-            }
-            __syncwarp();
-            // F_t double-buffered: the next stage's copy runs during this one
-            T* fb[2] = {wa + SQ_F, wa + SQ_F + 224};
-            wprefetch(fb[0], W.F + (size_t)c * FSTR, FREC, lane);
-            bool ok = true;
-            for (int t = c, k = 0; t >= 0 && ok; --t, k ^= 1) {
-                wwait();
-                if (t > 0) wprefetch(fb[k ^ 1], W.F + (size_t)(t - 1) * FSTR, FREC, lane);
-                ok = seq_stage(P, W, sh, wa, pos, t, n, t == c && !final_fac, lane, fb[k]);
-            }
-            cp_async_wait_all();
-            if (!ok && tid == 0) sh.fail = 1;
+        // the sequential stages on the whole block, in warp 0's work area
+        T* wa0 = reinterpret_cast<T*>(smem_raw);
+        // S_{c+1}'s J and eta (zero past the last stage)
+        for (int e = tid; e < SV; e += blockDim.x) {
+            const T v = c + 1 < n ? W.Sv[(size_t)(c + 1) * SV + e] : T(0);
+            wa0[e < M13 ? SQ_J + e : SQ_N + e - M13] = v;
         }
+        // F_t double-buffered: warp 0 copies the next stage's during this one
+        T* fb[2] = {wa0 + SQ_F, wa0 + SQ_F + FSTR};
+        if (tid < 32) wprefetch(fb[0], W.F + (size_t)c * FSTR, FREC, tid);
+        bool ok = true;
+        for (int t = c, k = 0; t >= 0 && ok; --t, k ^= 1) {
+            if (tid < 32) cp_async_wait_all();
+            __syncthreads();
+            if (tid < 32 && t > 0) wprefetch(fb[k ^ 1], W.F + (size_t)(t - 1) * FSTR, FREC, tid);
+            ok = seq_stage(P, W, sh, wa0, pos, t, n, t == c && !final_fac, tid, fb[k], &s_ok);
+        }
+        if (tid < 32) cp_async_wait_all();
+        if (!ok && tid == 0) sh.fail = 1;
         __syncthreads();
         fail = sh.fail != 0;
     }

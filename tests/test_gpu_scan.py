@@ -12,7 +12,7 @@ costate carries about 1e-4 of its size in rounding (the composed transition
 parts); the kernel's costate pass reruns the recursion's vector part
 sequentially, so the converged controls meet the sequential path's U_TOL32.
 With store-all the forward's final factorization (the tape) is the sequential
-recursion on one warp; the backward is the library's, and the gradients are
+recursion on the whole block; the backward is the library's, and the gradients are
 held to the sequential path's gates."""
 import numpy as np
 import pytest
