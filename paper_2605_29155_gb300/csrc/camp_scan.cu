@@ -1019,7 +1019,7 @@ __device__ void refine_costate(const Params<T>& P, const ScanWs<T>& W, T* ring, 
     rc_load(ring, col, cc, li, cur);
     T vr = T(0);                                        // v_{t+1}, component `lane`
     for (int t = n - 1, x = 0; t >= 0; --t, ++x) {
-        __syncwarp();                                   // the slot refilled below is read
+        __syncwarp();                                   // every lane is done with the slot refilled below
         const int ahead = t - (RC_RING - 1);
         if (ahead >= 0) fetch(ahead, ring + ((x + RC_RING - 1) % RC_RING) * RC_SIZE);
         else cp_async_commit();
