@@ -974,11 +974,11 @@ template <typename T> struct RcStage {
 };
 
 template <typename T>
-__device__ __forceinline__ void rc_load(const T* S, int col, int cc, int li, RcStage<T>& d) {
+__device__ __forceinline__ void rc_load(const T* S, int cc, int bidx, int li, RcStage<T>& d) {
     const T* G = S + RC_G;
 #pragma unroll
     for (int i = 0; i < NX; ++i) d.fc[i] = S[RC_F + i * NZ + cc];
-    d.base = col < 0 ? T(0) : (col < NX ? G[G_Q + col] : G[G_R + col - NX]);
+    d.base = bidx < 0 ? T(0) : G[bidx];
 #pragma unroll
     for (int a = 0; a < NU; ++a) {
         d.qr[a] = G[G_QU + a * NX + li];
@@ -1007,26 +1007,26 @@ __device__ void refine_costate(const Params<T>& P, const ScanWs<T>& W, T* ring, 
         else cp_async_commit();
     }
     // the column of F_t this lane takes: A_t's column `lane` (lanes 0..12, for
-    // A_t' v) or B_t's column lane - 16 (lanes 16..19, for g)
+    // A_t' v) or B_t's column lane - 16 (lanes 16..19, for g), and the record
+    // entry that goes with it (q_t or r_t)
     const int col = lane < NX ? lane : (lane >= 16 && lane < 16 + NU ? NX + lane - 16 : -1);
     const int cc = col < 0 ? 0 : col;
+    const int bidx = col < 0 ? -1 : (col < NX ? G_Q + col : G_R + col - NX);
     const int li = lane < NX ? lane : 0;
     // k_t's entry `lane` in the stage records, stage n-1 first
     T* kst = P.stg + srow(P, pos, n - 1, 0) + (size_t)(R_KK + (lane < NU ? lane : 0)) * GW;
     asm volatile("cp.async.wait_group %0;\n" ::"n"(RC_RING - 2) : "memory");
     __syncwarp();
-    RcStage<T> cur, nxt;
-    rc_load(ring, col, cc, li, cur);
     T vr = T(0);                                        // v_{t+1}, component `lane`
-    for (int t = n - 1, x = 0; t >= 0; --t, ++x) {
+    // stage t from `cur`, with stage t-1's data loaded into `nxt` meanwhile
+    auto step = [&](int t, int x, const RcStage<T>& cur, RcStage<T>& nxt) {
         __syncwarp();                                   // every lane is done with the slot refilled below
         const int ahead = t - (RC_RING - 1);
         if (ahead >= 0) fetch(ahead, ring + ((x + RC_RING - 1) % RC_RING) * RC_SIZE);
         else cp_async_commit();
-        // stage t-1's data into registers while stage t runs
         asm volatile("cp.async.wait_group %0;\n" ::"n"(RC_RING - 2) : "memory");
         __syncwarp();
-        if (t > 0) rc_load(ring + ((x + 1) % RC_RING) * RC_SIZE, col, cc, li, nxt);
+        if (t > 0) rc_load(ring + ((x + 1) % RC_RING) * RC_SIZE, cc, bidx, li, nxt);
         // q_t + A_t' v (lanes 0..12) and g = r_t + B_t' v (lanes 16..19)
         T s0 = cur.base, s1 = T(0);
 #pragma unroll
@@ -1060,7 +1060,14 @@ __device__ void refine_costate(const Params<T>& P, const ScanWs<T>& W, T* ring, 
         vr = lane < NX ? v : T(0);
         if (lane < NU) *kst = lane == 0 ? kk[0] : (lane == 1 ? kk[1] : (lane == 2 ? kk[2] : kk[3]));
         kst -= (size_t)SREC * GW;
-        if (t > 0) cur = nxt;
+    };
+    // two stages a trip, the two register sets swapping roles
+    RcStage<T> ra, rb;
+    rc_load(ring, cc, bidx, li, ra);
+    for (int t = n - 1, x = 0; t >= 0; t -= 2, x += 2) {
+        step(t, x, ra, rb);
+        if (t == 0) break;
+        step(t - 1, x + 1, rb, ra);
     }
     cp_async_wait_all();
 }
